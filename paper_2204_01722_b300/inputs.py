@@ -1,0 +1,108 @@
+"""Seeded synthetic inputs shared by the CUDA path, its tests and the oracle.
+
+This module holds no finite-element arithmetic: it only draws meshes,
+displacement fields, vectors, boundary masks and material layouts from
+seeded numpy generators.  Recipes:
+
+* ``box_vertices``: unit-cube vertex lattice, interior vertices shifted by
+  U(-f h, f h) per coordinate (boundary vertices stay put so faces stay planar).
+* ``smooth_field``: u_i(X) = sum_m a_im sin(pi k_m . X + phi_m), m = 1..8,
+  k_m in {1,2}^3, a and phi seeded, rescaled so max_nodes |u| = amplitude.
+* ``normal_vector``: N(0, 1) entries.
+* ``uniaxial_mask`` / ``uniaxial_bc``: x = 0 face clamped (all components),
+  x = 1 face has its x-component prescribed to -delta, the rest free.
+* ``inclusion_modulus``: per-element Young's modulus from seeded spheres
+  (centres uniform in the box, radius U(rmin, rmax) elements) added until the
+  element-centroid volume fraction reaches ``vf``; E = contrast inside, 1 outside.
+"""
+import numpy as np
+
+
+def box_vertices(nx, ny, nz, perturb=0.0, seed=0):
+    x = np.linspace(0.0, 1.0, nx + 1)
+    y = np.linspace(0.0, 1.0, ny + 1)
+    z = np.linspace(0.0, 1.0, nz + 1)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    V = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    if perturb > 0.0:
+        rng = np.random.default_rng(seed)
+        h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+        vi = np.tile(np.arange(nx + 1), (ny + 1) * (nz + 1))
+        vj = np.tile(np.repeat(np.arange(ny + 1), nx + 1), nz + 1)
+        vk = np.repeat(np.arange(nz + 1), (nx + 1) * (ny + 1))
+        interior = (vi > 0) & (vi < nx) & (vj > 0) & (vj < ny) & (vk > 0) & (vk < nz)
+        d = rng.uniform(-perturb, perturb, size=V.shape) * h[None, :]
+        V[interior] += d[interior]
+    return V
+
+
+def smooth_field(xyz, amplitude=0.05, seed=0, modes=8):
+    xyz = np.asarray(xyz, dtype=np.float64).reshape(-1, 3)
+    rng = np.random.default_rng(seed)
+    k = rng.integers(1, 3, size=(modes, 3)).astype(np.float64)
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=(modes,))
+    a = rng.normal(size=(3, modes))
+    arg = np.pi * (xyz @ k.T) + phi[None, :]          # [n, modes]
+    u = np.sin(arg) @ a.T                              # [n, 3]
+    u *= amplitude / np.max(np.linalg.norm(u, axis=1))
+    return u
+
+
+def normal_vector(n, seed=0):
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+def uniform_vector(n, seed=0):
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=n)
+
+
+def lattice_index(node_dims):
+    Nx, Ny, Nz = node_dims
+    I = np.tile(np.arange(Nx), Ny * Nz)
+    J = np.tile(np.repeat(np.arange(Ny), Nx), Nz)
+    K = np.repeat(np.arange(Nz), Nx * Ny)
+    return I, J, K
+
+
+def uniaxial_mask(node_dims):
+    """Boolean DoF mask [3 n_nodes]: x = 0 face all components, x = 1 face x-component."""
+    Nx = node_dims[0]
+    I, _, _ = lattice_index(node_dims)
+    m = np.zeros((I.size, 3), dtype=bool)
+    m[I == 0, :] = True
+    m[I == Nx - 1, 0] = True
+    return m.ravel()
+
+
+def uniaxial_bc(node_dims, delta):
+    """Prescribed displacement [3 n_nodes]: u_x = -delta on x = 1, zero elsewhere."""
+    Nx = node_dims[0]
+    I, _, _ = lattice_index(node_dims)
+    g = np.zeros((I.size, 3))
+    g[I == Nx - 1, 0] = -delta
+    return g.ravel()
+
+
+def all_faces_mask(node_dims):
+    Nx, Ny, Nz = node_dims
+    I, J, K = lattice_index(node_dims)
+    b = (I == 0) | (I == Nx - 1) | (J == 0) | (J == Ny - 1) | (K == 0) | (K == Nz - 1)
+    return np.repeat(b, 3)
+
+
+def inclusion_modulus(nx, ny, nz, seed=0, vf=0.3, rmin=2.0, rmax=6.0, contrast=1e3):
+    rng = np.random.default_rng(seed)
+    cx = (np.arange(nx) + 0.5) / nx
+    cy = (np.arange(ny) + 0.5) / ny
+    cz = (np.arange(nz) + 0.5) / nz
+    Z, Y, X = np.meshgrid(cz, cy, cx, indexing="ij")
+    C = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    h = 1.0 / max(nx, ny, nz)
+    inside = np.zeros(C.shape[0], dtype=bool)
+    for _ in range(100000):
+        if inside.mean() >= vf:
+            break
+        c = rng.uniform(0.0, 1.0, size=3)
+        r = rng.uniform(rmin, rmax) * h
+        inside |= np.sum((C - c) ** 2, axis=1) <= r * r
+    return np.where(inside, contrast, 1.0)
