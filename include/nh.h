@@ -1,0 +1,168 @@
+/*
+ * nh.h -- C ABI of the matrix-free Neo-Hookean operator library for B300 (sm_103a).
+ *
+ * The library applies the operators of compressible Neo-Hookean
+ * hyperelasticity on continuous Q_p hexahedral spaces in the decomposition
+ * A = P^T E^T B^T D B E P of arXiv 2204.01722 (Sec. II-C, Eq.
+ * libceed_representation): element restriction E, tensor-product basis B,
+ * pointwise quadrature function D.  On one GPU the parallel restriction P is
+ * the identity, so T-vectors and L-vectors coincide.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Vectors are caller-owned DEVICE pointers unless a name ends in _host.
+ *   The library never frees them.  Layout: node-major interleaved
+ *   [n_nodes][3] (x, y, z displacement components), nodes numbered
+ *   lexicographically over the (p nx + 1)(p ny + 1)(p nz + 1) lattice with x
+ *   fastest.  Vectors cover every DoF, constrained ones included.
+ * - NH_F64 entry points take double vectors, NH_F32 entry points take float
+ *   vectors.  Device pointers must be 16-byte aligned (torch allocations are).
+ * - Every call is stream-ordered on the context stream and does not block
+ *   the host, except those returning host scalars (documented per call).
+ * - Argument errors return at once (NH_ERR_ARG, NH_ERR_UNSUPPORTED) and
+ *   launch nothing.  Asynchronous device errors are returned by the next
+ *   call that synchronises, or by nh_sync.  nh_last_error gives the text.
+ * - Handles (ctx, space, op) are owned by the caller through create/destroy;
+ *   the library owns every internal device buffer (maps, qdata, scratch).
+ * - Dirichlet convention: the Jacobian acts as the identity on constrained
+ *   DoFs and drops constrained columns; the residual returns u - g there.
+ * - Not thread-safe per context: calls on one context must be serialised.
+ */
+#ifndef NH_H
+#define NH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nh_ctx_s* nh_ctx;
+typedef struct nh_space_s* nh_space;
+typedef struct nh_op_s* nh_op;
+
+typedef enum {
+  NH_OK = 0,
+  NH_ERR_ARG = 1,            /* invalid argument (null handle, bad size, misaligned pointer) */
+  NH_ERR_CUDA = 2,           /* a CUDA runtime call failed; see nh_last_error */
+  NH_ERR_OOM = 3,            /* device allocation failed */
+  NH_ERR_INVERTED = 4,       /* det F <= 0 (or not finite) at some quadrature point */
+  NH_ERR_NOT_CONVERGED = 5,  /* a solver hit its iteration limit; the report is filled */
+  NH_ERR_NAN = 6,            /* a NaN/Inf appeared in a solver scalar */
+  NH_ERR_TIMEOUT = 7,        /* a bounded device wait expired */
+  NH_ERR_STATE = 8,          /* call out of order (e.g. apply before nh_qdata_setup) */
+  NH_ERR_UNSUPPORTED = 9     /* (p, q) or layout outside the compiled set */
+} nh_status;
+
+typedef enum { NH_F64 = 0, NH_F32 = 1 } nh_prec;
+
+/* Stored quadrature data.  NH_LAYOUT_CURRENT is the paper's 17 scalars per
+ * point (Sec. III-B and Table different-storage "current"): grad_x xi (9),
+ * W tau (6), W lambda, W (mu - lambda log J).  NH_LAYOUT_INITIAL stores the
+ * initial-configuration data of Table different-storage "initial tuned" with
+ * the material folded in (27 scalars): grad_X xi (9), H = grad_X u (9),
+ * C^-1 (6), W mu, W lambda log J, W lambda; its Jacobian is
+ * dP = dF S + F dS (Sec. V-E). */
+typedef enum { NH_LAYOUT_CURRENT = 0, NH_LAYOUT_INITIAL = 1 } nh_layout;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on (borrowed, not destroyed), or NULL to create a private
+ * non-blocking stream.  Errors: NH_ERR_ARG (null out), NH_ERR_CUDA, NH_ERR_OOM. */
+nh_status nh_create(nh_ctx* out, int device, void* cuda_stream);
+nh_status nh_destroy(nh_ctx ctx);
+/* Text of the last error on this context (storage owned by the context). */
+const char* nh_last_error(nh_ctx ctx);
+/* Block until the context stream is idle; returns any latched device error. */
+nh_status nh_sync(nh_ctx ctx);
+/* Number of kernels this context has launched since creation. */
+int64_t nh_launch_count(nh_ctx ctx);
+
+/* ---- spaces: mesh + element restriction + basis (Sec. II-B) ------------ */
+
+/* Structured box of nx*ny*nz hexahedra with a trilinear geometry.
+ * vertex_xyz: HOST array [(nx+1)(ny+1)(nz+1)][3], x fastest, or NULL for the
+ * unit cube.  p: polynomial order (1..4); q: Gauss points per direction,
+ * p+1 <= q <= 6.  Lagrange nodes are Gauss-Lobatto (GLL).  Outputs the node
+ * and DoF counts.  Copies the mesh to the device; builds the element
+ * restriction E as an int32 map [n_elem][(p+1)^3] and the node coordinates
+ * (trilinear image of the GLL lattice).  Synchronises.
+ * Errors: NH_ERR_ARG, NH_ERR_UNSUPPORTED, NH_ERR_OOM. */
+nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const double* vertex_xyz,
+                       int p, int q, nh_space* out, int64_t* n_nodes, int64_t* n_dof);
+/* Node coordinates, HOST out [n_nodes][3]. */
+nh_status nh_space_coords(nh_space s, double* xyz_host);
+/* Dirichlet DoFs: HOST array [n_dof], nonzero = constrained.  Copied; synchronises. */
+nh_status nh_space_set_dirichlet(nh_space s, const uint8_t* dof_mask_host);
+nh_status nh_space_destroy(nh_space s);
+
+/* ---- operators (Sec. II-A, II-B, III-B) -------------------------------- */
+
+/* Neo-Hookean operator on `fine`.  Young's modulus per element from the HOST
+ * array E_per_elem [n_elem], or the constant E when it is NULL; Poisson
+ * ratio nu in (-1, 0.5).  layout: nh_layout.  Allocates the FP64 quadrature
+ * data (S * n_elem * q^3 doubles).  Errors: NH_ERR_ARG, NH_ERR_UNSUPPORTED,
+ * NH_ERR_OOM. */
+nh_status nh_op_create(nh_space fine, double nu, const double* E_per_elem, double E,
+                       int layout, nh_op* out);
+/* Galerkin coarse operator on `coarse` (same mesh, lower p, same q) that
+ * shares the fine operator's quadrature data: coarse basis tabulated at the
+ * fine quadrature points, an exact Galerkin coarse operator (Sec. III-B).
+ * The fine operator must outlive it. */
+nh_status nh_op_level(nh_op fine, nh_space coarse, nh_op* out);
+nh_status nh_op_destroy(nh_op op);
+/* Scalars per quadrature point and bytes of stored quadrature data for prec. */
+nh_status nh_op_info(nh_op op, nh_prec prec, int* scalars_per_qp, int64_t* qdata_bytes);
+
+/* Quadrature data from the displacement u (device, double [n_dof]): F, J,
+ * log J (from the invariants of H, so log1p does not cancel), tau, grad_x xi,
+ * W (Eq. Kirchhoff-stress, Sec. III-B), always in FP64; an FP32 copy is made
+ * on first FP32 use.  Writes min det F over all points to *min_J (HOST;
+ * this call synchronises).  Returns NH_ERR_INVERTED if min det F <= 0 or is
+ * not finite (the stored data are then invalid).
+ * Errors: NH_ERR_ARG, NH_ERR_STATE (coarse op). */
+nh_status nh_qdata_setup(nh_op op, const double* u, double* min_J);
+
+/* Residual r = F(u) (Eq. residual-discrete-ref with f_1 = tau, f_0 = 0):
+ * sum_e E^T B_xi^T W tau (grad_x xi)^T; constrained rows r = u - g_bc.
+ * g_bc may be NULL (zero).  FP64 device vectors; does not touch the stored
+ * quadrature data.  Errors: NH_ERR_ARG, NH_ERR_STATE (coarse op). */
+nh_status nh_residual(nh_op op, const double* u, const double* g_bc, double* r);
+
+/* Jacobian action y = J du (Eq. Jacobian-discrete-ref with Eqs. dtau and
+ * depsilon): fused gather E, sum-factorised collocated gradient, pointwise
+ * linearised stress from stored quadrature data, transposed contractions
+ * and scatter-add E^T.  du and y: device [n_dof] of prec type, must not
+ * alias.  Errors: NH_ERR_ARG, NH_ERR_STATE (no quadrature data yet). */
+nh_status nh_jacobian_apply(nh_op op, nh_prec prec, const void* du, void* y);
+/* Same, with HOST du_host and y_host (pinned memory recommended): copies in,
+ * applies, copies out through library-owned device buffers; synchronises. */
+nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* du_host, void* y_host);
+
+/* Diagonal of the assembled Jacobian for Jacobi smoothing (Sec. III-B):
+ * diag[a,c] = sum_e sum_q sum_{d,d'} B_xi,d[q,a] D[q; c,d; c,d'] B_xi,d'[q,a];
+ * 1 on constrained DoFs.  Device out [n_dof] of prec type. */
+nh_status nh_jacobian_diagonal(nh_op op, nh_prec prec, void* diag);
+
+/* ---- p-multigrid transfer (Eq. mg_prolong) ----------------------------- */
+
+/* uf = P uc, P = sum_e E_f^T Lambda(m_f^-1) B_ctof E_c, m_f = node multiplicity.
+ * coarse and fine: same mesh, p_c < p_f.  Device vectors of prec type. */
+nh_status nh_prolong(nh_space coarse, nh_space fine, nh_prec prec, const void* uc, void* uf);
+/* rc = P^T rf (restriction = prolongation transposed, Sec. III-B). */
+nh_status nh_restrict(nh_space fine, nh_space coarse, nh_prec prec, const void* rf, void* rc);
+
+/* ---- vector kernels --------------------------------------------------- */
+
+/* Deterministic FP64 dot product of two device double vectors of length n
+ * (the Krylov inner products of Sec. III-A): per-block partial sums in
+ * library scratch, then one fixed-order pass.  Result to *result_host (HOST;
+ * synchronises). */
+nh_status nh_dot(nh_ctx ctx, int64_t n, const double* x, const double* y, double* result_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NH_H */

@@ -1,0 +1,526 @@
+// C ABI of the nh library (declared in include/nh.h): contexts, spaces,
+// operators and the stream-ordered calls that launch the fused kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nh_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+nh_status nh_fail(nh_ctx ctx, nh_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+nh_status nh_cuda_check(nh_ctx ctx, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // clear the non-sticky error
+    return nh_fail(ctx, NH_ERR_OOM, m);
+  }
+  return nh_fail(ctx, NH_ERR_CUDA, m);
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// ---------------------------------------------------------------------------
+// launcher dispatch over P
+// ---------------------------------------------------------------------------
+cudaError_t nh_launch_apply(int P, int Q, nh_prec prec, const OpArgs& a, cudaStream_t s) {
+  switch (P) {
+    case 2: return nh_launch_apply_P2(Q, prec, a, s);
+    case 3: return nh_launch_apply_P3(Q, prec, a, s);
+    case 4: return nh_launch_apply_P4(Q, prec, a, s);
+    case 5: return nh_launch_apply_P5(Q, prec, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t nh_launch_setup(int P, int Q, const OpArgs& a, cudaStream_t s) {
+  switch (P) {
+    case 2: return nh_launch_setup_P2(Q, a, s);
+    case 3: return nh_launch_setup_P3(Q, a, s);
+    case 4: return nh_launch_setup_P4(Q, a, s);
+    case 5: return nh_launch_setup_P5(Q, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t nh_launch_diag(int P, int Q, const OpArgs& a, cudaStream_t s) {
+  switch (P) {
+    case 2: return nh_launch_diag_P2(Q, a, s);
+    case 3: return nh_launch_diag_P3(Q, a, s);
+    case 4: return nh_launch_diag_P4(Q, a, s);
+    case 5: return nh_launch_diag_P5(Q, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+static const int kRedBlocks = 148 * 8;
+
+extern "C" nh_status nh_create(nh_ctx* out, int device, void* cuda_stream) {
+  if (!out) return NH_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return NH_ERR_CUDA;
+  nh_ctx c = new nh_ctx_s();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return NH_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  c->red_len = kRedBlocks + 8;
+  if (cudaMalloc(&c->red, c->red_len * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->minj, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&c->red_host, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->red) cudaFree(c->red);
+    if (c->minj) cudaFree(c->minj);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return NH_ERR_OOM;
+  }
+  *out = c;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_destroy(nh_ctx c) {
+  if (!c) return NH_ERR_ARG;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->red);
+  cudaFree(c->minj);
+  cudaFreeHost(c->red_host);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return NH_OK;
+}
+
+extern "C" const char* nh_last_error(nh_ctx c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" nh_status nh_sync(nh_ctx c) {
+  if (!c) return NH_ERR_ARG;
+  NH_CUDA(c, cudaSetDevice(c->device));
+  NH_CUDA(c, cudaStreamSynchronize(c->stream));
+  NH_CUDA(c, cudaGetLastError());
+  return NH_OK;
+}
+
+extern "C" int64_t nh_launch_count(nh_ctx c) { return c ? c->launches : -1; }
+
+// ---------------------------------------------------------------------------
+// spaces
+// ---------------------------------------------------------------------------
+extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const double* vxyz, int p, int q,
+                                  nh_space* out, int64_t* n_nodes, int64_t* n_dof) {
+  if (!ctx || !out) return NH_ERR_ARG;
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return nh_fail(ctx, NH_ERR_ARG, "nh_space_box: element counts must be >= 1");
+  if (p < 1 || p > 4 || q < p + 1 || q > NH_MAXQ)
+    return nh_fail(ctx, NH_ERR_UNSUPPORTED, "nh_space_box: need 1 <= p <= 4 and p+1 <= q <= 6");
+  const int P = p + 1;
+  const int64_t Nx = (int64_t)p * nx + 1, Ny = (int64_t)p * ny + 1, Nz = (int64_t)p * nz + 1;
+  const int64_t ne = (int64_t)nx * ny * nz, nn = Nx * Ny * Nz;
+  if (nn > INT32_MAX / 3 || ne > INT32_MAX / 8)
+    return nh_fail(ctx, NH_ERR_UNSUPPORTED, "nh_space_box: mesh too large for int32 node ids");
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  nh_space s = new nh_space_s();
+  s->ctx = ctx;
+  s->nx = nx; s->ny = ny; s->nz = nz; s->p = p; s->q = q; s->P = P; s->Q = q;
+  s->ne = ne; s->n_nodes = nn; s->n_dof = 3 * nn;
+  s->Nx = (int)Nx; s->Ny = (int)Ny; s->Nz = (int)Nz;
+  nh_tabulate(p, q, &s->tab);
+
+  // element restriction and node coordinates (trilinear image of the GLL lattice)
+  const int P3 = P * P * P;
+  std::vector<int> emap((size_t)ne * P3);
+  s->coords_host.assign((size_t)nn * 3, 0.0);
+  std::vector<double> mult((size_t)nn, 0.0);
+  double xn[NH_MAXP];
+  nh_lobatto(P, xn);
+  double sh[NH_MAXP][2];  // 1-D trilinear factors at the GLL nodes
+  for (int i = 0; i < P; i++) {
+    sh[i][0] = 0.5 * (1.0 - xn[i]);
+    sh[i][1] = 0.5 * (1.0 + xn[i]);
+  }
+  const int64_t VX = nx + 1, VY = ny + 1;
+  for (int64_t ez = 0; ez < nz; ez++)
+    for (int64_t ey = 0; ey < ny; ey++)
+      for (int64_t ex = 0; ex < nx; ex++) {
+        const int64_t e = ex + nx * (ey + ny * ez);
+        double V[8][3];
+        for (int v = 0; v < 8; v++) {
+          const int64_t vi = ex + (v & 1), vj = ey + ((v >> 1) & 1), vk = ez + ((v >> 2) & 1);
+          const int64_t vid = vi + VX * (vj + VY * vk);
+          if (vxyz) {
+            for (int d = 0; d < 3; d++) V[v][d] = vxyz[3 * vid + d];
+          } else {
+            V[v][0] = (double)vi / nx;
+            V[v][1] = (double)vj / ny;
+            V[v][2] = (double)vk / nz;
+          }
+        }
+        for (int k = 0; k < P; k++)
+          for (int j = 0; j < P; j++)
+            for (int i = 0; i < P; i++) {
+              const int64_t gi = p * ex + i, gj = p * ey + j, gk = p * ez + k;
+              const int64_t nid = gi + Nx * (gj + Ny * gk);
+              emap[(size_t)e * P3 + (k * P + j) * P + i] = (int)nid;
+              mult[nid] += 1.0;
+              double X[3] = {0, 0, 0};
+              for (int v = 0; v < 8; v++) {
+                const double w = sh[i][v & 1] * sh[j][(v >> 1) & 1] * sh[k][(v >> 2) & 1];
+                for (int d = 0; d < 3; d++) X[d] += w * V[v][d];
+              }
+              for (int d = 0; d < 3; d++) s->coords_host[3 * nid + d] = X[d];
+            }
+      }
+  std::vector<double> im(nn);
+  std::vector<float> imf(nn);
+  for (int64_t n = 0; n < nn; n++) {
+    im[n] = 1.0 / mult[n];
+    imf[n] = (float)im[n];
+  }
+  cudaError_t e1 = cudaMalloc(&s->emap, sizeof(int) * emap.size());
+  cudaError_t e2 = cudaMalloc(&s->coords, sizeof(double) * 3 * nn);
+  cudaError_t e3 = cudaMalloc(&s->bc, nn);
+  cudaError_t e4 = cudaMalloc(&s->inv_mult, sizeof(double) * nn);
+  cudaError_t e5 = cudaMalloc(&s->inv_mult_f, sizeof(float) * nn);
+  if (e1 || e2 || e3 || e4 || e5) {
+    cudaGetLastError();
+    nh_space_destroy(s);
+    return nh_fail(ctx, NH_ERR_OOM, "nh_space_box: device allocation failed");
+  }
+  NH_CUDA(ctx, cudaMemcpy(s->emap, emap.data(), sizeof(int) * emap.size(), cudaMemcpyHostToDevice));
+  NH_CUDA(ctx, cudaMemcpy(s->coords, s->coords_host.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice));
+  NH_CUDA(ctx, cudaMemset(s->bc, 0, nn));
+  NH_CUDA(ctx, cudaMemcpy(s->inv_mult, im.data(), sizeof(double) * nn, cudaMemcpyHostToDevice));
+  NH_CUDA(ctx, cudaMemcpy(s->inv_mult_f, imf.data(), sizeof(float) * nn, cudaMemcpyHostToDevice));
+  NH_CUDA(ctx, cudaDeviceSynchronize());
+  *out = s;
+  if (n_nodes) *n_nodes = nn;
+  if (n_dof) *n_dof = 3 * nn;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_space_coords(nh_space s, double* xyz) {
+  if (!s || !xyz) return NH_ERR_ARG;
+  memcpy(xyz, s->coords_host.data(), sizeof(double) * 3 * s->n_nodes);
+  return NH_OK;
+}
+
+extern "C" nh_status nh_space_set_dirichlet(nh_space s, const uint8_t* mask) {
+  if (!s || !mask) return NH_ERR_ARG;
+  std::vector<uint8_t> bits((size_t)s->n_nodes, 0);
+  int64_t nc = 0;
+  for (int64_t n = 0; n < s->n_nodes; n++)
+    for (int c = 0; c < 3; c++)
+      if (mask[3 * n + c]) {
+        bits[n] |= (uint8_t)(1u << c);
+        nc++;
+      }
+  s->n_constrained = nc;
+  NH_CUDA(s->ctx, cudaSetDevice(s->ctx->device));
+  NH_CUDA(s->ctx, cudaMemcpyAsync(s->bc, bits.data(), s->n_nodes, cudaMemcpyHostToDevice, s->ctx->stream));
+  NH_CUDA(s->ctx, cudaStreamSynchronize(s->ctx->stream));
+  return NH_OK;
+}
+
+extern "C" nh_status nh_space_destroy(nh_space s) {
+  if (!s) return NH_ERR_ARG;
+  cudaFree(s->emap);
+  cudaFree(s->coords);
+  cudaFree(s->bc);
+  cudaFree(s->inv_mult);
+  cudaFree(s->inv_mult_f);
+  delete s;
+  return NH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// operators
+// ---------------------------------------------------------------------------
+static int scalars_for(int layout) { return layout == NH_LAYOUT_CURRENT ? 17 : 27; }
+
+extern "C" nh_status nh_op_create(nh_space fine, double nu, const double* Epe, double E, int layout, nh_op* out) {
+  if (!fine || !out) return NH_ERR_ARG;
+  *out = nullptr;
+  nh_ctx ctx = fine->ctx;
+  if (layout != NH_LAYOUT_CURRENT && layout != NH_LAYOUT_INITIAL)
+    return nh_fail(ctx, NH_ERR_UNSUPPORTED, "nh_op_create: unknown layout");
+  if (!(nu > -1.0 && nu < 0.5)) return nh_fail(ctx, NH_ERR_ARG, "nh_op_create: need -1 < nu < 0.5");
+  std::vector<double> lam(fine->ne), mu(fine->ne);
+  for (int64_t e = 0; e < fine->ne; e++) {
+    const double Ee = Epe ? Epe[e] : E;
+    if (!(Ee > 0.0)) return nh_fail(ctx, NH_ERR_ARG, "nh_op_create: Young's modulus must be > 0");
+    lam[e] = Ee * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    mu[e] = Ee / (2.0 * (1.0 + nu));
+  }
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  nh_op op = new nh_op_s();
+  op->space = fine;
+  op->layout = layout;
+  op->S = scalars_for(layout);
+  op->nu = nu;
+  const int64_t nq = fine->ne * (int64_t)fine->Q * fine->Q * fine->Q;
+  if (cudaMalloc(&op->lam, sizeof(double) * fine->ne) || cudaMalloc(&op->mu, sizeof(double) * fine->ne) ||
+      cudaMalloc(&op->qd, sizeof(double) * nq * op->S)) {
+    cudaGetLastError();
+    nh_op_destroy(op);
+    return nh_fail(ctx, NH_ERR_OOM, "nh_op_create: device allocation failed");
+  }
+  NH_CUDA(ctx, cudaMemcpy(op->lam, lam.data(), sizeof(double) * fine->ne, cudaMemcpyHostToDevice));
+  NH_CUDA(ctx, cudaMemcpy(op->mu, mu.data(), sizeof(double) * fine->ne, cudaMemcpyHostToDevice));
+  *out = op;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_op_level(nh_op fine, nh_space coarse, nh_op* out) {
+  if (!fine || !coarse || !out) return NH_ERR_ARG;
+  *out = nullptr;
+  nh_op root = fine->parent ? fine->parent : fine;
+  nh_space fs = root->space;
+  nh_ctx ctx = fs->ctx;
+  if (coarse->nx != fs->nx || coarse->ny != fs->ny || coarse->nz != fs->nz || coarse->Q != fs->Q ||
+      coarse->p > fs->p)
+    return nh_fail(ctx, NH_ERR_ARG, "nh_op_level: coarse space must share the mesh and q, with p_c <= p_f");
+  nh_op op = new nh_op_s();
+  op->space = coarse;
+  op->parent = root;
+  op->layout = root->layout;
+  op->S = root->S;
+  op->nu = root->nu;
+  *out = op;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_op_destroy(nh_op op) {
+  if (!op) return NH_ERR_ARG;
+  if (!op->parent) {
+    cudaFree(op->lam);
+    cudaFree(op->mu);
+    cudaFree(op->qd);
+    cudaFree(op->qd_f);
+  }
+  cudaFree(op->hbuf_in);
+  cudaFree(op->hbuf_out);
+  delete op;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_op_info(nh_op op, nh_prec prec, int* S, int64_t* bytes) {
+  if (!op) return NH_ERR_ARG;
+  nh_op root = op->parent ? op->parent : op;
+  const int64_t nq = root->space->ne * (int64_t)root->space->Q * root->space->Q * root->space->Q;
+  if (S) *S = root->S;
+  if (bytes) *bytes = nq * root->S * (prec == NH_F64 ? 8 : 4);
+  return NH_OK;
+}
+
+static OpArgs base_args(nh_op op) {
+  nh_op root = op->parent ? op->parent : op;
+  OpArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ne = op->space->ne;
+  a.emap = op->space->emap;
+  a.bc = op->space->bc;
+  a.qstride = root->space->ne * (int64_t)root->space->Q * root->space->Q * root->space->Q;
+  a.layout = root->layout;
+  a.tab = &op->space->tab;
+  a.coords = op->space->coords;
+  a.lam = root->lam;
+  a.mu = root->mu;
+  return a;
+}
+
+extern "C" nh_status nh_qdata_setup(nh_op op, const double* u, double* min_J) {
+  if (!op || !u) return NH_ERR_ARG;
+  nh_ctx ctx = op->space->ctx;
+  if (op->parent) return nh_fail(ctx, NH_ERR_STATE, "nh_qdata_setup: coarse operators share the fine data");
+  if (!aligned(u, 16)) return nh_fail(ctx, NH_ERR_ARG, "nh_qdata_setup: u must be 16-byte aligned");
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  OpArgs a = base_args(op);
+  a.in = u;
+  a.qd_out = op->qd;
+  a.store = 1;
+  a.resid = 0;
+  a.minj = ctx->minj;
+  NH_CUDA(ctx, cudaMemsetAsync(ctx->minj, 0xff, sizeof(unsigned long long), ctx->stream));
+  NH_CUDA(ctx, nh_launch_setup(op->space->P, op->space->Q, a, ctx->stream));
+  ctx->launches++;
+  unsigned long long bits = 0;
+  NH_CUDA(ctx, cudaMemcpyAsync(ctx->red_host, ctx->minj, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
+  NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  memcpy(&bits, ctx->red_host, sizeof(bits));
+  bits = (bits >> 63) ? (bits & 0x7fffffffffffffffull) : ~bits;
+  double mj;
+  memcpy(&mj, &bits, sizeof(mj));
+  if (min_J) *min_J = mj;
+  op->qd_f_valid = false;
+  if (!(mj > 0.0) || !isfinite(mj)) {
+    op->have_qd = false;
+    char buf[128];
+    snprintf(buf, sizeof(buf), "nh_qdata_setup: inverted element, min det F = %g", mj);
+    return nh_fail(ctx, NH_ERR_INVERTED, buf);
+  }
+  op->have_qd = true;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_residual(nh_op op, const double* u, const double* g_bc, double* r) {
+  if (!op || !u || !r) return NH_ERR_ARG;
+  nh_ctx ctx = op->space->ctx;
+  if (op->parent) return nh_fail(ctx, NH_ERR_STATE, "nh_residual: only on the fine operator");
+  if ((const void*)u == (const void*)r) return nh_fail(ctx, NH_ERR_ARG, "nh_residual: u and r must not alias");
+  if (!aligned(u, 16) || !aligned(r, 16)) return nh_fail(ctx, NH_ERR_ARG, "nh_residual: misaligned vector");
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  OpArgs a = base_args(op);
+  a.in = u;
+  a.out = r;
+  a.gbc = g_bc;
+  a.store = 0;
+  a.resid = 1;
+  NH_CUDA(ctx, cudaMemsetAsync(r, 0, sizeof(double) * op->space->n_dof, ctx->stream));
+  NH_CUDA(ctx, nh_launch_setup(op->space->P, op->space->Q, a, ctx->stream));
+  ctx->launches++;
+  return NH_OK;
+}
+
+static nh_status ensure_f32(nh_op root) {
+  nh_ctx ctx = root->space->ctx;
+  if (root->qd_f_valid) return NH_OK;
+  const int64_t n = root->S * root->space->ne * (int64_t)root->space->Q * root->space->Q * root->space->Q;
+  if (!root->qd_f) NH_CUDA(ctx, cudaMalloc(&root->qd_f, sizeof(float) * n));
+  NH_CUDA(ctx, nh_launch_f64_to_f32(n, root->qd, root->qd_f, ctx->stream));
+  ctx->launches++;
+  root->qd_f_valid = true;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_jacobian_apply(nh_op op, nh_prec prec, const void* du, void* y) {
+  if (!op || !du || !y) return NH_ERR_ARG;
+  nh_ctx ctx = op->space->ctx;
+  nh_op root = op->parent ? op->parent : op;
+  if (prec != NH_F64 && prec != NH_F32) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply: bad precision");
+  if (du == (const void*)y) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply: du and y must not alias");
+  if (!aligned(du, 16) || !aligned(y, 16)) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply: misaligned vector");
+  if (!root->have_qd) return nh_fail(ctx, NH_ERR_STATE, "nh_jacobian_apply: call nh_qdata_setup first");
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (prec == NH_F32) {
+    nh_status st = ensure_f32(root);
+    if (st != NH_OK) return st;
+  }
+  OpArgs a = base_args(op);
+  a.in = du;
+  a.out = y;
+  a.prec = prec;
+  a.qd = prec == NH_F64 ? (const void*)root->qd : (const void*)root->qd_f;
+  const size_t w = prec == NH_F64 ? 8 : 4;
+  NH_CUDA(ctx, cudaMemsetAsync(y, 0, w * op->space->n_dof, ctx->stream));
+  NH_CUDA(ctx, nh_launch_apply(op->space->P, op->space->Q, prec, a, ctx->stream));
+  ctx->launches++;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* du_h, void* y_h) {
+  if (!op || !du_h || !y_h) return NH_ERR_ARG;
+  nh_ctx ctx = op->space->ctx;
+  if (prec != NH_F64 && prec != NH_F32) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply_host: bad precision");
+  const size_t bytes = (prec == NH_F64 ? 8 : 4) * (size_t)op->space->n_dof;
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (op->hbuf_bytes < bytes) {
+    NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(op->hbuf_in);
+    cudaFree(op->hbuf_out);
+    op->hbuf_in = op->hbuf_out = nullptr;
+    op->hbuf_bytes = 0;
+    NH_CUDA(ctx, cudaMalloc(&op->hbuf_in, bytes));
+    NH_CUDA(ctx, cudaMalloc(&op->hbuf_out, bytes));
+    op->hbuf_bytes = bytes;
+  }
+  NH_CUDA(ctx, cudaMemcpyAsync(op->hbuf_in, du_h, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  nh_status st = nh_jacobian_apply(op, prec, op->hbuf_in, op->hbuf_out);
+  if (st != NH_OK) return st;
+  NH_CUDA(ctx, cudaMemcpyAsync(y_h, op->hbuf_out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return NH_OK;
+}
+
+extern "C" nh_status nh_jacobian_diagonal(nh_op op, nh_prec prec, void* diag) {
+  if (!op || !diag) return NH_ERR_ARG;
+  nh_ctx ctx = op->space->ctx;
+  nh_op root = op->parent ? op->parent : op;
+  if (prec != NH_F64 && prec != NH_F32) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_diagonal: bad precision");
+  if (!aligned(diag, 16)) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_diagonal: misaligned vector");
+  if (!root->have_qd) return nh_fail(ctx, NH_ERR_STATE, "nh_jacobian_diagonal: call nh_qdata_setup first");
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  OpArgs a = base_args(op);
+  a.out = diag;
+  a.prec = prec;
+  a.qd = root->qd;
+  NH_CUDA(ctx, cudaMemsetAsync(diag, 0, (prec == NH_F64 ? 8 : 4) * op->space->n_dof, ctx->stream));
+  NH_CUDA(ctx, nh_launch_diag(op->space->P, op->space->Q, a, ctx->stream));
+  ctx->launches++;
+  return NH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// transfer
+// ---------------------------------------------------------------------------
+static nh_status transfer(nh_space c, nh_space f, nh_prec prec, int dir, const void* in, void* out) {
+  if (!c || !f || !in || !out) return NH_ERR_ARG;
+  nh_ctx ctx = f->ctx;
+  if (c->nx != f->nx || c->ny != f->ny || c->nz != f->nz || c->p >= f->p)
+    return nh_fail(ctx, NH_ERR_ARG, "nh_prolong/nh_restrict: spaces must share the mesh with p_c < p_f");
+  if (prec != NH_F64 && prec != NH_F32) return nh_fail(ctx, NH_ERR_ARG, "transfer: bad precision");
+  if (in == (const void*)out) return nh_fail(ctx, NH_ERR_ARG, "transfer: in and out must not alias");
+  if (!aligned(in, 16) || !aligned(out, 16)) return nh_fail(ctx, NH_ERR_ARG, "transfer: misaligned vector");
+  double xc[NH_MAXP], xf[NH_MAXP], B[NH_MAXP * NH_MAXP];
+  nh_lobatto(c->P, xc);
+  nh_lobatto(f->P, xf);
+  nh_lagrange(c->P, xc, f->P, xf, B, nullptr);  // [Pf][Pc]
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  nh_space dst = dir == 0 ? f : c;
+  NH_CUDA(ctx, cudaMemsetAsync(out, 0, (prec == NH_F64 ? 8 : 4) * dst->n_dof, ctx->stream));
+  cudaError_t e = nh_launch_transfer(c->P, f->P, prec, dir, f->ne, c->emap, f->emap, f->inv_mult, f->inv_mult_f, in,
+                                     out, B, ctx->stream);
+  if (e == cudaErrorInvalidValue) return nh_fail(ctx, NH_ERR_UNSUPPORTED, "transfer: (p_c, p_f) not compiled");
+  NH_CUDA(ctx, e);
+  ctx->launches++;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_prolong(nh_space coarse, nh_space fine, nh_prec prec, const void* uc, void* uf) {
+  return transfer(coarse, fine, prec, 0, uc, uf);
+}
+
+extern "C" nh_status nh_restrict(nh_space fine, nh_space coarse, nh_prec prec, const void* rf, void* rc) {
+  return transfer(coarse, fine, prec, 1, rf, rc);
+}
+
+// ---------------------------------------------------------------------------
+// vectors
+// ---------------------------------------------------------------------------
+extern "C" nh_status nh_dot(nh_ctx ctx, int64_t n, const double* x, const double* y, double* res) {
+  if (!ctx || !x || !y || !res || n < 0) return NH_ERR_ARG;
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  NH_CUDA(ctx, nh_launch_dot_partials(n, x, y, ctx->red, kRedBlocks, ctx->stream));
+  NH_CUDA(ctx, nh_launch_sum_partials(ctx->red, kRedBlocks, ctx->red + kRedBlocks, ctx->stream));
+  ctx->launches += 2;
+  NH_CUDA(ctx, cudaMemcpyAsync(ctx->red_host, ctx->red + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *res = ctx->red_host[0];
+  return NH_OK;
+}

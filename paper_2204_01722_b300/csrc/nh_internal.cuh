@@ -1,0 +1,152 @@
+// Internal declarations of the nh library: handles, 1-D basis tables and the
+// per-(P,Q) kernel launchers.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nh.h"
+
+#define NH_MAXP 5   // nodes per direction (p <= 4)
+#define NH_MAXQ 6   // Gauss points per direction
+
+// ---- 1-D tables ---------------------------------------------------------------
+// Host-side tabulations in double; kernels receive them by value as kernel
+// parameters (constant bank), converted to the kernel's scalar type.
+struct Tab1D {
+  int P, Q;
+  double B[NH_MAXQ][NH_MAXP];    // GLL Lagrange basis at Gauss points (B_I)
+  double G[NH_MAXQ][NH_MAXP];    // its derivative (B_xi)
+  double D[NH_MAXQ][NH_MAXQ];    // collocated derivative B_xi B_I^+ (Sec. II-B)
+  double w[NH_MAXQ];             // Gauss weights
+};
+
+// 1-D rules and Lagrange tabulation (nh_basis.cu)
+void nh_gauss(int q, double* x, double* w);
+void nh_lobatto(int n, double* x);
+void nh_lagrange(int n, const double* nodes, int m, const double* pts, double* val, double* der);
+void nh_tabulate(int p, int q, Tab1D* t);
+
+template <int P, int Q, typename T>
+struct KTab {
+  T B[Q][P];
+  T D[Q][Q];
+};
+
+template <int P, int Q, typename T>
+inline KTab<P, Q, T> make_ktab(const Tab1D& t) {
+  KTab<P, Q, T> k;
+  for (int i = 0; i < Q; i++)
+    for (int j = 0; j < P; j++) k.B[i][j] = (T)t.B[i][j];
+  for (int i = 0; i < Q; i++)
+    for (int j = 0; j < Q; j++) k.D[i][j] = (T)t.D[i][j];
+  return k;
+}
+
+// ---- handles -------------------------------------------------------------------
+struct nh_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 148;
+  std::string err;
+  int64_t launches = 0;
+  // scratch for reductions (library owned)
+  double* red = nullptr;               // partial sums + result slot
+  size_t red_len = 0;
+  double* red_host = nullptr;          // pinned
+  unsigned long long* minj = nullptr;  // ordered-bits min of det F
+};
+
+struct nh_space_s {
+  nh_ctx ctx = nullptr;
+  int nx = 0, ny = 0, nz = 0, p = 0, q = 0, P = 0, Q = 0;
+  int64_t ne = 0, n_nodes = 0, n_dof = 0;
+  int Nx = 0, Ny = 0, Nz = 0;     // node lattice dims
+  Tab1D tab;
+  int* emap = nullptr;            // [ne][P^3] element restriction
+  double* coords = nullptr;       // [n_nodes][3] device
+  std::vector<double> coords_host;
+  uint8_t* bc = nullptr;          // [n_nodes] bit c set = component c constrained (device)
+  double* inv_mult = nullptr;     // [n_nodes] 1 / multiplicity
+  float* inv_mult_f = nullptr;
+  int64_t n_constrained = 0;
+};
+
+struct nh_op_s {
+  nh_space space = nullptr;       // space this operator acts on
+  nh_op parent = nullptr;         // fine operator whose qdata is shared (coarse levels)
+  int layout = 0;
+  int S = 17;                     // scalars per quadrature point
+  double nu = 0.3;
+  double* lam = nullptr;          // [ne] device
+  double* mu = nullptr;
+  double* qd = nullptr;           // [S][ne*Q^3] FP64 quadrature data (fine op only)
+  float* qd_f = nullptr;          // FP32 copy
+  bool have_qd = false;
+  bool qd_f_valid = false;
+  // device staging for nh_jacobian_apply_host
+  void* hbuf_in = nullptr;
+  void* hbuf_out = nullptr;
+  size_t hbuf_bytes = 0;
+};
+
+// ---- error helpers -------------------------------------------------------------
+nh_status nh_fail(nh_ctx ctx, nh_status st, const std::string& msg);
+nh_status nh_cuda_check(nh_ctx ctx, cudaError_t e, const char* what);
+#define NH_CUDA(ctx, call)                                        \
+  do {                                                            \
+    cudaError_t _e = (call);                                      \
+    if (_e != cudaSuccess) return nh_cuda_check(ctx, _e, #call);  \
+  } while (0)
+
+// ---- kernel launchers (nh_operator.cu, one object per P) -------------------------
+struct OpArgs {
+  int64_t ne;
+  const int* emap;
+  const uint8_t* bc;
+  const void* qd;      // quadrature data of the prec type
+  int64_t qstride;     // ne * Q^3
+  const void* in;      // du (apply) / u (setup, residual)
+  void* out;           // y / r / diag
+  const double* coords;
+  const double* gbc;
+  const double* lam;
+  const double* mu;
+  double* qd_out;      // setup: FP64 quadrature data to write (nullable)
+  unsigned long long* minj;
+  int layout;
+  int prec;            // nh_prec of in/out vectors (apply, diagonal)
+  int store;           // setup: write quadrature data
+  int resid;           // setup: compute residual
+  const Tab1D* tab;
+};
+
+// Return cudaErrorInvalidValue if (P, Q) is outside the compiled set.
+cudaError_t nh_launch_apply(int P, int Q, nh_prec prec, const OpArgs& a, cudaStream_t s);
+cudaError_t nh_launch_setup(int P, int Q, const OpArgs& a, cudaStream_t s);
+cudaError_t nh_launch_diag(int P, int Q, const OpArgs& a, cudaStream_t s);
+
+#define NH_DECLARE_P(PP)                                                                  \
+  cudaError_t nh_launch_apply_P##PP(int Q, nh_prec prec, const OpArgs& a, cudaStream_t s); \
+  cudaError_t nh_launch_setup_P##PP(int Q, const OpArgs& a, cudaStream_t s);              \
+  cudaError_t nh_launch_diag_P##PP(int Q, const OpArgs& a, cudaStream_t s);
+NH_DECLARE_P(2)
+NH_DECLARE_P(3)
+NH_DECLARE_P(4)
+NH_DECLARE_P(5)
+
+// transfer (nh_transfer.cu)
+cudaError_t nh_launch_transfer(int Pc, int Pf, nh_prec prec, int restrict_dir, int64_t ne,
+                               const int* emap_c, const int* emap_f, const double* inv_mult,
+                               const float* inv_mult_f, const void* in, void* out,
+                               const double* ctof /* [Pf][Pc] */, cudaStream_t s);
+
+// vector kernels (nh_vector.cu)
+cudaError_t nh_launch_dot_partials(int64_t n, const double* x, const double* y, double* partials,
+                                   int nblocks, cudaStream_t s);
+cudaError_t nh_launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
+cudaError_t nh_launch_f64_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);

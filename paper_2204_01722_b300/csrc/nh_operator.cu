@@ -1,0 +1,778 @@
+// Fused element kernels of the Neo-Hookean operator (Sec. II-B, II-C):
+//   Jacobian action  y = E^T B^T D B E du     (Eq. Jacobian-discrete-ref)
+//   residual/qdata   r = E^T B_xi^T W f1(u)   (Eq. residual-discrete-ref)
+//   diagonal of J for Jacobi smoothing         (Sec. III-B)
+// E (gather/scatter through the element map), B (sum-factorised tensor
+// contractions, gradients by the collocated derivative B_xi B_I^+ so a gradient
+// costs 6 instead of 9 contractions) and D (pointwise quadrature function) run in
+// one kernel; E-vectors and Q-vectors live only in registers and shared memory.
+//
+// Thread layout: each element is handled by Q*Q threads, thread (a, b) owning the
+// quadrature column (qi = a, qj = b) and looping over qk in registers; the
+// x- and y-contractions exchange data through shared memory.  A block holds EPB
+// elements (about 128 threads).  Scatter-add uses atomics.
+//
+// This file is compiled once per P (nodes per direction), with -DNH_P_INST=P.
+#include "nh_internal.cuh"
+
+#ifndef NH_P_INST
+#error "compile with -DNH_P_INST=<P>"
+#endif
+
+namespace {
+
+__host__ __device__ constexpr int epb_for(int Q) { return (128 / (Q * Q)) > 0 ? 128 / (Q * Q) : 1; }
+
+template <int Q>
+__device__ __forceinline__ int sidx(int c, int k, int j, int i) {
+  return ((c * Q + k) * Q + j) * Q + i;
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise linearised stress (the D of A = E^T B^T D B E).
+// g[c][d] = d du_c / d xi_d at one quadrature point; f[c][d] is the reference
+// flux tested against d v_c / d xi_d.  q points at this point's scalar 0,
+// consecutive scalars are s apart.
+// ---------------------------------------------------------------------------
+
+// Current configuration (Eqs. Jacobian, dtau, depsilon): G = g grad_x xi,
+// W sigma = G (W tau) + W lambda tr(G) I + W (mu - lambda log J) (G + G^T),
+// f = W sigma (grad_x xi)^T.  Stored: grad_x xi (9, row d = xi_d), W tau
+// (00, 11, 22, 12, 02, 01), W lambda, W (mu - lambda log J).
+template <typename T>
+__device__ __forceinline__ void pw_current(const T* __restrict__ q, int64_t s, const T (&g)[3][3],
+                                           T (&f)[3][3]) {
+  T X[3][3];
+#pragma unroll
+  for (int i = 0; i < 9; i++) X[i / 3][i % 3] = q[i * s];
+  const T t00 = q[9 * s], t11 = q[10 * s], t22 = q[11 * s];
+  const T t12 = q[12 * s], t02 = q[13 * s], t01 = q[14 * s];
+  const T wl = q[15 * s], wm = q[16 * s];
+  const T tau[3][3] = {{t00, t01, t02}, {t01, t11, t12}, {t02, t12, t22}};
+  T G[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int k = 0; k < 3; k++) G[c][k] = g[c][0] * X[0][k] + g[c][1] * X[1][k] + g[c][2] * X[2][k];
+  const T trG = wl * (G[0][0] + G[1][1] + G[2][2]);
+  T S[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+      S[c][k] = G[c][0] * tau[0][k] + G[c][1] * tau[1][k] + G[c][2] * tau[2][k] + wm * (G[c][k] + G[k][c]);
+  S[0][0] += trG;
+  S[1][1] += trG;
+  S[2][2] += trG;
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int d = 0; d < 3; d++) f[c][d] = S[c][0] * X[d][0] + S[c][1] * X[d][1] + S[c][2] * X[d][2];
+}
+
+// Initial configuration (Sec. V-E, "initial tuned" storage): dF = g grad_X xi,
+// dE = sym(F^T dF), W S = W mu I + (W lambda log J - W mu) C^-1,
+// W dS = W lambda (C^-1 : dE) C^-1 + 2 (W mu - W lambda log J) C^-1 dE C^-1,
+// W dP = dF (W S) + F (W dS), f = W dP (grad_X xi)^T.  Stored: grad_X xi (9),
+// H = grad_X u (9), C^-1 (00, 11, 22, 12, 02, 01), W mu, W lambda log J, W lambda.
+template <typename T>
+__device__ __forceinline__ void pw_initial(const T* __restrict__ q, int64_t s, const T (&g)[3][3],
+                                           T (&f)[3][3]) {
+  T R[3][3], F[3][3];
+#pragma unroll
+  for (int i = 0; i < 9; i++) R[i / 3][i % 3] = q[i * s];
+#pragma unroll
+  for (int i = 0; i < 9; i++) F[i / 3][i % 3] = q[(9 + i) * s] + (i % 4 == 0 ? T(1) : T(0));
+  const T c00 = q[18 * s], c11 = q[19 * s], c22 = q[20 * s];
+  const T c12 = q[21 * s], c02 = q[22 * s], c01 = q[23 * s];
+  const T wmu = q[24 * s], wll = q[25 * s], wl = q[26 * s];
+  const T Ci[3][3] = {{c00, c01, c02}, {c01, c11, c12}, {c02, c12, c22}};
+  T dF[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int k = 0; k < 3; k++) dF[c][k] = g[c][0] * R[0][k] + g[c][1] * R[1][k] + g[c][2] * R[2][k];
+  T dE[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) dE[k][l] = F[0][k] * dF[0][l] + F[1][k] * dF[1][l] + F[2][k] * dF[2][l];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = k + 1; l < 3; l++) {
+      T m = T(0.5) * (dE[k][l] + dE[l][k]);
+      dE[k][l] = m;
+      dE[l][k] = m;
+    }
+  T trc = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) trc += Ci[k][l] * dE[k][l];
+  T CdE[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) CdE[k][l] = Ci[k][0] * dE[0][l] + Ci[k][1] * dE[1][l] + Ci[k][2] * dE[2][l];
+  const T two_m = T(2) * (wmu - wll);
+  T WdS[3][3], WS[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) {
+      T cdec = CdE[k][0] * Ci[0][l] + CdE[k][1] * Ci[1][l] + CdE[k][2] * Ci[2][l];
+      WdS[k][l] = wl * trc * Ci[k][l] + two_m * cdec;
+      WS[k][l] = (wll - wmu) * Ci[k][l] + (k == l ? wmu : T(0));
+    }
+  T dP[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int K = 0; K < 3; K++)
+      dP[c][K] = dF[c][0] * WS[0][K] + dF[c][1] * WS[1][K] + dF[c][2] * WS[2][K] + F[c][0] * WdS[0][K] +
+                 F[c][1] * WdS[1][K] + F[c][2] * WdS[2][K];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int d = 0; d < 3; d++) f[c][d] = dP[c][0] * R[d][0] + dP[c][1] * R[d][1] + dP[c][2] * R[d][2];
+}
+
+template <int LAYOUT, typename T>
+__device__ __forceinline__ void pointwise(const T* __restrict__ q, int64_t s, const T (&g)[3][3], T (&f)[3][3]) {
+  if (LAYOUT == NH_LAYOUT_CURRENT)
+    pw_current<T>(q, s, g, f);
+  else
+    pw_initial<T>(q, s, g, f);
+}
+
+// ---------------------------------------------------------------------------
+// Sum-factorised element stages.  Shared buffers bA, bB, bC are [3][Q][Q][Q].
+// ---------------------------------------------------------------------------
+
+// E then B_I: gather the element's P^3 nodes (masking constrained components if
+// MASK) and interpolate to the Q^3 points.  Leaves the point values in U
+// (registers, this thread's column) and in bC; remembers node ids in nid.
+template <int P, int Q, typename T, bool MASK>
+__device__ __forceinline__ void gather_interp(bool live, int64_t e, int a, int b, const int* __restrict__ emap,
+                                              const uint8_t* __restrict__ bc, const T* __restrict__ src,
+                                              const KTab<P, Q, T>& tab, T* bA, T* bB, T* bC, T (&U)[3][Q],
+                                              int (&nid)[P]) {
+  constexpr int P3 = P * P * P;
+  if (a < P && b < P) {
+    T r[3][P];
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+      int n = live ? __ldg(&emap[e * P3 + (k * P + b) * P + a]) : 0;
+      nid[k] = n;
+      unsigned m = (MASK && live) ? (unsigned)__ldg(&bc[n]) : 0u;
+#pragma unroll
+      for (int c = 0; c < 3; c++) r[c][k] = (live && !((m >> c) & 1u)) ? src[3 * (int64_t)n + c] : T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int qk = 0; qk < Q; qk++) {
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < P; k++) s += tab.B[qk][k] * r[c][k];
+        bA[sidx<Q>(c, qk, b, a)] = s;
+      }
+  } else {
+#pragma unroll
+    for (int k = 0; k < P; k++) nid[k] = 0;
+  }
+  __syncthreads();
+  if (a < P) {
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int qk = 0; qk < Q; qk++) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < P; j++) s += tab.B[b][j] * bA[sidx<Q>(c, qk, j, a)];
+        bB[sidx<Q>(c, qk, b, a)] = s;
+      }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int qk = 0; qk < Q; qk++) {
+      T s = T(0);
+#pragma unroll
+      for (int i = 0; i < P; i++) s += tab.B[a][i] * bB[sidx<Q>(c, qk, b, i)];
+      U[c][qk] = s;
+      bC[sidx<Q>(c, qk, b, a)] = s;
+    }
+}
+
+// Collocated gradient at point (a, b, qk): g[c][d] = d u_c / d xi_d.
+template <int P, int Q, typename T>
+__device__ __forceinline__ void colloc_grad(int a, int b, int qk, const KTab<P, Q, T>& tab, const T* bC,
+                                            const T (&U)[3][Q], T (&g)[3][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+    for (int m = 0; m < Q; m++) {
+      gx += tab.D[a][m] * bC[sidx<Q>(c, qk, b, m)];
+      gy += tab.D[b][m] * bC[sidx<Q>(c, qk, m, a)];
+      gz += tab.D[qk][m] * U[c][m];
+    }
+    g[c][0] = gx;
+    g[c][1] = gy;
+    g[c][2] = gz;
+  }
+}
+
+// Transposed collocated derivative and B_I^T: from fluxes f_x (bA), f_y (bB) and
+// f_z (registers Fz) back to the element's nodes.  Leaves the nodal result of
+// thread (i = a, j = b) in out[c][k].  The caller must have synchronised after
+// writing bA/bB and after the last read of bC.
+template <int P, int Q, typename T>
+__device__ __forceinline__ void transpose_to_nodes(int a, int b, const KTab<P, Q, T>& tab, T* bA, T* bB, T* bC,
+                                                   const T (&Fz)[3][Q], T (&out)[3][P]) {
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int qk = 0; qk < Q; qk++) {
+      T s = T(0);
+#pragma unroll
+      for (int m = 0; m < Q; m++) {
+        s += tab.D[m][a] * bA[sidx<Q>(c, qk, b, m)];
+        s += tab.D[m][b] * bB[sidx<Q>(c, qk, m, a)];
+        s += tab.D[m][qk] * Fz[c][m];
+      }
+      bC[sidx<Q>(c, qk, b, a)] = s;
+    }
+  __syncthreads();
+  if (a < P) {
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int qk = 0; qk < Q; qk++) {
+        T s = T(0);
+#pragma unroll
+        for (int qi = 0; qi < Q; qi++) s += tab.B[qi][a] * bC[sidx<Q>(c, qk, b, qi)];
+        bA[sidx<Q>(c, qk, b, a)] = s;
+      }
+  }
+  __syncthreads();
+  if (a < P && b < P) {
+    T w[3][Q];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int qk = 0; qk < Q; qk++) {
+        T s = T(0);
+#pragma unroll
+        for (int qj = 0; qj < Q; qj++) s += tab.B[qj][b] * bA[sidx<Q>(c, qk, qj, a)];
+        w[c][qk] = s;
+      }
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int k = 0; k < P; k++) {
+        T s = T(0);
+#pragma unroll
+        for (int qk = 0; qk < Q; qk++) s += tab.B[qk][k] * w[c][qk];
+        out[c][k] = s;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Jacobian action
+// ---------------------------------------------------------------------------
+template <int P, int Q, typename T, int LAYOUT>
+__global__ void __launch_bounds__(Q* Q* epb_for(Q))
+    k_jacobian_apply(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
+                     const T* __restrict__ qd, int64_t qstride, const KTab<P, Q, T> tab, const T* __restrict__ du,
+                     T* __restrict__ y) {
+  constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int t = threadIdx.x;
+  const int el = t / Q2, col = t - el * Q2;
+  const int a = col % Q, b = col / Q;
+  const int64_t e = (int64_t)blockIdx.x * EPB + el;
+  const bool live = e < ne;
+  T* bA = sm + el * 9 * Q3;
+  T* bB = bA + 3 * Q3;
+  T* bC = bB + 3 * Q3;
+
+  T U[3][Q];
+  int nid[P];
+  gather_interp<P, Q, T, true>(live, e, a, b, emap, bc, du, tab, bA, bB, bC, U, nid);
+  __syncthreads();
+  T Fz[3][Q];
+  const T* qe = qd + (live ? e : 0) * Q3 + b * Q + a;
+#pragma unroll
+  for (int qk = 0; qk < Q; qk++) {
+    T g[3][3], f[3][3];
+    colloc_grad<P, Q, T>(a, b, qk, tab, bC, U, g);
+    if (live) {
+      pointwise<LAYOUT, T>(qe + qk * Q2, qstride, g, f);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; i++) f[i / 3][i % 3] = T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      bA[sidx<Q>(c, qk, b, a)] = f[c][0];
+      bB[sidx<Q>(c, qk, b, a)] = f[c][1];
+      Fz[c][qk] = f[c][2];
+    }
+  }
+  __syncthreads();
+  T out[3][P];
+  transpose_to_nodes<P, Q, T>(a, b, tab, bA, bB, bC, Fz, out);
+  if (live && a < P && b < P) {
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+      const int n = nid[k];
+      const unsigned m = __ldg(&bc[n]);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const int64_t dof = 3 * (int64_t)n + c;
+        if ((m >> c) & 1u)
+          y[dof] = du[dof];  // identity row; every writer stores the same value
+        else
+          atomicAdd(&y[dof], out[c][k]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Quadrature-data setup and residual (FP64).  Gradients of the node
+// coordinates X (isoparametric geometry) and of u at each point give
+// dX/dxi, W = w det(dX/dxi), H = grad_X u, F = I + H, J - 1 from the invariants
+// of H (log J = log1p(J - 1) without cancellation), Green-Euler strain
+// e = (H + H^T + H H^T)/2, Kirchhoff stress tau = 2 mu e + lambda log J I
+// (Eq. Kirchhoff-stress) and grad_x xi = grad_X xi F^-1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double det3(const double (&A)[3][3]) {
+  return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+         A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+// inverse via the adjugate; returns det
+__device__ __forceinline__ double inv3(const double (&A)[3][3], double (&Ai)[3][3]) {
+  const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+  const double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+  const double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+  const double det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+  const double id = 1.0 / det;
+  Ai[0][0] = c00 * id;
+  Ai[1][0] = c01 * id;
+  Ai[2][0] = c02 * id;
+  Ai[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * id;
+  Ai[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * id;
+  Ai[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * id;
+  Ai[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * id;
+  Ai[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id;
+  Ai[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id;
+  return det;
+}
+
+template <int P, int Q>
+struct SetupTab {
+  KTab<P, Q, double> k;
+  double w[Q];
+};
+
+template <int P, int Q, int LAYOUT>
+__global__ void __launch_bounds__(Q* Q* epb_for(Q))
+    k_setup(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
+            const double* __restrict__ coords, const double* __restrict__ u, const double* __restrict__ lamv,
+            const double* __restrict__ muv, const SetupTab<P, Q> st, double* __restrict__ qd, int64_t qstride,
+            int store, int resid, const double* __restrict__ gbc, double* __restrict__ r,
+            unsigned long long* __restrict__ minj) {
+  constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sm = reinterpret_cast<double*>(smraw);
+  const int t = threadIdx.x;
+  const int el = t / Q2, col = t - el * Q2;
+  const int a = col % Q, b = col / Q;
+  const int64_t e = (int64_t)blockIdx.x * EPB + el;
+  const bool live = e < ne;
+  double* bA = sm + el * 12 * Q3;
+  double* bB = bA + 3 * Q3;
+  double* bX = bB + 3 * Q3;
+  double* bU = bX + 3 * Q3;
+  const KTab<P, Q, double>& tab = st.k;
+
+  double UX[3][Q], UU[3][Q];
+  int nid[P];
+  gather_interp<P, Q, double, false>(live, e, a, b, emap, bc, coords, tab, bA, bB, bX, UX, nid);
+  __syncthreads();
+  gather_interp<P, Q, double, false>(live, e, a, b, emap, bc, u, tab, bA, bB, bU, UU, nid);
+  __syncthreads();
+
+  const double lam = live ? lamv[e] : 0.0, mu = live ? muv[e] : 0.0;
+  double Fz[3][Q];
+  double jmin = 1e300;
+  for (int qk = 0; qk < Q; qk++) {
+    double gX[3][3], gU[3][3];
+    colloc_grad<P, Q, double>(a, b, qk, tab, bX, UX, gX);
+    colloc_grad<P, Q, double>(a, b, qk, tab, bU, UU, gU);
+    double f[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (live) {
+      double R[3][3];  // grad_X xi
+      const double detx = inv3(gX, R);
+      const double W = st.w[a] * st.w[b] * st.w[qk] * detx;
+      double H[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int K = 0; K < 3; K++) H[c][K] = gU[c][0] * R[0][K] + gU[c][1] * R[1][K] + gU[c][2] * R[2][K];
+      const double trH = H[0][0] + H[1][1] + H[2][2];
+      double trH2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) trH2 += H[i][j] * H[j][i];
+      const double Jm1 = trH + 0.5 * (trH * trH - trH2) + det3(H);
+      const double J = 1.0 + Jm1;
+      // a NaN J or an inverted geometry counts as inverted
+      jmin = fmin(jmin, (J > 0.0 && detx > 0.0) ? J : (J <= 0.0 ? J : -1.0));
+      const double logJ = log1p(Jm1);
+      double Fm[3][3], Fi[3][3];
+#pragma unroll
+      for (int i = 0; i < 9; i++) Fm[i / 3][i % 3] = H[i / 3][i % 3] + (i % 4 == 0 ? 1.0 : 0.0);
+      inv3(Fm, Fi);
+      double tau[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          const double hh = H[i][0] * H[j][0] + H[i][1] * H[j][1] + H[i][2] * H[j][2];
+          tau[i][j] = mu * (H[i][j] + H[j][i] + hh) + (i == j ? lam * logJ : 0.0);
+        }
+      double X[3][3];  // grad_x xi = grad_X xi F^-1
+#pragma unroll
+      for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) X[d][k] = R[d][0] * Fi[0][k] + R[d][1] * Fi[1][k] + R[d][2] * Fi[2][k];
+      if (store) {
+        double* qp = qd + e * Q3 + qk * Q2 + b * Q + a;
+        if (LAYOUT == NH_LAYOUT_CURRENT) {
+#pragma unroll
+          for (int i = 0; i < 9; i++) qp[i * qstride] = X[i / 3][i % 3];
+          qp[9 * qstride] = W * tau[0][0];
+          qp[10 * qstride] = W * tau[1][1];
+          qp[11 * qstride] = W * tau[2][2];
+          qp[12 * qstride] = W * tau[1][2];
+          qp[13 * qstride] = W * tau[0][2];
+          qp[14 * qstride] = W * tau[0][1];
+          qp[15 * qstride] = W * lam;
+          qp[16 * qstride] = W * (mu - lam * logJ);
+        } else {
+          double Ci[3][3];
+#pragma unroll
+          for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) Ci[i][j] = Fi[i][0] * Fi[j][0] + Fi[i][1] * Fi[j][1] + Fi[i][2] * Fi[j][2];
+#pragma unroll
+          for (int i = 0; i < 9; i++) qp[i * qstride] = R[i / 3][i % 3];
+#pragma unroll
+          for (int i = 0; i < 9; i++) qp[(9 + i) * qstride] = H[i / 3][i % 3];
+          qp[18 * qstride] = Ci[0][0];
+          qp[19 * qstride] = Ci[1][1];
+          qp[20 * qstride] = Ci[2][2];
+          qp[21 * qstride] = Ci[1][2];
+          qp[22 * qstride] = Ci[0][2];
+          qp[23 * qstride] = Ci[0][1];
+          qp[24 * qstride] = W * mu;
+          qp[25 * qstride] = W * lam * logJ;
+          qp[26 * qstride] = W * lam;
+        }
+      }
+      if (resid) {
+        // f1 = W tau (grad_x xi)^T
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+          for (int d = 0; d < 3; d++)
+            f[c][d] = W * (tau[c][0] * X[d][0] + tau[c][1] * X[d][1] + tau[c][2] * X[d][2]);
+      }
+    }
+    if (resid) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        bA[sidx<Q>(c, qk, b, a)] = f[c][0];
+        bB[sidx<Q>(c, qk, b, a)] = f[c][1];
+        Fz[c][qk] = f[c][2];
+      }
+    }
+  }
+  if (minj) {  // block-wide min of det F, one atomic per block
+    __shared__ double red[32];
+    double v = jmin;
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((t & 31) == 0) red[t >> 5] = v;
+    __syncthreads();
+    if (t == 0) {
+      double m = red[0];
+      for (int w = 1; w < (int)((blockDim.x + 31) >> 5); w++) m = fmin(m, red[w]);
+      atomicMin(minj, ordered_bits(m));
+    }
+  }
+  if (!resid) return;  // uniform across the block
+  __syncthreads();
+  double out[3][P];
+  transpose_to_nodes<P, Q, double>(a, b, tab, bA, bB, bX, Fz, out);
+  if (live && a < P && b < P) {
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+      const int n = nid[k];
+      const unsigned m = __ldg(&bc[n]);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const int64_t dof = 3 * (int64_t)n + c;
+        if ((m >> c) & 1u)
+          r[dof] = u[dof] - (gbc ? gbc[dof] : 0.0);
+        else
+          atomicAdd(&r[dof], out[c][k]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal of J.  For component c the pointwise tangent block
+// D^c[d][d'] = d f[c][d] / d g[c][d'] is obtained by applying the pointwise map
+// to the three unit gradients e_c (x) e_d'.  Then
+// diag[c](i,j,k) = sum_q sum_{d,d'} Phi_d Phi_d' D^c[d][d'], Phi_d = B_xi,d[q, node],
+// contracted direction by direction with the elementwise products of the 1-D
+// value/derivative tables (B.B, B.G, G.G).
+// ---------------------------------------------------------------------------
+template <int P, int Q>
+struct DiagTab {
+  double BB[Q][P], BG[Q][P], GG[Q][P];
+};
+
+template <int P, int Q, int LAYOUT, typename TO>
+__global__ void __launch_bounds__(Q* Q* epb_for(Q))
+    k_diagonal(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
+               const double* __restrict__ qd, int64_t qstride, const DiagTab<P, Q> dt, TO* __restrict__ diag) {
+  constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sm = reinterpret_cast<double*>(smraw);
+  const int t = threadIdx.x;
+  const int el = t / Q2, col = t - el * Q2;
+  const int a = col % Q, b = col / Q;
+  const int64_t e = (int64_t)blockIdx.x * EPB + el;
+  const bool live = e < ne;
+  double* Dsm = sm + el * 11 * Q3;  // [9][Q][Q][Q]
+  double* s1 = Dsm + 9 * Q3;        // [P][Q][Q]
+  double* s2 = s1 + Q3;             // [P][P][Q]
+  const double* qe = qd + (live ? e : 0) * Q3 + b * Q + a;
+
+  for (int c = 0; c < 3; c++) {
+    for (int qk = 0; qk < Q; qk++) {
+#pragma unroll
+      for (int dp = 0; dp < 3; dp++) {
+        double g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, f[3][3];
+        g[c][dp] = 1.0;
+        if (live) {
+          pointwise<LAYOUT, double>(qe + qk * Q2, qstride, g, f);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.0;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) Dsm[((d * 3 + dp) * Q + qk) * Q2 + b * Q + a] = f[c][d];
+      }
+    }
+    __syncthreads();
+    double acc[P];
+#pragma unroll
+    for (int k = 0; k < P; k++) acc[k] = 0.0;
+#pragma unroll
+    for (int pr = 0; pr < 9; pr++) {
+      const int d = pr / 3, dp = pr % 3;
+      const double(*Mx)[P] = (d == 0 && dp == 0) ? dt.GG : ((d == 0 || dp == 0) ? dt.BG : dt.BB);
+      const double(*My)[P] = (d == 1 && dp == 1) ? dt.GG : ((d == 1 || dp == 1) ? dt.BG : dt.BB);
+      const double(*Mz)[P] = (d == 2 && dp == 2) ? dt.GG : ((d == 2 || dp == 2) ? dt.BG : dt.BB);
+      const double* F = Dsm + pr * Q3;
+      // z: thread (qi=a, qj=b)
+#pragma unroll
+      for (int k = 0; k < P; k++) {
+        double s = 0.0;
+#pragma unroll
+        for (int qk = 0; qk < Q; qk++) s += Mz[qk][k] * F[qk * Q2 + b * Q + a];
+        s1[(k * Q + b) * Q + a] = s;
+      }
+      __syncthreads();
+      // y: thread (qi=a, j=b<P)
+      if (b < P) {
+#pragma unroll
+        for (int k = 0; k < P; k++) {
+          double s = 0.0;
+#pragma unroll
+          for (int qj = 0; qj < Q; qj++) s += My[qj][b] * s1[(k * Q + qj) * Q + a];
+          s2[(k * P + b) * Q + a] = s;
+        }
+      }
+      __syncthreads();
+      // x: thread (i=a<P, j=b<P)
+      if (a < P && b < P) {
+#pragma unroll
+        for (int k = 0; k < P; k++) {
+          double s = 0.0;
+#pragma unroll
+          for (int qi = 0; qi < Q; qi++) s += Mx[qi][a] * s2[(k * P + b) * Q + qi];
+          acc[k] += s;
+        }
+      }
+    }
+    if (live && a < P && b < P) {
+#pragma unroll
+      for (int k = 0; k < P; k++) {
+        const int n = __ldg(&emap[e * P3 + (k * P + b) * P + a]);
+        const unsigned m = __ldg(&bc[n]);
+        const int64_t dof = 3 * (int64_t)n + c;
+        if ((m >> c) & 1u)
+          diag[dof] = TO(1);
+        else
+          atomicAdd(&diag[dof], TO(acc[k]));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+// Raise the dynamic shared-memory limit of one kernel, once per device.
+template <auto Kern>
+cudaError_t prep(size_t smem) {
+  static unsigned long long done = 0ull;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done & bit)) {
+    e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    done |= bit;
+  }
+  return cudaSuccess;
+}
+
+template <int P, int Q, typename T, int LAYOUT>
+cudaError_t apply_launch(const OpArgs& A, cudaStream_t s) {
+  constexpr int EPB = epb_for(Q), Q3 = Q * Q * Q;
+  const int threads = Q * Q * EPB;
+  const int64_t blocks = (A.ne + EPB - 1) / EPB;
+  if (blocks == 0) return cudaSuccess;
+  const size_t smem = (size_t)EPB * 9 * Q3 * sizeof(T);
+  const KTab<P, Q, T> tab = make_ktab<P, Q, T>(*A.tab);
+  cudaError_t e = prep<k_jacobian_apply<P, Q, T, LAYOUT>>(smem);
+  if (e != cudaSuccess) return e;
+  k_jacobian_apply<P, Q, T, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
+      A.ne, A.emap, A.bc, (const T*)A.qd, A.qstride, tab, (const T*)A.in, (T*)A.out);
+  return cudaGetLastError();
+}
+
+template <int P, int Q>
+cudaError_t apply_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
+  if (prec == NH_F64)
+    return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, double, NH_LAYOUT_CURRENT>(A, s)
+                                         : apply_launch<P, Q, double, NH_LAYOUT_INITIAL>(A, s);
+  return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, float, NH_LAYOUT_CURRENT>(A, s)
+                                       : apply_launch<P, Q, float, NH_LAYOUT_INITIAL>(A, s);
+}
+
+template <int P, int Q, int LAYOUT>
+cudaError_t setup_launch(const OpArgs& A, cudaStream_t s) {
+  constexpr int EPB = epb_for(Q), Q3 = Q * Q * Q;
+  const int threads = Q * Q * EPB;
+  const int64_t blocks = (A.ne + EPB - 1) / EPB;
+  if (blocks == 0) return cudaSuccess;
+  const size_t smem = (size_t)EPB * 12 * Q3 * sizeof(double);
+  SetupTab<P, Q> st;
+  st.k = make_ktab<P, Q, double>(*A.tab);
+  for (int i = 0; i < Q; i++) st.w[i] = A.tab->w[i];
+  cudaError_t e = prep<k_setup<P, Q, LAYOUT>>(smem);
+  if (e != cudaSuccess) return e;
+  k_setup<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(A.ne, A.emap, A.bc, A.coords, (const double*)A.in,
+                                                                A.lam, A.mu, st, A.qd_out, A.qstride, A.store,
+                                                                A.resid, A.gbc, (double*)A.out, A.minj);
+  return cudaGetLastError();
+}
+
+template <int P, int Q>
+cudaError_t setup_pq(const OpArgs& A, cudaStream_t s) {
+  return A.layout == NH_LAYOUT_CURRENT ? setup_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
+                                       : setup_launch<P, Q, NH_LAYOUT_INITIAL>(A, s);
+}
+
+template <int P, int Q, int LAYOUT, typename TO>
+cudaError_t diag_launch(const OpArgs& A, cudaStream_t s) {
+  constexpr int EPB = epb_for(Q), Q3 = Q * Q * Q;
+  const int threads = Q * Q * EPB;
+  const int64_t blocks = (A.ne + EPB - 1) / EPB;
+  if (blocks == 0) return cudaSuccess;
+  const size_t smem = (size_t)EPB * 11 * Q3 * sizeof(double);
+  DiagTab<P, Q> dt;
+  for (int i = 0; i < Q; i++)
+    for (int j = 0; j < P; j++) {
+      dt.BB[i][j] = A.tab->B[i][j] * A.tab->B[i][j];
+      dt.BG[i][j] = A.tab->B[i][j] * A.tab->G[i][j];
+      dt.GG[i][j] = A.tab->G[i][j] * A.tab->G[i][j];
+    }
+  cudaError_t e = prep<k_diagonal<P, Q, LAYOUT, TO>>(smem);
+  if (e != cudaSuccess) return e;
+  k_diagonal<P, Q, LAYOUT, TO><<<(unsigned)blocks, threads, smem, s>>>(A.ne, A.emap, A.bc, (const double*)A.qd,
+                                                                       A.qstride, dt, (TO*)A.out);
+  return cudaGetLastError();
+}
+
+template <int P, int Q>
+cudaError_t diag_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
+  if (A.layout == NH_LAYOUT_CURRENT)
+    return prec == NH_F64 ? diag_launch<P, Q, NH_LAYOUT_CURRENT, double>(A, s)
+                          : diag_launch<P, Q, NH_LAYOUT_CURRENT, float>(A, s);
+  return prec == NH_F64 ? diag_launch<P, Q, NH_LAYOUT_INITIAL, double>(A, s)
+                        : diag_launch<P, Q, NH_LAYOUT_INITIAL, float>(A, s);
+}
+
+}  // namespace
+
+#define NH_CAT2(a, b) a##b
+#define NH_CAT(a, b) NH_CAT2(a, b)
+#define PI NH_P_INST
+// Q >= P always holds in the instantiated set: out-of-range cases are never taken.
+#define QQ(v) ((v) < PI ? PI : (v))
+
+#define NH_QCASES(FN, ...)                                      \
+  switch (Q) {                                                  \
+    case 2: if (PI <= 2) return FN<PI, QQ(2)>(__VA_ARGS__); break; \
+    case 3: if (PI <= 3) return FN<PI, QQ(3)>(__VA_ARGS__); break; \
+    case 4: if (PI <= 4) return FN<PI, QQ(4)>(__VA_ARGS__); break; \
+    case 5: if (PI <= 5) return FN<PI, QQ(5)>(__VA_ARGS__); break; \
+    case 6: return FN<PI, 6>(__VA_ARGS__);                      \
+    default: break;                                             \
+  }                                                             \
+  return cudaErrorInvalidValue;
+
+cudaError_t NH_CAT(nh_launch_apply_P, NH_P_INST)(int Q, nh_prec prec, const OpArgs& a, cudaStream_t s) {
+  NH_QCASES(apply_pq, prec, a, s)
+}
+cudaError_t NH_CAT(nh_launch_setup_P, NH_P_INST)(int Q, const OpArgs& a, cudaStream_t s) {
+  NH_QCASES(setup_pq, a, s)
+}
+cudaError_t NH_CAT(nh_launch_diag_P, NH_P_INST)(int Q, const OpArgs& a, cudaStream_t s) {
+  NH_QCASES(diag_pq, (nh_prec)a.prec, a, s)
+}

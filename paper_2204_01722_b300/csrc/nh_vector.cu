@@ -1,0 +1,70 @@
+// Vector kernels: deterministic FP64 dot products (fixed grid, per-block
+// partial sums, then one fixed-order pass, so results do not depend on timing)
+// and precision conversion.
+#include "nh_internal.cuh"
+
+namespace {
+
+constexpr int kDotThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+    v = warp_sum(v);
+  }
+  return v;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kDotThreads)
+    k_dot_partials(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                   double* __restrict__ partials) {
+  double s = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) s = fma(x[i], y[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ p, int nb, double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += p[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (float)x[i];
+}
+
+}  // namespace
+
+cudaError_t nh_launch_dot_partials(int64_t n, const double* x, const double* y, double* partials, int nblocks,
+                                   cudaStream_t s) {
+  k_dot_partials<<<nblocks, kDotThreads, 0, s>>>(n, x, y, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t nh_launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s) {
+  k_sum_partials<<<1, 1024, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t nh_launch_f64_to_f32(int64_t n, const double* x, float* y, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  if (blocks < 1) blocks = 1;
+  k_f64_to_f32<<<(unsigned)blocks, 256, 0, s>>>(n, x, y);
+  return cudaGetLastError();
+}

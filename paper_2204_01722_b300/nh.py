@@ -1,0 +1,214 @@
+"""Thin Python binding of the nh C ABI (include/nh.h).
+
+Argument marshalling only: every call goes straight to libnh.so and every
+step of the computation runs in its CUDA kernels.  Function names match the
+C entry points; each takes the context first (for error text) where the C
+call does not.  Vectors are torch CUDA tensors (or raw device addresses as
+ints); host arrays are numpy arrays.  A missing or unloadable libnh.so raises
+ImportError -- there is no fallback path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnh.so")
+
+NH_OK, NH_ERR_ARG, NH_ERR_CUDA, NH_ERR_OOM, NH_ERR_INVERTED = 0, 1, 2, 3, 4
+NH_ERR_NOT_CONVERGED, NH_ERR_NAN, NH_ERR_TIMEOUT, NH_ERR_STATE, NH_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
+STATUS_NAMES = {0: "NH_OK", 1: "NH_ERR_ARG", 2: "NH_ERR_CUDA", 3: "NH_ERR_OOM", 4: "NH_ERR_INVERTED",
+                5: "NH_ERR_NOT_CONVERGED", 6: "NH_ERR_NAN", 7: "NH_ERR_TIMEOUT", 8: "NH_ERR_STATE",
+                9: "NH_ERR_UNSUPPORTED"}
+NH_F64, NH_F32 = 0, 1
+NH_LAYOUT_CURRENT, NH_LAYOUT_INITIAL = 0, 1
+
+_vp = C.c_void_p
+_i64 = C.c_int64
+_st = C.c_int
+
+# name -> (restype, argtypes); every symbol here is declared in include/nh.h
+SIGNATURES = {
+    "nh_create": (_st, [C.POINTER(_vp), C.c_int, _vp]),
+    "nh_destroy": (_st, [_vp]),
+    "nh_last_error": (C.c_char_p, [_vp]),
+    "nh_sync": (_st, [_vp]),
+    "nh_launch_count": (_i64, [_vp]),
+    "nh_space_box": (_st, [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(_vp),
+                           C.POINTER(_i64), C.POINTER(_i64)]),
+    "nh_space_coords": (_st, [_vp, _vp]),
+    "nh_space_set_dirichlet": (_st, [_vp, _vp]),
+    "nh_space_destroy": (_st, [_vp]),
+    "nh_op_create": (_st, [_vp, C.c_double, _vp, C.c_double, C.c_int, C.POINTER(_vp)]),
+    "nh_op_level": (_st, [_vp, _vp, C.POINTER(_vp)]),
+    "nh_op_destroy": (_st, [_vp]),
+    "nh_op_info": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_i64)]),
+    "nh_qdata_setup": (_st, [_vp, _vp, C.POINTER(C.c_double)]),
+    "nh_residual": (_st, [_vp, _vp, _vp, _vp]),
+    "nh_jacobian_apply": (_st, [_vp, C.c_int, _vp, _vp]),
+    "nh_jacobian_apply_host": (_st, [_vp, C.c_int, _vp, _vp]),
+    "nh_jacobian_diagonal": (_st, [_vp, C.c_int, _vp]),
+    "nh_prolong": (_st, [_vp, _vp, C.c_int, _vp, _vp]),
+    "nh_restrict": (_st, [_vp, _vp, C.c_int, _vp, _vp]),
+    "nh_dot": (_st, [_vp, _i64, _vp, _vp, C.POINTER(C.c_double)]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2204_01722_b300.build`")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class NhError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check(st, ctx):
+    if st != NH_OK:
+        msg = lib.nh_last_error(ctx).decode() if ctx else ""
+        raise NhError(st, msg)
+
+
+def _prec_of(t):
+    dt = str(getattr(t, "dtype", ""))
+    if dt in ("torch.float64", "float64"):
+        return NH_F64
+    if dt in ("torch.float32", "float32"):
+        return NH_F32
+    raise TypeError("vectors must be float64 or float32")
+
+
+# ---- same-name wrappers ----------------------------------------------------------
+
+def nh_create(device=0, stream=None):
+    h = _vp()
+    _check(lib.nh_create(C.byref(h), device, stream), None)
+    return h.value
+
+
+def nh_destroy(ctx):
+    _check(lib.nh_destroy(ctx), None)
+
+
+def nh_last_error(ctx):
+    return lib.nh_last_error(ctx).decode()
+
+
+def nh_sync(ctx):
+    _check(lib.nh_sync(ctx), ctx)
+
+
+def nh_launch_count(ctx):
+    return int(lib.nh_launch_count(ctx))
+
+
+def nh_space_box(ctx, nx, ny, nz, vertices, p, q):
+    """Returns (space, n_nodes, n_dof)."""
+    h = _vp()
+    nn, nd = _i64(), _i64()
+    V = None if vertices is None else np.ascontiguousarray(vertices, dtype=np.float64)
+    _check(lib.nh_space_box(ctx, nx, ny, nz, _ptr(V), p, q, C.byref(h), C.byref(nn), C.byref(nd)), ctx)
+    return h.value, nn.value, nd.value
+
+
+def nh_space_coords(ctx, space, n_nodes):
+    X = np.empty((n_nodes, 3))
+    _check(lib.nh_space_coords(space, _ptr(X)), ctx)
+    return X
+
+
+def nh_space_set_dirichlet(ctx, space, mask):
+    m = np.ascontiguousarray(np.asarray(mask).astype(np.uint8))
+    _check(lib.nh_space_set_dirichlet(space, _ptr(m)), ctx)
+
+
+def nh_space_destroy(space):
+    lib.nh_space_destroy(space)
+
+
+def nh_op_create(ctx, space, nu, E_per_elem=None, E=1.0, layout=NH_LAYOUT_CURRENT):
+    h = _vp()
+    Ee = None if E_per_elem is None else np.ascontiguousarray(E_per_elem, dtype=np.float64)
+    _check(lib.nh_op_create(space, nu, _ptr(Ee), E, layout, C.byref(h)), ctx)
+    return h.value
+
+
+def nh_op_level(ctx, fine_op, coarse_space):
+    h = _vp()
+    _check(lib.nh_op_level(fine_op, coarse_space, C.byref(h)), ctx)
+    return h.value
+
+
+def nh_op_destroy(op):
+    lib.nh_op_destroy(op)
+
+
+def nh_op_info(ctx, op, prec=NH_F64):
+    S = C.c_int()
+    b = _i64()
+    _check(lib.nh_op_info(op, prec, C.byref(S), C.byref(b)), ctx)
+    return S.value, b.value
+
+
+def nh_qdata_setup(ctx, op, u):
+    mj = C.c_double()
+    _check(lib.nh_qdata_setup(op, _ptr(u), C.byref(mj)), ctx)
+    return mj.value
+
+
+def nh_residual(ctx, op, u, g_bc, r):
+    _check(lib.nh_residual(op, _ptr(u), _ptr(g_bc), _ptr(r)), ctx)
+
+
+def nh_jacobian_apply(ctx, op, du, y, prec=None):
+    prec = _prec_of(du) if prec is None else prec
+    _check(lib.nh_jacobian_apply(op, prec, _ptr(du), _ptr(y)), ctx)
+
+
+def nh_jacobian_apply_host(ctx, op, du_host, y_host, prec=None):
+    prec = _prec_of(du_host) if prec is None else prec
+    _check(lib.nh_jacobian_apply_host(op, prec, _ptr(du_host), _ptr(y_host)), ctx)
+
+
+def nh_jacobian_diagonal(ctx, op, diag, prec=None):
+    prec = _prec_of(diag) if prec is None else prec
+    _check(lib.nh_jacobian_diagonal(op, prec, _ptr(diag)), ctx)
+
+
+def nh_prolong(ctx, coarse, fine, uc, uf, prec=None):
+    prec = _prec_of(uc) if prec is None else prec
+    _check(lib.nh_prolong(coarse, fine, prec, _ptr(uc), _ptr(uf)), ctx)
+
+
+def nh_restrict(ctx, fine, coarse, rf, rc, prec=None):
+    prec = _prec_of(rf) if prec is None else prec
+    _check(lib.nh_restrict(fine, coarse, prec, _ptr(rf), _ptr(rc)), ctx)
+
+
+def nh_dot(ctx, n, x, y):
+    r = C.c_double()
+    _check(lib.nh_dot(ctx, n, _ptr(x), _ptr(y), C.byref(r)), ctx)
+    return r.value
