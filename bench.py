@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Jacobian-apply throughput of matrix-free Neo-Hookean hyperelasticity on B300.
+
+One step = one Jacobian action y = J du (gather, sum-factorised collocated
+gradient, pointwise linearised stress from stored quadrature data, transposed
+contractions, atomic scatter, Dirichlet rows) through the C ABI call
+nh_jacobian_apply.  Default workload: Q3 (q = 4 Gauss points) on 48^3
+hexahedra of the unit cube, 9,145,875 DoF, FP64, 17 stored scalars per point.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nh|reference]
+
+Prints ONE JSON line (rank 0).  N > 1 (torchrun) runs independent replicas,
+one per GPU: the operator has no exchange step on a single-GPU mesh, so the
+job value is the sum of all ranks' DoF over the slowest rank's time.
+The reference arm (--impl reference) times the plain FP64 CPU oracle on a
+bounded window of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jacobian apply GDoF/s Q2–Q4; solve time to rel. residual 1e-8, plain vs chosen"
+NU = 0.3
+PERTURB = 0.1
+AMP = 0.05
+SEED = 42
+# FP64 pipe of a B300: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+# FP32 pipe: 148 SMs x 128 FFMA/clk x 2 flop x 2.032 GHz
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+DEFAULT_N = {2: 74, 3: 48, 4: 37}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def n_dof_of(p, n):
+    return 3 * (p * n + 1) ** 3
+
+
+def apply_bytes(p, n, wbytes, S=17):
+    """Algorithmic bytes of one apply: stored quadrature data, du read, y written,
+    int32 element map, one Dirichlet-bit byte per node."""
+    P, Q = p + 1, p + 1
+    ne = n ** 3
+    nn = (p * n + 1) ** 3
+    return ne * Q ** 3 * S * wbytes + 2 * 3 * nn * wbytes + ne * P ** 3 * 4 + nn
+
+
+def apply_flops(p, n):
+    """Algorithmic flops of one apply with sum factorisation and the collocated
+    gradient: interpolation and its transpose 3 (P^3 Q + P^2 Q^2 + P Q^3) FMA each,
+    gradient and its transpose 9 Q^4 FMA each, 168 flops pointwise per point."""
+    P, Q = p + 1, p + 1
+    fma = 6 * (P ** 3 * Q + P ** 2 * Q ** 2 + P * Q ** 3) + 18 * Q ** 4
+    return n ** 3 * (2 * fma + 168 * Q ** 3)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-i", str(gpu_index)],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the library arm
+# ---------------------------------------------------------------------------
+class Case:
+    def __init__(self, nh, torch, ctx, p, n, layout=0):
+        self.nh, self.ctx, self.p, self.n = nh, ctx, p, n
+        from paper_2204_01722_b300 import inputs
+        V = inputs.box_vertices(n, n, n, perturb=PERTURB, seed=SEED)
+        self.space, self.nn, self.nd = nh.nh_space_box(ctx, n, n, n, V, p, p + 1)
+        N = p * n + 1
+        nh.nh_space_set_dirichlet(ctx, self.space, inputs.uniaxial_mask((N, N, N)))
+        self.op = nh.nh_op_create(ctx, self.space, NU, None, 1.0, layout)
+        X = nh.nh_space_coords(ctx, self.space, self.nn)
+        u = inputs.smooth_field(X, AMP, seed=SEED + 1).ravel()
+        self.minJ = nh.nh_qdata_setup(ctx, self.op, torch.from_numpy(u).cuda())
+        self.du64 = torch.from_numpy(inputs.normal_vector(self.nd, seed=SEED + 2)).cuda()
+        self.du32 = self.du64.float()
+        self.y64 = torch.empty_like(self.du64)
+        self.y32 = torch.empty_like(self.du32)
+
+    def vecs(self, prec):
+        return (self.du64, self.y64) if prec == "f64" else (self.du32, self.y32)
+
+    def close(self):
+        self.nh.nh_op_destroy(self.op)
+        self.nh.nh_space_destroy(self.space)
+
+
+def time_applies(nh, torch, ctx, stream, case, prec, steps, warmup, barrier):
+    du, y = case.vecs(prec)
+    for _ in range(warmup):
+        nh.nh_jacobian_apply(ctx, case.op, du, y)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = nh.nh_launch_count(ctx)
+    e0.record(stream)
+    for _ in range(steps):
+        nh.nh_jacobian_apply(ctx, case.op, du, y)
+    e1.record(stream)
+    e1.synchronize()
+    launches = nh.nh_launch_count(ctx) - l0
+    barrier()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), launches
+
+
+def kernel_ms(nh, ctx, case, prec, steps):
+    du, y = case.vecs(prec)
+    nh.nh_profile_read(ctx)
+    nh.nh_profile_enable(ctx, True)
+    for _ in range(steps):
+        nh.nh_jacobian_apply(ctx, case.op, du, y)
+    tot, k = nh.nh_profile_read(ctx)
+    nh.nh_profile_enable(ctx, False)
+    return tot / max(k, 1)
+
+
+def run_nh(args):
+    import torch
+    from paper_2204_01722_b300 import nh
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.Stream()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gpu_index = vis.split(",")[local] if vis and vis.split(",")[local].strip().isdigit() else str(local)
+    out = {}
+    with torch.cuda.stream(stream):
+        ctx = nh.nh_create(local, stream.cuda_stream)
+        p, n = args.p, args.n
+        case = Case(nh, torch, ctx, p, n)
+        clocks = ClockSampler(gpu_index)
+        ms, launches = time_applies(nh, torch, ctx, stream, case, args.prec, args.steps, args.warmup, barrier)
+        clk = clocks.stop()
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        value = world * case.nd * args.steps / (ms_max * 1e-3) / 1e9
+        # roofline of the apply kernel alone (CUDA events around each launch)
+        kms = kernel_ms(nh, ctx, case, args.prec, args.steps)
+        hbm, hbm_src = peaks()
+        wb = 8 if args.prec == "f64" else 4
+        S, _ = nh.nh_op_info(ctx, case.op)
+        if args.prec == "f64":
+            ach = apply_flops(p, n) / (kms * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": args.traffic,
+                    "peak_source": "FP64 pipe: 148 SM x 2 DFMA/clk x 2.032 GHz (unit count x max clock)",
+                    "kernel_ms": round(kms, 4), "hbm_frac": round(apply_bytes(p, n, wb, S) / (kms * 1e-3) / 1e9 / hbm, 4)}
+        else:
+            ach = apply_bytes(p, n, wb, S) / (kms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(ach / hbm, 4), "traffic": args.traffic, "peak_source": hbm_src + " (copy)",
+                    "kernel_ms": round(kms, 4)}
+        # end to end through the host-buffer entry point
+        dt = np.float64 if args.prec == "f64" else np.float32
+        hin = torch.from_numpy(np.ascontiguousarray(case.vecs(args.prec)[0].cpu().numpy())).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        for _ in range(2):
+            nh.nh_jacobian_apply_host(ctx, case.op, hin, hout)
+        ek = max(3, args.steps // 10)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ek):
+            nh.nh_jacobian_apply_host(ctx, case.op, hin, hout)
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": round(world * case.nd * ek / float(tt.item()) / 1e9, 4), "unit": "GDoF/s",
+               "h2d_bytes_per_step": int(case.nd * np.dtype(dt).itemsize),
+               "d2h_bytes_per_step": int(case.nd * np.dtype(dt).itemsize),
+               "entry_point": "nh_jacobian_apply_host (pinned host du, y)"}
+        minJ = case.minJ
+        nd = case.nd
+        case.close()
+        sweep = []
+        if args.sweep and rank == 0:
+            for sp_ in (2, 3, 4):
+                c = Case(nh, torch, ctx, sp_, DEFAULT_N[sp_])
+                Sx, _ = nh.nh_op_info(ctx, c.op)
+                for pr in ("f64", "f32"):
+                    k = kernel_ms(nh, ctx, c, pr, 5)  # warm (FP32 copy of the qdata on first use)
+                    k = kernel_ms(nh, ctx, c, pr, 20)
+                    w_ = 8 if pr == "f64" else 4
+                    gbs = apply_bytes(sp_, c.n, w_, Sx) / (k * 1e-3) / 1e9
+                    tfl = apply_flops(sp_, c.n) / (k * 1e-3) / 1e12
+                    sweep.append({"p": sp_, "n": c.n, "n_dof": c.nd, "prec": pr,
+                                  "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4),
+                                  "algorithmic_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                                  "tflops": round(tfl, 3),
+                                  "alu_frac": round(tfl / (FP64_PEAK_TFLOPS if pr == "f64" else FP32_PEAK_TFLOPS), 4)})
+                c.close()
+        nh.nh_destroy(ctx)
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 4), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+               "config": {"workload": f"Jacobian apply, Q{p} (q={p + 1}) on {n}^3 hexahedra of the unit cube, "
+                                      f"{nd} DoF, vertices perturbed 10% h, smooth displacement amplitude 0.05, "
+                                      f"du ~ N(0,1), x=0 clamped + x=1 normal component fixed",
+                          "p": p, "q": p + 1, "elements": n ** 3, "n_dof": nd, "layout": "current (17 scalars/point)",
+                          "min_det_F": minJ, "l2": "inputs larger than L2 (quadrature data %.2f GB)"
+                                                   % (n ** 3 * (p + 1) ** 3 * S * wb / 1e9),
+                          "parallelism": f"replicas x{world}"},
+               "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+        if args.cpu_baseline:
+            out["cpu_baseline"] = oracle_baseline(p, n, args.cpu_seconds)
+        if sweep:
+            out["sweep"] = sweep
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# oracle arm (CPU baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_baseline(p, n, seconds, w=8):
+    """Time the plain FP64 oracle's Jacobian apply on a w^3-element window of the
+    same workload (same p, q, material, perturbed mesh, displacement recipe)."""
+    from oracle import fem
+    from paper_2204_01722_b300 import inputs
+    V = inputs.box_vertices(n, n, n, perturb=PERTURB, seed=SEED).reshape(n + 1, n + 1, n + 1, 3)
+    x0 = (n - w) // 2
+    sub = V[x0:x0 + w + 1, x0:x0 + w + 1, x0:x0 + w + 1].reshape(-1, 3)
+    sp = fem.Space(w, w, w, sub, p, p + 1)
+    mat = fem.Material(1.0, NU, sp.ne)
+    u = inputs.smooth_field(sp.node_coords(), AMP, seed=SEED + 1).ravel()
+    st = fem.qp_state(sp, mat, u)
+    du = inputs.normal_vector(sp.n_dof, seed=SEED + 2)
+    mask = np.zeros(sp.n_dof, dtype=bool)
+    fem.jacobian_apply(sp, st, du, mask)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        fem.jacobian_apply(sp, st, du, mask)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": round(sp.n_dof * reps / el / 1e9, 6), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} FP64 oracle applies on a {w}^3-element window (Q{p}, {sp.n_dof} DoF) of the "
+                      f"{n}^3 workload, {el:.1f} s, single-threaded numpy"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per = max(1.0, args.cpu_seconds / max(args.steps, 1))
+    vals = []
+    base = None
+    for _ in range(args.warmup):
+        oracle_baseline(args.p, args.n, 0.0)
+    for _ in range(args.steps):
+        base = oracle_baseline(args.p, args.n, per)
+        vals.append(base["value"])
+    v = statistics.median(vals)
+    nd = n_dof_of(args.p, args.n)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(nd / (v * 1e9) * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"Jacobian apply, Q{args.p} (q={args.p + 1}) on {args.n}^3 hexahedra "
+                                  f"(oracle timed on a window)", "p": args.p, "n_dof": nd},
+           "cpu_baseline": dict(base, value=v),
+           "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="nh", choices=["nh", "reference"])
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per apply from an ncu capture of this kernel (reported as is)")
+    args = ap.parse_args()
+    args.n = args.n or DEFAULT_N[args.p]
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_nh(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -154,6 +154,15 @@ nh_status nh_prolong(nh_space coarse, nh_space fine, nh_prec prec, const void* u
 /* rc = P^T rf (restriction = prolongation transposed, Sec. III-B). */
 nh_status nh_restrict(nh_space fine, nh_space coarse, nh_prec prec, const void* rf, void* rc);
 
+/* ---- kernel timing ----------------------------------------------------- */
+
+/* When on, every Jacobian-apply kernel launch on this context is bracketed by
+ * CUDA events on the context stream (up to 65536 launches are kept). */
+nh_status nh_profile_enable(nh_ctx ctx, int on);
+/* Total device time (ms) and number of Jacobian-apply kernels recorded since
+ * the last read; clears the record.  Synchronises. */
+nh_status nh_profile_read(nh_ctx ctx, double* total_ms, int64_t* launches);
+
 /* ---- vector kernels --------------------------------------------------- */
 
 /* Deterministic FP64 dot product of two device double vectors of length n

@@ -63,6 +63,7 @@ cudaError_t nh_launch_diag(int P, int Q, const OpArgs& a, cudaStream_t s) {
 // context
 // ---------------------------------------------------------------------------
 static const int kRedBlocks = 148 * 8;
+static const size_t kMaxProfEvents = 2 * 65536;
 
 extern "C" nh_status nh_create(nh_ctx* out, int device, void* cuda_stream) {
   if (!out) return NH_ERR_ARG;
@@ -99,6 +100,7 @@ extern "C" nh_status nh_destroy(nh_ctx c) {
   if (!c) return NH_ERR_ARG;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
   cudaFree(c->red);
   cudaFree(c->minj);
   cudaFreeHost(c->red_host);
@@ -428,8 +430,42 @@ extern "C" nh_status nh_jacobian_apply(nh_op op, nh_prec prec, const void* du, v
   a.qd = prec == NH_F64 ? (const void*)root->qd : (const void*)root->qd_f;
   const size_t w = prec == NH_F64 ? 8 : 4;
   NH_CUDA(ctx, cudaMemsetAsync(y, 0, w * op->space->n_dof, ctx->stream));
+  cudaEvent_t* ev = nullptr;
+  if (ctx->prof_on && ctx->ev_used + 2 <= kMaxProfEvents) {
+    while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+      cudaEvent_t e;
+      NH_CUDA(ctx, cudaEventCreate(&e));
+      ctx->ev_pool.push_back(e);
+    }
+    ev = &ctx->ev_pool[ctx->ev_used];
+    ctx->ev_used += 2;
+    NH_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
+  }
   NH_CUDA(ctx, nh_launch_apply(op->space->P, op->space->Q, prec, a, ctx->stream));
+  if (ev) NH_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
   ctx->launches++;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_profile_enable(nh_ctx ctx, int on) {
+  if (!ctx) return NH_ERR_ARG;
+  ctx->prof_on = on != 0;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_profile_read(nh_ctx ctx, double* total_ms, int64_t* launches) {
+  if (!ctx) return NH_ERR_ARG;
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    float ms = 0.f;
+    NH_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = (int64_t)(ctx->ev_used / 2);
+  ctx->ev_used = 0;
   return NH_OK;
 }
 

@@ -59,6 +59,10 @@ struct nh_ctx_s {
   size_t red_len = 0;
   double* red_host = nullptr;          // pinned
   unsigned long long* minj = nullptr;  // ordered-bits min of det F
+  // kernel timing (nh_profile_*)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;   // 2 per recorded launch
+  size_t ev_used = 0;
 };
 
 struct nh_space_s {

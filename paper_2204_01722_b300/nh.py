@@ -51,6 +51,8 @@ SIGNATURES = {
     "nh_prolong": (_st, [_vp, _vp, C.c_int, _vp, _vp]),
     "nh_restrict": (_st, [_vp, _vp, C.c_int, _vp, _vp]),
     "nh_dot": (_st, [_vp, _i64, _vp, _vp, C.POINTER(C.c_double)]),
+    "nh_profile_enable": (_st, [_vp, C.c_int]),
+    "nh_profile_read": (_st, [_vp, C.POINTER(C.c_double), C.POINTER(_i64)]),
 }
 
 
@@ -212,3 +214,15 @@ def nh_dot(ctx, n, x, y):
     r = C.c_double()
     _check(lib.nh_dot(ctx, n, _ptr(x), _ptr(y), C.byref(r)), ctx)
     return r.value
+
+
+def nh_profile_enable(ctx, on=True):
+    _check(lib.nh_profile_enable(ctx, 1 if on else 0), ctx)
+
+
+def nh_profile_read(ctx):
+    """Returns (total_ms, launches) of Jacobian-apply kernels since the last read."""
+    ms = C.c_double()
+    k = _i64()
+    _check(lib.nh_profile_read(ctx, C.byref(ms), C.byref(k)), ctx)
+    return ms.value, k.value

@@ -1,0 +1,249 @@
+"""GPU parity: every operator entry point of libnh against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (relative, norm-wise: entries that nearly cancel make entry-wise
+checks meaningless, Sec. II-B sums many element contributions):
+* FP64 paths: 1e-12.
+* FP32 paths: 2e-5 -- unit roundoff 6e-8 times a few hundred rounded
+  operations along the gather / six contraction stages / pointwise /
+  scatter chain, with FP32-rounded quadrature data.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem
+from paper_2204_01722_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype).cuda()
+
+
+def host(t):
+    torch.cuda.current_stream().synchronize()
+    return t.double().cpu().numpy()
+
+
+class Case:
+    """One mesh/material/state set up on both sides from the same seeded inputs."""
+
+    def __init__(self, ctx, n, p, q=None, perturb=0.1, seed=0, layout=0, E=None, amp=0.05, mask="uniaxial"):
+        from paper_2204_01722_b300 import nh
+        self.nh = nh
+        q = q or p + 1
+        self.ctx = ctx
+        V = inputs.box_vertices(*n, perturb=perturb, seed=seed)
+        self.sp = fem.Space(*n, V, p, q)
+        self.E = E
+        self.mat = fem.Material(1.0 if E is None else E, 0.3, self.sp.ne)
+        self.X = self.sp.node_coords()
+        self.u = inputs.smooth_field(self.X, amp, seed=seed + 1).ravel()
+        if mask == "uniaxial":
+            self.mask = inputs.uniaxial_mask(self.sp.node_dims)
+        elif mask == "none":
+            self.mask = np.zeros(self.sp.n_dof, dtype=bool)
+        else:
+            self.mask = mask
+        self.space, nn, nd = nh.nh_space_box(ctx, *n, V, p, q)
+        assert nn == self.sp.n_nodes and nd == self.sp.n_dof
+        nh.nh_space_set_dirichlet(ctx, self.space, self.mask)
+        self.op = nh.nh_op_create(ctx, self.space, 0.3, E, 1.0, layout)
+        self.ud = dev(self.u)
+        self.minJ = nh.nh_qdata_setup(ctx, self.op, self.ud)
+        self.state = fem.qp_state(self.sp, self.mat, self.u)
+
+    def close(self):
+        self.nh.nh_op_destroy(self.op)
+        self.nh.nh_space_destroy(self.space)
+
+
+@pytest.mark.parametrize("n,p,q", [((3, 2, 4), 1, 2), ((3, 2, 4), 2, 3), ((3, 3, 2), 3, 4), ((2, 3, 2), 4, 5),
+                                   ((3, 2, 2), 2, 4), ((2, 2, 3), 3, 5), ((2, 2, 2), 4, 6), ((5, 4, 3), 2, 3)])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_jacobian_apply_fp64(nhctx, n, p, q, layout):
+    ctx, _ = nhctx
+    c = Case(ctx, n, p, q, layout=layout, seed=p + 10 * q)
+    du = inputs.normal_vector(c.sp.n_dof, seed=7)
+    y = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
+    c.nh.nh_jacobian_apply(ctx, c.op, dev(du), y)
+    ref = fem.jacobian_apply(c.sp, c.state, du, c.mask, form="A" if layout == 0 else "B")
+    assert rel(host(y), ref) < TOL64
+    assert abs(c.minJ - c.state["J"].min()) < 1e-13
+    c.close()
+
+
+@pytest.mark.parametrize("n,p", [((3, 2, 4), 2), ((3, 3, 2), 3), ((2, 3, 2), 4)])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_jacobian_apply_fp32(nhctx, n, p, layout):
+    ctx, _ = nhctx
+    c = Case(ctx, n, p, layout=layout, seed=3)
+    du = inputs.normal_vector(c.sp.n_dof, seed=8)
+    y = torch.empty(c.sp.n_dof, dtype=torch.float32, device="cuda")
+    c.nh.nh_jacobian_apply(ctx, c.op, dev(du, torch.float32), y)
+    ref = fem.jacobian_apply(c.sp, c.state, du.astype(np.float32).astype(np.float64), c.mask)
+    assert rel(host(y), ref) < TOL32
+    c.close()
+
+
+def test_jacobian_apply_inclusions_and_empty_mask(nhctx):
+    """Per-element modulus with contrast 1e3 and no Dirichlet DoFs."""
+    ctx, _ = nhctx
+    E = inputs.inclusion_modulus(4, 3, 3, seed=2, rmin=0.6, rmax=1.2, contrast=1e3)
+    c = Case(ctx, (4, 3, 3), 2, E=E, mask="none", seed=5)
+    du = inputs.normal_vector(c.sp.n_dof, seed=9)
+    y = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
+    c.nh.nh_jacobian_apply(ctx, c.op, dev(du), y)
+    assert rel(host(y), fem.jacobian_apply(c.sp, c.state, du)) < TOL64
+    c.close()
+
+
+def test_single_element_and_host_apply(nhctx):
+    ctx, _ = nhctx
+    c = Case(ctx, (1, 1, 1), 3, seed=4, perturb=0.0)
+    du = inputs.normal_vector(c.sp.n_dof, seed=1)
+    yh = np.empty(c.sp.n_dof)
+    c.nh.nh_jacobian_apply_host(ctx, c.op, du, yh)
+    assert rel(yh, fem.jacobian_apply(c.sp, c.state, du, c.mask)) < TOL64
+    c.close()
+
+
+@pytest.mark.parametrize("n,p,q", [((3, 2, 4), 2, 3), ((2, 3, 2), 4, 5), ((3, 2, 2), 1, 3)])
+def test_residual(nhctx, n, p, q):
+    ctx, _ = nhctx
+    c = Case(ctx, n, p, q, seed=11)
+    g = inputs.uniaxial_bc(c.sp.node_dims, 0.01)
+    r = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
+    c.nh.nh_residual(ctx, c.op, c.ud, dev(g), r)
+    ref = fem.residual(c.sp, c.mat, c.u, c.mask, g)
+    assert rel(host(r), ref) < TOL64
+    c.close()
+
+
+@pytest.mark.parametrize("n,p,q,layout", [((3, 2, 2), 2, 3, 0), ((2, 2, 3), 3, 4, 0), ((2, 2, 2), 4, 5, 0),
+                                          ((2, 3, 2), 2, 3, 1), ((2, 2, 2), 1, 3, 0)])
+def test_diagonal(nhctx, n, p, q, layout):
+    ctx, _ = nhctx
+    c = Case(ctx, n, p, q, layout=layout, seed=12)
+    d = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
+    c.nh.nh_jacobian_diagonal(ctx, c.op, d)
+    ref = fem.diagonal(c.sp, c.state, c.mask, form="A" if layout == 0 else "B")
+    assert rel(host(d), ref) < TOL64
+    d32 = torch.empty(c.sp.n_dof, dtype=torch.float32, device="cuda")
+    c.nh.nh_jacobian_diagonal(ctx, c.op, d32)
+    assert rel(host(d32), ref) < TOL32
+    c.close()
+
+
+@pytest.mark.parametrize("pf,pc", [(4, 2), (4, 1), (3, 2), (3, 1), (2, 1)])
+def test_coarse_level_operator(nhctx, pf, pc):
+    """Galerkin coarse operator sharing the fine quadrature data (Sec. III-B)."""
+    ctx, _ = nhctx
+    n = (2, 3, 2)
+    c = Case(ctx, n, pf, seed=13)
+    V = c.sp.vertices
+    spc = fem.Space(*n, V, pc, pf + 1)
+    maskc = inputs.uniaxial_mask(spc.node_dims)
+    nh = c.nh
+    sc, _, ndc = nh.nh_space_box(ctx, *n, V, pc, pf + 1)
+    nh.nh_space_set_dirichlet(ctx, sc, maskc)
+    opc = nh.nh_op_level(ctx, c.op, sc)
+    du = inputs.normal_vector(ndc, seed=3)
+    ref = fem.jacobian_apply(spc, c.state, du, maskc)
+    for dt, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+        y = torch.empty(ndc, dtype=dt, device="cuda")
+        nh.nh_jacobian_apply(ctx, opc, dev(du, dt), y)
+        assert rel(host(y), ref) < tol
+    d = torch.empty(ndc, dtype=torch.float64, device="cuda")
+    nh.nh_jacobian_diagonal(ctx, opc, d)
+    assert rel(host(d), fem.diagonal(spc, c.state, maskc)) < TOL64
+    nh.nh_op_destroy(opc)
+    nh.nh_space_destroy(sc)
+    c.close()
+
+
+@pytest.mark.parametrize("pc,pf", [(1, 2), (1, 3), (1, 4), (2, 3), (2, 4), (3, 4)])
+def test_prolong_restrict(nhctx, pc, pf):
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    n = (3, 2, 3)
+    V = inputs.box_vertices(*n, perturb=0.1, seed=1)
+    c = fem.Space(*n, V, pc, pf + 1)
+    f = fem.Space(*n, V, pf, pf + 1)
+    sc, _, ndc = nh.nh_space_box(ctx, *n, V, pc, pf + 1)
+    sf, _, ndf = nh.nh_space_box(ctx, *n, V, pf, pf + 1)
+    uc = inputs.normal_vector(ndc, seed=2)
+    rf = inputs.normal_vector(ndf, seed=3)
+    for dt, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+        out = torch.empty(ndf, dtype=dt, device="cuda")
+        nh.nh_prolong(ctx, sc, sf, dev(uc, dt), out)
+        assert rel(host(out), fem.prolong(c, f, uc)) < tol
+        outc = torch.empty(ndc, dtype=dt, device="cuda")
+        nh.nh_restrict(ctx, sf, sc, dev(rf, dt), outc)
+        assert rel(host(outc), fem.restrict(f, c, rf)) < tol
+    nh.nh_space_destroy(sc)
+    nh.nh_space_destroy(sf)
+
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 1_234_567])
+def test_dot(nhctx, n):
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    x = inputs.normal_vector(n, seed=1)
+    y = inputs.normal_vector(n, seed=2)
+    xd, yd = dev(x), dev(y)
+    r = nh.nh_dot(ctx, n, xd, yd)
+    exact = float(np.dot(x, y)) if n else 0.0
+    assert abs(r - exact) <= 1e-12 * max(1.0, np.linalg.norm(x) * np.linalg.norm(y))
+    assert nh.nh_dot(ctx, n, xd, yd) == r       # deterministic
+
+
+def test_inverted_element_is_reported(nhctx):
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    n = (2, 2, 2)
+    V = inputs.box_vertices(*n)
+    sp = fem.Space(*n, V, 2, 3)
+    s, _, nd = nh.nh_space_box(ctx, *n, V, 2, 3)
+    op = nh.nh_op_create(ctx, s, 0.3)
+    u = -1.5 * sp.node_coords()          # x = X + u = -X/2: det F = -1/8
+    with pytest.raises(nh.NhError) as ei:
+        nh.nh_qdata_setup(ctx, op, dev(u.ravel()))
+    assert ei.value.status == nh.NH_ERR_INVERTED
+    y = torch.empty(nd, dtype=torch.float64, device="cuda")
+    with pytest.raises(nh.NhError) as ei:
+        nh.nh_jacobian_apply(ctx, op, dev(np.zeros(nd)), y)
+    assert ei.value.status == nh.NH_ERR_STATE
+    nh.nh_op_destroy(op)
+    nh.nh_space_destroy(s)
+
+
+def test_argument_errors(nhctx):
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    with pytest.raises(nh.NhError) as ei:
+        nh.nh_space_box(ctx, 2, 2, 2, None, 5, 6)
+    assert ei.value.status == nh.NH_ERR_UNSUPPORTED
+    with pytest.raises(nh.NhError):
+        nh.nh_space_box(ctx, 0, 2, 2, None, 2, 3)
+    s, _, nd = nh.nh_space_box(ctx, 2, 2, 2, None, 2, 3)
+    with pytest.raises(nh.NhError):
+        nh.nh_op_create(ctx, s, 0.5)
+    op = nh.nh_op_create(ctx, s, 0.3)
+    x = torch.zeros(nd + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(nh.NhError) as ei:      # misaligned (offset by one double)
+        nh.nh_qdata_setup(ctx, op, x.data_ptr() + 8)
+    assert ei.value.status == nh.NH_ERR_ARG
+    nh.nh_op_destroy(op)
+    nh.nh_space_destroy(s)
