@@ -549,7 +549,12 @@ extern "C" nh_status nh_restrict(nh_space fine, nh_space coarse, nh_prec prec, c
 // vectors
 // ---------------------------------------------------------------------------
 extern "C" nh_status nh_dot(nh_ctx ctx, int64_t n, const double* x, const double* y, double* res) {
-  if (!ctx || !x || !y || !res || n < 0) return NH_ERR_ARG;
+  if (!ctx || !res || n < 0) return NH_ERR_ARG;
+  if (n == 0) {
+    *res = 0.0;
+    return NH_OK;
+  }
+  if (!x || !y) return NH_ERR_ARG;
   NH_CUDA(ctx, cudaSetDevice(ctx->device));
   NH_CUDA(ctx, nh_launch_dot_partials(n, x, y, ctx->red, kRedBlocks, ctx->stream));
   NH_CUDA(ctx, nh_launch_sum_partials(ctx->red, kRedBlocks, ctx->red + kRedBlocks, ctx->stream));

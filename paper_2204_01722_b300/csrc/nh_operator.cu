@@ -513,17 +513,13 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       }
     }
   }
-  if (minj) {  // block-wide min of det F, one atomic per block
-    __shared__ double red[32];
-    double v = jmin;
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((t & 31) == 0) red[t >> 5] = v;
+  if (minj) {  // block-wide min of det F (blocks may end in a partial warp), one global atomic
+    __shared__ unsigned long long bmin;
+    if (t == 0) bmin = ~0ull;
     __syncthreads();
-    if (t == 0) {
-      double m = red[0];
-      for (int w = 1; w < (int)((blockDim.x + 31) >> 5); w++) m = fmin(m, red[w]);
-      atomicMin(minj, ordered_bits(m));
-    }
+    atomicMin(&bmin, ordered_bits(jmin));
+    __syncthreads();
+    if (t == 0) atomicMin(minj, bmin);
   }
   if (!resid) return;  // uniform across the block
   __syncthreads();
