@@ -171,6 +171,34 @@ nh_status nh_profile_read(nh_ctx ctx, double* total_ms, int64_t* launches);
  * synchronises). */
 nh_status nh_dot(nh_ctx ctx, int64_t n, const double* x, const double* y, double* result_host);
 
+/* ---- allocation-free variant ------------------------------------------ */
+
+/* Largest n accepted by nh_dot_noalloc (2^28 elements). */
+#define NH_DOT_NOALLOC_MAX_N ((int64_t)1 << 28)
+
+/* Deterministic FP64 dot product that allocates nothing.  The paper has no
+ * counterpart: this is a service for callers that cannot let a library call
+ * cudaMalloc -- applications whose device memory is owned by their own pool
+ * allocator (an allocation behind its back breaks the pool's budget or fails),
+ * and latency-critical loops where cudaMalloc/cudaFree would synchronise the
+ * device.  It needs no nh_ctx (nh_create itself allocates).
+ * x, y: device double [n]; result: device double [1], caller-owned; all three
+ * 8-byte aligned.  Runs on the current CUDA device, stream-ordered on
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream); does not block
+ * the host.  Summation order depends only on n (one partial sum per 8192
+ * elements, then a fixed-order sum), so repeated calls give identical results.
+ * Scratch: a fixed 256 KiB array in the library's device image, held by every
+ * GPU that loads the library until the process exits; n > NH_DOT_NOALLOC_MAX_N
+ * returns NH_ERR_UNSUPPORTED.  The first call on each device looks up the
+ * scratch address with that device current: make that first call before any
+ * stream capture.  All calls share the one scratch array, which keeps the last
+ * call's partial sums (no slot needs clearing: each call writes every slot it
+ * reads); calls that can overlap on the GPU (two streams, two host threads)
+ * race and must be serialised by the caller.
+ * Errors: NH_ERR_ARG (n < 0, null or misaligned pointer), NH_ERR_UNSUPPORTED,
+ * NH_ERR_CUDA (symbol lookup or launch failed). */
+nh_status nh_dot_noalloc(void* cuda_stream, int64_t n, const double* x, const double* y, double* result);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,6 +53,7 @@ SIGNATURES = {
     "nh_dot": (_st, [_vp, _i64, _vp, _vp, C.POINTER(C.c_double)]),
     "nh_profile_enable": (_st, [_vp, C.c_int]),
     "nh_profile_read": (_st, [_vp, C.POINTER(C.c_double), C.POINTER(_i64)]),
+    "nh_dot_noalloc": (_st, [_vp, _i64, _vp, _vp, _vp]),
 }
 
 
@@ -226,3 +227,13 @@ def nh_profile_read(ctx):
     k = _i64()
     _check(lib.nh_profile_read(ctx, C.byref(ms), C.byref(k)), ctx)
     return ms.value, k.value
+
+
+NH_DOT_NOALLOC_MAX_N = 1 << 28
+
+
+def nh_dot_noalloc(stream, n, x, y, result):
+    """Allocation-free dot product into the device scalar `result` (stream-ordered)."""
+    st = lib.nh_dot_noalloc(stream, n, _ptr(x), _ptr(y), _ptr(result))
+    if st != NH_OK:
+        raise NhError(st, "nh_dot_noalloc")
