@@ -171,6 +171,74 @@ nh_status nh_profile_read(nh_ctx ctx, double* total_ms, int64_t* launches);
  * synchronises). */
 nh_status nh_dot(nh_ctx ctx, int64_t n, const double* x, const double* y, double* result_host);
 
+/* ---- p-multigrid and the Newton-Krylov solve (Sec. III-A, III-B) -------- */
+
+typedef struct nh_mg_s* nh_mg;
+
+typedef struct {
+  int n_levels;            /* levels including the fine one (2..8) */
+  int level_p[8];          /* polynomial order per level, fine first, e.g. {4, 2, 1} */
+  int cheb_degree;         /* Chebyshev smoother degree (paper: 2; default 3) */
+  double cheb_lo, cheb_hi; /* target interval [lo, hi] * lambda_max (0.1, 1.1) */
+  int lanczos_iters;       /* CG/Lanczos steps for lambda_max on a rough seed (10) */
+  double coarse_rtol;      /* coarsest-level Jacobi-PCG relative tolerance, natural norm (1e-3) */
+  int coarse_maxit;        /* (2000) */
+  int coarse_assembled;    /* 1: a p = 1 coarsest level is assembled into a 27-point block stencil */
+  int mixed;               /* 1: FP32 applies, smoothers and transfers on levels with p > 1 */
+  uint64_t seed;           /* seed of the rough Lanczos start vector (splitmix64, uniform(-1, 1)) */
+  int load_steps;          /* pseudo-time steps t_k = k / load_steps (1) */
+  double newton_rtol;      /* stop when ||F(u)|| <= rtol ||F(u_k^0)||, u_k^0 = lifted start (1e-8) */
+  double newton_atol;      /* or ||F(u)|| <= atol (1e-13) */
+  int newton_maxit;        /* per load step (30) */
+  double krylov_rtol;      /* FCG relative tolerance on sqrt(r^T M r) (1e-3) */
+  int krylov_maxit;        /* (500) */
+  int line_search;         /* 1: one secant step on F(u + a du)^T du = 0 (critical point) */
+  int verbose;             /* 1: one line per Newton step on stderr */
+} nh_mg_opts;
+
+typedef struct {
+  int status;              /* nh_status of the solve */
+  int load_steps, newton_its, krylov_its, vcycles, coarse_its;
+  double rel_residual;     /* ||F(u)|| / ||F(u_k^0)|| at the end of the last load step */
+  double abs_residual;
+  double seconds;          /* wall time of the call */
+  double t_setup, t_krylov, t_residual; /* qdata + multigrid setup, FCG, residuals + line search */
+  int learned_accepted, learned_rejected;
+} nh_solve_report;
+
+/* Defaults: 3 levels {p, 2, 1} from the fine order (2 levels for p = 2), the
+ * values in parentheses above. */
+nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* out);
+/* Build the hierarchy: coarse spaces on the same mesh with the fine q, their
+ * Dirichlet DoFs taken face by face from the fine space (a face component is
+ * constrained on the coarse level when it is constrained at every fine node of
+ * that face), Galerkin coarse operators sharing the fine quadrature data
+ * (nh_op_level), vectors in each level's precision. */
+nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out);
+/* From the fine operator's current quadrature data: diagonals, the assembled
+ * coarse stencil, and lambda_max of D^-1 A on every level (FP64). Synchronises. */
+nh_status nh_mg_setup(nh_mg mg);
+/* Space, operator and lambda_max of level `level` (0 = fine); any out may be NULL. */
+nh_status nh_mg_level_info(nh_mg mg, int level, nh_space* space, nh_op* op, double* lambda_max);
+/* z = M r: one V-cycle (Algorithm multigrid_algorithm) with Chebyshev/Jacobi
+ * pre- and post-smoothing, restriction = prolongation^T and a Jacobi-PCG
+ * coarsest solve.  r, z: device double [n_dof] of the fine space. */
+nh_status nh_mg_vcycle(nh_mg mg, const double* r, double* z);
+nh_status nh_mg_destroy(nh_mg mg);
+/* Flexible CG (Notay's FCG with truncation 1) on J x = b with the V-cycle as
+ * preconditioner; x is the initial guess and the result.  norm: 0 = natural
+ * norm sqrt(r^T M r), 1 = ||r||_2.  Returns NH_ERR_NOT_CONVERGED (report
+ * filled) if maxit is reached. */
+nh_status nh_linear_solve(nh_mg mg, const double* b, double* x, double rtol, int maxit, int norm,
+                          nh_solve_report* report);
+/* Load-stepped Newton-Krylov solve (Sec. III-A): for t_k = k / load_steps the
+ * constrained DoFs of u are set to t_k g_bc, then Newton steps J du = -F(u)
+ * solved by FCG + V-cycle to krylov_rtol, with the secant line search, until
+ * the residual criterion holds.  u: device double [n_dof], initial guess in,
+ * solution out.  g_bc: device double [n_dof], boundary values at t = 1.
+ * Errors: NH_ERR_INVERTED, NH_ERR_NOT_CONVERGED, NH_ERR_NAN (report filled). */
+nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_report* report);
+
 /* ---- allocation-free variant ------------------------------------------ */
 
 /* Largest n accepted by nh_dot_noalloc (2^28 elements). */

@@ -143,6 +143,7 @@ extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const doub
   s->ne = ne; s->n_nodes = nn; s->n_dof = 3 * nn;
   s->Nx = (int)Nx; s->Ny = (int)Ny; s->Nz = (int)Nz;
   nh_tabulate(p, q, &s->tab);
+  if (vxyz) s->verts_host.assign(vxyz, vxyz + 3 * (size_t)(nx + 1) * (ny + 1) * (nz + 1));
 
   // element restriction and node coordinates (trilinear image of the GLL lattice)
   const int P3 = P * P * P;
@@ -514,7 +515,7 @@ extern "C" nh_status nh_jacobian_diagonal(nh_op op, nh_prec prec, void* diag) {
 // ---------------------------------------------------------------------------
 // transfer
 // ---------------------------------------------------------------------------
-static nh_status transfer(nh_space c, nh_space f, nh_prec prec, int dir, const void* in, void* out) {
+nh_status nh_transfer_internal(nh_space c, nh_space f, nh_prec prec, int dir, const void* in, void* out) {
   if (!c || !f || !in || !out) return NH_ERR_ARG;
   nh_ctx ctx = f->ctx;
   if (c->nx != f->nx || c->ny != f->ny || c->nz != f->nz || c->p >= f->p)
@@ -538,11 +539,11 @@ static nh_status transfer(nh_space c, nh_space f, nh_prec prec, int dir, const v
 }
 
 extern "C" nh_status nh_prolong(nh_space coarse, nh_space fine, nh_prec prec, const void* uc, void* uf) {
-  return transfer(coarse, fine, prec, 0, uc, uf);
+  return nh_transfer_internal(coarse, fine, prec, 0, uc, uf);
 }
 
 extern "C" nh_status nh_restrict(nh_space fine, nh_space coarse, nh_prec prec, const void* rf, void* rc) {
-  return transfer(coarse, fine, prec, 1, rf, rc);
+  return nh_transfer_internal(coarse, fine, prec, 1, rf, rc);
 }
 
 // ---------------------------------------------------------------------------

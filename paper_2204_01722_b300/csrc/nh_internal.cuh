@@ -74,6 +74,7 @@ struct nh_space_s {
   int* emap = nullptr;            // [ne][P^3] element restriction
   double* coords = nullptr;       // [n_nodes][3] device
   std::vector<double> coords_host;
+  std::vector<double> verts_host; // [(nx+1)(ny+1)(nz+1)][3], empty for the unit cube
   uint8_t* bc = nullptr;          // [n_nodes] bit c set = component c constrained (device)
   double* inv_mult = nullptr;     // [n_nodes] 1 / multiplicity
   float* inv_mult_f = nullptr;
@@ -142,6 +143,9 @@ NH_DECLARE_P(2)
 NH_DECLARE_P(3)
 NH_DECLARE_P(4)
 NH_DECLARE_P(5)
+
+// transfer with the ABI's checks (nh_api.cu); dir 0 = prolong, 1 = restrict
+nh_status nh_transfer_internal(nh_space c, nh_space f, nh_prec prec, int dir, const void* in, void* out);
 
 // transfer (nh_transfer.cu)
 cudaError_t nh_launch_transfer(int Pc, int Pf, nh_prec prec, int restrict_dir, int64_t ne,

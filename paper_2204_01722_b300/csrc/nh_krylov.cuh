@@ -1,0 +1,36 @@
+// Launchers of the Krylov / smoother vector kernels (nh_krylov.cu) and of the
+// assembled Q1 block stencil (nh_stencil.cu).  Internal.
+#pragma once
+#include "nh_internal.cuh"
+
+template <typename T>
+cudaError_t kv_axpby(cudaStream_t st, int64_t n, double a, const T* x, double b, T* y);
+template <typename T>
+cudaError_t kv_axpy_dev(cudaStream_t st, int64_t n, const T* x, T* y, const double* sc, int num, int den, double s);
+template <typename T>
+cudaError_t kv_cg_update(cudaStream_t st, int64_t n, const T* p, const T* q, T* x, T* r, const double* sc, int num,
+                         int den);
+template <typename T>
+cudaError_t kv_xpby_dev(cudaStream_t st, int64_t n, const T* z, T* p, const double* sc, int num, int den, double s);
+template <typename T>
+cudaError_t kv_mul(cudaStream_t st, int64_t n, const T* d, const T* x, T* y);
+template <typename T>
+cudaError_t kv_recip(cudaStream_t st, int64_t n, T* d);
+template <typename TI, typename TO>
+cudaError_t kv_convert(cudaStream_t st, int64_t n, const TI* x, TO* y);
+template <typename T>
+cudaError_t kv_mask_zero(cudaStream_t st, int64_t nn, const uint8_t* bc, T* v);
+cudaError_t kv_lift(cudaStream_t st, int64_t nn, const uint8_t* bc, double* v, const double* g, double s);
+template <typename T>
+cudaError_t kv_cheb(cudaStream_t st, int64_t n, double c1, double c2, const T* dinv, const T* r, T* d, T* x);
+cudaError_t kv_uniform(cudaStream_t st, int64_t n, uint64_t seed, double* v);
+template <typename TA, typename TB>
+cudaError_t kv_dot(cudaStream_t st, int64_t n, const TA* x, const TB* y, double* part, double* out);
+
+// Assembled Q1 operator on a structured node lattice: 27 neighbour 3x3 blocks per
+// node, stored [27][9][n_nodes].
+cudaError_t ks_assemble_q1(int Q, cudaStream_t st, int64_t ne, int nx, int ny, int nz, const uint8_t* bc,
+                           const double* qd, int64_t qstride, int layout, const Tab1D* tab, double* A);
+cudaError_t ks_apply(cudaStream_t st, int Nx, int Ny, int Nz, const uint8_t* bc, const double* A, const double* x,
+                     double* y);
+cudaError_t ks_diag(cudaStream_t st, int64_t nn, const uint8_t* bc, const double* A, double* d);

@@ -1,0 +1,126 @@
+// Pointwise linearised stress (the D of A = E^T B^T D B E), shared by the
+// matrix-free kernels and the Q1 stencil assembly.  Internal.
+#pragma once
+#include "nh_internal.cuh"
+
+namespace nhpw {
+
+// ---------------------------------------------------------------------------
+// Pointwise linearised stress (the D of A = E^T B^T D B E).
+// g[c][d] = d du_c / d xi_d at one quadrature point; f[c][d] is the reference
+// flux tested against d v_c / d xi_d.  q points at this point's scalar 0,
+// consecutive scalars are s apart.
+// ---------------------------------------------------------------------------
+
+// Current configuration (Eqs. Jacobian, dtau, depsilon): G = g grad_x xi,
+// W sigma = G (W tau) + W lambda tr(G) I + W (mu - lambda log J) (G + G^T),
+// f = W sigma (grad_x xi)^T.  Stored: grad_x xi (9, row d = xi_d), W tau
+// (00, 11, 22, 12, 02, 01), W lambda, W (mu - lambda log J).
+template <typename T>
+__device__ __forceinline__ void pw_current(const T* __restrict__ q, int64_t s, const T (&g)[3][3],
+                                           T (&f)[3][3]) {
+  T X[3][3];
+#pragma unroll
+  for (int i = 0; i < 9; i++) X[i / 3][i % 3] = q[i * s];
+  const T t00 = q[9 * s], t11 = q[10 * s], t22 = q[11 * s];
+  const T t12 = q[12 * s], t02 = q[13 * s], t01 = q[14 * s];
+  const T wl = q[15 * s], wm = q[16 * s];
+  const T tau[3][3] = {{t00, t01, t02}, {t01, t11, t12}, {t02, t12, t22}};
+  T G[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int k = 0; k < 3; k++) G[c][k] = g[c][0] * X[0][k] + g[c][1] * X[1][k] + g[c][2] * X[2][k];
+  const T trG = wl * (G[0][0] + G[1][1] + G[2][2]);
+  T S[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+      S[c][k] = G[c][0] * tau[0][k] + G[c][1] * tau[1][k] + G[c][2] * tau[2][k] + wm * (G[c][k] + G[k][c]);
+  S[0][0] += trG;
+  S[1][1] += trG;
+  S[2][2] += trG;
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int d = 0; d < 3; d++) f[c][d] = S[c][0] * X[d][0] + S[c][1] * X[d][1] + S[c][2] * X[d][2];
+}
+
+// Initial configuration (Sec. V-E, "initial tuned" storage): dF = g grad_X xi,
+// dE = sym(F^T dF), W S = W mu I + (W lambda log J - W mu) C^-1,
+// W dS = W lambda (C^-1 : dE) C^-1 + 2 (W mu - W lambda log J) C^-1 dE C^-1,
+// W dP = dF (W S) + F (W dS), f = W dP (grad_X xi)^T.  Stored: grad_X xi (9),
+// H = grad_X u (9), C^-1 (00, 11, 22, 12, 02, 01), W mu, W lambda log J, W lambda.
+template <typename T>
+__device__ __forceinline__ void pw_initial(const T* __restrict__ q, int64_t s, const T (&g)[3][3],
+                                           T (&f)[3][3]) {
+  T R[3][3], F[3][3];
+#pragma unroll
+  for (int i = 0; i < 9; i++) R[i / 3][i % 3] = q[i * s];
+#pragma unroll
+  for (int i = 0; i < 9; i++) F[i / 3][i % 3] = q[(9 + i) * s] + (i % 4 == 0 ? T(1) : T(0));
+  const T c00 = q[18 * s], c11 = q[19 * s], c22 = q[20 * s];
+  const T c12 = q[21 * s], c02 = q[22 * s], c01 = q[23 * s];
+  const T wmu = q[24 * s], wll = q[25 * s], wl = q[26 * s];
+  const T Ci[3][3] = {{c00, c01, c02}, {c01, c11, c12}, {c02, c12, c22}};
+  T dF[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int k = 0; k < 3; k++) dF[c][k] = g[c][0] * R[0][k] + g[c][1] * R[1][k] + g[c][2] * R[2][k];
+  T dE[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) dE[k][l] = F[0][k] * dF[0][l] + F[1][k] * dF[1][l] + F[2][k] * dF[2][l];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = k + 1; l < 3; l++) {
+      T m = T(0.5) * (dE[k][l] + dE[l][k]);
+      dE[k][l] = m;
+      dE[l][k] = m;
+    }
+  T trc = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) trc += Ci[k][l] * dE[k][l];
+  T CdE[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) CdE[k][l] = Ci[k][0] * dE[0][l] + Ci[k][1] * dE[1][l] + Ci[k][2] * dE[2][l];
+  const T two_m = T(2) * (wmu - wll);
+  T WdS[3][3], WS[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) {
+      T cdec = CdE[k][0] * Ci[0][l] + CdE[k][1] * Ci[1][l] + CdE[k][2] * Ci[2][l];
+      WdS[k][l] = wl * trc * Ci[k][l] + two_m * cdec;
+      WS[k][l] = (wll - wmu) * Ci[k][l] + (k == l ? wmu : T(0));
+    }
+  T dP[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int K = 0; K < 3; K++)
+      dP[c][K] = dF[c][0] * WS[0][K] + dF[c][1] * WS[1][K] + dF[c][2] * WS[2][K] + F[c][0] * WdS[0][K] +
+                 F[c][1] * WdS[1][K] + F[c][2] * WdS[2][K];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int d = 0; d < 3; d++) f[c][d] = dP[c][0] * R[d][0] + dP[c][1] * R[d][1] + dP[c][2] * R[d][2];
+}
+
+template <int LAYOUT, typename T>
+__device__ __forceinline__ void pointwise(const T* __restrict__ q, int64_t s, const T (&g)[3][3], T (&f)[3][3]) {
+  if (LAYOUT == NH_LAYOUT_CURRENT)
+    pw_current<T>(q, s, g, f);
+  else
+    pw_initial<T>(q, s, g, f);
+}
+
+}  // namespace nhpw

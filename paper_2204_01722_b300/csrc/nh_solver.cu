@@ -1,0 +1,795 @@
+// p-multigrid preconditioner and the load-stepped Newton-Krylov solve
+// (Sec. III-A, Sec. III-B, Algorithm multigrid_algorithm), orchestrated from the
+// host; every vector operation is a kernel on the context stream.
+//
+// * Levels share the fine quadrature data (Galerkin coarse operators, Sec. III-B).
+//   A p = 1 coarsest level is assembled into a 27-point block stencil once per
+//   setup (nh_stencil.cu); other levels are matrix-free.
+// * Smoother: Chebyshev semi-iteration on D^-1 A over [lo, hi] lambda_max
+//   (Saad, Iterative Methods, Alg. 12.1), lambda_max from a few CG/Lanczos steps
+//   on a rough seed.
+// * Coarsest solve: Jacobi-PCG to a relative tolerance in the natural norm.
+// * Outer Krylov: flexible CG with truncation 1 (Notay 2000), since a
+//   preconditioner with an inner tolerance is not a fixed linear operator.
+// * Mixed precision: levels with p > 1 keep FP32 vectors, FP32 quadrature data,
+//   FP32 smoothers and transfers; the outer residual, dot products, eigenvalue
+//   estimates, the coarsest solve and the Newton residual stay FP64.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "nh_krylov.cuh"
+
+namespace {
+
+// device scalar slots
+enum {
+  S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_PR = 3, S_ZQ = 4, S_RR = 5, S_TMP = 6,
+  S_HIST = 16,            // Lanczos history: rz[k] at S_HIST + k, pq[k] at S_HIST + 64 + k
+  S_LEN = S_HIST + 128
+};
+
+struct Level {
+  nh_space space = nullptr;
+  nh_op op = nullptr;
+  bool own = false;        // space/op created by the hierarchy
+  int p = 1;
+  nh_prec prec = NH_F64;
+  int64_t n = 0, nn = 0;
+  // level-precision vectors
+  void *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *dinv = nullptr;
+  void* ct = nullptr;      // coarse-sized temporary in this level's precision (precision change)
+  // FP64 work vectors (Lanczos, coarsest PCG)
+  double *w[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* dinv64 = nullptr;
+  double lmax = 0.0;
+  bool stencil = false;
+  double* A = nullptr;     // [27][9][nn]
+};
+
+}  // namespace
+
+struct nh_mg_s {
+  nh_ctx ctx = nullptr;
+  nh_op fine = nullptr;
+  nh_mg_opts o;
+  std::vector<Level> L;
+  double* sc = nullptr;    // device scalars
+  double* part = nullptr;  // dot partials
+  double* hsc = nullptr;   // pinned host mirror
+  // FCG / Newton work (fine, FP64)
+  double *fr = nullptr, *fz = nullptr, *fp = nullptr, *fq = nullptr;  // FCG work
+  double *fx = nullptr, *fu = nullptr, *fg = nullptr, *fb = nullptr, *ft = nullptr, *fs = nullptr;  // Newton
+  bool setup_done = false;
+  int vcycles = 0, coarse_its = 0;
+};
+
+namespace {
+
+size_t wsize(nh_prec p) { return p == NH_F64 ? 8 : 4; }
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return nh_cuda_check(mg->ctx, _e, #call); \
+  } while (0)
+#define ST(call)                         \
+  do {                                   \
+    nh_status _s = (call);               \
+    if (_s != NH_OK) return _s;          \
+  } while (0)
+
+nh_status dalloc(nh_mg mg, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nh_fail(mg->ctx, NH_ERR_OOM, "nh_mg: device allocation failed");
+  }
+  return NH_OK;
+}
+
+// read device scalar slots [i0, i0 + k) to the host (synchronises)
+nh_status read_sc(nh_mg mg, int i0, int k, double* out) {
+  CK(cudaMemcpyAsync(mg->hsc, mg->sc + i0, sizeof(double) * k, cudaMemcpyDeviceToHost, mg->ctx->stream));
+  CK(cudaStreamSynchronize(mg->ctx->stream));
+  memcpy(out, mg->hsc, sizeof(double) * k);
+  return NH_OK;
+}
+
+template <typename TA, typename TB>
+nh_status dot(nh_mg mg, int64_t n, const TA* x, const TB* y, int slot) {
+  CK((kv_dot<TA, TB>(mg->ctx->stream, n, x, y, mg->part, mg->sc + slot)));
+  mg->ctx->launches += 2;
+  return NH_OK;
+}
+
+nh_status dot_host(nh_mg mg, int64_t n, const double* x, const double* y, double* out) {
+  ST(dot(mg, n, x, y, S_TMP));
+  return read_sc(mg, S_TMP, 1, out);
+}
+
+// y = A_l x in precision prec (the stencil is FP64 only)
+nh_status level_apply(nh_mg mg, Level& l, nh_prec prec, const void* x, void* y) {
+  if (l.stencil && prec == NH_F64) {
+    CK(ks_apply(mg->ctx->stream, l.space->Nx, l.space->Ny, l.space->Nz, l.space->bc, l.A, (const double*)x,
+                (double*)y));
+    mg->ctx->launches++;
+    return NH_OK;
+  }
+  return nh_jacobian_apply(l.op, prec, x, y);
+}
+
+// --- smallest building blocks, templated on the level precision ----------------
+template <typename T>
+nh_status cheb(nh_mg mg, Level& l, T* x, const T* b, bool zero_init) {
+  cudaStream_t st = mg->ctx->stream;
+  const double a = mg->o.cheb_lo * l.lmax, bb = mg->o.cheb_hi * l.lmax;
+  const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  T* r = (T*)l.r;
+  T* d = (T*)l.d;
+  T* t = (T*)l.t;
+  const T* dinv = (const T*)l.dinv;
+  const nh_prec pr = l.prec;
+  if (zero_init) {
+    CK(cudaMemcpyAsync(r, b, sizeof(T) * l.n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(x, 0, sizeof(T) * l.n, st));
+  } else {
+    ST(level_apply(mg, l, pr, x, r));
+    CK(kv_axpby<T>(st, l.n, 1.0, b, -1.0, r));  // r = b - A x
+    mg->ctx->launches++;
+  }
+  CK(cudaMemsetAsync(d, 0, sizeof(T) * l.n, st));
+  // d = dinv r / theta ; x += d
+  CK(kv_cheb<T>(st, l.n, 0.0, 1.0 / theta, dinv, r, d, x));
+  mg->ctx->launches++;
+  for (int k = 1; k < mg->o.cheb_degree; k++) {
+    ST(level_apply(mg, l, pr, d, t));
+    CK(kv_axpby<T>(st, l.n, -1.0, t, 1.0, r));  // r -= A d
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    CK(kv_cheb<T>(st, l.n, rho_new * rho, 2.0 * rho_new / delta, dinv, r, d, x));
+    mg->ctx->launches += 2;
+    rho = rho_new;
+  }
+  return NH_OK;
+}
+
+// Jacobi-PCG in FP64 on level l: A x = b, x = 0 start.  With hist, runs exactly
+// `maxit` steps and leaves rz_k, pq_k in the history slots (Lanczos).
+// Returns iterations in *its.
+nh_status pcg64(nh_mg mg, Level& l, const double* b, double* x, double rtol, int maxit, bool hist, int* its) {
+  cudaStream_t st = mg->ctx->stream;
+  const int64_t n = l.n;
+  double *r = l.w[0], *z = l.w[1], *p = l.w[2], *q = l.w[3];
+  const double* dinv = l.dinv64;
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+  CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  CK(kv_mul<double>(st, n, dinv, r, z));
+  CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  mg->ctx->launches++;
+  int cur = S_RZ0;
+  ST(dot(mg, n, r, z, hist ? S_HIST : cur));
+  double rz0 = 0.0;
+  if (!hist) {
+    ST(read_sc(mg, cur, 1, &rz0));
+    if (!(rz0 > 0.0)) {
+      *its = 0;
+      return NH_OK;
+    }
+  }
+  const int check = 4;
+  int k = 0;
+  for (; k < maxit; k++) {
+    const int rz_slot = hist ? S_HIST + k : cur;
+    const int pq_slot = hist ? S_HIST + 64 + k : S_PQ;
+    const int nx_slot = hist ? S_HIST + k + 1 : (cur == S_RZ0 ? S_RZ1 : S_RZ0);
+    ST(level_apply(mg, l, NH_F64, p, q));
+    ST(dot(mg, n, p, q, pq_slot));
+    CK(kv_cg_update<double>(st, n, p, q, x, r, mg->sc, rz_slot, pq_slot));
+    CK(kv_mul<double>(st, n, dinv, r, z));
+    mg->ctx->launches += 2;
+    ST(dot(mg, n, r, z, nx_slot));
+    CK(kv_xpby_dev<double>(st, n, z, p, mg->sc, nx_slot, rz_slot, 1.0));
+    mg->ctx->launches++;
+    if (!hist) {
+      cur = nx_slot;
+      if ((k + 1) % check == 0 || k + 1 == maxit) {
+        double rz = 0.0;
+        ST(read_sc(mg, cur, 1, &rz));
+        if (!isfinite(rz)) return nh_fail(mg->ctx, NH_ERR_NAN, "coarse PCG: non-finite residual");
+        if (sqrt(fabs(rz)) <= rtol * sqrt(rz0)) {
+          k++;
+          break;
+        }
+      }
+    }
+  }
+  *its = k;
+  return NH_OK;
+}
+
+// largest eigenvalue of a symmetric tridiagonal matrix (Sturm bisection)
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int n = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < n; i++) {
+    double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {  // eigenvalues < x
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < n; i++) {
+      d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) c++;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, fabs(hi)); it++) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) < n) lo = mid; else hi = mid;
+  }
+  return hi;
+}
+
+nh_status lanczos(nh_mg mg, Level& l) {
+  cudaStream_t st = mg->ctx->stream;
+  const int k = std::max(1, std::min(mg->o.lanczos_iters, 60));
+  double* seed = l.w[4];
+  CK(kv_uniform(st, l.n, mg->o.seed, seed));
+  CK(kv_mask_zero<double>(st, l.nn, l.space->bc, seed));
+  mg->ctx->launches += 2;
+  // x goes to l.x only when the level is FP64; use w-scratch otherwise: reuse seed as x after copy
+  double* x = (l.prec == NH_F64) ? (double*)l.x : nullptr;
+  std::vector<double> hx;
+  if (!x) {
+    // FP32 level: x of the Lanczos run is not needed; borrow the fine FCG buffer sized for level 0
+    x = mg->fx;
+  }
+  int its = 0;
+  ST(pcg64(mg, l, seed, x, 0.0, k, true, &its));
+  std::vector<double> h(2 * 64 + 1);
+  ST(read_sc(mg, S_HIST, 128, h.data()));
+  std::vector<double> al(k), be(k > 1 ? k - 1 : 0);
+  int m = k;
+  for (int i = 0; i < k; i++) {
+    const double rz = h[i], pq = h[64 + i];
+    if (!(pq > 0.0) || !(rz > 0.0)) {
+      m = i;
+      break;
+    }
+    const double alpha = rz / pq;
+    const double beta_prev = i > 0 ? h[i] / h[i - 1] : 0.0;
+    const double alpha_prev = i > 0 ? h[i - 1] / h[64 + i - 1] : 1.0;
+    al[i] = 1.0 / alpha + (i > 0 ? beta_prev / alpha_prev : 0.0);
+    if (i + 1 < k) {
+      const double beta = h[i + 1] / h[i];
+      be[i] = sqrt(fabs(beta)) / alpha;
+    }
+  }
+  if (m == 0) return nh_fail(mg->ctx, NH_ERR_NAN, "Lanczos: no positive curvature on the seed vector");
+  al.resize(m);
+  be.resize(m > 1 ? m - 1 : 0);
+  l.lmax = tridiag_max_eig(al, be);
+  if (!(l.lmax > 0.0) || !isfinite(l.lmax)) return nh_fail(mg->ctx, NH_ERR_NAN, "Lanczos: lambda_max <= 0");
+  return NH_OK;
+}
+
+template <typename T>
+nh_status vcycle_t(nh_mg mg, int lv);
+
+// x_lv = V-cycle(b_lv), dispatch on the level precision
+nh_status vcycle(nh_mg mg, int lv) {
+  Level& l = mg->L[lv];
+  if (lv == (int)mg->L.size() - 1) {
+    // coarsest: FP64 Jacobi-PCG (the coarsest level is always FP64)
+    int its = 0;
+    ST(pcg64(mg, l, (const double*)l.b, (double*)l.x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
+    mg->coarse_its += its;
+    return NH_OK;
+  }
+  return l.prec == NH_F64 ? vcycle_t<double>(mg, lv) : vcycle_t<float>(mg, lv);
+}
+
+template <typename T>
+nh_status vcycle_t(nh_mg mg, int lv) {
+  cudaStream_t st = mg->ctx->stream;
+  Level& l = mg->L[lv];
+  Level& c = mg->L[lv + 1];
+  T* x = (T*)l.x;
+  T* b = (T*)l.b;
+  T* r = (T*)l.r;
+  ST(cheb<T>(mg, l, x, b, true));
+  // r = b - A x
+  ST(level_apply(mg, l, l.prec, x, r));
+  CK(kv_axpby<T>(st, l.n, 1.0, b, -1.0, r));
+  mg->ctx->launches++;
+  // restrict in this level's precision, convert if the coarse level differs
+  if (c.prec == l.prec) {
+    ST(nh_transfer_internal(c.space, l.space, l.prec, 1, r, c.b));
+  } else {
+    ST(nh_transfer_internal(c.space, l.space, l.prec, 1, r, l.ct));
+    if (l.prec == NH_F32)
+      CK((kv_convert<float, double>(st, c.n, (const float*)l.ct, (double*)c.b)));
+    else
+      CK((kv_convert<double, float>(st, c.n, (const double*)l.ct, (float*)c.b)));
+    mg->ctx->launches++;
+  }
+  if (c.prec == NH_F64)
+    CK(kv_mask_zero<double>(st, c.nn, c.space->bc, (double*)c.b));
+  else
+    CK(kv_mask_zero<float>(st, c.nn, c.space->bc, (float*)c.b));
+  mg->ctx->launches++;
+  ST(vcycle(mg, lv + 1));
+  // prolong the correction
+  const void* xc = c.x;
+  if (c.prec != l.prec) {
+    if (l.prec == NH_F32)
+      CK((kv_convert<double, float>(st, c.n, (const double*)c.x, (float*)l.ct)));
+    else
+      CK((kv_convert<float, double>(st, c.n, (const float*)c.x, (double*)l.ct)));
+    mg->ctx->launches++;
+    xc = l.ct;
+  }
+  ST(nh_transfer_internal(c.space, l.space, l.prec, 0, xc, l.t));
+  CK(kv_mask_zero<T>(st, l.nn, l.space->bc, (T*)l.t));
+  CK(kv_axpby<T>(st, l.n, 1.0, (const T*)l.t, 1.0, x));
+  mg->ctx->launches += 2;
+  ST(cheb<T>(mg, l, x, b, false));
+  return NH_OK;
+}
+
+// the coarse Dirichlet mask by faces: a face component is constrained on the
+// coarse space if it is constrained at every fine node of that face
+nh_status coarse_mask(nh_mg mg, nh_space f, nh_space c, std::vector<uint8_t>& out) {
+  std::vector<uint8_t> fb((size_t)f->n_nodes);
+  CK(cudaMemcpy(fb.data(), f->bc, f->n_nodes, cudaMemcpyDeviceToHost));
+  const int dims_f[3] = {f->Nx, f->Ny, f->Nz}, dims_c[3] = {c->Nx, c->Ny, c->Nz};
+  unsigned face[6];  // (axis, side) -> component bits constrained everywhere on that face
+  for (int ax = 0; ax < 3; ax++)
+    for (int sd = 0; sd < 2; sd++) {
+      unsigned acc = 7u;
+      const int fixed = sd ? dims_f[ax] - 1 : 0;
+      const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+      for (int i = 0; i < dims_f[a1]; i++)
+        for (int j = 0; j < dims_f[a2]; j++) {
+          int idx[3];
+          idx[ax] = fixed;
+          idx[a1] = i;
+          idx[a2] = j;
+          acc &= fb[idx[0] + (int64_t)dims_f[0] * (idx[1] + (int64_t)dims_f[1] * idx[2])];
+        }
+      face[ax * 2 + sd] = acc;
+    }
+  out.assign((size_t)c->n_dof, 0);
+  for (int64_t n = 0; n < c->n_nodes; n++) {
+    const int I[3] = {(int)(n % dims_c[0]), (int)((n / dims_c[0]) % dims_c[1]), (int)(n / ((int64_t)dims_c[0] * dims_c[1]))};
+    unsigned m = 0;
+    for (int ax = 0; ax < 3; ax++) {
+      if (I[ax] == 0) m |= face[ax * 2];
+      if (I[ax] == dims_c[ax] - 1) m |= face[ax * 2 + 1];
+    }
+    for (int cc = 0; cc < 3; cc++) out[3 * n + cc] = (m >> cc) & 1u;
+  }
+  return NH_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
+  if (!fine || !o) return NH_ERR_ARG;
+  memset(o, 0, sizeof(*o));
+  const int p = fine->space->p;
+  if (p >= 3) {
+    o->n_levels = 3;
+    o->level_p[0] = p;
+    o->level_p[1] = 2;
+    o->level_p[2] = 1;
+  } else if (p == 2) {
+    o->n_levels = 2;
+    o->level_p[0] = 2;
+    o->level_p[1] = 1;
+  } else {
+    o->n_levels = 1;
+    o->level_p[0] = 1;
+  }
+  o->cheb_degree = 3;
+  o->cheb_lo = 0.1;
+  o->cheb_hi = 1.1;
+  o->lanczos_iters = 10;
+  o->coarse_rtol = 1e-3;
+  o->coarse_maxit = 2000;
+  o->coarse_assembled = 1;
+  o->mixed = 0;
+  o->seed = 12345;
+  o->load_steps = 1;
+  o->newton_rtol = 1e-8;
+  o->newton_atol = 1e-13;
+  o->newton_maxit = 30;
+  o->krylov_rtol = 1e-3;
+  o->krylov_maxit = 500;
+  o->line_search = 1;
+  o->verbose = 0;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_mg_destroy(nh_mg mg) {
+  if (!mg) return NH_ERR_ARG;
+  cudaStreamSynchronize(mg->ctx->stream);
+  for (Level& l : mg->L) {
+    for (void* p : {l.x, l.b, l.r, l.d, l.t, l.dinv, l.ct}) cudaFree(p);
+    for (double* p : l.w) cudaFree(p);
+    if (l.dinv64 != (double*)l.dinv) cudaFree(l.dinv64);
+    cudaFree(l.A);
+    if (l.own) {
+      nh_op_destroy(l.op);
+      nh_space_destroy(l.space);
+    }
+  }
+  cudaFree(mg->sc);
+  cudaFree(mg->part);
+  cudaFreeHost(mg->hsc);
+  for (double* p : {mg->fr, mg->fz, mg->fp, mg->fq, mg->fx, mg->fu, mg->fg, mg->fb, mg->ft, mg->fs}) cudaFree(p);
+  delete mg;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out) {
+  if (!fine || !out) return NH_ERR_ARG;
+  *out = nullptr;
+  if (fine->parent) return nh_fail(fine->space->ctx, NH_ERR_ARG, "nh_mg_create: needs the fine operator");
+  nh_mg mg = new nh_mg_s();
+  mg->ctx = fine->space->ctx;
+  mg->fine = fine;
+  if (opts)
+    mg->o = *opts;
+  else
+    nh_mg_default_opts(fine, &mg->o);
+  const nh_mg_opts& o = mg->o;
+  nh_space fs = fine->space;
+  auto bad = [&](const char* m) {
+    nh_fail(mg->ctx, NH_ERR_ARG, m);
+    delete mg;
+    return NH_ERR_ARG;
+  };
+  if (o.n_levels < 1 || o.n_levels > 8) return bad("nh_mg_create: 1 <= n_levels <= 8");
+  if (o.level_p[0] != fs->p) return bad("nh_mg_create: level_p[0] must be the fine order");
+  for (int i = 1; i < o.n_levels; i++)
+    if (o.level_p[i] < 1 || o.level_p[i] >= o.level_p[i - 1]) return bad("nh_mg_create: orders must decrease to >= 1");
+  if (o.cheb_degree < 1 || !(o.cheb_hi > o.cheb_lo) || !(o.cheb_lo > 0)) return bad("nh_mg_create: bad Chebyshev options");
+  cudaSetDevice(mg->ctx->device);
+  nh_status s;
+  mg->L.resize(o.n_levels);
+  for (int i = 0; i < o.n_levels; i++) {
+    Level& l = mg->L[i];
+    l.p = o.level_p[i];
+    if (i == 0) {
+      l.space = fs;
+      l.op = fine;
+    } else {
+      int64_t nn, nd;
+      s = nh_space_box(mg->ctx, fs->nx, fs->ny, fs->nz, fs->verts_host.empty() ? nullptr : fs->verts_host.data(), l.p,
+                       fs->q, &l.space, &nn, &nd);
+      if (s != NH_OK) { nh_mg_destroy(mg); return s; }
+      l.own = true;
+      std::vector<uint8_t> m;
+      if ((s = coarse_mask(mg, fs, l.space, m)) != NH_OK) { nh_mg_destroy(mg); return s; }
+      if ((s = nh_space_set_dirichlet(l.space, m.data())) != NH_OK) { nh_mg_destroy(mg); return s; }
+      if ((s = nh_op_level(fine, l.space, &l.op)) != NH_OK) { nh_mg_destroy(mg); return s; }
+    }
+    l.n = l.space->n_dof;
+    l.nn = l.space->n_nodes;
+    l.prec = (o.mixed && l.p > 1) ? NH_F32 : NH_F64;
+    l.stencil = (i == o.n_levels - 1) && l.p == 1 && o.coarse_assembled && o.n_levels > 1;
+    const size_t wb = wsize(l.prec) * l.n;
+    for (void** v : {&l.x, &l.b, &l.r, &l.d, &l.t, &l.dinv})
+      if ((s = dalloc(mg, v, wb)) != NH_OK) { nh_mg_destroy(mg); return s; }
+    for (int k = 0; k < 5; k++)
+      if ((s = dalloc(mg, (void**)&l.w[k], 8 * l.n)) != NH_OK) { nh_mg_destroy(mg); return s; }
+    if (l.prec == NH_F64) {
+      l.dinv64 = (double*)l.dinv;
+    } else if ((s = dalloc(mg, (void**)&l.dinv64, 8 * l.n)) != NH_OK) {
+      nh_mg_destroy(mg);
+      return s;
+    }
+    if (l.stencil && (s = dalloc(mg, (void**)&l.A, sizeof(double) * 243 * l.nn)) != NH_OK) {
+      nh_mg_destroy(mg);
+      return s;
+    }
+  }
+  for (int i = 0; i + 1 < o.n_levels; i++) {
+    Level& l = mg->L[i];
+    if (mg->L[i + 1].prec != l.prec && (s = dalloc(mg, &l.ct, wsize(l.prec) * mg->L[i + 1].n)) != NH_OK) {
+      nh_mg_destroy(mg);
+      return s;
+    }
+  }
+  const size_t fb = 8 * (size_t)fs->n_dof;
+  if ((s = dalloc(mg, (void**)&mg->sc, sizeof(double) * S_LEN)) != NH_OK ||
+      (s = dalloc(mg, (void**)&mg->part, sizeof(double) * 148 * 8 + 64)) != NH_OK) {
+    nh_mg_destroy(mg);
+    return s;
+  }
+  for (double** v : {&mg->fr, &mg->fz, &mg->fp, &mg->fq, &mg->fx, &mg->fu, &mg->fg, &mg->fb, &mg->ft, &mg->fs})
+    if ((s = dalloc(mg, (void**)v, fb)) != NH_OK) { nh_mg_destroy(mg); return s; }
+  if (cudaMallocHost(&mg->hsc, sizeof(double) * S_LEN) != cudaSuccess) {
+    cudaGetLastError();
+    nh_mg_destroy(mg);
+    return NH_ERR_OOM;
+  }
+  cudaMemset(mg->sc, 0, sizeof(double) * S_LEN);
+  *out = mg;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_mg_setup(nh_mg mg) {
+  if (!mg) return NH_ERR_ARG;
+  nh_op root = mg->fine;
+  if (!root->have_qd) return nh_fail(mg->ctx, NH_ERR_STATE, "nh_mg_setup: call nh_qdata_setup first");
+  cudaStream_t st = mg->ctx->stream;
+  CK(cudaSetDevice(mg->ctx->device));
+  for (Level& l : mg->L) {
+    if (l.stencil) {
+      CK(cudaMemsetAsync(l.A, 0, sizeof(double) * 243 * l.nn, st));
+      const int64_t Q3 = (int64_t)root->space->Q * root->space->Q * root->space->Q;
+      CK(ks_assemble_q1(root->space->Q, st, l.space->ne, l.space->nx, l.space->ny, l.space->nz, l.space->bc, root->qd,
+                        root->space->ne * Q3, root->layout, &l.space->tab, l.A));
+      CK(ks_diag(st, l.nn, l.space->bc, l.A, l.dinv64));
+      mg->ctx->launches += 2;
+    } else {
+      ST(nh_jacobian_diagonal(l.op, NH_F64, l.dinv64));
+    }
+    CK(kv_recip<double>(st, l.n, l.dinv64));
+    mg->ctx->launches++;
+    if (l.prec == NH_F32) {
+      CK((kv_convert<double, float>(st, l.n, l.dinv64, (float*)l.dinv)));
+      mg->ctx->launches++;
+    }
+    if (&l != &mg->L.back()) ST(lanczos(mg, l));
+  }
+  CK(cudaStreamSynchronize(st));
+  mg->setup_done = true;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_mg_level_info(nh_mg mg, int level, nh_space* space, nh_op* op, double* lmax) {
+  if (!mg || level < 0 || level >= (int)mg->L.size()) return NH_ERR_ARG;
+  if (space) *space = mg->L[level].space;
+  if (op) *op = mg->L[level].op;
+  if (lmax) *lmax = mg->L[level].lmax;
+  return NH_OK;
+}
+
+static nh_status vcycle_fp64(nh_mg mg, const double* r, double* z) {
+  cudaStream_t st = mg->ctx->stream;
+  Level& l = mg->L[0];
+  if (mg->L.size() == 1) {
+    int its = 0;
+    ST(pcg64(mg, l, r, z, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
+    mg->coarse_its += its;
+    mg->vcycles++;
+    return NH_OK;
+  }
+  if (l.prec == NH_F64) {
+    CK(cudaMemcpyAsync(l.b, r, 8 * l.n, cudaMemcpyDeviceToDevice, st));
+  } else {
+    CK((kv_convert<double, float>(st, l.n, r, (float*)l.b)));
+    mg->ctx->launches++;
+  }
+  ST(vcycle(mg, 0));
+  if (l.prec == NH_F64) {
+    CK(cudaMemcpyAsync(z, l.x, 8 * l.n, cudaMemcpyDeviceToDevice, st));
+  } else {
+    CK((kv_convert<float, double>(st, l.n, (const float*)l.x, z)));
+    mg->ctx->launches++;
+  }
+  mg->vcycles++;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_mg_vcycle(nh_mg mg, const double* r, double* z) {
+  if (!mg || !r || !z) return NH_ERR_ARG;
+  if (!mg->setup_done) return nh_fail(mg->ctx, NH_ERR_STATE, "nh_mg_vcycle: call nh_mg_setup first");
+  CK(cudaSetDevice(mg->ctx->device));
+  return vcycle_fp64(mg, r, z);
+}
+
+// FCG(1): J x = b, x in/out; returns iterations, final relative norm
+static nh_status fcg(nh_mg mg, const double* b, double* x, double rtol, int maxit, int norm, int* its_out,
+                     double* rel_out) {
+  cudaStream_t st = mg->ctx->stream;
+  nh_op A = mg->fine;
+  const int64_t n = mg->L[0].n;
+  double *r = mg->fr, *z = mg->fz, *p = mg->fp, *q = mg->fq;
+  ST(nh_jacobian_apply(A, NH_F64, x, r));
+  CK(kv_axpby<double>(st, n, 1.0, b, -1.0, r));  // r = b - A x
+  mg->ctx->launches++;
+  ST(vcycle_fp64(mg, r, z));
+  CK(cudaMemcpyAsync(p, z, 8 * n, cudaMemcpyDeviceToDevice, st));
+  ST(nh_jacobian_apply(A, NH_F64, p, q));
+  double nrm0 = 0.0;
+  ST(norm == 0 ? dot(mg, n, r, z, S_RR) : dot(mg, n, r, r, S_RR));
+  ST(read_sc(mg, S_RR, 1, &nrm0));
+  nrm0 = sqrt(fabs(nrm0));
+  if (!isfinite(nrm0)) return nh_fail(mg->ctx, NH_ERR_NAN, "FCG: non-finite initial residual");
+  double nrm = nrm0;
+  int k = 0;
+  if (nrm0 == 0.0) {
+    *its_out = 0;
+    *rel_out = 0.0;
+    return NH_OK;
+  }
+  while (k < maxit) {
+    ST(dot(mg, n, p, q, S_PQ));
+    ST(dot(mg, n, p, r, S_PR));
+    CK(kv_cg_update<double>(st, n, p, q, x, r, mg->sc, S_PR, S_PQ));  // x += a p, r -= a q
+    mg->ctx->launches++;
+    k++;
+    ST(vcycle_fp64(mg, r, z));
+    ST(norm == 0 ? dot(mg, n, r, z, S_RR) : dot(mg, n, r, r, S_RR));
+    ST(read_sc(mg, S_RR, 1, &nrm));
+    nrm = sqrt(fabs(nrm));
+    if (!isfinite(nrm)) return nh_fail(mg->ctx, NH_ERR_NAN, "FCG: non-finite residual");
+    if (nrm <= rtol * nrm0) break;
+    ST(dot(mg, n, z, q, S_ZQ));
+    CK(kv_xpby_dev<double>(st, n, z, p, mg->sc, S_ZQ, S_PQ, -1.0));  // p = z - (z.q / p.q) p
+    mg->ctx->launches++;
+    ST(nh_jacobian_apply(A, NH_F64, p, q));
+  }
+  *its_out = k;
+  *rel_out = nrm / nrm0;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_linear_solve(nh_mg mg, const double* b, double* x, double rtol, int maxit, int norm,
+                                     nh_solve_report* rep) {
+  if (!mg || !b || !x) return NH_ERR_ARG;
+  if (!mg->setup_done) return nh_fail(mg->ctx, NH_ERR_STATE, "nh_linear_solve: call nh_mg_setup first");
+  CK(cudaSetDevice(mg->ctx->device));
+  auto t0 = std::chrono::steady_clock::now();
+  mg->vcycles = mg->coarse_its = 0;
+  int its = 0;
+  double rel = 0.0;
+  nh_status s = fcg(mg, b, x, rtol, maxit, norm, &its, &rel);
+  CK(cudaStreamSynchronize(mg->ctx->stream));
+  if (rep) {
+    memset(rep, 0, sizeof(*rep));
+    rep->krylov_its = its;
+    rep->vcycles = mg->vcycles;
+    rep->coarse_its = mg->coarse_its;
+    rep->rel_residual = rel;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    rep->t_krylov = rep->seconds;
+  }
+  if (s == NH_OK && rel > rtol) s = nh_fail(mg->ctx, NH_ERR_NOT_CONVERGED, "nh_linear_solve: maxit reached");
+  if (rep) rep->status = s;
+  return s;
+}
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_report* rep) {
+  if (!mg || !u) return NH_ERR_ARG;
+  nh_ctx ctx = mg->ctx;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  nh_op F = mg->fine;
+  nh_space fs = F->space;
+  const nh_mg_opts& o = mg->o;
+  const int64_t n = fs->n_dof;
+  double *r = mg->fu, *gk = mg->fg, *du = mg->fx, *rhs = mg->fb;
+  double *ut = mg->ft, *rt = mg->fs;  // trial point and its residual
+  nh_solve_report R;
+  memset(&R, 0, sizeof(R));
+  const double T0 = now_s();
+  double tS = 0, tK = 0, tR = 0;
+  nh_status status = NH_OK;
+  const int K = std::max(1, o.load_steps);
+  double rel = 0.0, nr = 0.0;
+  for (int step = 1; step <= K && status == NH_OK; step++) {
+    const double t = (double)step / K;
+    double t1 = now_s();
+    if (g_bc) {
+      CK(cudaMemcpyAsync(gk, g_bc, 8 * n, cudaMemcpyDeviceToDevice, st));
+      CK(kv_axpby<double>(st, n, 0.0, gk, t, gk));
+    } else {
+      CK(cudaMemsetAsync(gk, 0, 8 * n, st));
+    }
+    CK(kv_lift(st, fs->n_nodes, fs->bc, u, gk, 1.0));
+    ctx->launches += 2;
+    ST(nh_residual(F, u, gk, r));
+    double nr0 = 0.0;
+    ST(dot_host(mg, n, r, r, &nr0));
+    nr0 = sqrt(nr0);
+    nr = nr0;
+    tR += now_s() - t1;
+    int it = 0;
+    while (!(nr <= o.newton_rtol * nr0) && !(nr <= o.newton_atol)) {
+      if (it >= o.newton_maxit) {
+        status = nh_fail(ctx, NH_ERR_NOT_CONVERGED, "nh_solve: Newton iteration limit");
+        break;
+      }
+      if (!isfinite(nr)) {
+        status = nh_fail(ctx, NH_ERR_NAN, "nh_solve: non-finite residual");
+        break;
+      }
+      t1 = now_s();
+      double minJ = 0.0;
+      status = nh_qdata_setup(F, u, &minJ);
+      if (status != NH_OK) break;
+      status = nh_mg_setup(mg);
+      if (status != NH_OK) break;
+      tS += now_s() - t1;
+      // J du = -r
+      t1 = now_s();
+      CK(kv_axpby<double>(st, n, -1.0, r, 0.0, rhs));  // rhs = -F(u)
+      CK(cudaMemsetAsync(du, 0, 8 * n, st));
+      ctx->launches++;
+      int kits = 0;
+      double krel = 0.0;
+      mg->vcycles = 0;
+      mg->coarse_its = 0;
+      status = fcg(mg, rhs, du, o.krylov_rtol, o.krylov_maxit, 0, &kits, &krel);
+      R.krylov_its += kits;
+      R.vcycles += mg->vcycles;
+      R.coarse_its += mg->coarse_its;
+      tK += now_s() - t1;
+      if (status != NH_OK) break;
+      // line search along du (secant on phi(a) = F(u + a du) . du)
+      t1 = now_s();
+      double alpha = 1.0, phi0 = 0.0, phi1 = 0.0;
+      CK(cudaMemcpyAsync(ut, u, 8 * n, cudaMemcpyDeviceToDevice, st));
+      CK(kv_axpby<double>(st, n, 1.0, du, 1.0, ut));
+      ctx->launches++;
+      ST(nh_residual(F, ut, gk, rt));
+      if (o.line_search) {
+        ST(dot_host(mg, n, r, du, &phi0));
+        ST(dot_host(mg, n, rt, du, &phi1));
+        if (phi0 * phi1 < 0.0) {
+          alpha = phi0 / (phi0 - phi1);
+          if (!isfinite(alpha)) alpha = 1.0;
+          alpha = std::min(1.5, std::max(0.1, alpha));
+        }
+      }
+      if (alpha == 1.0) {
+        CK(cudaMemcpyAsync(u, ut, 8 * n, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(r, rt, 8 * n, cudaMemcpyDeviceToDevice, st));
+      } else {
+        CK(kv_axpby<double>(st, n, alpha, du, 1.0, u));
+        ctx->launches++;
+        ST(nh_residual(F, u, gk, r));
+      }
+      double nr2 = 0.0;
+      ST(dot_host(mg, n, r, r, &nr2));
+      nr = sqrt(nr2);
+      tR += now_s() - t1;
+      it++;
+      R.newton_its++;
+      if (o.verbose)
+        fprintf(stderr, "nh_solve step %d newton %d |F| %.3e rel %.3e fcg %d vcyc %d coarse %d alpha %.3f minJ %.3f\n",
+                step, it, nr, nr / nr0, kits, mg->vcycles, mg->coarse_its, alpha, minJ);
+    }
+    rel = nr0 > 0 ? nr / nr0 : 0.0;
+    R.load_steps = step;
+  }
+  CK(cudaStreamSynchronize(st));
+  R.status = status;
+  R.rel_residual = rel;
+  R.abs_residual = nr;
+  R.seconds = now_s() - T0;
+  R.t_setup = tS;
+  R.t_krylov = tK;
+  R.t_residual = tR;
+  if (rep) *rep = R;
+  return status;
+}

@@ -56,6 +56,21 @@ def uniform_vector(n, seed=0):
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=n)
 
 
+def splitmix_uniform(n, seed):
+    """Counter-based uniform(-1, 1) vector: splitmix64 (Steele, Lea, Flood 2014)
+    of seed * 0x100000001b3 + i, top 53 bits scaled.  The CUDA library draws the
+    rough Lanczos start vector with its own implementation of the same generator."""
+    M = np.uint64(0xFFFFFFFFFFFFFFFF)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) * np.uint64(0x100000001b3) + np.arange(n, dtype=np.uint64)
+        z = z + np.uint64(0x9e3779b97f4a7c15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xbf58476d1ce4e5b9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94d049bb133111eb)
+        z = z ^ (z >> np.uint64(31))
+    del M
+    return 2.0 * ((z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)) - 1.0
+
+
 def lattice_index(node_dims):
     Nx, Ny, Nz = node_dims
     I = np.tile(np.arange(Nx), Ny * Nz)

@@ -54,7 +54,37 @@ SIGNATURES = {
     "nh_profile_enable": (_st, [_vp, C.c_int]),
     "nh_profile_read": (_st, [_vp, C.POINTER(C.c_double), C.POINTER(_i64)]),
     "nh_dot_noalloc": (_st, [_vp, _i64, _vp, _vp, _vp]),
+    "nh_mg_default_opts": (_st, [_vp, _vp]),
+    "nh_mg_create": (_st, [_vp, _vp, C.POINTER(_vp)]),
+    "nh_mg_setup": (_st, [_vp]),
+    "nh_mg_level_info": (_st, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_double)]),
+    "nh_mg_vcycle": (_st, [_vp, _vp, _vp]),
+    "nh_mg_destroy": (_st, [_vp]),
+    "nh_linear_solve": (_st, [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp]),
+    "nh_solve": (_st, [_vp, _vp, _vp, _vp]),
 }
+
+
+class MgOpts(C.Structure):
+    """Mirror of nh_mg_opts."""
+    _fields_ = [("n_levels", C.c_int), ("level_p", C.c_int * 8), ("cheb_degree", C.c_int),
+                ("cheb_lo", C.c_double), ("cheb_hi", C.c_double), ("lanczos_iters", C.c_int),
+                ("coarse_rtol", C.c_double), ("coarse_maxit", C.c_int), ("coarse_assembled", C.c_int),
+                ("mixed", C.c_int), ("seed", C.c_uint64), ("load_steps", C.c_int), ("newton_rtol", C.c_double),
+                ("newton_atol", C.c_double), ("newton_maxit", C.c_int), ("krylov_rtol", C.c_double),
+                ("krylov_maxit", C.c_int), ("line_search", C.c_int), ("verbose", C.c_int)]
+
+
+class SolveReport(C.Structure):
+    """Mirror of nh_solve_report."""
+    _fields_ = [("status", C.c_int), ("load_steps", C.c_int), ("newton_its", C.c_int), ("krylov_its", C.c_int),
+                ("vcycles", C.c_int), ("coarse_its", C.c_int), ("rel_residual", C.c_double),
+                ("abs_residual", C.c_double), ("seconds", C.c_double), ("t_setup", C.c_double),
+                ("t_krylov", C.c_double), ("t_residual", C.c_double), ("learned_accepted", C.c_int),
+                ("learned_rejected", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 def _load():
@@ -237,3 +267,59 @@ def nh_dot_noalloc(stream, n, x, y, result):
     st = lib.nh_dot_noalloc(stream, n, _ptr(x), _ptr(y), _ptr(result))
     if st != NH_OK:
         raise NhError(st, "nh_dot_noalloc")
+
+
+def nh_mg_default_opts(ctx, fine_op, **kw):
+    """Default options for `fine_op`, with any field overridden by keyword
+    (level_p may be given as a sequence)."""
+    o = MgOpts()
+    _check(lib.nh_mg_default_opts(fine_op, C.byref(o)), ctx)
+    for k, v in kw.items():
+        if k == "level_p":
+            o.n_levels = len(v)
+            for i, pv in enumerate(v):
+                o.level_p[i] = pv
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def nh_mg_create(ctx, fine_op, opts=None):
+    h = _vp()
+    _check(lib.nh_mg_create(fine_op, None if opts is None else C.byref(opts), C.byref(h)), ctx)
+    return h.value
+
+
+def nh_mg_setup(ctx, mg):
+    _check(lib.nh_mg_setup(mg), ctx)
+
+
+def nh_mg_level_info(ctx, mg, level):
+    """Returns (space, op, lambda_max)."""
+    s, o, lm = _vp(), _vp(), C.c_double()
+    _check(lib.nh_mg_level_info(mg, level, C.byref(s), C.byref(o), C.byref(lm)), ctx)
+    return s.value, o.value, lm.value
+
+
+def nh_mg_vcycle(ctx, mg, r, z):
+    _check(lib.nh_mg_vcycle(mg, _ptr(r), _ptr(z)), ctx)
+
+
+def nh_mg_destroy(mg):
+    lib.nh_mg_destroy(mg)
+
+
+def nh_linear_solve(ctx, mg, b, x, rtol=1e-8, maxit=500, norm=1, check=True):
+    rep = SolveReport()
+    st = lib.nh_linear_solve(mg, _ptr(b), _ptr(x), rtol, maxit, norm, C.byref(rep))
+    if check:
+        _check(st, ctx)
+    return rep
+
+
+def nh_solve(ctx, mg, g_bc, u, check=True):
+    rep = SolveReport()
+    st = lib.nh_solve(mg, _ptr(g_bc), _ptr(u), C.byref(rep))
+    if check:
+        _check(st, ctx)
+    return rep

@@ -1,0 +1,165 @@
+"""GPU parity of the p-multigrid pieces and the Newton-Krylov solve against the
+FP64 oracle (Sec. III-A, III-B, Algorithm multigrid_algorithm).
+
+Tolerances:
+* lambda_max (10 Lanczos steps, same splitmix64 seed vector): 1e-9 relative --
+  ten CG steps in a different summation order.
+* one V-cycle with a near-exact coarsest solve (rtol 1e-14 on both sides):
+  1e-8 relative -- coarse CG residual 1e-14 amplified by the coarse condition
+  number (< 1e4 on these meshes).
+* mixed-precision V-cycle against the FP64 one: 1e-4 (FP32 smoothing of a
+  preconditioner; the outer Krylov and residuals stay FP64).
+* linear solve to ||r|| <= 1e-11 ||b||: 1e-7 against a sparse direct solve.
+* nonlinear solve to ||F|| <= 1e-8 ||F_0||: 1e-6 against the oracle's Newton
+  with a direct solver (both converged; iteration counts may differ).
+"""
+import numpy as np
+import pytest
+
+from oracle import fem, solvers
+from paper_2204_01722_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEED = 12345
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.current_stream().synchronize()
+    return t.cpu().numpy()
+
+
+class Problem:
+    def __init__(self, ctx, n, p, levels, E=None, perturb=0.1, seed=3, mixed=0, assembled=1, coarse_rtol=1e-14,
+                 amp=0.04):
+        from paper_2204_01722_b300 import nh
+        self.nh, self.ctx = nh, ctx
+        q = p + 1
+        self.V = inputs.box_vertices(*n, perturb=perturb, seed=seed)
+        self.n, self.p, self.q = n, p, q
+        self.sps = [fem.Space(*n, self.V, pl, q) for pl in levels]
+        self.mat = fem.Material(1.0 if E is None else E, 0.3, self.sps[0].ne)
+        self.masks = [inputs.uniaxial_mask(s.node_dims) for s in self.sps]
+        self.u = inputs.smooth_field(self.sps[0].node_coords(), amp, seed=seed + 1).ravel()
+        self.u[self.masks[0]] = 0.0
+        self.space, _, self.nd = nh.nh_space_box(ctx, *n, self.V, p, q)
+        nh.nh_space_set_dirichlet(ctx, self.space, self.masks[0])
+        self.op = nh.nh_op_create(ctx, self.space, 0.3, E)
+        self.opts = nh.nh_mg_default_opts(ctx, self.op, level_p=levels, mixed=mixed, coarse_assembled=assembled,
+                                          coarse_rtol=coarse_rtol, coarse_maxit=5000, seed=SEED)
+        self.mg = nh.nh_mg_create(ctx, self.op, self.opts)
+
+    def setup(self, u=None):
+        u = self.u if u is None else u
+        self.nh.nh_qdata_setup(self.ctx, self.op, dev(u))
+        self.nh.nh_mg_setup(self.ctx, self.mg)
+
+    def oracle_levels(self, u=None):
+        st = fem.qp_state(self.sps[0], self.mat, self.u if u is None else u)
+        levels = []
+        for i, sp in enumerate(self.sps):
+            m = self.masks[i]
+            A = (lambda s, mm: (lambda v: fem.jacobian_apply(s, st, v, mm)))(sp, m)
+            dinv = 1.0 / fem.diagonal(sp, st, m)
+            seed = inputs.splitmix_uniform(sp.n_dof, SEED)
+            seed[m] = 0.0
+            L = dict(A=A, dinv=dinv, mask=m, degree=self.opts.cheb_degree,
+                     lmax=solvers.estimate_lambda_max(A, dinv, seed, iters=self.opts.lanczos_iters))
+            if i + 1 < len(self.sps):
+                c = self.sps[i + 1]
+                L["restrict"] = (lambda f, cc: (lambda v: fem.restrict(f, cc, v)))(sp, c)
+                L["prolong"] = (lambda f, cc: (lambda v: fem.prolong(cc, f, v)))(sp, c)
+            levels.append(L)
+        return st, levels
+
+    def close(self):
+        self.nh.nh_mg_destroy(self.mg)
+        self.nh.nh_op_destroy(self.op)
+        self.nh.nh_space_destroy(self.space)
+
+
+@pytest.mark.parametrize("n,p,levels", [((3, 2, 3), 4, (4, 2, 1)), ((3, 3, 2), 3, (3, 2, 1)), ((4, 3, 3), 2, (2, 1))])
+@pytest.mark.parametrize("assembled", [1, 0])
+def test_lambda_and_vcycle(nhctx, n, p, levels, assembled):
+    ctx, _ = nhctx
+    P = Problem(ctx, n, p, levels, assembled=assembled)
+    P.setup()
+    _, L = P.oracle_levels()
+    for i in range(len(levels) - 1):
+        lm = P.nh.nh_mg_level_info(ctx, P.mg, i)[2]
+        assert abs(lm - L[i]["lmax"]) <= 1e-9 * L[i]["lmax"], (i, lm, L[i]["lmax"])
+    r = inputs.normal_vector(P.nd, seed=9)
+    r[P.masks[0]] = 0.0
+    z = torch.empty(P.nd, dtype=torch.float64, device="cuda")
+    P.nh.nh_mg_vcycle(ctx, P.mg, dev(r), z)
+    ref = solvers.vcycle(L, r, coarse_rtol=1e-14, coarse_maxit=5000)
+    assert rel(host(z), ref) < 1e-8
+    P.close()
+
+
+def test_mixed_vcycle_close_to_fp64(nhctx):
+    ctx, _ = nhctx
+    P64 = Problem(ctx, (3, 2, 3), 4, (4, 2, 1))
+    P32 = Problem(ctx, (3, 2, 3), 4, (4, 2, 1), mixed=1)
+    P64.setup()
+    P32.setup()
+    r = inputs.normal_vector(P64.nd, seed=4)
+    r[P64.masks[0]] = 0.0
+    z64 = torch.empty(P64.nd, dtype=torch.float64, device="cuda")
+    z32 = torch.empty(P64.nd, dtype=torch.float64, device="cuda")
+    P64.nh.nh_mg_vcycle(ctx, P64.mg, dev(r), z64)
+    P32.nh.nh_mg_vcycle(ctx, P32.mg, dev(r), z32)
+    assert rel(host(z32), host(z64)) < 1e-4
+    P64.close()
+    P32.close()
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_linear_solve_matches_direct(nhctx, mixed):
+    import scipy.sparse.linalg as spla
+    ctx, _ = nhctx
+    P = Problem(ctx, (3, 3, 2), 3, (3, 2, 1), mixed=mixed, coarse_rtol=1e-3)
+    P.setup()
+    st = fem.qp_state(P.sps[0], P.mat, P.u)
+    J = fem.assemble(P.sps[0], fem.element_matrices(P.sps[0], st), P.masks[0])
+    b = inputs.normal_vector(P.nd, seed=6)
+    b[P.masks[0]] = 0.0
+    x = torch.zeros(P.nd, dtype=torch.float64, device="cuda")
+    rep = P.nh.nh_linear_solve(ctx, P.mg, dev(b), x, rtol=1e-11, maxit=300, norm=1)
+    ref = spla.spsolve(J.tocsc(), b)
+    assert rel(host(x), ref) < 1e-7
+    assert rep.krylov_its < 100
+    P.close()
+
+
+@pytest.mark.parametrize("n,p,levels,steps,mixed,delta", [((4, 4, 4), 2, (2, 1), 1, 0, 0.01),
+                                                          ((2, 2, 3), 4, (4, 2, 1), 2, 0, 0.05),
+                                                          ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05),
+                                                          ((3, 2, 2), 3, (3, 2, 1), 1, 1, 0.03)])
+def test_newton_solve_matches_oracle(nhctx, n, p, levels, steps, mixed, delta):
+    """Uniaxial compression (x = 0 clamped, x = 1 pushed by delta), load-stepped."""
+    ctx, _ = nhctx
+    P = Problem(ctx, n, p, levels, mixed=mixed, coarse_rtol=1e-3)
+    P.opts.load_steps = steps
+    P.nh.nh_mg_destroy(P.mg)
+    P.mg = P.nh.nh_mg_create(ctx, P.op, P.opts)
+    g = inputs.uniaxial_bc(P.sps[0].node_dims, delta)
+    u = torch.zeros(P.nd, dtype=torch.float64, device="cuda")
+    rep = P.nh.nh_solve(ctx, P.mg, dev(g), u)
+    assert rep.rel_residual <= 1e-8 or rep.abs_residual <= 1e-13
+    assert rep.newton_its <= 12 * steps
+    # oracle: Newton with a direct solver, same load steps
+    uo = np.zeros(P.nd)
+    for k in range(1, steps + 1):
+        uo, _ = solvers.newton_direct(P.sps[0], P.mat, uo, P.masks[0], g * k / steps, rtol=1e-12)
+    assert rel(host(u), uo) < 1e-6
+    P.close()
