@@ -27,8 +27,12 @@
 namespace {
 
 // device scalar slots
+// (the coarsest PCG runs inside the V-cycle, i.e. inside an FCG step: the two
+// must not share slots)
 enum {
-  S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2, S_PR = 3, S_ZQ = 4, S_RR = 5, S_TMP = 6,
+  S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2,                   // PCG / Lanczos
+  S_FPQ = 8, S_FPR = 9, S_FZQ = 10, S_FRR = 11,      // FCG
+  S_TMP = 12,
   S_HIST = 16,            // Lanczos history: rz[k] at S_HIST + k, pq[k] at S_HIST + 64 + k
   S_LEN = S_HIST + 128
 };
@@ -616,8 +620,8 @@ static nh_status fcg(nh_mg mg, const double* b, double* x, double rtol, int maxi
   CK(cudaMemcpyAsync(p, z, 8 * n, cudaMemcpyDeviceToDevice, st));
   ST(nh_jacobian_apply(A, NH_F64, p, q));
   double nrm0 = 0.0;
-  ST(norm == 0 ? dot(mg, n, r, z, S_RR) : dot(mg, n, r, r, S_RR));
-  ST(read_sc(mg, S_RR, 1, &nrm0));
+  ST(norm == 0 ? dot(mg, n, r, z, S_FRR) : dot(mg, n, r, r, S_FRR));
+  ST(read_sc(mg, S_FRR, 1, &nrm0));
   nrm0 = sqrt(fabs(nrm0));
   if (!isfinite(nrm0)) return nh_fail(mg->ctx, NH_ERR_NAN, "FCG: non-finite initial residual");
   double nrm = nrm0;
@@ -628,19 +632,19 @@ static nh_status fcg(nh_mg mg, const double* b, double* x, double rtol, int maxi
     return NH_OK;
   }
   while (k < maxit) {
-    ST(dot(mg, n, p, q, S_PQ));
-    ST(dot(mg, n, p, r, S_PR));
-    CK(kv_cg_update<double>(st, n, p, q, x, r, mg->sc, S_PR, S_PQ));  // x += a p, r -= a q
+    ST(dot(mg, n, p, q, S_FPQ));
+    ST(dot(mg, n, p, r, S_FPR));
+    CK(kv_cg_update<double>(st, n, p, q, x, r, mg->sc, S_FPR, S_FPQ));  // x += a p, r -= a q
     mg->ctx->launches++;
     k++;
     ST(vcycle_fp64(mg, r, z));
-    ST(norm == 0 ? dot(mg, n, r, z, S_RR) : dot(mg, n, r, r, S_RR));
-    ST(read_sc(mg, S_RR, 1, &nrm));
+    ST(norm == 0 ? dot(mg, n, r, z, S_FRR) : dot(mg, n, r, r, S_FRR));
+    ST(read_sc(mg, S_FRR, 1, &nrm));
     nrm = sqrt(fabs(nrm));
     if (!isfinite(nrm)) return nh_fail(mg->ctx, NH_ERR_NAN, "FCG: non-finite residual");
     if (nrm <= rtol * nrm0) break;
-    ST(dot(mg, n, z, q, S_ZQ));
-    CK(kv_xpby_dev<double>(st, n, z, p, mg->sc, S_ZQ, S_PQ, -1.0));  // p = z - (z.q / p.q) p
+    ST(dot(mg, n, z, q, S_FZQ));
+    CK(kv_xpby_dev<double>(st, n, z, p, mg->sc, S_FZQ, S_FPQ, -1.0));  // p = z - (z.q / p.q) p
     mg->ctx->launches++;
     ST(nh_jacobian_apply(A, NH_F64, p, q));
   }
