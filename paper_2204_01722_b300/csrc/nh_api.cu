@@ -470,6 +470,22 @@ extern "C" nh_status nh_profile_read(nh_ctx ctx, double* total_ms, int64_t* laun
   return NH_OK;
 }
 
+nh_status nh_jacobian_apply_lift(nh_op op, const double* x, double* y) {
+  nh_ctx ctx = op->space->ctx;
+  nh_op root = op->parent ? op->parent : op;
+  if (!root->have_qd) return nh_fail(ctx, NH_ERR_STATE, "lift apply: no quadrature data");
+  OpArgs a = base_args(op);
+  a.in = x;
+  a.out = y;
+  a.prec = NH_F64;
+  a.lift = 1;
+  a.qd = root->qd;
+  NH_CUDA(ctx, cudaMemsetAsync(y, 0, 8 * op->space->n_dof, ctx->stream));
+  NH_CUDA(ctx, nh_launch_apply(op->space->P, op->space->Q, NH_F64, a, ctx->stream));
+  ctx->launches++;
+  return NH_OK;
+}
+
 extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* du_h, void* y_h) {
   if (!op || !du_h || !y_h) return NH_ERR_ARG;
   nh_ctx ctx = op->space->ctx;

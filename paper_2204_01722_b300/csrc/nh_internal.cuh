@@ -127,6 +127,7 @@ struct OpArgs {
   int prec;            // nh_prec of in/out vectors (apply, diagonal)
   int store;           // setup: write quadrature data
   int resid;           // setup: compute residual
+  int lift;            // apply: keep constrained inputs, leave constrained rows zero
   const Tab1D* tab;
 };
 
@@ -143,6 +144,10 @@ NH_DECLARE_P(2)
 NH_DECLARE_P(3)
 NH_DECLARE_P(4)
 NH_DECLARE_P(5)
+
+// y = J_full x on unconstrained rows, 0 on constrained rows, constrained inputs kept
+// (lifting of a Dirichlet increment); FP64 (nh_api.cu)
+nh_status nh_jacobian_apply_lift(nh_op op, const double* x, double* y);
 
 // transfer with the ABI's checks (nh_api.cu); dir 0 = prolong, 1 = restrict
 nh_status nh_transfer_internal(nh_space c, nh_space f, nh_prec prec, int dir, const void* in, void* out);

@@ -82,6 +82,16 @@ __global__ void k_mask_zero(int64_t nn, const uint8_t* __restrict__ bc, T* __res
   }
 }
 
+// unconstrained components of v are zeroed
+template <typename T>
+__global__ void k_mask_keep(int64_t nn, const uint8_t* __restrict__ bc, T* __restrict__ v) {
+  GRID_STRIDE(i, nn) {
+    const unsigned m = bc[i];
+    for (int c = 0; c < 3; c++)
+      if (!((m >> c) & 1u)) v[3 * i + c] = T(0);
+  }
+}
+
 // constrained components of v take the values of g (scaled by s)
 __global__ void k_lift(int64_t nn, const uint8_t* __restrict__ bc, double* __restrict__ v,
                        const double* __restrict__ g, double s) {
@@ -185,6 +195,9 @@ template <typename TI, typename TO>
 cudaError_t kv_convert(cudaStream_t st, int64_t n, const TI* x, TO* y) { L1((k_convert<TI, TO>), n, x, y); }
 template <typename T>
 cudaError_t kv_mask_zero(cudaStream_t st, int64_t nn, const uint8_t* bc, T* v) { L1(k_mask_zero<T>, nn, bc, v); }
+cudaError_t kv_mask_keep(cudaStream_t st, int64_t nn, const uint8_t* bc, double* v) {
+  L1(k_mask_keep<double>, nn, bc, v);
+}
 cudaError_t kv_lift(cudaStream_t st, int64_t nn, const uint8_t* bc, double* v, const double* g, double s) {
   L1(k_lift, nn, bc, v, g, s);
 }

@@ -20,6 +20,7 @@ template <typename TI, typename TO>
 cudaError_t kv_convert(cudaStream_t st, int64_t n, const TI* x, TO* y);
 template <typename T>
 cudaError_t kv_mask_zero(cudaStream_t st, int64_t nn, const uint8_t* bc, T* v);
+cudaError_t kv_mask_keep(cudaStream_t st, int64_t nn, const uint8_t* bc, double* v);
 cudaError_t kv_lift(cudaStream_t st, int64_t nn, const uint8_t* bc, double* v, const double* g, double s);
 template <typename T>
 cudaError_t kv_cheb(cudaStream_t st, int64_t n, double c1, double c2, const T* dinv, const T* r, T* d, T* x);

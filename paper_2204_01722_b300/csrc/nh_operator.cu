@@ -36,10 +36,10 @@ using nhpw::pointwise;
 // ---------------------------------------------------------------------------
 
 // E then B_I: gather the element's P^3 nodes (masking constrained components if
-// MASK) and interpolate to the Q^3 points.  Leaves the point values in U
+// mask_in) and interpolate to the Q^3 points.  Leaves the point values in U
 // (registers, this thread's column) and in bC; remembers node ids in nid.
-template <int P, int Q, typename T, bool MASK>
-__device__ __forceinline__ void gather_interp(bool live, int64_t e, int a, int b, const int* __restrict__ emap,
+template <int P, int Q, typename T>
+__device__ __forceinline__ void gather_interp(bool live, bool mask_in, int64_t e, int a, int b, const int* __restrict__ emap,
                                               const uint8_t* __restrict__ bc, const T* __restrict__ src,
                                               const KTab<P, Q, T>& tab, T* bA, T* bB, T* bC, T (&U)[3][Q],
                                               int (&nid)[P]) {
@@ -50,7 +50,7 @@ __device__ __forceinline__ void gather_interp(bool live, int64_t e, int a, int b
     for (int k = 0; k < P; k++) {
       int n = live ? __ldg(&emap[e * P3 + (k * P + b) * P + a]) : 0;
       nid[k] = n;
-      unsigned m = (MASK && live) ? (unsigned)__ldg(&bc[n]) : 0u;
+      unsigned m = (mask_in && live) ? (unsigned)__ldg(&bc[n]) : 0u;
 #pragma unroll
       for (int c = 0; c < 3; c++) r[c][k] = (live && !((m >> c) & 1u)) ? src[3 * (int64_t)n + c] : T(0);
     }
@@ -174,7 +174,7 @@ template <int P, int Q, typename T, int LAYOUT>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     k_jacobian_apply(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
                      const T* __restrict__ qd, int64_t qstride, const KTab<P, Q, T> tab, const T* __restrict__ du,
-                     T* __restrict__ y) {
+                     T* __restrict__ y, int lift) {
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 
   T U[3][Q];
   int nid[P];
-  gather_interp<P, Q, T, true>(live, e, a, b, emap, bc, du, tab, bA, bB, bC, U, nid);
+  gather_interp<P, Q, T>(live, !lift, e, a, b, emap, bc, du, tab, bA, bB, bC, U, nid);
   __syncthreads();
   T Fz[3][Q];
   const T* qe = qd + (live ? e : 0) * Q3 + b * Q + a;
@@ -221,10 +221,11 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         const int64_t dof = 3 * (int64_t)n + c;
-        if ((m >> c) & 1u)
-          y[dof] = du[dof];  // identity row; every writer stores the same value
-        else
+        if ((m >> c) & 1u) {
+          if (!lift) y[dof] = du[dof];  // identity row; every writer stores the same value
+        } else {
           atomicAdd(&y[dof], out[c][k]);
+        }
       }
     }
   }
@@ -296,9 +297,9 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 
   double UX[3][Q], UU[3][Q];
   int nid[P];
-  gather_interp<P, Q, double, false>(live, e, a, b, emap, bc, coords, tab, bA, bB, bX, UX, nid);
+  gather_interp<P, Q, double>(live, false, e, a, b, emap, bc, coords, tab, bA, bB, bX, UX, nid);
   __syncthreads();
-  gather_interp<P, Q, double, false>(live, e, a, b, emap, bc, u, tab, bA, bB, bU, UU, nid);
+  gather_interp<P, Q, double>(live, false, e, a, b, emap, bc, u, tab, bA, bB, bU, UU, nid);
   __syncthreads();
 
   const double lam = live ? lamv[e] : 0.0, mu = live ? muv[e] : 0.0;
@@ -562,7 +563,7 @@ cudaError_t apply_launch(const OpArgs& A, cudaStream_t s) {
   cudaError_t e = prep<k_jacobian_apply<P, Q, T, LAYOUT>>(smem);
   if (e != cudaSuccess) return e;
   k_jacobian_apply<P, Q, T, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
-      A.ne, A.emap, A.bc, (const T*)A.qd, A.qstride, tab, (const T*)A.in, (T*)A.out);
+      A.ne, A.emap, A.bc, (const T*)A.qd, A.qstride, tab, (const T*)A.in, (T*)A.out, A.lift);
   return cudaGetLastError();
 }
 

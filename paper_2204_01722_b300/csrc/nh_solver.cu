@@ -682,6 +682,15 @@ static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// ||F(v)||_2 with F evaluated into `out`; non-finite when v inverts an element
+static nh_status resid_norm(nh_mg mg, const double* v, const double* g, double* out, double* nrm) {
+  ST(nh_residual(mg->fine, v, g, out));
+  double s2 = 0.0;
+  ST(dot_host(mg, mg->L[0].n, out, out, &s2));
+  *nrm = sqrt(s2);
+  return NH_OK;
+}
+
 extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_report* rep) {
   if (!mg || !u) return NH_ERR_ARG;
   nh_ctx ctx = mg->ctx;
@@ -692,7 +701,7 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
   const nh_mg_opts& o = mg->o;
   const int64_t n = fs->n_dof;
   double *r = mg->fu, *gk = mg->fg, *du = mg->fx, *rhs = mg->fb;
-  double *ut = mg->ft, *rt = mg->fs;  // trial point and its residual
+  double *ut = mg->ft, *rt = mg->fs;  // trial point and its residual; ut also holds the lift w
   nh_solve_report R;
   memset(&R, 0, sizeof(R));
   const double T0 = now_s();
@@ -700,8 +709,33 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
   nh_status status = NH_OK;
   const int K = std::max(1, o.load_steps);
   double rel = 0.0, nr = 0.0;
-  for (int step = 1; step <= K && status == NH_OK; step++) {
-    const double t = (double)step / K;
+  double t_prev = 0.0;
+  int halvings = 0;
+  auto setup = [&](const double* v, double* minJ) -> nh_status {
+    const double t1 = now_s();
+    nh_status s = nh_qdata_setup(F, v, minJ);
+    if (s == NH_OK) s = nh_mg_setup(mg);
+    tS += now_s() - t1;
+    return s;
+  };
+  auto krylov = [&](const double* b, double* x) -> nh_status {
+    const double t1 = now_s();
+    int kits = 0;
+    double krel = 0.0;
+    mg->vcycles = 0;
+    mg->coarse_its = 0;
+    CK(cudaMemsetAsync(x, 0, 8 * n, st));
+    nh_status s = fcg(mg, b, x, o.krylov_rtol, o.krylov_maxit, 0, &kits, &krel);
+    R.krylov_its += kits;
+    R.vcycles += mg->vcycles;
+    R.coarse_its += mg->coarse_its;
+    tK += now_s() - t1;
+    return s;
+  };
+  int step = 0;
+  while (step < K && status == NH_OK) {
+    const double t_target = (double)(step + 1) / K;
+    const double t = t_prev + (t_target - t_prev) / (double)(1 << halvings);
     double t1 = now_s();
     if (g_bc) {
       CK(cudaMemcpyAsync(gk, g_bc, 8 * n, cudaMemcpyDeviceToDevice, st));
@@ -709,82 +743,122 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
     } else {
       CK(cudaMemsetAsync(gk, 0, 8 * n, st));
     }
-    CK(kv_lift(st, fs->n_nodes, fs->bc, u, gk, 1.0));
+    ctx->launches++;
+    tR += now_s() - t1;
+    // --- predictor: carry the boundary increment w = g_k - u (constrained DoFs) into
+    // the interior through the tangent at the current state:
+    //   J_uu du = -(F_u(u) + J_uc w),   u <- u + w + du
+    double minJ = 0.0;
+    status = setup(u, &minJ);
+    if (status != NH_OK) break;
+    t1 = now_s();
+    CK(cudaMemcpyAsync(ut, gk, 8 * n, cudaMemcpyDeviceToDevice, st));
+    CK(kv_axpby<double>(st, n, -1.0, u, 1.0, ut));  // ut = g_k - u
+    CK(kv_mask_keep(st, fs->n_nodes, fs->bc, ut));   // w: constrained entries only
     ctx->launches += 2;
     ST(nh_residual(F, u, gk, r));
-    double nr0 = 0.0;
-    ST(dot_host(mg, n, r, r, &nr0));
-    nr0 = sqrt(nr0);
-    nr = nr0;
+    CK(kv_mask_zero<double>(st, fs->n_nodes, fs->bc, r));  // F_u(u)
+    ST(nh_jacobian_apply_lift(F, ut, rhs));                 // J_uc w
+    CK(kv_axpby<double>(st, n, -1.0, r, -1.0, rhs));       // rhs = -(F_u + J_uc w)
+    ctx->launches += 2;
     tR += now_s() - t1;
+    status = krylov(rhs, du);
+    if (status != NH_OK) break;
+    t1 = now_s();
+    CK(kv_axpby<double>(st, n, 1.0, ut, 1.0, du));  // du = w + du
+    CK(cudaMemcpyAsync(ut, u, 8 * n, cudaMemcpyDeviceToDevice, st));
+    CK(kv_axpby<double>(st, n, 1.0, du, 1.0, ut));  // ut = u + w + du
+    ctx->launches += 2;
+    double nr0 = 0.0;
+    ST(resid_norm(mg, ut, gk, r, &nr0));
+    tR += now_s() - t1;
+    if (!isfinite(nr0)) {
+      // the predicted state inverts an element: halve this load increment
+      if (++halvings > 8) {
+        status = nh_fail(ctx, NH_ERR_INVERTED, "nh_solve: load increment cannot be halved further");
+        break;
+      }
+      continue;
+    }
+    CK(cudaMemcpyAsync(u, ut, 8 * n, cudaMemcpyDeviceToDevice, st));
+    nr = nr0;
+    // --- Newton corrector at fixed t
     int it = 0;
     while (!(nr <= o.newton_rtol * nr0) && !(nr <= o.newton_atol)) {
       if (it >= o.newton_maxit) {
         status = nh_fail(ctx, NH_ERR_NOT_CONVERGED, "nh_solve: Newton iteration limit");
         break;
       }
-      if (!isfinite(nr)) {
-        status = nh_fail(ctx, NH_ERR_NAN, "nh_solve: non-finite residual");
-        break;
-      }
-      t1 = now_s();
-      double minJ = 0.0;
-      status = nh_qdata_setup(F, u, &minJ);
+      status = setup(u, &minJ);
       if (status != NH_OK) break;
-      status = nh_mg_setup(mg);
-      if (status != NH_OK) break;
-      tS += now_s() - t1;
-      // J du = -r
-      t1 = now_s();
       CK(kv_axpby<double>(st, n, -1.0, r, 0.0, rhs));  // rhs = -F(u)
-      CK(cudaMemsetAsync(du, 0, 8 * n, st));
       ctx->launches++;
-      int kits = 0;
-      double krel = 0.0;
-      mg->vcycles = 0;
-      mg->coarse_its = 0;
-      status = fcg(mg, rhs, du, o.krylov_rtol, o.krylov_maxit, 0, &kits, &krel);
-      R.krylov_its += kits;
-      R.vcycles += mg->vcycles;
-      R.coarse_its += mg->coarse_its;
-      tK += now_s() - t1;
+      status = krylov(rhs, du);
       if (status != NH_OK) break;
-      // line search along du (secant on phi(a) = F(u + a du) . du)
+      // line search: backtrack while the trial state inverts, then one secant
+      // step on phi(a) = F(u + a du) . du (critical point)
       t1 = now_s();
-      double alpha = 1.0, phi0 = 0.0, phi1 = 0.0;
-      CK(cudaMemcpyAsync(ut, u, 8 * n, cudaMemcpyDeviceToDevice, st));
-      CK(kv_axpby<double>(st, n, 1.0, du, 1.0, ut));
-      ctx->launches++;
-      ST(nh_residual(F, ut, gk, rt));
+      double at = 1.0, nrt = 0.0;
+      for (int bt = 0;; bt++) {
+        CK(cudaMemcpyAsync(ut, u, 8 * n, cudaMemcpyDeviceToDevice, st));
+        CK(kv_axpby<double>(st, n, at, du, 1.0, ut));
+        ctx->launches++;
+        ST(resid_norm(mg, ut, gk, rt, &nrt));
+        if (isfinite(nrt)) break;
+        if (bt >= 12) {
+          status = nh_fail(ctx, NH_ERR_INVERTED, "nh_solve: every trial step inverts an element");
+          break;
+        }
+        at *= 0.5;
+      }
+      if (status != NH_OK) break;
+      double alpha = at;
       if (o.line_search) {
+        double phi0 = 0.0, phi1 = 0.0;
         ST(dot_host(mg, n, r, du, &phi0));
         ST(dot_host(mg, n, rt, du, &phi1));
         if (phi0 * phi1 < 0.0) {
-          alpha = phi0 / (phi0 - phi1);
-          if (!isfinite(alpha)) alpha = 1.0;
-          alpha = std::min(1.5, std::max(0.1, alpha));
+          const double a = at * phi0 / (phi0 - phi1);
+          if (isfinite(a)) alpha = std::min(at < 1.0 ? at : 1.5, std::max(0.1 * at, a));
         }
       }
-      if (alpha == 1.0) {
+      bool took_trial = (alpha == at);
+      if (!took_trial) {
+        CK(cudaMemcpyAsync(rhs, u, 8 * n, cudaMemcpyDeviceToDevice, st));
+        CK(kv_axpby<double>(st, n, alpha, du, 1.0, rhs));
+        ctx->launches++;
+        double nra = 0.0;
+        ST(resid_norm(mg, rhs, gk, r, &nra));
+        if (isfinite(nra)) {
+          CK(cudaMemcpyAsync(u, rhs, 8 * n, cudaMemcpyDeviceToDevice, st));
+          nr = nra;
+        } else {
+          took_trial = true;
+          alpha = at;
+        }
+      }
+      if (took_trial) {
         CK(cudaMemcpyAsync(u, ut, 8 * n, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(r, rt, 8 * n, cudaMemcpyDeviceToDevice, st));
-      } else {
-        CK(kv_axpby<double>(st, n, alpha, du, 1.0, u));
-        ctx->launches++;
-        ST(nh_residual(F, u, gk, r));
+        nr = nrt;
       }
-      double nr2 = 0.0;
-      ST(dot_host(mg, n, r, r, &nr2));
-      nr = sqrt(nr2);
       tR += now_s() - t1;
       it++;
       R.newton_its++;
       if (o.verbose)
-        fprintf(stderr, "nh_solve step %d newton %d |F| %.3e rel %.3e fcg %d vcyc %d coarse %d alpha %.3f minJ %.3f\n",
-                step, it, nr, nr / nr0, kits, mg->vcycles, mg->coarse_its, alpha, minJ);
+        fprintf(stderr, "nh_solve t %.4f newton %d |F| %.3e rel %.3e fcg %d vcyc %d coarse %d alpha %.3f minJ %.3f\n",
+                t, it, nr, nr / nr0, R.krylov_its, mg->vcycles, mg->coarse_its, alpha, minJ);
     }
     rel = nr0 > 0 ? nr / nr0 : 0.0;
-    R.load_steps = step;
+    if (status != NH_OK) break;
+    t_prev = t;
+    if (halvings > 0 && t < t_target) {
+      halvings--;  // retry the rest of the increment with a larger step
+    } else {
+      halvings = 0;
+      step++;
+      R.load_steps = step;
+    }
   }
   CK(cudaStreamSynchronize(st));
   R.status = status;
