@@ -268,6 +268,7 @@ def run_nh(args):
                                   "tflops": round(tfl, 3),
                                   "alu_frac": round(tfl / (FP64_PEAK_TFLOPS if pr == "f64" else FP32_PEAK_TFLOPS), 4)})
                 c.close()
+        solve = run_solves(nh, torch, ctx, stream) if (args.solve and rank == 0) else None
         nh.nh_destroy(ctx)
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 4), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -285,9 +286,43 @@ def run_nh(args):
             out["cpu_baseline"] = oracle_baseline(p, n, args.cpu_seconds)
         if sweep:
             out["sweep"] = sweep
+        if solve:
+            out["solve"] = solve
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# solve time to relative residual 1e-8, plain FP64 p-MG vs the chosen solver
+# ---------------------------------------------------------------------------
+def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusions=False, learned=None):
+    """Load-stepped Newton-Krylov p-MG solve of uniaxial compression; returns the
+    reports of the plain FP64 solver and of the chosen one (mixed precision)."""
+    from paper_2204_01722_b300 import inputs
+    V = inputs.box_vertices(n, n, n)
+    sp, nn, nd = nh.nh_space_box(ctx, n, n, n, V, p, p + 1)
+    N = p * n + 1
+    nh.nh_space_set_dirichlet(ctx, sp, inputs.uniaxial_mask((N, N, N)))
+    E = inputs.inclusion_modulus(n, n, n, seed=SEED) if inclusions else None
+    op = nh.nh_op_create(ctx, sp, NU, E, 1.0)
+    g = torch.from_numpy(inputs.uniaxial_bc((N, N, N), delta)).cuda()
+    out = {}
+    for name, mixed in (("plain_fp64", 0), ("chosen_mixed", 1)):
+        o = nh.nh_mg_default_opts(ctx, op, mixed=mixed, load_steps=steps)
+        mg = nh.nh_mg_create(ctx, op, o)
+        u = torch.zeros(nd, dtype=torch.float64, device="cuda")
+        rep = nh.nh_solve(ctx, mg, g, u, check=False)
+        stream.synchronize()
+        out[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.as_dict().items()}
+        nh.nh_mg_destroy(mg)
+    nh.nh_op_destroy(op)
+    nh.nh_space_destroy(sp)
+    out["workload"] = (f"Q{p} on {n}^3 ({nd} DoF), {'inclusions E 1e3/1, ' if inclusions else ''}"
+                       f"{int(delta * 100)}% uniaxial compression in {steps} load steps, p-MG "
+                       f"{p}->2->1, Chebyshev(3)-Jacobi, Q1 coarse Jacobi-PCG 1e-3, FCG 1e-3, Newton to 1e-8")
+    out["speedup"] = round(out["plain_fp64"]["seconds"] / max(out["chosen_mixed"]["seconds"], 1e-9), 3)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -355,6 +390,7 @@ def main():
     ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
     ap.add_argument("--no-sweep", dest="sweep", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-solve", dest="solve", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per apply from an ncu capture of this kernel (reported as is)")
