@@ -239,6 +239,49 @@ nh_status nh_linear_solve(nh_mg mg, const double* b, double* x, double rtol, int
  * Errors: NH_ERR_INVERTED, NH_ERR_NOT_CONVERGED, NH_ERR_NAN (report filled). */
 nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_report* report);
 
+/* ---- learned coarse correction (not in the paper) ----------------------- */
+
+typedef struct nh_net_s* nh_net;
+
+/* A 3-D convolution U-Net on the Q1 vertex grid (N^3 nodes, N odd): input
+ * 4 channels (restricted residual x, y, z scaled by its RMS, and log10 of the
+ * node-averaged Young's modulus), output 3 channels (error estimate in the same
+ * scaling).  `levels` resolutions N, (N-1)/2+1, ...; channels[l] in
+ * {8, 16, 32, 48, 64}; 3x3x3 convolutions with zero padding, stride-2
+ * vertex-centred downsampling, linear upsampling, additive skips, ReLU.
+ * bf16 = 1: activations and weights in BF16, FP32 accumulation (0: FP32).
+ * Weights He-normal from a splitmix64 stream of `seed`, biases zero.
+ * Parameter layout: layers in network order, each W [Cout][Cin][27] (tap
+ * kx + 3 (ky + 3 kz)) then b [Cout].  Fields are channel-major [C][N^3], x fastest. */
+nh_status nh_net_create(nh_ctx ctx, int N, int levels, const int* channels, int bf16, uint64_t seed, nh_net* out);
+nh_status nh_net_destroy(nh_net net);
+nh_status nh_net_param_count(nh_net net, int64_t* count);
+/* FP32 master parameters to / from HOST memory (set resets the Adam state). */
+nh_status nh_net_get_params(nh_net net, float* host);
+nh_status nh_net_set_params(nh_net net, const float* host);
+/* out [3][N^3] = net(in [4][N^3]); device float pointers. */
+nh_status nh_net_forward(nh_net net, const float* in, float* out);
+/* Gradient of the relative squared error ||net(in) - target||^2 / ||target||^2
+ * with respect to the parameters, to device float dparams [count]; the loss to
+ * *loss (HOST, may be NULL; synchronises when given). */
+nh_status nh_net_gradient(nh_net net, const float* in, const float* target, float* dparams, double* loss);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on the mean loss of `batch`
+ * samples in [batch][4][N^3] / [batch][3][N^3]. */
+nh_status nh_net_train_step(nh_net net, int batch, const float* in, const float* target, float lr, double* loss);
+/* Insert the network as an extra flexible-CG preconditioner stage of nh_solve /
+ * nh_linear_solve (NULL removes it): z1 = P net(R r) (R, P through the p levels
+ * down to the Q1 level), accepted when ||r - J z1|| < ||r||, then
+ * z = z1 + V-cycle(r - J z1); otherwise z = V-cycle(r).  Needs a hierarchy
+ * ending at p = 1 whose vertex grid matches the network's N. */
+nh_status nh_mg_set_learned(nh_mg mg, nh_net net);
+/* Training pairs from the linear system J x = b at the current quadrature data:
+ * solves to ||r|| <= 1e-10 ||b|| for x*, then runs FCG + V-cycle to
+ * krylov_rtol from zero and, before every preconditioner application, stores
+ * the network input for the residual r_k and the target (x* - x_k injected at
+ * the vertex nodes, in the input's scaling).  feats: device float
+ * [max_pairs][4][N^3], targets [max_pairs][3][N^3]; *n_pairs = pairs written. */
+nh_status nh_mg_collect(nh_mg mg, const double* b, int max_pairs, float* feats, float* targets, int* n_pairs);
+
 /* ---- allocation-free variant ------------------------------------------ */
 
 /* Largest n accepted by nh_dot_noalloc (2^28 elements). */

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "nh_krylov.cuh"
+#include "nh_net.cuh"
 
 namespace {
 
@@ -70,6 +71,11 @@ struct nh_mg_s {
   double *fx = nullptr, *fu = nullptr, *fg = nullptr, *fb = nullptr, *ft = nullptr, *fs = nullptr;  // Newton
   bool setup_done = false;
   int vcycles = 0, coarse_its = 0;
+  // learned stage
+  nh_net net = nullptr;
+  float *feat = nullptr, *nout = nullptr, *logE = nullptr;
+  double *lz1 = nullptr, *lw = nullptr, *lxs = nullptr, *lx = nullptr, *lt = nullptr;
+  int acc = 0, rej = 0;
 };
 
 namespace {
@@ -442,6 +448,9 @@ extern "C" nh_status nh_mg_destroy(nh_mg mg) {
   cudaFree(mg->part);
   cudaFreeHost(mg->hsc);
   for (double* p : {mg->fr, mg->fz, mg->fp, mg->fq, mg->fx, mg->fu, mg->fg, mg->fb, mg->ft, mg->fs}) cudaFree(p);
+  for (void* p : {(void*)mg->feat, (void*)mg->nout, (void*)mg->logE, (void*)mg->lz1, (void*)mg->lw, (void*)mg->lxs,
+                  (void*)mg->lx, (void*)mg->lt})
+    cudaFree(p);
   delete mg;
   return NH_OK;
 }
@@ -606,9 +615,102 @@ extern "C" nh_status nh_mg_vcycle(nh_mg mg, const double* r, double* z) {
   return vcycle_fp64(mg, r, z);
 }
 
+// ---- learned stage ---------------------------------------------------------------
+struct Collect {
+  const double* xs;  // converged solution
+  float* feats;
+  float* tgts;
+  int max, n;
+};
+
+// network input for the fine residual r: restrict through the levels to Q1,
+// scale by the RMS of the restricted residual.  Returns the scale (0 if r = 0).
+static nh_status learned_features(nh_mg mg, const double* r, float* feat, double* scale) {
+  cudaStream_t st = mg->ctx->stream;
+  const double* cur = r;
+  for (size_t l = 0; l + 1 < mg->L.size(); l++) {
+    Level& c = mg->L[l + 1];
+    ST(nh_transfer_internal(c.space, mg->L[l].space, NH_F64, 1, cur, c.w[4]));
+    CK(kv_mask_zero<double>(st, c.nn, c.space->bc, c.w[4]));
+    mg->ctx->launches++;
+    cur = c.w[4];
+  }
+  Level& c = mg->L.back();
+  double rr = 0.0;
+  ST(dot_host(mg, c.n, cur, cur, &rr));
+  *scale = sqrt(rr / (double)c.n);
+  if (!(*scale > 0.0) || !isfinite(*scale)) {
+    *scale = 0.0;
+    return NH_OK;
+  }
+  CK(kn_features(st, c.nn, cur, 1.0 / *scale, mg->logE, feat));
+  mg->ctx->launches++;
+  return NH_OK;
+}
+
+static nh_status vcycle_fp64(nh_mg mg, const double* r, double* z);
+
+// z = M r with the learned stage in front of the V-cycle (see nh_mg_set_learned)
+static nh_status precond(nh_mg mg, const double* r, double* z) {
+  if (!mg->net) return vcycle_fp64(mg, r, z);
+  cudaStream_t st = mg->ctx->stream;
+  double scale = 0.0;
+  ST(learned_features(mg, r, mg->feat, &scale));
+  if (scale == 0.0) return vcycle_fp64(mg, r, z);
+  ST(nh_net_forward_internal(mg->net, mg->feat, mg->nout));
+  Level& c = mg->L.back();
+  CK(kn_from_net(st, c.nn, mg->nout, scale, c.w[3]));
+  mg->ctx->launches++;
+  const double* cur = c.w[3];
+  for (int l = (int)mg->L.size() - 2; l >= 0; l--) {
+    double* out = l == 0 ? mg->lz1 : mg->L[l].w[4];
+    ST(nh_transfer_internal(mg->L[l + 1].space, mg->L[l].space, NH_F64, 0, cur, out));
+    CK(kv_mask_zero<double>(st, mg->L[l].nn, mg->L[l].space->bc, out));
+    mg->ctx->launches++;
+    cur = out;
+  }
+  const int64_t n = mg->L[0].n;
+  ST(nh_jacobian_apply(mg->fine, NH_F64, mg->lz1, mg->lw));
+  CK(kv_axpby<double>(st, n, 1.0, r, -1.0, mg->lw));  // w = r - J z1
+  mg->ctx->launches++;
+  double nw = 0.0, nr = 0.0;
+  ST(dot_host(mg, n, mg->lw, mg->lw, &nw));
+  ST(dot_host(mg, n, r, r, &nr));
+  if (isfinite(nw) && nw < nr) {
+    ST(vcycle_fp64(mg, mg->lw, z));
+    CK(kv_axpby<double>(st, n, 1.0, mg->lz1, 1.0, z));
+    mg->ctx->launches++;
+    mg->acc++;
+  } else {
+    ST(vcycle_fp64(mg, r, z));
+    mg->rej++;
+  }
+  return NH_OK;
+}
+
+static nh_status record_pair(nh_mg mg, Collect* col, const double* r, const double* x) {
+  if (!col || col->n >= col->max) return NH_OK;
+  cudaStream_t st = mg->ctx->stream;
+  Level& c = mg->L.back();
+  const int64_t nc = c.nn;
+  float* f = col->feats + (int64_t)col->n * 4 * nc;
+  float* t = col->tgts + (int64_t)col->n * 3 * nc;
+  double scale = 0.0;
+  ST(learned_features(mg, r, f, &scale));
+  if (scale == 0.0) return NH_OK;
+  const int64_t n = mg->L[0].n;
+  CK(cudaMemcpyAsync(mg->lt, col->xs, 8 * n, cudaMemcpyDeviceToDevice, st));
+  CK(kv_axpby<double>(st, n, -1.0, x, 1.0, mg->lt));  // x* - x
+  nh_space fs = mg->L[0].space;
+  CK(kn_inject(st, c.space->Nx, fs->p, fs->Nx, mg->lt, 1.0 / scale, t));
+  mg->ctx->launches += 2;
+  col->n++;
+  return NH_OK;
+}
+
 // FCG(1): J x = b, x in/out; returns iterations, final relative norm
 static nh_status fcg(nh_mg mg, const double* b, double* x, double rtol, int maxit, int norm, int* its_out,
-                     double* rel_out) {
+                     double* rel_out, Collect* col = nullptr) {
   cudaStream_t st = mg->ctx->stream;
   nh_op A = mg->fine;
   const int64_t n = mg->L[0].n;
@@ -616,7 +718,8 @@ static nh_status fcg(nh_mg mg, const double* b, double* x, double rtol, int maxi
   ST(nh_jacobian_apply(A, NH_F64, x, r));
   CK(kv_axpby<double>(st, n, 1.0, b, -1.0, r));  // r = b - A x
   mg->ctx->launches++;
-  ST(vcycle_fp64(mg, r, z));
+  ST(record_pair(mg, col, r, x));
+  ST(precond(mg, r, z));
   CK(cudaMemcpyAsync(p, z, 8 * n, cudaMemcpyDeviceToDevice, st));
   ST(nh_jacobian_apply(A, NH_F64, p, q));
   double nrm0 = 0.0;
@@ -637,7 +740,8 @@ static nh_status fcg(nh_mg mg, const double* b, double* x, double rtol, int maxi
     CK(kv_cg_update<double>(st, n, p, q, x, r, mg->sc, S_FPR, S_FPQ));  // x += a p, r -= a q
     mg->ctx->launches++;
     k++;
-    ST(vcycle_fp64(mg, r, z));
+    ST(record_pair(mg, col, r, x));
+    ST(precond(mg, r, z));
     ST(norm == 0 ? dot(mg, n, r, z, S_FRR) : dot(mg, n, r, r, S_FRR));
     ST(read_sc(mg, S_FRR, 1, &nrm));
     nrm = sqrt(fabs(nrm));
@@ -660,6 +764,7 @@ extern "C" nh_status nh_linear_solve(nh_mg mg, const double* b, double* x, doubl
   CK(cudaSetDevice(mg->ctx->device));
   auto t0 = std::chrono::steady_clock::now();
   mg->vcycles = mg->coarse_its = 0;
+  mg->acc = mg->rej = 0;
   int its = 0;
   double rel = 0.0;
   nh_status s = fcg(mg, b, x, rtol, maxit, norm, &its, &rel);
@@ -672,6 +777,8 @@ extern "C" nh_status nh_linear_solve(nh_mg mg, const double* b, double* x, doubl
     rep->rel_residual = rel;
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     rep->t_krylov = rep->seconds;
+    rep->learned_accepted = mg->acc;
+    rep->learned_rejected = mg->rej;
   }
   if (s == NH_OK && rel > rtol) s = nh_fail(mg->ctx, NH_ERR_NOT_CONVERGED, "nh_linear_solve: maxit reached");
   if (rep) rep->status = s;
@@ -704,6 +811,7 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
   double *ut = mg->ft, *rt = mg->fs;  // trial point and its residual; ut also holds the lift w
   nh_solve_report R;
   memset(&R, 0, sizeof(R));
+  mg->acc = mg->rej = 0;
   const double T0 = now_s();
   double tS = 0, tK = 0, tR = 0;
   nh_status status = NH_OK;
@@ -868,6 +976,89 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
   R.t_setup = tS;
   R.t_krylov = tK;
   R.t_residual = tR;
+  R.learned_accepted = mg->acc;
+  R.learned_rejected = mg->rej;
   if (rep) *rep = R;
   return status;
+}
+
+// ---------------------------------------------------------------------------
+// learned stage: buffers, ABI
+// ---------------------------------------------------------------------------
+static nh_status learned_buffers(nh_mg mg) {
+  if (mg->feat) return NH_OK;
+  Level& c = mg->L.back();
+  nh_space fs = mg->L[0].space;
+  if (mg->L.size() < 2 || c.p != 1 || fs->nx != fs->ny || fs->nx != fs->nz || !(fs->nx % 2 == 0))
+    return nh_fail(mg->ctx, NH_ERR_UNSUPPORTED,
+                   "learned stage: needs a hierarchy ending at p = 1 on an n^3 mesh with n even");
+  const int64_t nc = c.nn, n = mg->L[0].n;
+  nh_status s;
+  for (void** v : {(void**)&mg->feat, (void**)&mg->logE})
+    if ((s = dalloc(mg, v, sizeof(float) * 4 * nc)) != NH_OK) return s;
+  if ((s = dalloc(mg, (void**)&mg->nout, sizeof(float) * 3 * nc)) != NH_OK) return s;
+  for (double** v : {&mg->lz1, &mg->lw, &mg->lxs, &mg->lx, &mg->lt})
+    if ((s = dalloc(mg, (void**)v, 8 * n)) != NH_OK) return s;
+  // log10 E at the vertices: mean over the adjacent elements, E = 2 mu (1 + nu)
+  nh_op root = mg->fine;
+  std::vector<double> mu((size_t)fs->ne);
+  CK(cudaMemcpy(mu.data(), root->mu, 8 * fs->ne, cudaMemcpyDeviceToHost));
+  const int nx = fs->nx, V = nx + 1;
+  std::vector<float> le((size_t)nc, 0.f);
+  for (int k = 0; k < V; k++)
+    for (int j = 0; j < V; j++)
+      for (int i = 0; i < V; i++) {
+        double acc = 0.0;
+        int cnt = 0;
+        for (int dk = -1; dk <= 0; dk++)
+          for (int dj = -1; dj <= 0; dj++)
+            for (int di = -1; di <= 0; di++) {
+              const int ei = i + di, ej = j + dj, ek = k + dk;
+              if (ei < 0 || ej < 0 || ek < 0 || ei >= nx || ej >= nx || ek >= nx) continue;
+              acc += log10(2.0 * mu[ei + (int64_t)nx * (ej + (int64_t)nx * ek)] * (1.0 + root->nu));
+              cnt++;
+            }
+        le[i + (int64_t)V * (j + (int64_t)V * k)] = (float)(acc / cnt);
+      }
+  CK(cudaMemcpy(mg->logE, le.data(), sizeof(float) * nc, cudaMemcpyHostToDevice));
+  return NH_OK;
+}
+
+extern "C" nh_status nh_mg_set_learned(nh_mg mg, nh_net net) {
+  if (!mg) return NH_ERR_ARG;
+  if (!net) {
+    mg->net = nullptr;
+    return NH_OK;
+  }
+  CK(cudaSetDevice(mg->ctx->device));
+  ST(learned_buffers(mg));
+  if (nh_net_grid(net) != (int)mg->L.back().space->Nx)
+    return nh_fail(mg->ctx, NH_ERR_ARG, "nh_mg_set_learned: network grid does not match the Q1 vertex grid");
+  mg->net = net;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_mg_collect(nh_mg mg, const double* b, int max_pairs, float* feats, float* targets,
+                                   int* n_pairs) {
+  if (!mg || !b || !feats || !targets || !n_pairs || max_pairs < 1) return NH_ERR_ARG;
+  if (!mg->setup_done) return nh_fail(mg->ctx, NH_ERR_STATE, "nh_mg_collect: call nh_mg_setup first");
+  CK(cudaSetDevice(mg->ctx->device));
+  ST(learned_buffers(mg));
+  nh_net keep = mg->net;
+  mg->net = nullptr;  // pairs describe the plain V-cycle's iterates
+  const int64_t n = mg->L[0].n;
+  cudaStream_t st = mg->ctx->stream;
+  int its = 0;
+  double rel = 0.0;
+  CK(cudaMemsetAsync(mg->lxs, 0, 8 * n, st));
+  nh_status s = fcg(mg, b, mg->lxs, 1e-10, 2000, 1, &its, &rel);
+  if (s == NH_OK) {
+    Collect col{mg->lxs, feats, targets, max_pairs, 0};
+    CK(cudaMemsetAsync(mg->lx, 0, 8 * n, st));
+    s = fcg(mg, b, mg->lx, mg->o.krylov_rtol, std::min(mg->o.krylov_maxit, max_pairs), 0, &its, &rel, &col);
+    *n_pairs = col.n;
+  }
+  mg->net = keep;
+  CK(cudaStreamSynchronize(st));
+  return s;
 }

@@ -62,6 +62,16 @@ SIGNATURES = {
     "nh_mg_destroy": (_st, [_vp]),
     "nh_linear_solve": (_st, [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp]),
     "nh_solve": (_st, [_vp, _vp, _vp, _vp]),
+    "nh_net_create": (_st, [_vp, C.c_int, C.c_int, _vp, C.c_int, C.c_uint64, C.POINTER(_vp)]),
+    "nh_net_destroy": (_st, [_vp]),
+    "nh_net_param_count": (_st, [_vp, C.POINTER(_i64)]),
+    "nh_net_get_params": (_st, [_vp, _vp]),
+    "nh_net_set_params": (_st, [_vp, _vp]),
+    "nh_net_forward": (_st, [_vp, _vp, _vp]),
+    "nh_net_gradient": (_st, [_vp, _vp, _vp, _vp, C.POINTER(C.c_double)]),
+    "nh_net_train_step": (_st, [_vp, C.c_int, _vp, _vp, C.c_float, C.POINTER(C.c_double)]),
+    "nh_mg_set_learned": (_st, [_vp, _vp]),
+    "nh_mg_collect": (_st, [_vp, _vp, C.c_int, _vp, _vp, C.POINTER(C.c_int)]),
 }
 
 
@@ -323,3 +333,57 @@ def nh_solve(ctx, mg, g_bc, u, check=True):
     if check:
         _check(st, ctx)
     return rep
+
+
+def nh_net_create(ctx, N, levels, channels, bf16=True, seed=0):
+    h = _vp()
+    ch = np.ascontiguousarray(channels, dtype=np.int32)
+    _check(lib.nh_net_create(ctx, N, levels, _ptr(ch), 1 if bf16 else 0, seed, C.byref(h)), ctx)
+    return h.value
+
+
+def nh_net_destroy(net):
+    lib.nh_net_destroy(net)
+
+
+def nh_net_param_count(ctx, net):
+    k = _i64()
+    _check(lib.nh_net_param_count(net, C.byref(k)), ctx)
+    return k.value
+
+
+def nh_net_get_params(ctx, net):
+    th = np.empty(nh_net_param_count(ctx, net), dtype=np.float32)
+    _check(lib.nh_net_get_params(net, _ptr(th)), ctx)
+    return th
+
+
+def nh_net_set_params(ctx, net, theta):
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(lib.nh_net_set_params(net, _ptr(th)), ctx)
+
+
+def nh_net_forward(ctx, net, x, y):
+    _check(lib.nh_net_forward(net, _ptr(x), _ptr(y)), ctx)
+
+
+def nh_net_gradient(ctx, net, x, t, dparams):
+    loss = C.c_double()
+    _check(lib.nh_net_gradient(net, _ptr(x), _ptr(t), _ptr(dparams), C.byref(loss)), ctx)
+    return loss.value
+
+
+def nh_net_train_step(ctx, net, batch, x, t, lr):
+    loss = C.c_double()
+    _check(lib.nh_net_train_step(net, batch, _ptr(x), _ptr(t), lr, C.byref(loss)), ctx)
+    return loss.value
+
+
+def nh_mg_set_learned(ctx, mg, net):
+    _check(lib.nh_mg_set_learned(mg, net), ctx)
+
+
+def nh_mg_collect(ctx, mg, b, max_pairs, feats, targets):
+    k = C.c_int()
+    _check(lib.nh_mg_collect(mg, _ptr(b), max_pairs, _ptr(feats), _ptr(targets), C.byref(k)), ctx)
+    return k.value

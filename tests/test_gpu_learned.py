@@ -1,0 +1,155 @@
+"""GPU parity of the learned coarse-correction network and its solver stage.
+
+* FP32 mode (same kernels, FP32 activations and weights): forward 2e-5 and
+  gradient 2e-4 relative against the FP64 oracle -- FP32 rounding over a few
+  thousand accumulated products per output.
+* BF16 mode: forward 3e-2 relative, gradient cosine > 0.99 -- BF16 keeps 8
+  significant bits of every activation and weight.
+* The solver stage never breaks convergence: FCG with an untrained network
+  still solves J x = b to the oracle's direct solution.
+* Collected training targets equal (x* - x_k) at the vertex nodes in the
+  feature scaling; the first pair (x_0 = 0) is checked against a direct solve.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem, learned
+from paper_2204_01722_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LEVELS, CH = 3, (8, 16, 32)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.fixture(scope="module")
+def sample():
+    rng = np.random.default_rng(0)
+    N = 9
+    x = rng.normal(size=(4, N, N, N))
+    t = rng.normal(size=(3, N, N, N))
+    theta = learned.init_params(LEVELS, CH, seed=1) + 0.01 * rng.normal(size=learned.n_params(LEVELS, CH))
+    return N, x, t, theta
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_forward_and_gradient(nhctx, sample, bf16):
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    N, x, t, theta = sample
+    net = nh.nh_net_create(ctx, N, LEVELS, CH, bf16=bf16, seed=3)
+    assert nh.nh_net_param_count(ctx, net) == theta.size
+    nh.nh_net_set_params(ctx, net, theta.astype(np.float32))
+    th32 = theta.astype(np.float32).astype(np.float64)
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    td = torch.from_numpy(t.astype(np.float32)).cuda()
+    y = torch.empty((3, N, N, N), dtype=torch.float32, device="cuda")
+    nh.nh_net_forward(ctx, net, xd, y)
+    x32 = x.astype(np.float32).astype(np.float64)
+    y_ref = learned.forward(th32, x32, LEVELS, CH)
+    g = torch.empty(theta.size, dtype=torch.float32, device="cuda")
+    loss = nh.nh_net_gradient(ctx, net, xd, td, g)
+    torch.cuda.current_stream().synchronize()
+    t32 = t.astype(np.float32).astype(np.float64)
+    g_ref = learned.loss_grad(th32, x32, t32, LEVELS, CH)
+    gh = g.double().cpu().numpy()
+    if not bf16:
+        assert rel(y.double().cpu().numpy(), y_ref) < 2e-5
+        assert rel(gh, g_ref) < 2e-4
+        assert abs(loss - learned.loss(th32, x32, t32, LEVELS, CH)) < 1e-5 * loss
+    else:
+        assert rel(y.double().cpu().numpy(), y_ref) < 3e-2
+        cos = float(gh @ g_ref / (np.linalg.norm(gh) * np.linalg.norm(g_ref)))
+        assert cos > 0.99
+    nh.nh_net_destroy(net)
+
+
+def test_training_reduces_loss(nhctx, sample):
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    N, x, t, _ = sample
+    net = nh.nh_net_create(ctx, N, LEVELS, CH, bf16=True, seed=5)
+    xd = torch.from_numpy(x.astype(np.float32)).cuda().contiguous()
+    # a learnable target: a smooth function of the input
+    td = (0.5 * xd[:3] + 0.25 * torch.roll(xd[1:4], 1, dims=1)).contiguous()
+    first = nh.nh_net_train_step(ctx, net, 1, xd, td, 3e-3)
+    last = first
+    for _ in range(60):
+        last = nh.nh_net_train_step(ctx, net, 1, xd, td, 3e-3)
+    assert last < 0.5 * first
+    nh.nh_net_destroy(net)
+
+
+def _problem(ctx, n=4, p=2):
+    from paper_2204_01722_b300 import nh
+    V = inputs.box_vertices(n, n, n, perturb=0.1, seed=2)
+    sp = fem.Space(n, n, n, V, p, p + 1)
+    E = inputs.inclusion_modulus(n, n, n, seed=4, rmin=0.5, rmax=1.0, contrast=100.0)
+    mat = fem.Material(E, 0.3, sp.ne)
+    mask = inputs.uniaxial_mask(sp.node_dims)
+    s, _, nd = nh.nh_space_box(ctx, n, n, n, V, p, p + 1)
+    nh.nh_space_set_dirichlet(ctx, s, mask)
+    op = nh.nh_op_create(ctx, s, 0.3, E)
+    u = inputs.smooth_field(sp.node_coords(), 0.03, seed=5).ravel()
+    u[mask] = 0.0
+    nh.nh_qdata_setup(ctx, op, torch.from_numpy(u).cuda())
+    mg = nh.nh_mg_create(ctx, op, nh.nh_mg_default_opts(ctx, op))
+    nh.nh_mg_setup(ctx, mg)
+    st = fem.qp_state(sp, mat, u)
+    J = fem.assemble(sp, fem.element_matrices(sp, st), mask)
+    return s, op, mg, sp, mask, J, nd
+
+
+def test_learned_stage_keeps_fcg_exact(nhctx):
+    import scipy.sparse.linalg as spla
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    s, op, mg, sp, mask, J, nd = _problem(ctx)
+    net = nh.nh_net_create(ctx, 5, 2, (8, 16), bf16=True, seed=7)
+    nh.nh_mg_set_learned(ctx, mg, net)
+    b = inputs.normal_vector(nd, seed=8)
+    b[mask] = 0.0
+    x = torch.zeros(nd, dtype=torch.float64, device="cuda")
+    rep = nh.nh_linear_solve(ctx, mg, torch.from_numpy(b).cuda(), x, rtol=1e-11, maxit=300, norm=1)
+    assert rep.learned_accepted + rep.learned_rejected == rep.vcycles
+    assert rel(x.cpu().numpy(), spla.spsolve(J.tocsc(), b)) < 1e-7
+    nh.nh_mg_set_learned(ctx, mg, None)
+    nh.nh_net_destroy(net)
+    nh.nh_mg_destroy(mg)
+    nh.nh_op_destroy(op)
+    nh.nh_space_destroy(s)
+
+
+def test_collected_targets(nhctx):
+    import scipy.sparse.linalg as spla
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    n, p = 4, 2
+    s, op, mg, sp, mask, J, nd = _problem(ctx, n, p)
+    b = inputs.normal_vector(nd, seed=9)
+    b[mask] = 0.0
+    Nv = n + 1
+    feats = torch.zeros((8, 4, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
+    tg = torch.zeros((8, 3, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
+    k = nh.nh_mg_collect(ctx, mg, torch.from_numpy(b).cuda(), 8, feats, tg)
+    assert k >= 2
+    # first pair: residual b, error x*; features = R b / rms(R b), target = x* at vertices / rms(R b)
+    c = fem.Space(n, n, n, sp.vertices, 1, p + 1)
+    rc = fem.restrict(sp, c, b)
+    rc[inputs.uniaxial_mask(c.node_dims)] = 0.0
+    scale = np.sqrt(np.mean(rc ** 2))
+    f0 = feats[0].cpu().numpy()
+    np.testing.assert_allclose(f0[:3].reshape(3, -1).T.ravel(), rc / scale, rtol=1e-5, atol=1e-6)
+    xs = spla.spsolve(J.tocsc(), b).reshape(-1, 3)
+    N = p * n + 1
+    I, Jj, K = inputs.lattice_index((Nv, Nv, Nv))
+    vid = p * I + N * (p * Jj + N * p * K)
+    t0 = tg[0].cpu().numpy().reshape(3, -1).T
+    np.testing.assert_allclose(t0, xs[vid] / scale, rtol=1e-6, atol=1e-6 * np.abs(xs).max() / scale)
+    nh.nh_mg_destroy(mg)
+    nh.nh_op_destroy(op)
+    nh.nh_space_destroy(s)
