@@ -194,6 +194,8 @@ typedef struct {
   int krylov_maxit;        /* (500) */
   int line_search;         /* 1: one secant step on F(u + a du)^T du = 0 (critical point) */
   int verbose;             /* 1: one line per Newton step on stderr */
+  int learned_accept;      /* learned stage test: 0 = ||r - J z1||_2 < ||r||_2 (z1 as is);
+                              1 = energy decrease with the optimal step a = z1.r / z1.J z1, i.e. z1.r > 0 */
 } nh_mg_opts;
 
 typedef struct {
@@ -269,9 +271,10 @@ nh_status nh_net_gradient(nh_net net, const float* in, const float* target, floa
  * samples in [batch][4][N^3] / [batch][3][N^3]. */
 nh_status nh_net_train_step(nh_net net, int batch, const float* in, const float* target, float lr, double* loss);
 /* Insert the network as an extra flexible-CG preconditioner stage of nh_solve /
- * nh_linear_solve (NULL removes it): z1 = P net(R r) (R, P through the p levels
- * down to the Q1 level), accepted when ||r - J z1|| < ||r||, then
- * z = z1 + V-cycle(r - J z1); otherwise z = V-cycle(r).  Needs a hierarchy
+ * nh_linear_solve (NULL removes it): z1 = a P net(R r) (R, P through the p levels
+ * down to the Q1 level; a = 1, or the energy-optimal step, see learned_accept),
+ * accepted by the opts' test, then z = z1 + V-cycle(r - J z1); otherwise
+ * z = V-cycle(r).  Needs a hierarchy
  * ending at p = 1 whose vertex grid matches the network's N. */
 nh_status nh_mg_set_learned(nh_mg mg, nh_net net);
 /* Training pairs from the linear system J x = b at the current quadrature data:

@@ -428,6 +428,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->krylov_maxit = 500;
   o->line_search = 1;
   o->verbose = 0;
+  o->learned_accept = 1;
   return NH_OK;
 }
 
@@ -670,13 +671,29 @@ static nh_status precond(nh_mg mg, const double* r, double* z) {
     cur = out;
   }
   const int64_t n = mg->L[0].n;
-  ST(nh_jacobian_apply(mg->fine, NH_F64, mg->lz1, mg->lw));
-  CK(kv_axpby<double>(st, n, 1.0, r, -1.0, mg->lw));  // w = r - J z1
-  mg->ctx->launches++;
-  double nw = 0.0, nr = 0.0;
-  ST(dot_host(mg, n, mg->lw, mg->lw, &nw));
-  ST(dot_host(mg, n, r, r, &nr));
-  if (isfinite(nw) && nw < nr) {
+  ST(nh_jacobian_apply(mg->fine, NH_F64, mg->lz1, mg->lw));  // lw = J z1
+  bool accept = false;
+  if (mg->o.learned_accept == 1) {
+    // energy-optimal step: a = z1.r / z1.J z1; the A-norm of the error drops iff z1.r > 0
+    double zr = 0.0, zaz = 0.0;
+    ST(dot_host(mg, n, mg->lz1, r, &zr));
+    ST(dot_host(mg, n, mg->lz1, mg->lw, &zaz));
+    if (isfinite(zr) && isfinite(zaz) && zr > 0.0 && zaz > 0.0) {
+      const double a = zr / zaz;
+      CK(kv_axpby<double>(st, n, 1.0, r, -a, mg->lw));  // w = r - a J z1
+      CK(kv_axpby<double>(st, n, 0.0, mg->lz1, a, mg->lz1));
+      mg->ctx->launches += 2;
+      accept = true;
+    }
+  } else {
+    CK(kv_axpby<double>(st, n, 1.0, r, -1.0, mg->lw));  // w = r - J z1
+    mg->ctx->launches++;
+    double nw = 0.0, nr = 0.0;
+    ST(dot_host(mg, n, mg->lw, mg->lw, &nw));
+    ST(dot_host(mg, n, r, r, &nr));
+    accept = isfinite(nw) && nw < nr;
+  }
+  if (accept) {
     ST(vcycle_fp64(mg, mg->lw, z));
     CK(kv_axpby<double>(st, n, 1.0, mg->lz1, 1.0, z));
     mg->ctx->launches++;
