@@ -194,8 +194,12 @@ typedef struct {
   int krylov_maxit;        /* (500) */
   int line_search;         /* 1: one secant step on F(u + a du)^T du = 0 (critical point) */
   int verbose;             /* 1: one line per Newton step on stderr */
-  int learned_accept;      /* learned stage test: 0 = ||r - J z1||_2 < ||r||_2 (z1 as is);
+  int learned_accept;      /* outer learned stage test: 0 = ||r - J z1||_2 < ||r||_2 (z1 as is);
                               1 = energy decrease with the optimal step a = z1.r / z1.J z1, i.e. z1.r > 0 */
+  int learned_mode;        /* where a network set by nh_mg_set_learned acts:
+                              1 = outer FCG stage (predicts the fine error at the vertices);
+                              2 = coarse warm start (predicts A_c^-1 r_c; the coarsest PCG starts from it
+                                  when it lowers the coarse residual, else from zero) */
 } nh_mg_opts;
 
 typedef struct {
@@ -277,11 +281,14 @@ nh_status nh_net_train_step(nh_net net, int batch, const float* in, const float*
  * z = V-cycle(r).  Needs a hierarchy
  * ending at p = 1 whose vertex grid matches the network's N. */
 nh_status nh_mg_set_learned(nh_mg mg, nh_net net);
-/* Training pairs from the linear system J x = b at the current quadrature data:
- * solves to ||r|| <= 1e-10 ||b|| for x*, then runs FCG + V-cycle to
- * krylov_rtol from zero and, before every preconditioner application, stores
- * the network input for the residual r_k and the target (x* - x_k injected at
- * the vertex nodes, in the input's scaling).  feats: device float
+/* Training pairs from the linear system J x = b at the current quadrature data.
+ * learned_mode 1: solves to ||r|| <= 1e-10 ||b|| for x*, then runs FCG +
+ * V-cycle to krylov_rtol from zero and, before every preconditioner
+ * application, stores the network input for the residual r_k and the target
+ * (x* - x_k injected at the vertex nodes, in the input's scaling).
+ * learned_mode 2: runs FCG + V-cycle to krylov_rtol; at every coarsest solve
+ * stores the input for the coarse right-hand side r_c and the target
+ * A_c^-1 r_c (coarse PCG to 1e-9, in the input's scaling).  feats: device float
  * [max_pairs][4][N^3], targets [max_pairs][3][N^3]; *n_pairs = pairs written. */
 nh_status nh_mg_collect(nh_mg mg, const double* b, int max_pairs, float* feats, float* targets, int* n_pairs);
 

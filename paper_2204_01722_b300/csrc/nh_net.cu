@@ -565,7 +565,20 @@ __global__ void k_inject(int Nv, int p, int Nf, const double* __restrict__ ef, d
   }
 }
 
+__global__ void k_to_channels(int64_t nc, const double* __restrict__ ec, double inv, float* __restrict__ t) {
+  GSTRIDE(i, nc) {
+    t[i] = (float)(ec[3 * i] * inv);
+    t[nc + i] = (float)(ec[3 * i + 1] * inv);
+    t[2 * nc + i] = (float)(ec[3 * i + 2] * inv);
+  }
+}
+
 }  // namespace
+
+cudaError_t kn_to_channels(cudaStream_t st, int64_t nc, const double* ec, double inv, float* t) {
+  k_to_channels<<<blocks_for(nc), 256, 0, st>>>(nc, ec, inv, t);
+  return cudaGetLastError();
+}
 
 cudaError_t kn_features(cudaStream_t st, int64_t nc, const double* rc, double inv, const float* logE, float* feat) {
   k_features<<<blocks_for(nc), 256, 0, st>>>(nc, rc, inv, logE, feat);

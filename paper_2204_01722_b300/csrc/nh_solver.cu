@@ -76,6 +76,7 @@ struct nh_mg_s {
   float *feat = nullptr, *nout = nullptr, *logE = nullptr;
   double *lz1 = nullptr, *lw = nullptr, *lxs = nullptr, *lx = nullptr, *lt = nullptr;
   int acc = 0, rej = 0;
+  struct Collect* coll = nullptr;  // coarse-pair collection in progress
 };
 
 namespace {
@@ -170,13 +171,20 @@ nh_status cheb(nh_mg mg, Level& l, T* x, const T* b, bool zero_init) {
 // Jacobi-PCG in FP64 on level l: A x = b, x = 0 start.  With hist, runs exactly
 // `maxit` steps and leaves rz_k, pq_k in the history slots (Lanczos).
 // Returns iterations in *its.
-nh_status pcg64(nh_mg mg, Level& l, const double* b, double* x, double rtol, int maxit, bool hist, int* its) {
+nh_status pcg64(nh_mg mg, Level& l, const double* b, double* x, double rtol, int maxit, bool hist, int* its,
+                bool warm = false, double ref = 0.0) {
   cudaStream_t st = mg->ctx->stream;
   const int64_t n = l.n;
   double *r = l.w[0], *z = l.w[1], *p = l.w[2], *q = l.w[3];
   const double* dinv = l.dinv64;
-  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-  CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  if (warm) {  // r = b - A x for the given start x
+    ST(level_apply(mg, l, NH_F64, x, r));
+    CK(kv_axpby<double>(st, n, 1.0, b, -1.0, r));
+    mg->ctx->launches++;
+  } else {
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  }
   CK(kv_mul<double>(st, n, dinv, r, z));
   CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   mg->ctx->launches++;
@@ -185,6 +193,14 @@ nh_status pcg64(nh_mg mg, Level& l, const double* b, double* x, double rtol, int
   double rz0 = 0.0;
   if (!hist) {
     ST(read_sc(mg, cur, 1, &rz0));
+    if (warm) {
+      // tolerance relative to the right-hand side's natural norm (ref^2 = b.D^-1 b)
+      if (sqrt(fabs(rz0)) <= rtol * ref) {
+        *its = 0;
+        return NH_OK;
+      }
+      rz0 = ref * ref;
+    }
     if (!(rz0 > 0.0)) {
       *its = 0;
       return NH_OK;
@@ -294,15 +310,11 @@ template <typename T>
 nh_status vcycle_t(nh_mg mg, int lv);
 
 // x_lv = V-cycle(b_lv), dispatch on the level precision
+nh_status coarse_solve(nh_mg mg, Level& l);
+
 nh_status vcycle(nh_mg mg, int lv) {
   Level& l = mg->L[lv];
-  if (lv == (int)mg->L.size() - 1) {
-    // coarsest: FP64 Jacobi-PCG (the coarsest level is always FP64)
-    int its = 0;
-    ST(pcg64(mg, l, (const double*)l.b, (double*)l.x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
-    mg->coarse_its += its;
-    return NH_OK;
-  }
+  if (lv == (int)mg->L.size() - 1) return coarse_solve(mg, l);
   return l.prec == NH_F64 ? vcycle_t<double>(mg, lv) : vcycle_t<float>(mg, lv);
 }
 
@@ -429,6 +441,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->line_search = 1;
   o->verbose = 0;
   o->learned_accept = 1;
+  o->learned_mode = 2;
   return NH_OK;
 }
 
@@ -618,11 +631,84 @@ extern "C" nh_status nh_mg_vcycle(nh_mg mg, const double* r, double* z) {
 
 // ---- learned stage ---------------------------------------------------------------
 struct Collect {
-  const double* xs;  // converged solution
+  const double* xs;  // converged solution (outer mode)
   float* feats;
   float* tgts;
   int max, n;
 };
+
+namespace {
+
+// network input for a coarse right-hand side bc: scaled by its RMS (0 if bc = 0)
+nh_status coarse_features(nh_mg mg, const double* bc, float* feat, double* scale) {
+  Level& c = mg->L.back();
+  double rr = 0.0;
+  ST(dot_host(mg, c.n, bc, bc, &rr));
+  *scale = sqrt(rr / (double)c.n);
+  if (!(*scale > 0.0) || !isfinite(*scale)) {
+    *scale = 0.0;
+    return NH_OK;
+  }
+  CK(kn_features(mg->ctx->stream, c.nn, bc, 1.0 / *scale, mg->logE, feat));
+  mg->ctx->launches++;
+  return NH_OK;
+}
+
+// coarsest solve: FP64 Jacobi-PCG (the coarsest level is always FP64), with the
+// learned warm start in learned_mode 2 and pair recording in collection mode
+nh_status coarse_solve(nh_mg mg, Level& l) {
+  cudaStream_t st = mg->ctx->stream;
+  const double* b = (const double*)l.b;
+  double* x = (double*)l.x;
+  int its = 0;
+  if (mg->coll && mg->coll->n < mg->coll->max) {
+    // collection: tight solve, store (scaled b, scaled A^-1 b)
+    ST(pcg64(mg, l, b, x, 1e-9, 20000, false, &its));
+    double scale = 0.0;
+    float* f = mg->coll->feats + (int64_t)mg->coll->n * 4 * l.nn;
+    ST(coarse_features(mg, b, f, &scale));
+    if (scale > 0.0) {
+      CK(kn_to_channels(st, l.nn, x, 1.0 / scale, mg->coll->tgts + (int64_t)mg->coll->n * 3 * l.nn));
+      mg->ctx->launches++;
+      mg->coll->n++;
+    }
+    mg->coarse_its += its;
+    return NH_OK;
+  }
+  if (mg->net && mg->o.learned_mode == 2) {
+    double scale = 0.0;
+    ST(coarse_features(mg, b, mg->feat, &scale));
+    if (scale > 0.0) {
+      ST(nh_net_forward_internal(mg->net, mg->feat, mg->nout));
+      CK(kn_from_net(st, l.nn, mg->nout, scale, x));
+      CK(kv_mask_zero<double>(st, l.nn, l.space->bc, x));
+      mg->ctx->launches += 2;
+      // natural norms of b and of the warm-start residual
+      double *r = l.w[0], *z = l.w[1];
+      ST(level_apply(mg, l, NH_F64, x, r));
+      CK(kv_axpby<double>(st, l.n, 1.0, b, -1.0, r));
+      CK(kv_mul<double>(st, l.n, l.dinv64, r, z));
+      mg->ctx->launches += 2;
+      double rz = 0.0, bb = 0.0;
+      ST(dot_host(mg, l.n, r, z, &rz));
+      CK(kv_mul<double>(st, l.n, l.dinv64, b, z));
+      mg->ctx->launches++;
+      ST(dot_host(mg, l.n, b, z, &bb));
+      if (isfinite(rz) && rz < bb) {
+        ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its, true, sqrt(bb)));
+        mg->coarse_its += its;
+        mg->acc++;
+        return NH_OK;
+      }
+      mg->rej++;
+    }
+  }
+  ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
+  mg->coarse_its += its;
+  return NH_OK;
+}
+
+}  // namespace
 
 // network input for the fine residual r: restrict through the levels to Q1,
 // scale by the RMS of the restricted residual.  Returns the scale (0 if r = 0).
@@ -653,7 +739,7 @@ static nh_status vcycle_fp64(nh_mg mg, const double* r, double* z);
 
 // z = M r with the learned stage in front of the V-cycle (see nh_mg_set_learned)
 static nh_status precond(nh_mg mg, const double* r, double* z) {
-  if (!mg->net) return vcycle_fp64(mg, r, z);
+  if (!mg->net || mg->o.learned_mode != 1) return vcycle_fp64(mg, r, z);
   cudaStream_t st = mg->ctx->stream;
   double scale = 0.0;
   ST(learned_features(mg, r, mg->feat, &scale));
@@ -1067,6 +1153,17 @@ extern "C" nh_status nh_mg_collect(nh_mg mg, const double* b, int max_pairs, flo
   cudaStream_t st = mg->ctx->stream;
   int its = 0;
   double rel = 0.0;
+  if (mg->o.learned_mode == 2) {
+    Collect col{nullptr, feats, targets, max_pairs, 0};
+    mg->coll = &col;
+    CK(cudaMemsetAsync(mg->lx, 0, 8 * n, st));
+    nh_status s = fcg(mg, b, mg->lx, mg->o.krylov_rtol, mg->o.krylov_maxit, 0, &its, &rel);
+    mg->coll = nullptr;
+    mg->net = keep;
+    *n_pairs = col.n;
+    CK(cudaStreamSynchronize(st));
+    return s;
+  }
   CK(cudaMemsetAsync(mg->lxs, 0, 8 * n, st));
   nh_status s = fcg(mg, b, mg->lxs, 1e-10, 2000, 1, &its, &rel);
   if (s == NH_OK) {

@@ -84,7 +84,7 @@ def test_training_reduces_loss(nhctx, sample):
     nh.nh_net_destroy(net)
 
 
-def _problem(ctx, n=4, p=2):
+def _problem(ctx, n=4, p=2, mode=2):
     from paper_2204_01722_b300 import nh
     V = inputs.box_vertices(n, n, n, perturb=0.1, seed=2)
     sp = fem.Space(n, n, n, V, p, p + 1)
@@ -97,18 +97,19 @@ def _problem(ctx, n=4, p=2):
     u = inputs.smooth_field(sp.node_coords(), 0.03, seed=5).ravel()
     u[mask] = 0.0
     nh.nh_qdata_setup(ctx, op, torch.from_numpy(u).cuda())
-    mg = nh.nh_mg_create(ctx, op, nh.nh_mg_default_opts(ctx, op))
+    mg = nh.nh_mg_create(ctx, op, nh.nh_mg_default_opts(ctx, op, learned_mode=mode))
     nh.nh_mg_setup(ctx, mg)
     st = fem.qp_state(sp, mat, u)
     J = fem.assemble(sp, fem.element_matrices(sp, st), mask)
-    return s, op, mg, sp, mask, J, nd
+    return s, op, mg, sp, mask, J, nd, st
 
 
-def test_learned_stage_keeps_fcg_exact(nhctx):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_learned_stage_keeps_fcg_exact(nhctx, mode):
     import scipy.sparse.linalg as spla
     ctx, _ = nhctx
     from paper_2204_01722_b300 import nh
-    s, op, mg, sp, mask, J, nd = _problem(ctx)
+    s, op, mg, sp, mask, J, nd, _ = _problem(ctx, mode=mode)
     net = nh.nh_net_create(ctx, 5, 2, (8, 16), bf16=True, seed=7)
     nh.nh_mg_set_learned(ctx, mg, net)
     b = inputs.normal_vector(nd, seed=8)
@@ -124,12 +125,37 @@ def test_learned_stage_keeps_fcg_exact(nhctx):
     nh.nh_space_destroy(s)
 
 
+def test_collected_coarse_pairs(nhctx):
+    """Mode 2 pairs: target = A_c^-1 input, A_c the Q1 operator at the fine points."""
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    n, p = 4, 2
+    s, op, mg, sp, mask, J, nd, st = _problem(ctx, n, p, mode=2)
+    b = inputs.normal_vector(nd, seed=9)
+    b[mask] = 0.0
+    Nv = n + 1
+    feats = torch.zeros((6, 4, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
+    tg = torch.zeros((6, 3, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
+    k = nh.nh_mg_collect(ctx, mg, torch.from_numpy(b).cuda(), 6, feats, tg)
+    assert k >= 2
+    c = fem.Space(n, n, n, sp.vertices, 1, p + 1)
+    mc = inputs.uniaxial_mask(c.node_dims)
+    for i in range(k):
+        f = feats[i, :3].cpu().numpy().reshape(3, -1).T.ravel().astype(np.float64)
+        e = tg[i].cpu().numpy().reshape(3, -1).T.ravel().astype(np.float64)
+        Ae = fem.jacobian_apply(c, st, e, mc)
+        assert rel(Ae, f) < 2e-4   # FP32 storage of e, amplified by the coarse condition number
+    nh.nh_mg_destroy(mg)
+    nh.nh_op_destroy(op)
+    nh.nh_space_destroy(s)
+
+
 def test_collected_targets(nhctx):
     import scipy.sparse.linalg as spla
     ctx, _ = nhctx
     from paper_2204_01722_b300 import nh
     n, p = 4, 2
-    s, op, mg, sp, mask, J, nd = _problem(ctx, n, p)
+    s, op, mg, sp, mask, J, nd, _ = _problem(ctx, n, p, mode=1)
     b = inputs.normal_vector(nd, seed=9)
     b[mask] = 0.0
     Nv = n + 1
