@@ -69,6 +69,7 @@ struct nh_mg_s {
   // FCG / Newton work (fine, FP64)
   double *fr = nullptr, *fz = nullptr, *fp = nullptr, *fq = nullptr;  // FCG work
   double *fx = nullptr, *fu = nullptr, *fg = nullptr, *fb = nullptr, *ft = nullptr, *fs = nullptr;  // Newton
+  double* fsave = nullptr;  // state at the start of a load increment
   bool setup_done = false;
   int vcycles = 0, coarse_its = 0;
   // learned stage
@@ -440,7 +441,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->krylov_maxit = 500;
   o->line_search = 1;
   o->verbose = 0;
-  o->learned_accept = 1;
+  o->learned_accept = 0;
   o->learned_mode = 2;
   return NH_OK;
 }
@@ -461,7 +462,8 @@ extern "C" nh_status nh_mg_destroy(nh_mg mg) {
   cudaFree(mg->sc);
   cudaFree(mg->part);
   cudaFreeHost(mg->hsc);
-  for (double* p : {mg->fr, mg->fz, mg->fp, mg->fq, mg->fx, mg->fu, mg->fg, mg->fb, mg->ft, mg->fs}) cudaFree(p);
+  for (double* p : {mg->fr, mg->fz, mg->fp, mg->fq, mg->fx, mg->fu, mg->fg, mg->fb, mg->ft, mg->fs, mg->fsave})
+    cudaFree(p);
   for (void* p : {(void*)mg->feat, (void*)mg->nout, (void*)mg->logE, (void*)mg->lz1, (void*)mg->lw, (void*)mg->lxs,
                   (void*)mg->lx, (void*)mg->lt})
     cudaFree(p);
@@ -545,7 +547,7 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
     nh_mg_destroy(mg);
     return s;
   }
-  for (double** v : {&mg->fr, &mg->fz, &mg->fp, &mg->fq, &mg->fx, &mg->fu, &mg->fg, &mg->fb, &mg->ft, &mg->fs})
+  for (double** v : {&mg->fr, &mg->fz, &mg->fp, &mg->fq, &mg->fx, &mg->fu, &mg->fg, &mg->fb, &mg->ft, &mg->fs, &mg->fsave})
     if ((s = dalloc(mg, (void**)v, fb)) != NH_OK) { nh_mg_destroy(mg); return s; }
   if (cudaMallocHost(&mg->hsc, sizeof(double) * S_LEN) != cudaSuccess) {
     cudaGetLastError();
@@ -956,6 +958,7 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
     }
     ctx->launches++;
     tR += now_s() - t1;
+    CK(cudaMemcpyAsync(mg->fsave, u, 8 * n, cudaMemcpyDeviceToDevice, st));
     // --- predictor: carry the boundary increment w = g_k - u (constrained DoFs) into
     // the interior through the tangent at the current state:
     //   J_uu du = -(F_u(u) + J_uc w),   u <- u + w + du
@@ -996,7 +999,7 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
     // --- Newton corrector at fixed t
     int it = 0;
     while (!(nr <= o.newton_rtol * nr0) && !(nr <= o.newton_atol)) {
-      if (it >= o.newton_maxit) {
+      if (it >= o.newton_maxit || (it >= 10 && nr > 1e-4 * nr0)) {  // limit, or stagnation
         status = nh_fail(ctx, NH_ERR_NOT_CONVERGED, "nh_solve: Newton iteration limit");
         break;
       }
@@ -1061,6 +1064,17 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
                 t, it, nr, nr / nr0, R.krylov_its, mg->vcycles, mg->coarse_its, alpha, minJ);
     }
     rel = nr0 > 0 ? nr / nr0 : 0.0;
+    if (status == NH_ERR_NOT_CONVERGED || status == NH_ERR_INVERTED) {
+      // the increment was too large for Newton: restore its start state and halve it
+      CK(cudaMemcpyAsync(u, mg->fsave, 8 * n, cudaMemcpyDeviceToDevice, st));
+      if (++halvings > 8) {
+        status = nh_fail(ctx, NH_ERR_NOT_CONVERGED, "nh_solve: load increment cannot be halved further");
+        break;
+      }
+      if (o.verbose) fprintf(stderr, "nh_solve t %.4f: Newton failed, halving the increment\n", t);
+      status = NH_OK;
+      continue;
+    }
     if (status != NH_OK) break;
     t_prev = t;
     if (halvings > 0 && t < t_target) {
