@@ -84,6 +84,7 @@ extern "C" nh_status nh_create(nh_ctx* out, int device, void* cuda_stream) {
   c->red_len = kRedBlocks + 8;
   if (cudaMalloc(&c->red, c->red_len * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->minj, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&c->dev_err, sizeof(int)) != cudaSuccess || cudaMemset(c->dev_err, 0, sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&c->red_host, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     if (c->red) cudaFree(c->red);
@@ -103,6 +104,7 @@ extern "C" nh_status nh_destroy(nh_ctx c) {
   for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
   cudaFree(c->red);
   cudaFree(c->minj);
+  cudaFree(c->dev_err);
   cudaFreeHost(c->red_host);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -116,6 +118,12 @@ extern "C" nh_status nh_sync(nh_ctx c) {
   NH_CUDA(c, cudaSetDevice(c->device));
   NH_CUDA(c, cudaStreamSynchronize(c->stream));
   NH_CUDA(c, cudaGetLastError());
+  int err = 0;
+  NH_CUDA(c, cudaMemcpy(&err, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    NH_CUDA(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+    return nh_fail(c, NH_ERR_TIMEOUT, "a kernel's bounded wait for its shared-memory copy expired");
+  }
   return NH_OK;
 }
 
@@ -327,7 +335,7 @@ extern "C" nh_status nh_op_info(nh_op op, nh_prec prec, int* S, int64_t* bytes) 
   nh_op root = op->parent ? op->parent : op;
   const int64_t nq = root->space->ne * (int64_t)root->space->Q * root->space->Q * root->space->Q;
   if (S) *S = root->S;
-  if (bytes) *bytes = nq * root->S * (prec == NH_F64 ? 8 : 4);
+  if (bytes) *bytes = nq * root->S * (prec == NH_F64 ? 8 : 4);  // algorithmic size (the FP32 copy is padded per batch)
   return NH_OK;
 }
 
@@ -344,6 +352,7 @@ static OpArgs base_args(nh_op op) {
   a.coords = op->space->coords;
   a.lam = root->lam;
   a.mu = root->mu;
+  a.err = op->space->ctx->dev_err;
   return a;
 }
 
@@ -403,9 +412,10 @@ extern "C" nh_status nh_residual(nh_op op, const double* u, const double* g_bc, 
 static nh_status ensure_f32(nh_op root) {
   nh_ctx ctx = root->space->ctx;
   if (root->qd_f_valid) return NH_OK;
-  const int64_t n = root->S * root->space->ne * (int64_t)root->space->Q * root->space->Q * root->space->Q;
-  if (!root->qd_f) NH_CUDA(ctx, cudaMalloc(&root->qd_f, sizeof(float) * n));
-  NH_CUDA(ctx, nh_launch_f64_to_f32(n, root->qd, root->qd_f, ctx->stream));
+  const int Q = root->space->Q;
+  const int64_t nb = (root->space->ne + nh_epb(Q) - 1) / nh_epb(Q);
+  if (!root->qd_f) NH_CUDA(ctx, cudaMalloc(&root->qd_f, sizeof(float) * nb * nh_f32_batch_floats(Q, root->S)));
+  NH_CUDA(ctx, nh_launch_f32_blocked(Q, root->S, root->space->ne, root->qd, root->qd_f, ctx->stream));
   ctx->launches++;
   root->qd_f_valid = true;
   return NH_OK;

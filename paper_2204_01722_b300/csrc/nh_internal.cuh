@@ -13,6 +13,13 @@
 #define NH_MAXP 5   // nodes per direction (p <= 4)
 #define NH_MAXQ 6   // Gauss points per direction
 
+// elements per block of the fused element kernels (about 128 threads, Q*Q per element)
+__host__ __device__ constexpr int nh_epb(int Q) { return (128 / (Q * Q)) > 0 ? 128 / (Q * Q) : 1; }
+// floats per element batch of the blocked FP32 quadrature data ([S][EPB][Q^3], padded to 256 B)
+__host__ __device__ constexpr long long nh_f32_batch_floats(int Q, int S) {
+  return ((long long)S * nh_epb(Q) * Q * Q * Q + 63) / 64 * 64;
+}
+
 // ---- 1-D tables ---------------------------------------------------------------
 // Host-side tabulations in double; kernels receive them by value as kernel
 // parameters (constant bank), converted to the kernel's scalar type.
@@ -59,6 +66,7 @@ struct nh_ctx_s {
   size_t red_len = 0;
   double* red_host = nullptr;          // pinned
   unsigned long long* minj = nullptr;  // ordered-bits min of det F
+  int* dev_err = nullptr;              // set by a kernel whose bounded wait expired
   // kernel timing (nh_profile_*)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;   // 2 per recorded launch
@@ -90,7 +98,7 @@ struct nh_op_s {
   double* lam = nullptr;          // [ne] device
   double* mu = nullptr;
   double* qd = nullptr;           // [S][ne*Q^3] FP64 quadrature data (fine op only)
-  float* qd_f = nullptr;          // FP32 copy
+  float* qd_f = nullptr;          // FP32 copy, blocked per element batch (nh_f32_batch_floats)
   bool have_qd = false;
   bool qd_f_valid = false;
   // device staging for nh_jacobian_apply_host
@@ -128,6 +136,7 @@ struct OpArgs {
   int store;           // setup: write quadrature data
   int resid;           // setup: compute residual
   int lift;            // apply: keep constrained inputs, leave constrained rows zero
+  int* err;            // device error flag for bounded waits
   const Tab1D* tab;
 };
 
@@ -163,3 +172,5 @@ cudaError_t nh_launch_dot_partials(int64_t n, const double* x, const double* y, 
                                    int nblocks, cudaStream_t s);
 cudaError_t nh_launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
 cudaError_t nh_launch_f64_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);
+// FP64 SoA quadrature data [S][ne Q^3] -> blocked FP32 [batch][S][EPB][Q^3]
+cudaError_t nh_launch_f32_blocked(int Q, int S, int64_t ne, const double* qd, float* qdf, cudaStream_t s);

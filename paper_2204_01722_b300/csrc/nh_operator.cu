@@ -22,7 +22,57 @@
 
 namespace {
 
-__host__ __device__ constexpr int epb_for(int Q) { return (128 / (Q * Q)) > 0 ? 128 / (Q * Q) : 1; }
+__host__ __device__ constexpr int epb_for(int Q) { return nh_epb(Q); }
+
+// Shared-memory stride of one element's [9][Q^3] work area, padded so that the
+// Q*Q threads of consecutive elements in a warp fall on different banks
+// (stride = Q^2 modulo the number of T words that cover the 32 banks).
+template <int Q, typename T>
+__host__ __device__ constexpr int elem_stride() {
+  constexpr int base = 9 * Q * Q * Q, W = 128 / (int)sizeof(T), want = (Q * Q) % W;
+  return Q * Q >= W ? base : base + ((want - base % W) % W + W) % W;
+}
+
+// ---- TMA (1-D bulk copy) and mbarrier helpers -----------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// global -> shared bulk copy completing on the mbarrier (addresses 16-B aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: after kMaxSpin polls the kernel flags the error and goes on
+constexpr unsigned kMaxSpin = 1u << 26;
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+  for (unsigned it = 0; !mbar_try_wait(bar, parity); it++) {
+    if (it >= kMaxSpin) {
+      if (err) atomicExch(err, 1);
+      return;
+    }
+  }
+}
 
 template <int Q>
 __device__ __forceinline__ int sidx(int c, int k, int j, int i) {
@@ -183,7 +233,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
   const int a = col % Q, b = col / Q;
   const int64_t e = (int64_t)blockIdx.x * EPB + el;
   const bool live = e < ne;
-  T* bA = sm + el * 9 * Q3;
+  T* bA = sm + el * elem_stride<Q, T>();
   T* bB = bA + 3 * Q3;
   T* bC = bB + 3 * Q3;
 
@@ -223,6 +273,88 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
         const int64_t dof = 3 * (int64_t)n + c;
         if ((m >> c) & 1u) {
           if (!lift) y[dof] = du[dof];  // identity row; every writer stores the same value
+        } else {
+          atomicAdd(&y[dof], out[c][k]);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 Jacobian action with the block's quadrature data staged in shared memory
+// by one 1-D TMA bulk copy (blocked layout [batch][S][EPB][Q^3]), issued at
+// block start so it overlaps the gather and the interpolation.
+// ---------------------------------------------------------------------------
+template <int P, int Q, int LAYOUT>
+__global__ void __launch_bounds__(Q* Q* epb_for(Q))
+    k_jacobian_apply_f32tma(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
+                            const float* __restrict__ qdb, const KTab<P, Q, float> tab, const float* __restrict__ du,
+                            float* __restrict__ y, int lift, int* __restrict__ err) {
+  constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q;
+  constexpr int S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
+  constexpr long long BS = nh_f32_batch_floats(Q, S);
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar;
+  float* qs = reinterpret_cast<float*>(smraw);  // [S][EPB][Q^3]
+  float* sm = qs + BS;
+  const int t = threadIdx.x;
+  const int el = t / Q2, col = t - el * Q2;
+  const int a = col % Q, b = col / Q;
+  const int64_t e = (int64_t)blockIdx.x * EPB + el;
+  const bool live = e < ne;
+  float* bA = sm + el * elem_stride<Q, float>();
+  float* bB = bA + 3 * Q3;
+  float* bC = bB + 3 * Q3;
+  if (t == 0) mbar_init(&bar);
+  __syncthreads();
+  if (t == 0) {
+    const unsigned bytes = (unsigned)(BS * sizeof(float));
+    mbar_expect_tx(&bar, bytes);
+    const char* src = reinterpret_cast<const char*>(qdb + (int64_t)blockIdx.x * BS);
+    char* dst = reinterpret_cast<char*>(qs);
+    for (unsigned off = 0; off < bytes; off += 16384u) {
+      const unsigned chunk = bytes - off < 16384u ? bytes - off : 16384u;
+      bulk_g2s(dst + off, src + off, chunk, &bar);
+    }
+  }
+  float U[3][Q];
+  int nid[P];
+  gather_interp<P, Q, float>(live, !lift, e, a, b, emap, bc, du, tab, bA, bB, bC, U, nid);
+  mbar_wait_bounded(&bar, 0, err);
+  __syncthreads();
+  float Fz[3][Q];
+  const float* qe = qs + el * Q3 + b * Q + a;
+#pragma unroll
+  for (int qk = 0; qk < Q; qk++) {
+    float g[3][3], f[3][3];
+    colloc_grad<P, Q, float>(a, b, qk, tab, bC, U, g);
+    if (live) {
+      pointwise<LAYOUT, float>(qe + qk * Q2, (int64_t)EPB * Q3, g, f);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      bA[sidx<Q>(c, qk, b, a)] = f[c][0];
+      bB[sidx<Q>(c, qk, b, a)] = f[c][1];
+      Fz[c][qk] = f[c][2];
+    }
+  }
+  __syncthreads();
+  float out[3][P];
+  transpose_to_nodes<P, Q, float>(a, b, tab, bA, bB, bC, Fz, out);
+  if (live && a < P && b < P) {
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+      const int n = nid[k];
+      const unsigned m = __ldg(&bc[n]);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const int64_t dof = 3 * (int64_t)n + c;
+        if ((m >> c) & 1u) {
+          if (!lift) y[dof] = du[dof];
         } else {
           atomicAdd(&y[dof], out[c][k]);
         }
@@ -558,7 +690,7 @@ cudaError_t apply_launch(const OpArgs& A, cudaStream_t s) {
   const int threads = Q * Q * EPB;
   const int64_t blocks = (A.ne + EPB - 1) / EPB;
   if (blocks == 0) return cudaSuccess;
-  const size_t smem = (size_t)EPB * 9 * Q3 * sizeof(T);
+  const size_t smem = (size_t)EPB * elem_stride<Q, T>() * sizeof(T);
   const KTab<P, Q, T> tab = make_ktab<P, Q, T>(*A.tab);
   cudaError_t e = prep<k_jacobian_apply<P, Q, T, LAYOUT>>(smem);
   if (e != cudaSuccess) return e;
@@ -567,13 +699,28 @@ cudaError_t apply_launch(const OpArgs& A, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int P, int Q, int LAYOUT>
+cudaError_t apply_f32tma_launch(const OpArgs& A, cudaStream_t s) {
+  constexpr int EPB = epb_for(Q), S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
+  const int threads = Q * Q * EPB;
+  const int64_t blocks = (A.ne + EPB - 1) / EPB;
+  if (blocks == 0) return cudaSuccess;
+  const size_t smem = (size_t)nh_f32_batch_floats(Q, S) * 4 + (size_t)EPB * elem_stride<Q, float>() * 4;
+  const KTab<P, Q, float> tab = make_ktab<P, Q, float>(*A.tab);
+  cudaError_t e = prep<k_jacobian_apply_f32tma<P, Q, LAYOUT>>(smem);
+  if (e != cudaSuccess) return e;
+  k_jacobian_apply_f32tma<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
+      A.ne, A.emap, A.bc, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift, A.err);
+  return cudaGetLastError();
+}
+
 template <int P, int Q>
 cudaError_t apply_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
   if (prec == NH_F64)
     return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, double, NH_LAYOUT_CURRENT>(A, s)
                                          : apply_launch<P, Q, double, NH_LAYOUT_INITIAL>(A, s);
-  return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, float, NH_LAYOUT_CURRENT>(A, s)
-                                       : apply_launch<P, Q, float, NH_LAYOUT_INITIAL>(A, s);
+  return A.layout == NH_LAYOUT_CURRENT ? apply_f32tma_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
+                                       : apply_f32tma_launch<P, Q, NH_LAYOUT_INITIAL>(A, s);
 }
 
 template <int P, int Q, int LAYOUT>

@@ -924,6 +924,7 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
   double rel = 0.0, nr = 0.0;
   double t_prev = 0.0;
   int halvings = 0;
+  double nr_step = 0.0;  // initial residual of the current load step's first attempt
   auto setup = [&](const double* v, double* minJ) -> nh_status {
     const double t1 = now_s();
     nh_status s = nh_qdata_setup(F, v, minJ);
@@ -996,6 +997,9 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
     }
     CK(cudaMemcpyAsync(u, ut, 8 * n, cudaMemcpyDeviceToDevice, st));
     nr = nr0;
+    // the tolerance refers to the load step, not to a halved sub-increment of it
+    if (t_target - t_prev >= (t_target - t) * 1.000001 && halvings == 0) nr_step = nr0;
+    nr0 = std::max(nr0, nr_step);
     // --- Newton corrector at fixed t
     int it = 0;
     while (!(nr <= o.newton_rtol * nr0) && !(nr <= o.newton_atol)) {
@@ -1081,6 +1085,7 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
       halvings--;  // retry the rest of the increment with a larger step
     } else {
       halvings = 0;
+      nr_step = 0.0;
       step++;
       R.load_steps = step;
     }

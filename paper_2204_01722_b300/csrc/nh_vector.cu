@@ -48,7 +48,27 @@ __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ x, float* __r
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (float)x[i];
 }
 
+__global__ void k_f32_blocked(int Q3, int EPB, int S, long long BS, int64_t ne, const double* __restrict__ qd,
+                              float* __restrict__ qdf) {
+  const int64_t n = (int64_t)S * ne * Q3;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t s = i / (ne * Q3), r = i - s * ne * Q3;
+    const int64_t e = r / Q3, q = r - e * Q3;
+    qdf[(e / EPB) * BS + (s * EPB + e % EPB) * Q3 + q] = (float)qd[i];
+  }
+}
+
 }  // namespace
+
+cudaError_t nh_launch_f32_blocked(int Q, int S, int64_t ne, const double* qd, float* qdf, cudaStream_t s) {
+  const int64_t n = (int64_t)S * ne * Q * Q * Q;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  if (blocks < 1) blocks = 1;
+  k_f32_blocked<<<(unsigned)blocks, 256, 0, s>>>(Q * Q * Q, nh_epb(Q), S, nh_f32_batch_floats(Q, S), ne, qd, qdf);
+  return cudaGetLastError();
+}
 
 cudaError_t nh_launch_dot_partials(int64_t n, const double* x, const double* y, double* partials, int nblocks,
                                    cudaStream_t s) {
