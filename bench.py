@@ -314,7 +314,7 @@ def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusion
         u = torch.zeros(nd, dtype=torch.float64, device="cuda")
         rep = nh.nh_solve(ctx, mg, g, u, check=False)
         stream.synchronize()
-        out[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.as_dict().items()}
+        out[name] = {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.as_dict().items()}
         nh.nh_mg_destroy(mg)
     nh.nh_op_destroy(op)
     nh.nh_space_destroy(sp)
