@@ -592,6 +592,36 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 
   for (int c = 0; c < 3; c++) {
     for (int qk = 0; qk < Q; qk++) {
+      if (LAYOUT == NH_LAYOUT_CURRENT) {
+        // closed form of Eq. dtau's tangent block: D^c[d][d'] = A_dd' + (a + h) X_dc X_d'c,
+        // A = X (W tau) X^T + h X X^T, a = W lambda, h = W (mu - lambda log J)
+        double Dc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        if (live) {
+          const double* qp = qe + qk * Q2;
+          double X[3][3];
+#pragma unroll
+          for (int i = 0; i < 9; i++) X[i / 3][i % 3] = qp[i * qstride];
+          const double t00 = qp[9 * qstride], t11 = qp[10 * qstride], t22 = qp[11 * qstride];
+          const double t12 = qp[12 * qstride], t02 = qp[13 * qstride], t01 = qp[14 * qstride];
+          const double tau[3][3] = {{t00, t01, t02}, {t01, t11, t12}, {t02, t12, t22}};
+          const double wa = qp[15 * qstride], wh = qp[16 * qstride];
+#pragma unroll
+          for (int d = 0; d < 3; d++)
+#pragma unroll
+            for (int dp = 0; dp < 3; dp++) {
+              double v = (wa + wh) * X[d][c] * X[dp][c];
+#pragma unroll
+              for (int k = 0; k < 3; k++)
+                v += (X[d][0] * tau[0][k] + X[d][1] * tau[1][k] + X[d][2] * tau[2][k] + wh * X[d][k]) * X[dp][k];
+              Dc[d][dp] = v;
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+#pragma unroll
+          for (int dp = 0; dp < 3; dp++) Dsm[((d * 3 + dp) * Q + qk) * Q2 + b * Q + a] = Dc[d][dp];
+        continue;
+      }
 #pragma unroll
       for (int dp = 0; dp < 3; dp++) {
         double g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, f[3][3];

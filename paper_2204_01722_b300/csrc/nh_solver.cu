@@ -565,6 +565,17 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
   if (!root->have_qd) return nh_fail(mg->ctx, NH_ERR_STATE, "nh_mg_setup: call nh_qdata_setup first");
   cudaStream_t st = mg->ctx->stream;
   CK(cudaSetDevice(mg->ctx->device));
+  const bool timing = mg->o.verbose >= 2;
+  auto mark = [&](const char* what, int lv, double& t0) -> nh_status {
+    if (!timing) return NH_OK;
+    CK(cudaStreamSynchronize(st));
+    const double t1 = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    fprintf(stderr, "nh_mg_setup level %d %-9s %8.3f ms\n", lv, what, 1e3 * (t1 - t0));
+    t0 = t1;
+    return NH_OK;
+  };
+  double t0 = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  int lv = 0;
   for (Level& l : mg->L) {
     if (l.stencil) {
       CK(cudaMemsetAsync(l.A, 0, sizeof(double) * 243 * l.nn, st));
@@ -573,8 +584,10 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
                         root->space->ne * Q3, root->layout, &l.space->tab, l.A));
       CK(ks_diag(st, l.nn, l.space->bc, l.A, l.dinv64));
       mg->ctx->launches += 2;
+      ST(mark("stencil", lv, t0));
     } else {
       ST(nh_jacobian_diagonal(l.op, NH_F64, l.dinv64));
+      ST(mark("diagonal", lv, t0));
     }
     CK(kv_recip<double>(st, l.n, l.dinv64));
     mg->ctx->launches++;
@@ -582,7 +595,11 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
       CK((kv_convert<double, float>(st, l.n, l.dinv64, (float*)l.dinv)));
       mg->ctx->launches++;
     }
-    if (&l != &mg->L.back()) ST(lanczos(mg, l));
+    if (&l != &mg->L.back()) {
+      ST(lanczos(mg, l));
+      ST(mark("lanczos", lv, t0));
+    }
+    lv++;
   }
   CK(cudaStreamSynchronize(st));
   mg->setup_done = true;

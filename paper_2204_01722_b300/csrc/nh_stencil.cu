@@ -114,6 +114,93 @@ __global__ void k_diag(int64_t nn, const uint8_t* __restrict__ bc, const double*
   for (int c = 0; c < 3; c++) d[3 * n + c] = ((mb >> c) & 1u) ? 1.0 : A[((int64_t)13 * 9 + c * 4) * nn + n];
 }
 
+// Layout "current" (17 scalars) in closed form.  From Eq. dtau the reference
+// tangent is D[c,d,c',d'] = delta_cc' A_dd' + a X_dc X_d'c' + h X_dc' X_d'c with
+// X = grad_x xi, A = X (W tau) X^T + h X X^T, a = W lambda, h = W (mu - lambda log J),
+// so with g_a = grad_xi N_a and x_a = X^T g_a (the physical gradient)
+//   K_ab[c][c'] = sum_q delta_cc' g_a^T A g_b + a x_a,c x_b,c' + h x_a,c' x_b,c.
+// Per point, A and the 8 nodes' x_a and A g_a are formed once and shared by the
+// 64 (a, b) threads.
+template <int Q>
+__global__ void __launch_bounds__(64)
+    k_assemble_current(int64_t ne, int nx, int ny, const double* __restrict__ qd, int64_t qstride, const Q1Tab<Q> tb,
+                       double* __restrict__ A, int64_t nn, int Nx, int Ny) {
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
+  __shared__ double sa[kQC], sh[kQC];
+  __shared__ double sx[kQC][8][3], sAg[kQC][8][3], sg[kQC][8][3];
+  __shared__ double sA[kQC][6], sX[kQC][9];
+  const int t = threadIdx.x;
+  const int a = t & 7, b = t >> 3;
+  const int64_t e = blockIdx.x;
+  const int ai = a & 1, aj = (a >> 1) & 1, ak = a >> 2;
+  const int bi = b & 1, bj = (b >> 1) & 1, bk = b >> 2;
+  double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int q0 = 0; q0 < Q3; q0 += kQC) {
+    // per point: X, a, h and A = X (W tau) X^T + h X X^T
+    if (t < kQC && q0 + t < Q3) {
+      const double* qp = qd + e * Q3 + q0 + t;
+      double X[3][3];
+      for (int i = 0; i < 9; i++) X[i / 3][i % 3] = qp[i * qstride];
+      const double t00 = qp[9 * qstride], t11 = qp[10 * qstride], t22 = qp[11 * qstride];
+      const double t12 = qp[12 * qstride], t02 = qp[13 * qstride], t01 = qp[14 * qstride];
+      const double tau[3][3] = {{t00, t01, t02}, {t01, t11, t12}, {t02, t12, t22}};
+      const double h = qp[16 * qstride];
+      sa[t] = qp[15 * qstride];
+      sh[t] = h;
+      double XT[3][3];  // X (W tau)
+      for (int d = 0; d < 3; d++)
+        for (int k = 0; k < 3; k++) XT[d][k] = X[d][0] * tau[0][k] + X[d][1] * tau[1][k] + X[d][2] * tau[2][k];
+      const int ix[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+      for (int m = 0; m < 6; m++) {
+        const int d = ix[m][0], dp = ix[m][1];
+        double v = 0.0;
+        for (int k = 0; k < 3; k++) v += (XT[d][k] + h * X[d][k]) * X[dp][k];
+        sA[t][m] = v;
+      }
+      for (int i = 0; i < 9; i++) sX[t][i] = X[i / 3][i % 3];
+    }
+    __syncthreads();
+    // per (point, node): g_a, x_a = X^T g_a, A g_a  (64 threads = 8 points x 8 nodes)
+    {
+      const int ql = t >> 3, nd = t & 7;
+      const int q = q0 + ql;
+      if (q < Q3) {
+        const int qi = q % Q, qj = (q / Q) % Q, qk = q / Q2;
+        const int ni = nd & 1, nj = (nd >> 1) & 1, nk = nd >> 2;
+        const double g[3] = {tb.G[qi][ni] * tb.B[qj][nj] * tb.B[qk][nk], tb.B[qi][ni] * tb.G[qj][nj] * tb.B[qk][nk],
+                             tb.B[qi][ni] * tb.B[qj][nj] * tb.G[qk][nk]};
+        const double* X = sX[ql];
+        const double* Am = sA[ql];
+        const double As[3][3] = {{Am[0], Am[5], Am[4]}, {Am[5], Am[1], Am[3]}, {Am[4], Am[3], Am[2]}};
+        for (int c = 0; c < 3; c++) {
+          sx[ql][nd][c] = X[0 * 3 + c] * g[0] + X[1 * 3 + c] * g[1] + X[2 * 3 + c] * g[2];
+          sAg[ql][nd][c] = As[c][0] * g[0] + As[c][1] * g[1] + As[c][2] * g[2];
+          sg[ql][nd][c] = g[c];
+        }
+      }
+    }
+    __syncthreads();
+    for (int ql = 0; ql < kQC && q0 + ql < Q3; ql++) {
+      const double* xa = sx[ql][a];
+      const double* xb = sx[ql][b];
+      const double gAg = sAg[ql][a][0] * sg[ql][b][0] + sAg[ql][a][1] * sg[ql][b][1] + sAg[ql][a][2] * sg[ql][b][2];
+      const double wa = sa[ql], wh = sh[ql];
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int cp = 0; cp < 3; cp++) K[c][cp] += (c == cp ? gAg : 0.0) + wa * xa[c] * xb[cp] + wh * xa[cp] * xb[c];
+    }
+    __syncthreads();
+  }
+  const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+  const int64_t na = (ex + ai) + Nx * ((ey + aj) + (int64_t)Ny * (ez + ak));
+  const int s = (bi - ai + 1) + 3 * (bj - aj + 1) + 9 * (bk - ak + 1);
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int cp = 0; cp < 3; cp++) atomicAdd(&A[((int64_t)s * 9 + c * 3 + cp) * nn + na], K[c][cp]);
+}
+
 template <int Q>
 cudaError_t assemble_q(cudaStream_t st, int64_t ne, int nx, int ny, int nz, const double* qd, int64_t qstride,
                        int layout, const Tab1D* tab, double* A) {
@@ -127,7 +214,7 @@ cudaError_t assemble_q(cudaStream_t st, int64_t ne, int nx, int ny, int nz, cons
   const int64_t nn = (int64_t)Nx * Ny * (nz + 1);
   if (ne == 0) return cudaSuccess;
   if (layout == NH_LAYOUT_CURRENT)
-    k_assemble<Q, NH_LAYOUT_CURRENT><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny);
+    k_assemble_current<Q><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny);
   else
     k_assemble<Q, NH_LAYOUT_INITIAL><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny);
   return cudaGetLastError();
