@@ -13,8 +13,6 @@
 // elements (about 128 threads).  Scatter-add uses atomics.
 //
 // This file is compiled once per P (nodes per direction), with -DNH_P_INST=P.
-#include <algorithm>
-
 #include "nh_internal.cuh"
 #include "nh_pointwise.cuh"
 
@@ -284,35 +282,16 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 }
 
 // ---------------------------------------------------------------------------
-// FP32 Jacobian action, persistent and pipelined.  Each block loops over element
-// batches (EPB elements, blocked FP32 quadrature data [batch][S][EPB][Q^3]).  The
-// batch's quadrature data arrives in shared memory by one 1-D TMA bulk copy that
-// is issued as soon as the previous batch's pointwise stage has finished reading
-// the buffer, so the copy overlaps that batch's transposed contractions and
-// scatter and this batch's gather and interpolation; the next batch's element map
-// is loaded into registers one iteration ahead.
+// FP32 Jacobian action with the block's quadrature data staged in shared memory
+// by one 1-D TMA bulk copy (blocked layout [batch][S][EPB][Q^3]), issued at
+// block start so it overlaps the gather and the interpolation.
 // ---------------------------------------------------------------------------
-template <int P, int Q, int S>
-__device__ __forceinline__ void issue_batch_copy(const float* __restrict__ qdb, int64_t batch, float* qs,
-                                                 uint64_t* bar) {
-  constexpr long long BS = nh_f32_batch_floats(Q, S);
-  const unsigned bytes = (unsigned)(BS * sizeof(float));
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic reads of qs before async writes
-  mbar_expect_tx(bar, bytes);
-  const char* src = reinterpret_cast<const char*>(qdb + batch * BS);
-  char* dst = reinterpret_cast<char*>(qs);
-  for (unsigned off = 0; off < bytes; off += 16384u) {
-    const unsigned chunk = bytes - off < 16384u ? bytes - off : 16384u;
-    bulk_g2s(dst + off, src + off, chunk, bar);
-  }
-}
-
 template <int P, int Q, int LAYOUT>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     k_jacobian_apply_f32tma(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
                             const float* __restrict__ qdb, const KTab<P, Q, float> tab, const float* __restrict__ du,
                             float* __restrict__ y, int lift, int* __restrict__ err) {
-  constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
+  constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q;
   constexpr int S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
   constexpr long long BS = nh_f32_batch_floats(Q, S);
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -322,124 +301,65 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
   const int t = threadIdx.x;
   const int el = t / Q2, col = t - el * Q2;
   const int a = col % Q, b = col / Q;
+  const int64_t e = (int64_t)blockIdx.x * EPB + el;
+  const bool live = e < ne;
   float* bA = sm + el * elem_stride<Q, float>();
   float* bB = bA + 3 * Q3;
   float* bC = bB + 3 * Q3;
-  const int64_t nb = (ne + EPB - 1) / EPB;
-  int64_t batch = blockIdx.x;
   if (t == 0) mbar_init(&bar);
   __syncthreads();
-  if (batch >= nb) return;
-  if (t == 0) issue_batch_copy<P, Q, S>(qdb, batch, qs, &bar);
-  // element map of the first batch
-  int nid[P];
-  {
-    const int64_t e = batch * EPB + el;
-#pragma unroll
-    for (int k = 0; k < P; k++)
-      nid[k] = (e < ne && a < P && b < P) ? __ldg(&emap[e * P3 + (k * P + b) * P + a]) : 0;
+  if (t == 0) {
+    const unsigned bytes = (unsigned)(BS * sizeof(float));
+    mbar_expect_tx(&bar, bytes);
+    const char* src = reinterpret_cast<const char*>(qdb + (int64_t)blockIdx.x * BS);
+    char* dst = reinterpret_cast<char*>(qs);
+    for (unsigned off = 0; off < bytes; off += 16384u) {
+      const unsigned chunk = bytes - off < 16384u ? bytes - off : 16384u;
+      bulk_g2s(dst + off, src + off, chunk, &bar);
+    }
   }
-  for (unsigned it = 0; batch < nb; it++, batch += gridDim.x) {
-    const int64_t e = batch * EPB + el;
-    const bool live = e < ne;
-    const int64_t next = batch + gridDim.x;
-    // gather (node ids already in registers) and interpolation
-    float U[3][Q];
-    if (a < P && b < P) {
-      float r[3][P];
+  float U[3][Q];
+  int nid[P];
+  gather_interp<P, Q, float>(live, !lift, e, a, b, emap, bc, du, tab, bA, bB, bC, U, nid);
+  mbar_wait_bounded(&bar, 0, err);
+  __syncthreads();
+  float Fz[3][Q];
+  const float* qe = qs + el * Q3 + b * Q + a;
 #pragma unroll
-      for (int k = 0; k < P; k++) {
-        const int n = nid[k];
-        const unsigned m = (live && !lift) ? (unsigned)__ldg(&bc[n]) : 0u;
+  for (int qk = 0; qk < Q; qk++) {
+    float g[3][3], f[3][3];
+    colloc_grad<P, Q, float>(a, b, qk, tab, bC, U, g);
+    if (live) {
+      pointwise<LAYOUT, float>(qe + qk * Q2, (int64_t)EPB * Q3, g, f);
+    } else {
 #pragma unroll
-        for (int c = 0; c < 3; c++) r[c][k] = (live && !((m >> c) & 1u)) ? du[3 * (int64_t)n + c] : 0.f;
-      }
-#pragma unroll
-      for (int c = 0; c < 3; c++)
-#pragma unroll
-        for (int qk = 0; qk < Q; qk++) {
-          float sacc = 0.f;
-#pragma unroll
-          for (int k = 0; k < P; k++) sacc += tab.B[qk][k] * r[c][k];
-          bA[sidx<Q>(c, qk, b, a)] = sacc;
-        }
+      for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.f;
     }
-    __syncthreads();
-    if (a < P) {
 #pragma unroll
-      for (int c = 0; c < 3; c++)
-#pragma unroll
-        for (int qk = 0; qk < Q; qk++) {
-          float sacc = 0.f;
-#pragma unroll
-          for (int j = 0; j < P; j++) sacc += tab.B[b][j] * bA[sidx<Q>(c, qk, j, a)];
-          bB[sidx<Q>(c, qk, b, a)] = sacc;
-        }
+    for (int c = 0; c < 3; c++) {
+      bA[sidx<Q>(c, qk, b, a)] = f[c][0];
+      bB[sidx<Q>(c, qk, b, a)] = f[c][1];
+      Fz[c][qk] = f[c][2];
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  float out[3][P];
+  transpose_to_nodes<P, Q, float>(a, b, tab, bA, bB, bC, Fz, out);
+  if (live && a < P && b < P) {
 #pragma unroll
-    for (int c = 0; c < 3; c++)
-#pragma unroll
-      for (int qk = 0; qk < Q; qk++) {
-        float sacc = 0.f;
-#pragma unroll
-        for (int i = 0; i < P; i++) sacc += tab.B[a][i] * bB[sidx<Q>(c, qk, b, i)];
-        U[c][qk] = sacc;
-        bC[sidx<Q>(c, qk, b, a)] = sacc;
-      }
-    // this thread's node ids for the next batch (latency hidden by the work below)
-    int nid_next[P];
-    {
-      const int64_t en = next * EPB + el;
-#pragma unroll
-      for (int k = 0; k < P; k++)
-        nid_next[k] = (next < nb && en < ne && a < P && b < P) ? __ldg(&emap[en * P3 + (k * P + b) * P + a]) : 0;
-    }
-    mbar_wait_bounded(&bar, it & 1u, err);
-    __syncthreads();
-    float Fz[3][Q];
-    const float* qe = qs + el * Q3 + b * Q + a;
-#pragma unroll
-    for (int qk = 0; qk < Q; qk++) {
-      float g[3][3], f[3][3];
-      colloc_grad<P, Q, float>(a, b, qk, tab, bC, U, g);
-      if (live) {
-        pointwise<LAYOUT, float>(qe + qk * Q2, (int64_t)EPB * Q3, g, f);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.f;
-      }
+    for (int k = 0; k < P; k++) {
+      const int n = nid[k];
+      const unsigned m = __ldg(&bc[n]);
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        bA[sidx<Q>(c, qk, b, a)] = f[c][0];
-        bB[sidx<Q>(c, qk, b, a)] = f[c][1];
-        Fz[c][qk] = f[c][2];
-      }
-    }
-    __syncthreads();
-    // the quadrature-data buffer is free: fetch the next batch's
-    if (t == 0 && next < nb) issue_batch_copy<P, Q, S>(qdb, next, qs, &bar);
-    float out[3][P];
-    transpose_to_nodes<P, Q, float>(a, b, tab, bA, bB, bC, Fz, out);
-    if (live && a < P && b < P) {
-#pragma unroll
-      for (int k = 0; k < P; k++) {
-        const int n = nid[k];
-        const unsigned m = __ldg(&bc[n]);
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-          const int64_t dof = 3 * (int64_t)n + c;
-          if ((m >> c) & 1u) {
-            if (!lift) y[dof] = du[dof];
-          } else {
-            atomicAdd(&y[dof], out[c][k]);
-          }
+        const int64_t dof = 3 * (int64_t)n + c;
+        if ((m >> c) & 1u) {
+          if (!lift) y[dof] = du[dof];
+        } else {
+          atomicAdd(&y[dof], out[c][k]);
         }
       }
     }
-#pragma unroll
-    for (int k = 0; k < P; k++) nid[k] = nid_next[k];
-    __syncthreads();  // bA/bB/bC are reused by the next batch
   }
 }
 
@@ -813,24 +733,13 @@ template <int P, int Q, int LAYOUT>
 cudaError_t apply_f32tma_launch(const OpArgs& A, cudaStream_t s) {
   constexpr int EPB = epb_for(Q), S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
   const int threads = Q * Q * EPB;
-  const int64_t nbatch = (A.ne + EPB - 1) / EPB;
-  if (nbatch == 0) return cudaSuccess;
+  const int64_t blocks = (A.ne + EPB - 1) / EPB;
+  if (blocks == 0) return cudaSuccess;
   const size_t smem = (size_t)nh_f32_batch_floats(Q, S) * 4 + (size_t)EPB * elem_stride<Q, float>() * 4;
   const KTab<P, Q, float> tab = make_ktab<P, Q, float>(*A.tab);
   cudaError_t e = prep<k_jacobian_apply_f32tma<P, Q, LAYOUT>>(smem);
   if (e != cudaSuccess) return e;
-  // persistent grid: every resident block slot of every SM
-  static int per_sm = 0, sms = 0;
-  if (!per_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobian_apply_f32tma<P, Q, LAYOUT>, threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-  }
-  const int64_t grid = std::min<int64_t>(nbatch, (int64_t)per_sm * sms);
-  k_jacobian_apply_f32tma<P, Q, LAYOUT><<<(unsigned)grid, threads, smem, s>>>(
+  k_jacobian_apply_f32tma<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
       A.ne, A.emap, A.bc, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift, A.err);
   return cudaGetLastError();
 }
