@@ -142,7 +142,7 @@ class Case:
         self.y32 = torch.empty_like(self.du32)
 
     def vecs(self, prec):
-        return (self.du64, self.y64) if prec == "f64" else (self.du32, self.y32)
+        return (self.du32, self.y32) if prec == "f32" else (self.du64, self.y64)
 
     def close(self):
         self.nh.nh_op_destroy(self.op)
@@ -152,7 +152,7 @@ class Case:
 def time_applies(nh, torch, ctx, stream, case, prec, steps, warmup, barrier):
     du, y = case.vecs(prec)
     for _ in range(warmup):
-        nh.nh_jacobian_apply(ctx, case.op, du, y)
+        nh.nh_jacobian_apply(ctx, case.op, du, y, prec=PREC[prec])
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -160,7 +160,7 @@ def time_applies(nh, torch, ctx, stream, case, prec, steps, warmup, barrier):
     l0 = nh.nh_launch_count(ctx)
     e0.record(stream)
     for _ in range(steps):
-        nh.nh_jacobian_apply(ctx, case.op, du, y)
+        nh.nh_jacobian_apply(ctx, case.op, du, y, prec=PREC[prec])
     e1.record(stream)
     e1.synchronize()
     launches = nh.nh_launch_count(ctx) - l0
@@ -169,12 +169,15 @@ def time_applies(nh, torch, ctx, stream, case, prec, steps, warmup, barrier):
     return e0.elapsed_time(e1), launches
 
 
+PREC = {"f64": 0, "f32": 1, "f64x": 2}
+
+
 def kernel_ms(nh, ctx, case, prec, steps):
     du, y = case.vecs(prec)
     nh.nh_profile_read(ctx)
     nh.nh_profile_enable(ctx, True)
     for _ in range(steps):
-        nh.nh_jacobian_apply(ctx, case.op, du, y)
+        nh.nh_jacobian_apply(ctx, case.op, du, y, prec=PREC[prec])
     tot, k = nh.nh_profile_read(ctx)
     nh.nh_profile_enable(ctx, False)
     return tot / max(k, 1)
@@ -216,9 +219,9 @@ def run_nh(args):
         # roofline of the apply kernel alone (CUDA events around each launch)
         kms = kernel_ms(nh, ctx, case, args.prec, args.steps)
         hbm, hbm_src = peaks()
-        wb = 8 if args.prec == "f64" else 4
+        wb = 4 if args.prec == "f32" else 8
         S, _ = nh.nh_op_info(ctx, case.op)
-        if args.prec == "f64":
+        if args.prec in ("f64", "f64x"):
             ach = apply_flops(p, n) / (kms * 1e-3) / 1e12
             roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                     "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": args.traffic,
@@ -230,16 +233,16 @@ def run_nh(args):
                     "frac": round(ach / hbm, 4), "traffic": args.traffic, "peak_source": hbm_src + " (copy)",
                     "kernel_ms": round(kms, 4)}
         # end to end through the host-buffer entry point
-        dt = np.float64 if args.prec == "f64" else np.float32
+        dt = np.float32 if args.prec == "f32" else np.float64
         hin = torch.from_numpy(np.ascontiguousarray(case.vecs(args.prec)[0].cpu().numpy())).pin_memory()
         hout = torch.empty_like(hin).pin_memory()
         for _ in range(2):
-            nh.nh_jacobian_apply_host(ctx, case.op, hin, hout)
+            nh.nh_jacobian_apply_host(ctx, case.op, hin, hout, prec=PREC[args.prec])
         ek = max(3, args.steps // 10)
         barrier()
         t0 = time.perf_counter()
         for _ in range(ek):
-            nh.nh_jacobian_apply_host(ctx, case.op, hin, hout)
+            nh.nh_jacobian_apply_host(ctx, case.op, hin, hout, prec=PREC[args.prec])
         te = time.perf_counter() - t0
         tt = torch.tensor([te], dtype=torch.float64, device="cuda")
         if dist is not None:
@@ -256,10 +259,10 @@ def run_nh(args):
             for sp_ in (2, 3, 4):
                 c = Case(nh, torch, ctx, sp_, DEFAULT_N[sp_])
                 Sx, _ = nh.nh_op_info(ctx, c.op)
-                for pr in ("f64", "f32"):
+                for pr in ("f64", "f64x", "f32"):
                     k = kernel_ms(nh, ctx, c, pr, 5)  # warm (FP32 copy of the qdata on first use)
                     k = kernel_ms(nh, ctx, c, pr, 20)
-                    w_ = 8 if pr == "f64" else 4
+                    w_ = 4 if pr == "f32" else 8
                     gbs = apply_bytes(sp_, c.n, w_, Sx) / (k * 1e-3) / 1e9
                     tfl = apply_flops(sp_, c.n) / (k * 1e-3) / 1e12
                     sweep.append({"p": sp_, "n": c.n, "n_dof": c.nd, "prec": pr,
@@ -267,6 +270,8 @@ def run_nh(args):
                                   "algorithmic_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
                                   "tflops": round(tfl, 3),
                                   "alu_frac": round(tfl / (FP64_PEAK_TFLOPS if pr == "f64" else FP32_PEAK_TFLOPS), 4)})
+                    if pr == "f64x":  # ALU peak of float-float: FP32 pipe / ~15 instructions per FP64 op
+                        sweep[-1]["alu_frac"] = None
                 c.close()
         solve = run_solves(nh, torch, ctx, stream) if (args.solve and rank == 0) else None
         nh.nh_destroy(ctx)
@@ -387,7 +392,7 @@ def main():
     ap.add_argument("--impl", default="nh", choices=["nh", "reference"])
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "f64x"])
     ap.add_argument("--no-sweep", dest="sweep", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-solve", dest="solve", action="store_false")

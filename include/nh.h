@@ -55,7 +55,12 @@ typedef enum {
   NH_ERR_UNSUPPORTED = 9     /* (p, q) or layout outside the compiled set */
 } nh_status;
 
-typedef enum { NH_F64 = 0, NH_F32 = 1 } nh_prec;
+/* NH_F64X: FP64 vectors in and out, arithmetic in float-float (pairs of FP32
+ * with about 48 significant bits) on the FP32 pipes, which B300 runs at 64 times
+ * its FP64 FMA rate; results agree with NH_F64 to ~1e-13.  The quadrature data
+ * are converted to float pairs on first use.  Accepted by nh_jacobian_apply and
+ * nh_jacobian_apply_host only. */
+typedef enum { NH_F64 = 0, NH_F32 = 1, NH_F64X = 2 } nh_prec;
 
 /* Stored quadrature data.  NH_LAYOUT_CURRENT is the paper's 17 scalars per
  * point (Sec. III-B and Table different-storage "current"): grad_x xi (9),

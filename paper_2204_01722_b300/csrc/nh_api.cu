@@ -323,6 +323,7 @@ extern "C" nh_status nh_op_destroy(nh_op op) {
     cudaFree(op->mu);
     cudaFree(op->qd);
     cudaFree(op->qd_f);
+    cudaFree(op->qd_ff);
   }
   cudaFree(op->hbuf_in);
   cudaFree(op->hbuf_out);
@@ -380,6 +381,7 @@ extern "C" nh_status nh_qdata_setup(nh_op op, const double* u, double* min_J) {
   memcpy(&mj, &bits, sizeof(mj));
   if (min_J) *min_J = mj;
   op->qd_f_valid = false;
+  op->qd_ff_valid = false;
   if (!(mj > 0.0) || !isfinite(mj)) {
     op->have_qd = false;
     char buf[128];
@@ -421,11 +423,23 @@ static nh_status ensure_f32(nh_op root) {
   return NH_OK;
 }
 
+static nh_status ensure_ff(nh_op root) {
+  nh_ctx ctx = root->space->ctx;
+  if (root->qd_ff_valid) return NH_OK;
+  const int64_t n = root->S * root->space->ne * (int64_t)root->space->Q * root->space->Q * root->space->Q;
+  if (!root->qd_ff) NH_CUDA(ctx, cudaMalloc(&root->qd_ff, 2 * sizeof(float) * n));
+  NH_CUDA(ctx, nh_launch_f64_to_ff(n, root->qd, root->qd_ff, ctx->stream));
+  ctx->launches++;
+  root->qd_ff_valid = true;
+  return NH_OK;
+}
+
 extern "C" nh_status nh_jacobian_apply(nh_op op, nh_prec prec, const void* du, void* y) {
   if (!op || !du || !y) return NH_ERR_ARG;
   nh_ctx ctx = op->space->ctx;
   nh_op root = op->parent ? op->parent : op;
-  if (prec != NH_F64 && prec != NH_F32) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply: bad precision");
+  if (prec != NH_F64 && prec != NH_F32 && prec != NH_F64X)
+    return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply: bad precision");
   if (du == (const void*)y) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply: du and y must not alias");
   if (!aligned(du, 16) || !aligned(y, 16)) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply: misaligned vector");
   if (!root->have_qd) return nh_fail(ctx, NH_ERR_STATE, "nh_jacobian_apply: call nh_qdata_setup first");
@@ -433,13 +447,16 @@ extern "C" nh_status nh_jacobian_apply(nh_op op, nh_prec prec, const void* du, v
   if (prec == NH_F32) {
     nh_status st = ensure_f32(root);
     if (st != NH_OK) return st;
+  } else if (prec == NH_F64X) {
+    nh_status st = ensure_ff(root);
+    if (st != NH_OK) return st;
   }
   OpArgs a = base_args(op);
   a.in = du;
   a.out = y;
   a.prec = prec;
-  a.qd = prec == NH_F64 ? (const void*)root->qd : (const void*)root->qd_f;
-  const size_t w = prec == NH_F64 ? 8 : 4;
+  a.qd = prec == NH_F64 ? (const void*)root->qd : prec == NH_F32 ? (const void*)root->qd_f : (const void*)root->qd_ff;
+  const size_t w = prec == NH_F32 ? 4 : 8;
   NH_CUDA(ctx, cudaMemsetAsync(y, 0, w * op->space->n_dof, ctx->stream));
   cudaEvent_t* ev = nullptr;
   if (ctx->prof_on && ctx->ev_used + 2 <= kMaxProfEvents) {
@@ -499,8 +516,9 @@ nh_status nh_jacobian_apply_lift(nh_op op, const double* x, double* y) {
 extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* du_h, void* y_h) {
   if (!op || !du_h || !y_h) return NH_ERR_ARG;
   nh_ctx ctx = op->space->ctx;
-  if (prec != NH_F64 && prec != NH_F32) return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply_host: bad precision");
-  const size_t bytes = (prec == NH_F64 ? 8 : 4) * (size_t)op->space->n_dof;
+  if (prec != NH_F64 && prec != NH_F32 && prec != NH_F64X)
+    return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply_host: bad precision");
+  const size_t bytes = (prec == NH_F32 ? 4 : 8) * (size_t)op->space->n_dof;
   NH_CUDA(ctx, cudaSetDevice(ctx->device));
   if (op->hbuf_bytes < bytes) {
     NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

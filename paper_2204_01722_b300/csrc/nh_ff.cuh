@@ -1,0 +1,61 @@
+// Float-float ("double-single") arithmetic: a value is the unevaluated sum h + l
+// of two floats with |l| <= ulp(h) / 2, about 48 significant bits.  Built from the
+// error-free transformations TwoSum (Knuth), Fast2Sum (Dekker, |a| >= |b|) and
+// the FMA form of TwoProduct, with the "sloppy" addition (one TwoSum on the high
+// parts, the low parts added and renormalised): error ~ 2^-47 (|a| + |b|).
+// It lets the FP64-accurate Jacobian run on B300's FP32 pipes, which issue 64
+// FMAs for each FP64 FMA.  Compile without fast-math: the transformations rely
+// on IEEE round-to-nearest of each float operation.
+#pragma once
+#include <cuda_runtime.h>
+
+struct ff {
+  float h, l;
+  __host__ __device__ __forceinline__ ff() : h(0.f), l(0.f) {}
+  __host__ __device__ __forceinline__ ff(float a, float b) : h(a), l(b) {}
+  __host__ __device__ __forceinline__ ff(double d) {
+    h = (float)d;
+    l = (float)(d - (double)h);
+  }
+  __host__ __device__ __forceinline__ ff(int i) : ff((double)i) {}
+  __host__ __device__ __forceinline__ explicit operator double() const { return (double)h + (double)l; }
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return ff(s, e);
+}
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  const float e = b - (s - a);
+  return ff(s, e);
+}
+
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  const ff s = ff_two_sum(a.h, b.h);
+  return ff_fast_two_sum(s.h, s.l + (a.l + b.l));
+}
+
+__device__ __forceinline__ ff operator-(ff a) { return ff(-a.h, -a.l); }
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + ff(-b.h, -b.l); }
+
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return ff_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff& operator+=(ff& a, ff b) {
+  a = a + b;
+  return a;
+}
+
+__device__ __forceinline__ ff& operator*=(ff& a, ff b) {
+  a = a * b;
+  return a;
+}

@@ -99,6 +99,8 @@ struct nh_op_s {
   double* mu = nullptr;
   double* qd = nullptr;           // [S][ne*Q^3] FP64 quadrature data (fine op only)
   float* qd_f = nullptr;          // FP32 copy, blocked per element batch (nh_f32_batch_floats)
+  float* qd_ff = nullptr;         // float-float pairs (h, l), same indexing as qd (NH_F64X)
+  bool qd_ff_valid = false;
   bool have_qd = false;
   bool qd_f_valid = false;
   // device staging for nh_jacobian_apply_host
@@ -172,5 +174,7 @@ cudaError_t nh_launch_dot_partials(int64_t n, const double* x, const double* y, 
                                    int nblocks, cudaStream_t s);
 cudaError_t nh_launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
 cudaError_t nh_launch_f64_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);
+// FP64 -> float-float pairs (h, l) elementwise
+cudaError_t nh_launch_f64_to_ff(int64_t n, const double* x, float* y2, cudaStream_t s);
 // FP64 SoA quadrature data [S][ne Q^3] -> blocked FP32 [batch][S][EPB][Q^3]
 cudaError_t nh_launch_f32_blocked(int Q, int S, int64_t ne, const double* qd, float* qdf, cudaStream_t s);

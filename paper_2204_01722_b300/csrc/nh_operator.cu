@@ -15,6 +15,7 @@
 // This file is compiled once per P (nodes per direction), with -DNH_P_INST=P.
 #include "nh_internal.cuh"
 #include "nh_pointwise.cuh"
+#include "nh_ff.cuh"
 
 #ifndef NH_P_INST
 #error "compile with -DNH_P_INST=<P>"
@@ -88,9 +89,9 @@ using nhpw::pointwise;
 // E then B_I: gather the element's P^3 nodes (masking constrained components if
 // mask_in) and interpolate to the Q^3 points.  Leaves the point values in U
 // (registers, this thread's column) and in bC; remembers node ids in nid.
-template <int P, int Q, typename T>
+template <int P, int Q, typename T, typename TS = T>
 __device__ __forceinline__ void gather_interp(bool live, bool mask_in, int64_t e, int a, int b, const int* __restrict__ emap,
-                                              const uint8_t* __restrict__ bc, const T* __restrict__ src,
+                                              const uint8_t* __restrict__ bc, const TS* __restrict__ src,
                                               const KTab<P, Q, T>& tab, T* bA, T* bB, T* bC, T (&U)[3][Q],
                                               int (&nid)[P]) {
   constexpr int P3 = P * P * P;
@@ -102,7 +103,7 @@ __device__ __forceinline__ void gather_interp(bool live, bool mask_in, int64_t e
       nid[k] = n;
       unsigned m = (mask_in && live) ? (unsigned)__ldg(&bc[n]) : 0u;
 #pragma unroll
-      for (int c = 0; c < 3; c++) r[c][k] = (live && !((m >> c) & 1u)) ? src[3 * (int64_t)n + c] : T(0);
+      for (int c = 0; c < 3; c++) r[c][k] = (live && !((m >> c) & 1u)) ? T(src[3 * (int64_t)n + c]) : T(0);
     }
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -220,11 +221,13 @@ __device__ __forceinline__ void transpose_to_nodes(int a, int b, const KTab<P, Q
 // ---------------------------------------------------------------------------
 // Jacobian action
 // ---------------------------------------------------------------------------
-template <int P, int Q, typename T, int LAYOUT>
+// T: arithmetic type (double, or ff for FP64-accurate float-float on the FP32
+// pipes); TV: type of the vectors du and y.
+template <int P, int Q, typename T, typename TV, int LAYOUT>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     k_jacobian_apply(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
-                     const T* __restrict__ qd, int64_t qstride, const KTab<P, Q, T> tab, const T* __restrict__ du,
-                     T* __restrict__ y, int lift) {
+                     const T* __restrict__ qd, int64_t qstride, const KTab<P, Q, T> tab, const TV* __restrict__ du,
+                     TV* __restrict__ y, int lift) {
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 
   T U[3][Q];
   int nid[P];
-  gather_interp<P, Q, T>(live, !lift, e, a, b, emap, bc, du, tab, bA, bB, bC, U, nid);
+  gather_interp<P, Q, T, TV>(live, !lift, e, a, b, emap, bc, du, tab, bA, bB, bC, U, nid);
   __syncthreads();
   T Fz[3][Q];
   const T* qe = qd + (live ? e : 0) * Q3 + b * Q + a;
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
         if ((m >> c) & 1u) {
           if (!lift) y[dof] = du[dof];  // identity row; every writer stores the same value
         } else {
-          atomicAdd(&y[dof], out[c][k]);
+          atomicAdd(&y[dof], (TV)out[c][k]);
         }
       }
     }
@@ -714,18 +717,18 @@ cudaError_t prep(size_t smem) {
   return cudaSuccess;
 }
 
-template <int P, int Q, typename T, int LAYOUT>
+template <int P, int Q, typename T, typename TV, int LAYOUT>
 cudaError_t apply_launch(const OpArgs& A, cudaStream_t s) {
-  constexpr int EPB = epb_for(Q), Q3 = Q * Q * Q;
+  constexpr int EPB = epb_for(Q);
   const int threads = Q * Q * EPB;
   const int64_t blocks = (A.ne + EPB - 1) / EPB;
   if (blocks == 0) return cudaSuccess;
   const size_t smem = (size_t)EPB * elem_stride<Q, T>() * sizeof(T);
   const KTab<P, Q, T> tab = make_ktab<P, Q, T>(*A.tab);
-  cudaError_t e = prep<k_jacobian_apply<P, Q, T, LAYOUT>>(smem);
+  cudaError_t e = prep<k_jacobian_apply<P, Q, T, TV, LAYOUT>>(smem);
   if (e != cudaSuccess) return e;
-  k_jacobian_apply<P, Q, T, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
-      A.ne, A.emap, A.bc, (const T*)A.qd, A.qstride, tab, (const T*)A.in, (T*)A.out, A.lift);
+  k_jacobian_apply<P, Q, T, TV, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
+      A.ne, A.emap, A.bc, (const T*)A.qd, A.qstride, tab, (const TV*)A.in, (TV*)A.out, A.lift);
   return cudaGetLastError();
 }
 
@@ -747,8 +750,11 @@ cudaError_t apply_f32tma_launch(const OpArgs& A, cudaStream_t s) {
 template <int P, int Q>
 cudaError_t apply_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
   if (prec == NH_F64)
-    return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, double, NH_LAYOUT_CURRENT>(A, s)
-                                         : apply_launch<P, Q, double, NH_LAYOUT_INITIAL>(A, s);
+    return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, double, double, NH_LAYOUT_CURRENT>(A, s)
+                                         : apply_launch<P, Q, double, double, NH_LAYOUT_INITIAL>(A, s);
+  if (prec == NH_F64X)
+    return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, ff, double, NH_LAYOUT_CURRENT>(A, s)
+                                         : apply_launch<P, Q, ff, double, NH_LAYOUT_INITIAL>(A, s);
   return A.layout == NH_LAYOUT_CURRENT ? apply_f32tma_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
                                        : apply_f32tma_launch<P, Q, NH_LAYOUT_INITIAL>(A, s);
 }

@@ -2,6 +2,7 @@
 // partial sums, then one fixed-order pass, so results do not depend on timing)
 // and precision conversion.
 #include "nh_internal.cuh"
+#include "nh_ff.cuh"
 
 namespace {
 
@@ -59,7 +60,20 @@ __global__ void k_f32_blocked(int Q3, int EPB, int S, long long BS, int64_t ne, 
   }
 }
 
+__global__ void k_f64_to_ff(int64_t n, const double* __restrict__ x, ff* __restrict__ y) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = ff(x[i]);
+}
+
 }  // namespace
+
+cudaError_t nh_launch_f64_to_ff(int64_t n, const double* x, float* y2, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  if (blocks < 1) blocks = 1;
+  k_f64_to_ff<<<(unsigned)blocks, 256, 0, s>>>(n, x, reinterpret_cast<ff*>(y2));
+  return cudaGetLastError();
+}
 
 cudaError_t nh_launch_f32_blocked(int Q, int S, int64_t ne, const double* qd, float* qdf, cudaStream_t s) {
   const int64_t n = (int64_t)S * ne * Q * Q * Q;

@@ -20,7 +20,7 @@ NH_ERR_NOT_CONVERGED, NH_ERR_NAN, NH_ERR_TIMEOUT, NH_ERR_STATE, NH_ERR_UNSUPPORT
 STATUS_NAMES = {0: "NH_OK", 1: "NH_ERR_ARG", 2: "NH_ERR_CUDA", 3: "NH_ERR_OOM", 4: "NH_ERR_INVERTED",
                 5: "NH_ERR_NOT_CONVERGED", 6: "NH_ERR_NAN", 7: "NH_ERR_TIMEOUT", 8: "NH_ERR_STATE",
                 9: "NH_ERR_UNSUPPORTED"}
-NH_F64, NH_F32 = 0, 1
+NH_F64, NH_F32, NH_F64X = 0, 1, 2
 NH_LAYOUT_CURRENT, NH_LAYOUT_INITIAL = 0, 1
 
 _vp = C.c_void_p

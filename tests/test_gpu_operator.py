@@ -84,6 +84,21 @@ def test_jacobian_apply_fp64(nhctx, n, p, q, layout):
     c.close()
 
 
+@pytest.mark.parametrize("n,p,q", [((3, 2, 4), 2, 3), ((3, 3, 2), 3, 4), ((2, 3, 2), 4, 5), ((2, 2, 3), 2, 4),
+                                   ((4, 3, 3), 1, 2)])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_jacobian_apply_f64x(nhctx, n, p, q, layout):
+    """Float-float arithmetic on the FP32 pipes, FP64 vectors: same 1e-12 bar as FP64."""
+    ctx, _ = nhctx
+    c = Case(ctx, n, p, q, layout=layout, seed=21)
+    du = inputs.normal_vector(c.sp.n_dof, seed=22)
+    y = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
+    c.nh.nh_jacobian_apply(ctx, c.op, dev(du), y, prec=c.nh.NH_F64X)
+    ref = fem.jacobian_apply(c.sp, c.state, du, c.mask, form="A" if layout == 0 else "B")
+    assert rel(host(y), ref) < TOL64
+    c.close()
+
+
 @pytest.mark.parametrize("n,p", [((3, 2, 4), 2), ((3, 3, 2), 3), ((2, 3, 2), 4)])
 @pytest.mark.parametrize("layout", [0, 1])
 def test_jacobian_apply_fp32(nhctx, n, p, layout):
