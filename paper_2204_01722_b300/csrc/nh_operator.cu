@@ -25,6 +25,20 @@ namespace {
 
 __host__ __device__ constexpr int epb_for(int Q) { return nh_epb(Q); }
 
+// Resident blocks per SM requested from the register allocator.  The float-float
+// kernel runs on the FP32 pipes, which need more warps in flight than the FP64
+// pipe to stay busy; left unconstrained it takes up to 255 registers (2 blocks of
+// ~128 threads).  Measured on B300 (Q3 on 48^3): 2 blocks 2.97, 3 blocks 4.20,
+// 4 blocks 4.78 GDoF/s; for q = 5 three blocks beat four (4.32 vs 4.06), the
+// spills of a 128-register cap outweigh the extra warps.
+#ifndef NH_FF_MIN_BLOCKS_SMALLQ
+#define NH_FF_MIN_BLOCKS_SMALLQ 4
+#endif
+template <typename T, int Q>
+__host__ __device__ constexpr int apply_min_blocks() {
+  return std::is_same<T, ff>::value ? (Q <= 4 ? NH_FF_MIN_BLOCKS_SMALLQ : 3) : 1;
+}
+
 // Shared-memory stride of one element's [9][Q^3] work area, padded so that the
 // Q*Q threads of consecutive elements in a warp fall on different banks
 // (stride = Q^2 modulo the number of T words that cover the 32 banks).
@@ -224,7 +238,7 @@ __device__ __forceinline__ void transpose_to_nodes(int a, int b, const KTab<P, Q
 // T: arithmetic type (double, or ff for FP64-accurate float-float on the FP32
 // pipes); TV: type of the vectors du and y.
 template <int P, int Q, typename T, typename TV, int LAYOUT>
-__global__ void __launch_bounds__(Q* Q* epb_for(Q))
+__global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<T, Q>())
     k_jacobian_apply(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
                      const T* __restrict__ qd, int64_t qstride, const KTab<P, Q, T> tab, const TV* __restrict__ du,
                      TV* __restrict__ y, int lift) {
