@@ -59,3 +59,15 @@ __device__ __forceinline__ ff& operator*=(ff& a, ff b) {
   a = a * b;
   return a;
 }
+
+// s + a * b: TwoProduct of the high parts with the cross terms folded into its
+// error, one TwoSum of the high parts, then a single Fast2Sum renormalisation
+// (15 float operations against 18 for a separate product and sum).
+__device__ __forceinline__ ff ff_madd(ff s, ff a, ff b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const ff t = ff_two_sum(s.h, p);
+  return ff_fast_two_sum(t.h, t.l + (s.l + e));
+}

@@ -96,6 +96,12 @@ __device__ __forceinline__ int sidx(int c, int k, int j, int i) {
 
 using nhpw::pointwise;
 
+// s + a * b as one fused operation: FMA for float and double; for float-float
+// the product's error terms and the running sum share one renormalisation.
+__device__ __forceinline__ float madd(float s, float a, float b) { return s + a * b; }
+__device__ __forceinline__ double madd(double s, double a, double b) { return fma(a, b, s); }
+__device__ __forceinline__ ff madd(ff s, ff a, ff b) { return ff_madd(s, a, b); }
+
 // ---------------------------------------------------------------------------
 // Sum-factorised element stages.  Shared buffers bA, bB, bC are [3][Q][Q][Q].
 // ---------------------------------------------------------------------------
@@ -125,7 +131,7 @@ __device__ __forceinline__ void gather_interp(bool live, bool mask_in, int64_t e
       for (int qk = 0; qk < Q; qk++) {
         T s = T(0);
 #pragma unroll
-        for (int k = 0; k < P; k++) s += tab.B[qk][k] * r[c][k];
+        for (int k = 0; k < P; k++) s = madd(s, tab.B[qk][k], r[c][k]);
         bA[sidx<Q>(c, qk, b, a)] = s;
       }
   } else {
@@ -140,7 +146,7 @@ __device__ __forceinline__ void gather_interp(bool live, bool mask_in, int64_t e
       for (int qk = 0; qk < Q; qk++) {
         T s = T(0);
 #pragma unroll
-        for (int j = 0; j < P; j++) s += tab.B[b][j] * bA[sidx<Q>(c, qk, j, a)];
+        for (int j = 0; j < P; j++) s = madd(s, tab.B[b][j], bA[sidx<Q>(c, qk, j, a)]);
         bB[sidx<Q>(c, qk, b, a)] = s;
       }
   }
@@ -151,7 +157,7 @@ __device__ __forceinline__ void gather_interp(bool live, bool mask_in, int64_t e
     for (int qk = 0; qk < Q; qk++) {
       T s = T(0);
 #pragma unroll
-      for (int i = 0; i < P; i++) s += tab.B[a][i] * bB[sidx<Q>(c, qk, b, i)];
+      for (int i = 0; i < P; i++) s = madd(s, tab.B[a][i], bB[sidx<Q>(c, qk, b, i)]);
       U[c][qk] = s;
       bC[sidx<Q>(c, qk, b, a)] = s;
     }
@@ -166,9 +172,9 @@ __device__ __forceinline__ void colloc_grad(int a, int b, int qk, const KTab<P, 
     T gx = T(0), gy = T(0), gz = T(0);
 #pragma unroll
     for (int m = 0; m < Q; m++) {
-      gx += tab.D[a][m] * bC[sidx<Q>(c, qk, b, m)];
-      gy += tab.D[b][m] * bC[sidx<Q>(c, qk, m, a)];
-      gz += tab.D[qk][m] * U[c][m];
+      gx = madd(gx, tab.D[a][m], bC[sidx<Q>(c, qk, b, m)]);
+      gy = madd(gy, tab.D[b][m], bC[sidx<Q>(c, qk, m, a)]);
+      gz = madd(gz, tab.D[qk][m], U[c][m]);
     }
     g[c][0] = gx;
     g[c][1] = gy;
@@ -190,9 +196,9 @@ __device__ __forceinline__ void transpose_to_nodes(int a, int b, const KTab<P, Q
       T s = T(0);
 #pragma unroll
       for (int m = 0; m < Q; m++) {
-        s += tab.D[m][a] * bA[sidx<Q>(c, qk, b, m)];
-        s += tab.D[m][b] * bB[sidx<Q>(c, qk, m, a)];
-        s += tab.D[m][qk] * Fz[c][m];
+        s = madd(s, tab.D[m][a], bA[sidx<Q>(c, qk, b, m)]);
+        s = madd(s, tab.D[m][b], bB[sidx<Q>(c, qk, m, a)]);
+        s = madd(s, tab.D[m][qk], Fz[c][m]);
       }
       bC[sidx<Q>(c, qk, b, a)] = s;
     }
@@ -204,7 +210,7 @@ __device__ __forceinline__ void transpose_to_nodes(int a, int b, const KTab<P, Q
       for (int qk = 0; qk < Q; qk++) {
         T s = T(0);
 #pragma unroll
-        for (int qi = 0; qi < Q; qi++) s += tab.B[qi][a] * bC[sidx<Q>(c, qk, b, qi)];
+        for (int qi = 0; qi < Q; qi++) s = madd(s, tab.B[qi][a], bC[sidx<Q>(c, qk, b, qi)]);
         bA[sidx<Q>(c, qk, b, a)] = s;
       }
   }
@@ -217,7 +223,7 @@ __device__ __forceinline__ void transpose_to_nodes(int a, int b, const KTab<P, Q
       for (int qk = 0; qk < Q; qk++) {
         T s = T(0);
 #pragma unroll
-        for (int qj = 0; qj < Q; qj++) s += tab.B[qj][b] * bA[sidx<Q>(c, qk, qj, a)];
+        for (int qj = 0; qj < Q; qj++) s = madd(s, tab.B[qj][b], bA[sidx<Q>(c, qk, qj, a)]);
         w[c][qk] = s;
       }
 #pragma unroll
@@ -226,7 +232,7 @@ __device__ __forceinline__ void transpose_to_nodes(int a, int b, const KTab<P, Q
       for (int k = 0; k < P; k++) {
         T s = T(0);
 #pragma unroll
-        for (int qk = 0; qk < Q; qk++) s += tab.B[qk][k] * w[c][qk];
+        for (int qk = 0; qk < Q; qk++) s = madd(s, tab.B[qk][k], w[c][qk]);
         out[c][k] = s;
       }
   }
