@@ -54,13 +54,14 @@ def n_dof_of(p, n):
     return 3 * (p * n + 1) ** 3
 
 
-def apply_bytes(p, n, wbytes, S=17):
+def apply_bytes(p, n, wbytes, S=17, bc_byte=True):
     """Algorithmic bytes of one apply: stored quadrature data, du read, y written,
-    int32 element map, one Dirichlet-bit byte per node."""
+    int32 element map, and (FP64 kernels) one Dirichlet-bit byte per node; the
+    FP32 kernel reads the Dirichlet bits packed into its element map."""
     P, Q = p + 1, p + 1
     ne = n ** 3
     nn = (p * n + 1) ** 3
-    return ne * Q ** 3 * S * wbytes + 2 * 3 * nn * wbytes + ne * P ** 3 * 4 + nn
+    return ne * Q ** 3 * S * wbytes + 2 * 3 * nn * wbytes + ne * P ** 3 * 4 + (nn if bc_byte else 0)
 
 
 def apply_flops(p, n):
@@ -228,7 +229,7 @@ def run_nh(args):
                     "peak_source": "FP64 pipe: 148 SM x 2 DFMA/clk x 2.032 GHz (unit count x max clock)",
                     "kernel_ms": round(kms, 4), "hbm_frac": round(apply_bytes(p, n, wb, S) / (kms * 1e-3) / 1e9 / hbm, 4)}
         else:
-            ach = apply_bytes(p, n, wb, S) / (kms * 1e-3) / 1e9
+            ach = apply_bytes(p, n, wb, S, bc_byte=False) / (kms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(ach / hbm, 4), "traffic": args.traffic, "peak_source": hbm_src + " (copy)",
                     "kernel_ms": round(kms, 4)}
@@ -263,7 +264,7 @@ def run_nh(args):
                     k = kernel_ms(nh, ctx, c, pr, 5)  # warm (FP32 copy of the qdata on first use)
                     k = kernel_ms(nh, ctx, c, pr, 20)
                     w_ = 4 if pr == "f32" else 8
-                    gbs = apply_bytes(sp_, c.n, w_, Sx) / (k * 1e-3) / 1e9
+                    gbs = apply_bytes(sp_, c.n, w_, Sx, bc_byte=pr != "f32") / (k * 1e-3) / 1e9
                     tfl = apply_flops(sp_, c.n) / (k * 1e-3) / 1e12
                     sweep.append({"p": sp_, "n": c.n, "n_dof": c.nd, "prec": pr,
                                   "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4),

@@ -94,7 +94,9 @@ int64_t nh_launch_count(nh_ctx ctx);
  * and DoF counts.  Copies the mesh to the device; builds the element
  * restriction E as an int32 map [n_elem][(p+1)^3] and the node coordinates
  * (trilinear image of the GLL lattice).  Synchronises.
- * Errors: NH_ERR_ARG, NH_ERR_UNSUPPORTED, NH_ERR_OOM. */
+ * Errors: NH_ERR_ARG, NH_ERR_UNSUPPORTED (also when the node count reaches
+ * 2^29: the FP32 apply packs the Dirichlet bits into the top three bits of
+ * a second copy of E), NH_ERR_OOM. */
 nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const double* vertex_xyz,
                        int p, int q, nh_space* out, int64_t* n_nodes, int64_t* n_dof);
 /* Node coordinates, HOST out [n_nodes][3]. */

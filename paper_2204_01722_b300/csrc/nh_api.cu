@@ -142,8 +142,8 @@ extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const doub
   const int P = p + 1;
   const int64_t Nx = (int64_t)p * nx + 1, Ny = (int64_t)p * ny + 1, Nz = (int64_t)p * nz + 1;
   const int64_t ne = (int64_t)nx * ny * nz, nn = Nx * Ny * Nz;
-  if (nn > INT32_MAX / 3 || ne > INT32_MAX / 8)
-    return nh_fail(ctx, NH_ERR_UNSUPPORTED, "nh_space_box: mesh too large for int32 node ids");
+  if (nn >= ((int64_t)1 << 29) || ne > INT32_MAX / 8)
+    return nh_fail(ctx, NH_ERR_UNSUPPORTED, "nh_space_box: mesh too large (node ids must fit 29 bits)");
   NH_CUDA(ctx, cudaSetDevice(ctx->device));
   nh_space s = new nh_space_s();
   s->ctx = ctx;
@@ -208,7 +208,8 @@ extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const doub
   cudaError_t e3 = cudaMalloc(&s->bc, nn);
   cudaError_t e4 = cudaMalloc(&s->inv_mult, sizeof(double) * nn);
   cudaError_t e5 = cudaMalloc(&s->inv_mult_f, sizeof(float) * nn);
-  if (e1 || e2 || e3 || e4 || e5) {
+  cudaError_t e6 = cudaMalloc(&s->emapb, sizeof(unsigned) * emap.size());
+  if (e1 || e2 || e3 || e4 || e5 || e6) {
     cudaGetLastError();
     nh_space_destroy(s);
     return nh_fail(ctx, NH_ERR_OOM, "nh_space_box: device allocation failed");
@@ -218,6 +219,8 @@ extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const doub
   NH_CUDA(ctx, cudaMemset(s->bc, 0, nn));
   NH_CUDA(ctx, cudaMemcpy(s->inv_mult, im.data(), sizeof(double) * nn, cudaMemcpyHostToDevice));
   NH_CUDA(ctx, cudaMemcpy(s->inv_mult_f, imf.data(), sizeof(float) * nn, cudaMemcpyHostToDevice));
+  NH_CUDA(ctx, cudaDeviceSynchronize());
+  NH_CUDA(ctx, nh_launch_pack_emap(ctx->stream, (int64_t)emap.size(), s->emap, s->bc, s->emapb));
   NH_CUDA(ctx, cudaDeviceSynchronize());
   *out = s;
   if (n_nodes) *n_nodes = nn;
@@ -244,6 +247,7 @@ extern "C" nh_status nh_space_set_dirichlet(nh_space s, const uint8_t* mask) {
   s->n_constrained = nc;
   NH_CUDA(s->ctx, cudaSetDevice(s->ctx->device));
   NH_CUDA(s->ctx, cudaMemcpyAsync(s->bc, bits.data(), s->n_nodes, cudaMemcpyHostToDevice, s->ctx->stream));
+  NH_CUDA(s->ctx, nh_launch_pack_emap(s->ctx->stream, s->ne * (int64_t)s->P * s->P * s->P, s->emap, s->bc, s->emapb));
   NH_CUDA(s->ctx, cudaStreamSynchronize(s->ctx->stream));
   return NH_OK;
 }
@@ -251,6 +255,7 @@ extern "C" nh_status nh_space_set_dirichlet(nh_space s, const uint8_t* mask) {
 extern "C" nh_status nh_space_destroy(nh_space s) {
   if (!s) return NH_ERR_ARG;
   cudaFree(s->emap);
+  cudaFree(s->emapb);
   cudaFree(s->coords);
   cudaFree(s->bc);
   cudaFree(s->inv_mult);
@@ -346,6 +351,7 @@ static OpArgs base_args(nh_op op) {
   memset(&a, 0, sizeof(a));
   a.ne = op->space->ne;
   a.emap = op->space->emap;
+  a.emapb = op->space->emapb;
   a.bc = op->space->bc;
   a.qstride = root->space->ne * (int64_t)root->space->Q * root->space->Q * root->space->Q;
   a.layout = root->layout;

@@ -15,7 +15,7 @@
 
 // elements per block of the fused element kernels (about 128 threads, Q*Q per element)
 __host__ __device__ constexpr int nh_epb(int Q) { return (128 / (Q * Q)) > 0 ? 128 / (Q * Q) : 1; }
-// floats per element batch of the blocked FP32 quadrature data ([S][EPB][Q^3], padded to 256 B)
+// floats per element batch of the blocked FP32 quadrature data ([S][Q][EPB][Q^2], padded to 256 B)
 __host__ __device__ constexpr long long nh_f32_batch_floats(int Q, int S) {
   return ((long long)S * nh_epb(Q) * Q * Q * Q + 63) / 64 * 64;
 }
@@ -84,6 +84,7 @@ struct nh_space_s {
   std::vector<double> coords_host;
   std::vector<double> verts_host; // [(nx+1)(ny+1)(nz+1)][3], empty for the unit cube
   uint8_t* bc = nullptr;          // [n_nodes] bit c set = component c constrained (device)
+  unsigned* emapb = nullptr;      // [ne][P^3] node id | constrained bits << 29 (FP32 apply)
   double* inv_mult = nullptr;     // [n_nodes] 1 / multiplicity
   float* inv_mult_f = nullptr;
   int64_t n_constrained = 0;
@@ -122,6 +123,7 @@ nh_status nh_cuda_check(nh_ctx ctx, cudaError_t e, const char* what);
 struct OpArgs {
   int64_t ne;
   const int* emap;
+  const unsigned* emapb;  // element map with the Dirichlet bits packed in (node id < 2^29)
   const uint8_t* bc;
   const void* qd;      // quadrature data of the prec type
   int64_t qstride;     // ne * Q^3
@@ -175,6 +177,7 @@ cudaError_t nh_launch_dot_partials(int64_t n, const double* x, const double* y, 
 cudaError_t nh_launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
 cudaError_t nh_launch_f64_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);
 // FP64 -> float-float pairs (h, l) elementwise
+cudaError_t nh_launch_pack_emap(cudaStream_t s, int64_t n, const int* emap, const uint8_t* bc, unsigned* out);
 cudaError_t nh_launch_f64_to_ff(int64_t n, const double* x, float* y2, cudaStream_t s);
 // FP64 SoA quadrature data [S][ne Q^3] -> blocked FP32 [batch][S][EPB][Q^3]
 cudaError_t nh_launch_f32_blocked(int Q, int S, int64_t ne, const double* qd, float* qdf, cudaStream_t s);

@@ -305,30 +305,71 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<T, Q>())
 }
 
 // ---------------------------------------------------------------------------
-// FP32 Jacobian action with the block's quadrature data staged in shared memory
-// by one 1-D TMA bulk copy (blocked layout [batch][S][EPB][Q^3]), issued at
-// block start so it overlaps the gather and the interpolation.
+// FP32 Jacobian action, line-parallel.  Each of an element's Q^2 threads owns one
+// 1-D line of the Q^3 (or P x Q^2 ...) lattice per stage -- an x-line (y, z), a
+// y-line (x, z) or a z-line (x, y) -- reads that line from shared memory once,
+// and produces all of the line's outputs in registers, so every 1-D contraction
+// reads each value once (instead of once per output) and its coefficients are
+// compile-time table entries (constant bank, no loads).  Stages:
+//   x-lines over nodes:  gather E, B_I along x            -> A[c][k][j][qx]
+//   y-lines:             B_I along y                       -> Bf[c][k][qy][qx]
+//   z-lines:             B_I along z (u in registers), D_z  -> A = u
+//   x-, y-lines:         D_x, D_y                          -> A = du/dx, Bf = du/dy
+//   z-lines:             pointwise (quadrature data staged by TMA since block
+//                        start), D_z^T of the z-flux in registers -> A, Bf = fluxes
+//   x-, y-lines:         D_x^T, D_y^T                      -> A, Bf
+//   z-lines:             sum the three directions, B_I^T along z -> A
+//   y-lines:             B_I^T along y                     -> Bf
+//   x-lines over nodes:  B_I^T along x, E^T (atomic scatter)
+// The element map carries the Dirichlet bits (node id in bits 0..28,
+// constrained components in bits 29..31).
 // ---------------------------------------------------------------------------
+constexpr unsigned kNodeBits = 29u, kNodeMask = (1u << kNodeBits) - 1u;
+
+// Placement of the two [3][Q][Q][Q] work buffers of each element in shared
+// memory.  q = 4 (16 threads per element, two elements per warp): the two
+// elements of a pair share each 32-word row, one per 16-bank half, and a
+// point's word within its plane is 4 ((y + z) mod 4) + ((x + y) mod 4) -- a
+// bijection of (y, x) whose bank is distinct across the 16 lanes of an x-, y-
+// or z-line access alike, so no access conflicts and nothing is padded.
+// Other q: line pitch LP, plane pitch PP and element slot ES chosen by an
+// exhaustive search over a 32-bank model of the kernel's accesses (all lanes of
+// a warp, consecutive elements included) for the fewest wavefronts.
+template <int Q>
+struct LineLayout {
+  static constexpr int LP = Q;
+  static constexpr int PP = Q == 3 ? 11 : Q == 4 ? 32 : Q == 5 ? 25 : 39;
+  static constexpr int CS = Q * PP;       // component stride
+  static constexpr int BUF = 3 * CS;      // one [3][Q][Q][Q] buffer
+  // floats per element slot (q = 4: per pair of elements, which share the rows)
+  static constexpr int ES = Q == 3 ? 201 : Q == 4 ? 2 * BUF : Q == 5 ? 761 : 1412;
+  static_assert(ES >= 2 * BUF, "element slot holds two buffers");
+  __host__ __device__ static constexpr int elem(int el) { return Q == 4 ? (el >> 1) * ES + (el & 1) * 16 : el * ES; }
+  __host__ __device__ static constexpr int block_floats(int epb) { return Q == 4 ? (epb + 1) / 2 * ES : epb * ES; }
+  __device__ static constexpr int ix(int c, int z, int y, int x) {
+    return Q == 4 ? c * CS + z * PP + 4 * ((y + z) & 3) + ((x + y) & 3) : c * CS + z * PP + y * LP + x;
+  }
+};
+
 template <int P, int Q, int LAYOUT>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q))
-    k_jacobian_apply_f32tma(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
-                            const float* __restrict__ qdb, const KTab<P, Q, float> tab, const float* __restrict__ du,
-                            float* __restrict__ y, int lift, int* __restrict__ err) {
-  constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q;
+    k_jacobian_apply_f32l(int64_t ne, const unsigned* __restrict__ emapb, const float* __restrict__ qdb,
+                          const KTab<P, Q, float> tab, const float* __restrict__ du, float* __restrict__ y, int lift,
+                          int* __restrict__ err) {
+  using L = LineLayout<Q>;
+  constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   constexpr int S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
   constexpr long long BS = nh_f32_batch_floats(Q, S);
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
   float* qs = reinterpret_cast<float*>(smraw);  // [S][EPB][Q^3]
-  float* sm = qs + BS;
   const int t = threadIdx.x;
-  const int el = t / Q2, col = t - el * Q2;
-  const int a = col % Q, b = col / Q;
+  const int el = t / Q2, r = t - el * Q2;
+  const int u = r % Q, v = r / Q;  // line coordinates of this thread
   const int64_t e = (int64_t)blockIdx.x * EPB + el;
   const bool live = e < ne;
-  float* bA = sm + el * elem_stride<Q, float>();
-  float* bB = bA + 3 * Q3;
-  float* bC = bB + 3 * Q3;
+  float* A = qs + BS + L::elem(el);
+  float* Bf = A + L::BUF;
   if (t == 0) mbar_init(&bar);
   __syncthreads();
   if (t == 0) {
@@ -341,45 +382,237 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       bulk_g2s(dst + off, src + off, chunk, &bar);
     }
   }
-  float U[3][Q];
-  int nid[P];
-  gather_interp<P, Q, float>(live, !lift, e, a, b, emap, bc, du, tab, bA, bB, bC, U, nid);
-  mbar_wait_bounded(&bar, 0, err);
-  __syncthreads();
-  float Fz[3][Q];
-  const float* qe = qs + el * Q3 + b * Q + a;
-#pragma unroll
-  for (int qk = 0; qk < Q; qk++) {
-    float g[3][3], f[3][3];
-    colloc_grad<P, Q, float>(a, b, qk, tab, bC, U, g);
-    if (live) {
-      pointwise<LAYOUT, float>(qe + qk * Q2, (int64_t)EPB * Q3, g, f);
+  // x-lines over nodes (j = u, k = v): gather and B_I along x
+  const bool node_line = u < P && v < P;
+  unsigned nid[P];
+  if (node_line) {
+    float w[3][P];
+    if constexpr (P == 4) {  // the node line is 16-byte aligned: one vector load
+      const uint4 q4 = live ? __ldg(reinterpret_cast<const uint4*>(emapb + e * P3 + (v * P + u) * P)) : make_uint4(0, 0, 0, 0);
+      nid[0] = q4.x;
+      nid[1] = q4.y;
+      nid[2] = q4.z;
+      nid[3] = q4.w;
     } else {
 #pragma unroll
-      for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.f;
+      for (int i = 0; i < P; i++) nid[i] = live ? __ldg(&emapb[e * P3 + (v * P + u) * P + i]) : 0u;
     }
 #pragma unroll
+    for (int i = 0; i < P; i++) {
+      const int64_t n = nid[i] & kNodeMask;
+      const unsigned m = (live && !lift) ? nid[i] >> kNodeBits : 0u;
+#pragma unroll
+      for (int c = 0; c < 3; c++) w[c][i] = (live && !((m >> c) & 1u)) ? __ldg(&du[3 * n + c]) : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int qx = 0; qx < Q; qx++) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < P; i++) s += tab.B[qx][i] * w[c][i];
+        A[L::ix(c, v, u, qx)] = s;
+      }
+  }
+  __syncthreads();
+  if (v < P) {  // y-lines (x = u, z = v)
+#pragma unroll
     for (int c = 0; c < 3; c++) {
-      bA[sidx<Q>(c, qk, b, a)] = f[c][0];
-      bB[sidx<Q>(c, qk, b, a)] = f[c][1];
-      Fz[c][qk] = f[c][2];
+      float w[P];
+#pragma unroll
+      for (int j = 0; j < P; j++) w[j] = A[L::ix(c, v, j, u)];
+#pragma unroll
+      for (int qy = 0; qy < Q; qy++) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; j++) s += tab.B[qy][j] * w[j];
+        Bf[L::ix(c, v, qy, u)] = s;
+      }
     }
   }
   __syncthreads();
-  float out[3][P];
-  transpose_to_nodes<P, Q, float>(a, b, tab, bA, bB, bC, Fz, out);
-  if (live && a < P && b < P) {
+  // z-lines (x = u, y = v): point values and their z-derivative in registers
+  float gz[3][Q];
 #pragma unroll
-    for (int k = 0; k < P; k++) {
-      const int n = nid[k];
-      const unsigned m = __ldg(&bc[n]);
+  for (int c = 0; c < 3; c++) {
+    float w[P], U[Q];
+#pragma unroll
+    for (int k = 0; k < P; k++) w[k] = Bf[L::ix(c, k, v, u)];
+#pragma unroll
+    for (int qz = 0; qz < Q; qz++) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < P; k++) s += tab.B[qz][k] * w[k];
+      U[qz] = s;
+      A[L::ix(c, qz, v, u)] = s;
+    }
+#pragma unroll
+    for (int qz = 0; qz < Q; qz++) {
+      float s = 0.f;
+#pragma unroll
+      for (int m = 0; m < Q; m++) s += tab.D[qz][m] * U[m];
+      gz[c][qz] = s;
+    }
+  }
+  __syncthreads();
+  // x-lines (y = u, z = v) and y-lines (x = u, z = v) of the collocated derivative
+  float gx[3][Q], gy[3][Q];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float wx[Q], wy[Q];
+#pragma unroll
+    for (int m = 0; m < Q; m++) {
+      wx[m] = A[L::ix(c, v, u, m)];
+      wy[m] = A[L::ix(c, v, m, u)];
+    }
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      float sx = 0.f, sy = 0.f;
+#pragma unroll
+      for (int m = 0; m < Q; m++) {
+        sx += tab.D[q][m] * wx[m];
+        sy += tab.D[q][m] * wy[m];
+      }
+      gx[c][q] = sx;
+      gy[c][q] = sy;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      A[L::ix(c, v, u, q)] = gx[c][q];
+      Bf[L::ix(c, v, q, u)] = gy[c][q];
+    }
+  mbar_wait_bounded(&bar, 0, err);
+  __syncthreads();
+  // z-lines (x = u, y = v): pointwise at (u, v, qz); each point is read and
+  // rewritten by its own z-line thread only
+  float vz[3][Q];
+  {
+    float fz[3][Q];
+    const float* qe = qs + el * Q2 + v * Q + u;  // [S][Q][EPB][Q^2]
+#pragma unroll
+    for (int qz = 0; qz < Q; qz++) {
+      float g[3][3], f[3][3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        const int64_t dof = 3 * (int64_t)n + c;
+        g[c][0] = A[L::ix(c, qz, v, u)];
+        g[c][1] = Bf[L::ix(c, qz, v, u)];
+        g[c][2] = gz[c][qz];
+      }
+      if (live) {
+        pointwise<LAYOUT, float>(qe + qz * EPB * Q2, (int64_t)EPB * Q3, g, f);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        A[L::ix(c, qz, v, u)] = f[c][0];
+        Bf[L::ix(c, qz, v, u)] = f[c][1];
+        fz[c][qz] = f[c][2];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int qz = 0; qz < Q; qz++) {
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < Q; m++) s += tab.D[m][qz] * fz[c][m];
+        vz[c][qz] = s;
+      }
+  }
+  __syncthreads();
+  // x-lines (y = u, z = v): D_x^T of the x-flux; y-lines (x = u, z = v): D_y^T
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float wx[Q], wy[Q];
+#pragma unroll
+    for (int m = 0; m < Q; m++) {
+      wx[m] = A[L::ix(c, v, u, m)];
+      wy[m] = Bf[L::ix(c, v, m, u)];
+    }
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      float sx = 0.f, sy = 0.f;
+#pragma unroll
+      for (int m = 0; m < Q; m++) {
+        sx += tab.D[m][q] * wx[m];
+        sy += tab.D[m][q] * wy[m];
+      }
+      gx[c][q] = sx;
+      gy[c][q] = sy;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      A[L::ix(c, v, u, q)] = gx[c][q];
+      Bf[L::ix(c, v, q, u)] = gy[c][q];
+    }
+  __syncthreads();
+  // z-lines (x = u, y = v): sum of the three directions, then B_I^T along z
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float w[Q];
+#pragma unroll
+    for (int qz = 0; qz < Q; qz++) w[qz] = A[L::ix(c, qz, v, u)] + Bf[L::ix(c, qz, v, u)] + vz[c][qz];
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+      float s = 0.f;
+#pragma unroll
+      for (int qz = 0; qz < Q; qz++) s += tab.B[qz][k] * w[qz];
+      A[L::ix(c, k, v, u)] = s;
+    }
+  }
+  __syncthreads();
+  if (v < P) {  // y-lines (x = u, z = v): B_I^T along y
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      float w[Q];
+#pragma unroll
+      for (int m = 0; m < Q; m++) w[m] = A[L::ix(c, v, m, u)];
+#pragma unroll
+      for (int j = 0; j < P; j++) {
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < Q; m++) s += tab.B[m][j] * w[m];
+        Bf[L::ix(c, v, j, u)] = s;
+      }
+    }
+  }
+  __syncthreads();
+  if (live && node_line) {  // x-lines over nodes (j = u, k = v): B_I^T along x, E^T
+    float o[3][P];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      float w[Q];
+#pragma unroll
+      for (int m = 0; m < Q; m++) w[m] = Bf[L::ix(c, v, u, m)];
+#pragma unroll
+      for (int i = 0; i < P; i++) {
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < Q; m++) s += tab.B[m][i] * w[m];
+        o[c][i] = s;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < P; i++) {
+      const int64_t n = nid[i] & kNodeMask;
+      const unsigned m = nid[i] >> kNodeBits;
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const int64_t dof = 3 * n + c;
         if ((m >> c) & 1u) {
-          if (!lift) y[dof] = du[dof];
+          if (!lift) y[dof] = du[dof];  // identity row; every writer stores the same value
         } else {
-          atomicAdd(&y[dof], out[c][k]);
+          atomicAdd(&y[dof], o[c][i]);
         }
       }
     }
@@ -753,17 +986,17 @@ cudaError_t apply_launch(const OpArgs& A, cudaStream_t s) {
 }
 
 template <int P, int Q, int LAYOUT>
-cudaError_t apply_f32tma_launch(const OpArgs& A, cudaStream_t s) {
+cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   constexpr int EPB = epb_for(Q), S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
   const int threads = Q * Q * EPB;
   const int64_t blocks = (A.ne + EPB - 1) / EPB;
   if (blocks == 0) return cudaSuccess;
-  const size_t smem = (size_t)nh_f32_batch_floats(Q, S) * 4 + (size_t)EPB * elem_stride<Q, float>() * 4;
+  const size_t smem = ((size_t)nh_f32_batch_floats(Q, S) + (size_t)LineLayout<Q>::block_floats(EPB)) * sizeof(float);
   const KTab<P, Q, float> tab = make_ktab<P, Q, float>(*A.tab);
-  cudaError_t e = prep<k_jacobian_apply_f32tma<P, Q, LAYOUT>>(smem);
+  cudaError_t e = prep<k_jacobian_apply_f32l<P, Q, LAYOUT>>(smem);
   if (e != cudaSuccess) return e;
-  k_jacobian_apply_f32tma<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
-      A.ne, A.emap, A.bc, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift, A.err);
+  k_jacobian_apply_f32l<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
+      A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift, A.err);
   return cudaGetLastError();
 }
 
@@ -775,8 +1008,8 @@ cudaError_t apply_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
   if (prec == NH_F64X)
     return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, ff, double, NH_LAYOUT_CURRENT>(A, s)
                                          : apply_launch<P, Q, ff, double, NH_LAYOUT_INITIAL>(A, s);
-  return A.layout == NH_LAYOUT_CURRENT ? apply_f32tma_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
-                                       : apply_f32tma_launch<P, Q, NH_LAYOUT_INITIAL>(A, s);
+  return A.layout == NH_LAYOUT_CURRENT ? apply_f32l_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
+                                       : apply_f32l_launch<P, Q, NH_LAYOUT_INITIAL>(A, s);
 }
 
 template <int P, int Q, int LAYOUT>

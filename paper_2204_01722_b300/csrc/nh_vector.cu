@@ -49,14 +49,19 @@ __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ x, float* __r
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (float)x[i];
 }
 
-__global__ void k_f32_blocked(int Q3, int EPB, int S, long long BS, int64_t ne, const double* __restrict__ qd,
+// FP32 quadrature data per batch of EPB elements as [S][Q (z)][EPB][Q^2 (y, x)]:
+// the z-line threads of a warp (consecutive elements, then y, x) read
+// consecutive words at each z level, for every Q.
+__global__ void k_f32_blocked(int Q, int EPB, int S, long long BS, int64_t ne, const double* __restrict__ qd,
                               float* __restrict__ qdf) {
+  const int Q2 = Q * Q, Q3 = Q2 * Q;
   const int64_t n = (int64_t)S * ne * Q3;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int64_t s = i / (ne * Q3), r = i - s * ne * Q3;
-    const int64_t e = r / Q3, q = r - e * Q3;
-    qdf[(e / EPB) * BS + (s * EPB + e % EPB) * Q3 + q] = (float)qd[i];
+    const int64_t e = r / Q3;
+    const int q = (int)(r - e * Q3), qz = q / Q2, qyx = q - qz * Q2;
+    qdf[(e / EPB) * BS + ((s * Q + qz) * EPB + e % EPB) * Q2 + qyx] = (float)qd[i];
   }
 }
 
@@ -65,7 +70,24 @@ __global__ void k_f64_to_ff(int64_t n, const double* __restrict__ x, ff* __restr
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = ff(x[i]);
 }
 
+__global__ void k_pack_emap(int64_t n, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
+                            unsigned* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int node = emap[i];
+    out[i] = (unsigned)node | ((unsigned)(bc[node] & 7u) << 29);
+  }
+}
+
 }  // namespace
+
+cudaError_t nh_launch_pack_emap(cudaStream_t s, int64_t n, const int* emap, const uint8_t* bc, unsigned* out) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  if (blocks < 1) blocks = 1;
+  k_pack_emap<<<(unsigned)blocks, 256, 0, s>>>(n, emap, bc, out);
+  return cudaGetLastError();
+}
 
 cudaError_t nh_launch_f64_to_ff(int64_t n, const double* x, float* y2, cudaStream_t s) {
   int64_t blocks = (n + 255) / 256;
@@ -80,7 +102,7 @@ cudaError_t nh_launch_f32_blocked(int Q, int S, int64_t ne, const double* qd, fl
   int64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 16) blocks = 148 * 16;
   if (blocks < 1) blocks = 1;
-  k_f32_blocked<<<(unsigned)blocks, 256, 0, s>>>(Q * Q * Q, nh_epb(Q), S, nh_f32_batch_floats(Q, S), ne, qd, qdf);
+  k_f32_blocked<<<(unsigned)blocks, 256, 0, s>>>(Q, nh_epb(Q), S, nh_f32_batch_floats(Q, S), ne, qd, qdf);
   return cudaGetLastError();
 }
 
