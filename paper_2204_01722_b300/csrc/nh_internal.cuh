@@ -15,10 +15,12 @@
 
 // elements per block of the fused element kernels (about 128 threads, Q*Q per element)
 __host__ __device__ constexpr int nh_epb(int Q) { return (128 / (Q * Q)) > 0 ? 128 / (Q * Q) : 1; }
-// floats per element batch of the blocked FP32 quadrature data ([S][Q][EPB][Q^2], padded to 256 B)
-__host__ __device__ constexpr long long nh_f32_batch_floats(int Q, int S) {
-  return ((long long)S * nh_epb(Q) * Q * Q * Q + 63) / 64 * 64;
+// Blocked FP32 quadrature data: per batch of EPB elements, Q z-planes, each
+// [S][EPB][Q^2] padded to a multiple of 4 floats (16 bytes, for the bulk copies).
+__host__ __device__ constexpr long long nh_f32_plane_floats(int Q, int S) {
+  return ((long long)S * nh_epb(Q) * Q * Q + 3) / 4 * 4;
 }
+__host__ __device__ constexpr long long nh_f32_batch_floats(int Q, int S) { return (long long)Q * nh_f32_plane_floats(Q, S); }
 
 // ---- 1-D tables ---------------------------------------------------------------
 // Host-side tabulations in double; kernels receive them by value as kernel

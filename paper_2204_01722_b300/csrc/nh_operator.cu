@@ -359,28 +359,37 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
   using L = LineLayout<Q>;
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   constexpr int S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
-  constexpr long long BS = nh_f32_batch_floats(Q, S);
+  constexpr long long BS = nh_f32_batch_floats(Q, S), PL = nh_f32_plane_floats(Q, S);
   extern __shared__ __align__(128) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t bar;
-  float* qs = reinterpret_cast<float*>(smraw);  // [S][EPB][Q^3]
+  __shared__ __align__(8) uint64_t bar[2];
+  float* qs = reinterpret_cast<float*>(smraw);  // two plane slots [2][PL]
   const int t = threadIdx.x;
   const int el = t / Q2, r = t - el * Q2;
   const int u = r % Q, v = r / Q;  // line coordinates of this thread
   const int64_t e = (int64_t)blockIdx.x * EPB + el;
   const bool live = e < ne;
-  float* A = qs + BS + L::elem(el);
+  float* A = qs + 2 * PL + L::elem(el);
   float* Bf = A + L::BUF;
-  if (t == 0) mbar_init(&bar);
-  __syncthreads();
-  if (t == 0) {
-    const unsigned bytes = (unsigned)(BS * sizeof(float));
-    mbar_expect_tx(&bar, bytes);
-    const char* src = reinterpret_cast<const char*>(qdb + (int64_t)blockIdx.x * BS);
-    char* dst = reinterpret_cast<char*>(qs);
+  // z-plane qz of the batch's quadrature data -> slot qz & 1 (one bulk copy)
+  auto issue_plane = [&](int qz) {
+    const unsigned bytes = (unsigned)(PL * sizeof(float));
+    uint64_t* b = &bar[qz & 1];
+    mbar_expect_tx(b, bytes);
+    const char* src = reinterpret_cast<const char*>(qdb + (int64_t)blockIdx.x * BS + qz * PL);
+    char* dst = reinterpret_cast<char*>(qs + (qz & 1) * PL);
     for (unsigned off = 0; off < bytes; off += 16384u) {
       const unsigned chunk = bytes - off < 16384u ? bytes - off : 16384u;
-      bulk_g2s(dst + off, src + off, chunk, &bar);
+      bulk_g2s(dst + off, src + off, chunk, b);
     }
+  };
+  if (t == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+  }
+  __syncthreads();
+  if (t == 0) {
+    issue_plane(0);
+    issue_plane(1);
   }
   // x-lines over nodes (j = u, k = v): gather and B_I along x
   const bool node_line = u < P && v < P;
@@ -485,16 +494,17 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       A[L::ix(c, v, u, q)] = gx[c][q];
       Bf[L::ix(c, v, q, u)] = gy[c][q];
     }
-  mbar_wait_bounded(&bar, 0, err);
   __syncthreads();
   // z-lines (x = u, y = v): pointwise at (u, v, qz); each point is read and
-  // rewritten by its own z-line thread only
+  // rewritten by its own z-line thread only.  Plane qz's data sits in slot
+  // qz & 1; once every thread is past plane qz, plane qz + 2 is copied there.
   float vz[3][Q];
   {
     float fz[3][Q];
-    const float* qe = qs + el * Q2 + v * Q + u;  // [S][Q][EPB][Q^2]
 #pragma unroll
     for (int qz = 0; qz < Q; qz++) {
+      mbar_wait_bounded(&bar[qz & 1], (qz >> 1) & 1, err);
+      const float* qe = qs + (qz & 1) * PL + el * Q2 + v * Q + u;  // [S][EPB][Q^2]
       float g[3][3], f[3][3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -503,7 +513,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
         g[c][2] = gz[c][qz];
       }
       if (live) {
-        pointwise<LAYOUT, float>(qe + qz * EPB * Q2, (int64_t)EPB * Q3, g, f);
+        pointwise<LAYOUT, float>(qe, (int64_t)EPB * Q2, g, f);
       } else {
 #pragma unroll
         for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.f;
@@ -513,6 +523,10 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
         A[L::ix(c, qz, v, u)] = f[c][0];
         Bf[L::ix(c, qz, v, u)] = f[c][1];
         fz[c][qz] = f[c][2];
+      }
+      if (qz + 2 < Q) {
+        __syncthreads();
+        if (t == 0) issue_plane(qz + 2);
       }
     }
 #pragma unroll
@@ -991,7 +1005,7 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   const int threads = Q * Q * EPB;
   const int64_t blocks = (A.ne + EPB - 1) / EPB;
   if (blocks == 0) return cudaSuccess;
-  const size_t smem = ((size_t)nh_f32_batch_floats(Q, S) + (size_t)LineLayout<Q>::block_floats(EPB)) * sizeof(float);
+  const size_t smem = ((size_t)2 * nh_f32_plane_floats(Q, S) + (size_t)LineLayout<Q>::block_floats(EPB)) * sizeof(float);
   const KTab<P, Q, float> tab = make_ktab<P, Q, float>(*A.tab);
   cudaError_t e = prep<k_jacobian_apply_f32l<P, Q, LAYOUT>>(smem);
   if (e != cudaSuccess) return e;

@@ -49,10 +49,11 @@ __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ x, float* __r
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (float)x[i];
 }
 
-// FP32 quadrature data per batch of EPB elements as [S][Q (z)][EPB][Q^2 (y, x)]:
-// the z-line threads of a warp (consecutive elements, then y, x) read
-// consecutive words at each z level, for every Q.
-__global__ void k_f32_blocked(int Q, int EPB, int S, long long BS, int64_t ne, const double* __restrict__ qd,
+// FP32 quadrature data per batch of EPB elements as Q z-planes of
+// [S][EPB][Q^2 (y, x)], each padded to PL floats: one plane is one bulk copy,
+// and the z-line threads of a warp (consecutive elements, then y, x) read
+// consecutive words.
+__global__ void k_f32_blocked(int Q, int EPB, int S, long long PL, int64_t ne, const double* __restrict__ qd,
                               float* __restrict__ qdf) {
   const int Q2 = Q * Q, Q3 = Q2 * Q;
   const int64_t n = (int64_t)S * ne * Q3;
@@ -61,7 +62,7 @@ __global__ void k_f32_blocked(int Q, int EPB, int S, long long BS, int64_t ne, c
     const int64_t s = i / (ne * Q3), r = i - s * ne * Q3;
     const int64_t e = r / Q3;
     const int q = (int)(r - e * Q3), qz = q / Q2, qyx = q - qz * Q2;
-    qdf[(e / EPB) * BS + ((s * Q + qz) * EPB + e % EPB) * Q2 + qyx] = (float)qd[i];
+    qdf[((e / EPB) * Q + qz) * PL + (s * EPB + e % EPB) * Q2 + qyx] = (float)qd[i];
   }
 }
 
@@ -102,7 +103,7 @@ cudaError_t nh_launch_f32_blocked(int Q, int S, int64_t ne, const double* qd, fl
   int64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 16) blocks = 148 * 16;
   if (blocks < 1) blocks = 1;
-  k_f32_blocked<<<(unsigned)blocks, 256, 0, s>>>(Q, nh_epb(Q), S, nh_f32_batch_floats(Q, S), ne, qd, qdf);
+  k_f32_blocked<<<(unsigned)blocks, 256, 0, s>>>(Q, nh_epb(Q), S, nh_f32_plane_floats(Q, S), ne, qd, qdf);
   return cudaGetLastError();
 }
 
