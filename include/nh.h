@@ -207,6 +207,8 @@ typedef struct {
                               1 = outer FCG stage (predicts the fine error at the vertices);
                               2 = coarse warm start (predicts A_c^-1 r_c; the coarsest PCG starts from it
                                   when it lowers the coarse residual, else from zero) */
+  int fp64_kind;           /* arithmetic of the FP64-accurate matrix-free applies (outer FCG, Lanczos,
+                              FP64 smoothers): 0 = native FP64 (NH_F64), 1 = float-float (NH_F64X) */
 } nh_mg_opts;
 
 typedef struct {

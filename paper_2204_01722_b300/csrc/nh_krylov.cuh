@@ -35,3 +35,25 @@ cudaError_t ks_assemble_q1(int Q, cudaStream_t st, int64_t ne, int nx, int ny, i
 cudaError_t ks_apply(cudaStream_t st, int Nx, int Ny, int Nz, const uint8_t* bc, const double* A, const double* x,
                      double* y);
 cudaError_t ks_diag(cudaStream_t st, int64_t nn, const uint8_t* bc, const double* A, double* d);
+
+// Jacobi-preconditioned CG on the assembled Q1 stencil in one cooperative
+// launch (all blocks co-resident, bounded grid barriers, convergence tested on
+// the device).  Solves A x = b from x = 0 (warm = 0) or from the given x
+// (warm = 1, tolerance relative to ref = sqrt(b . D^-1 b)); stops when
+// sqrt(r . z) <= rtol sqrt(r0 . z0) or after maxit iterations.  Work vectors
+// r, z, p, q of 3 n_nodes doubles; part: 2 * ks_pcg_max_blocks() doubles;
+// bar: 2 unsigned; out[0] = iterations, out[1] = 1 if a residual was not finite.
+struct KsPcg {
+  int Nx, Ny, Nz;
+  const uint8_t* bc;
+  const double *A, *dinv, *b;
+  double *x, *r, *z, *p, *q;
+  double* part;
+  unsigned* bar;
+  double* out;
+  double rtol, ref;
+  int maxit, warm;
+  int* err;
+};
+int ks_pcg_max_blocks();
+cudaError_t ks_pcg(cudaStream_t st, const KsPcg& a);

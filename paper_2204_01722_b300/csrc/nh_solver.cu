@@ -34,6 +34,7 @@ enum {
   S_RZ0 = 0, S_RZ1 = 1, S_PQ = 2,                   // PCG / Lanczos
   S_FPQ = 8, S_FPR = 9, S_FZQ = 10, S_FRR = 11,      // FCG
   S_TMP = 12,
+  S_PCG = 14,             // cooperative coarse PCG: iterations, non-finite flag
   S_HIST = 16,            // Lanczos history: rz[k] at S_HIST + k, pq[k] at S_HIST + 64 + k
   S_LEN = S_HIST + 128
 };
@@ -66,11 +67,14 @@ struct nh_mg_s {
   double* sc = nullptr;    // device scalars
   double* part = nullptr;  // dot partials
   double* hsc = nullptr;   // pinned host mirror
+  double* pcg_part = nullptr;      // coarse cooperative PCG: block partials
+  unsigned* pcg_bar = nullptr;     // its grid barrier words
   // FCG / Newton work (fine, FP64)
   double *fr = nullptr, *fz = nullptr, *fp = nullptr, *fq = nullptr;  // FCG work
   double *fx = nullptr, *fu = nullptr, *fg = nullptr, *fb = nullptr, *ft = nullptr, *fs = nullptr;  // Newton
   double* fsave = nullptr;  // state at the start of a load increment
   bool setup_done = false;
+  nh_prec p64 = NH_F64;    // arithmetic of the FP64-accurate matrix-free applies
   int vcycles = 0, coarse_its = 0;
   // learned stage
   nh_net net = nullptr;
@@ -131,7 +135,7 @@ nh_status level_apply(nh_mg mg, Level& l, nh_prec prec, const void* x, void* y) 
     mg->ctx->launches++;
     return NH_OK;
   }
-  return nh_jacobian_apply(l.op, prec, x, y);
+  return nh_jacobian_apply(l.op, prec == NH_F64 ? mg->p64 : prec, x, y);
 }
 
 // --- smallest building blocks, templated on the level precision ----------------
@@ -178,6 +182,37 @@ nh_status pcg64(nh_mg mg, Level& l, const double* b, double* x, double rtol, int
   const int64_t n = l.n;
   double *r = l.w[0], *z = l.w[1], *p = l.w[2], *q = l.w[3];
   const double* dinv = l.dinv64;
+  if (l.stencil && !hist) {  // assembled coarsest level: the whole solve in one cooperative launch
+    KsPcg a;
+    a.Nx = l.space->Nx;
+    a.Ny = l.space->Ny;
+    a.Nz = l.space->Nz;
+    a.bc = l.space->bc;
+    a.A = l.A;
+    a.dinv = dinv;
+    a.b = b;
+    a.x = x;
+    a.r = r;
+    a.z = z;
+    a.p = p;
+    a.q = q;
+    a.part = mg->pcg_part;
+    a.bar = mg->pcg_bar;
+    a.out = mg->sc + S_PCG;
+    a.rtol = rtol;
+    a.ref = ref;
+    a.maxit = maxit;
+    a.warm = warm ? 1 : 0;
+    a.err = mg->ctx->dev_err;
+    CK(ks_pcg(st, a));
+    mg->ctx->launches += 2;
+    double res[2] = {0.0, 0.0};
+    ST(read_sc(mg, S_PCG, 2, res));
+    ST(nh_sync(mg->ctx));
+    if (res[1] != 0.0) return nh_fail(mg->ctx, NH_ERR_NAN, "coarse PCG: non-finite residual");
+    *its = (int)res[0];
+    return NH_OK;
+  }
   if (warm) {  // r = b - A x for the given start x
     ST(level_apply(mg, l, NH_F64, x, r));
     CK(kv_axpby<double>(st, n, 1.0, b, -1.0, r));
@@ -443,6 +478,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->verbose = 0;
   o->learned_accept = 0;
   o->learned_mode = 2;
+  o->fp64_kind = 0;
   return NH_OK;
 }
 
@@ -461,6 +497,8 @@ extern "C" nh_status nh_mg_destroy(nh_mg mg) {
   }
   cudaFree(mg->sc);
   cudaFree(mg->part);
+  cudaFree(mg->pcg_part);
+  cudaFree(mg->pcg_bar);
   cudaFreeHost(mg->hsc);
   for (double* p : {mg->fr, mg->fz, mg->fp, mg->fq, mg->fx, mg->fu, mg->fg, mg->fb, mg->ft, mg->fs, mg->fsave})
     cudaFree(p);
@@ -494,6 +532,8 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
   for (int i = 1; i < o.n_levels; i++)
     if (o.level_p[i] < 1 || o.level_p[i] >= o.level_p[i - 1]) return bad("nh_mg_create: orders must decrease to >= 1");
   if (o.cheb_degree < 1 || !(o.cheb_hi > o.cheb_lo) || !(o.cheb_lo > 0)) return bad("nh_mg_create: bad Chebyshev options");
+  if (o.fp64_kind != 0 && o.fp64_kind != 1) return bad("nh_mg_create: fp64_kind must be 0 or 1");
+  mg->p64 = o.fp64_kind ? NH_F64X : NH_F64;
   cudaSetDevice(mg->ctx->device);
   nh_status s;
   mg->L.resize(o.n_levels);
@@ -543,7 +583,9 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
   }
   const size_t fb = 8 * (size_t)fs->n_dof;
   if ((s = dalloc(mg, (void**)&mg->sc, sizeof(double) * S_LEN)) != NH_OK ||
-      (s = dalloc(mg, (void**)&mg->part, sizeof(double) * 148 * 8 + 64)) != NH_OK) {
+      (s = dalloc(mg, (void**)&mg->part, sizeof(double) * 148 * 8 + 64)) != NH_OK ||
+      (s = dalloc(mg, (void**)&mg->pcg_part, sizeof(double) * (2 * (size_t)ks_pcg_max_blocks() + 2))) != NH_OK ||
+      (s = dalloc(mg, (void**)&mg->pcg_bar, 64)) != NH_OK) {
     nh_mg_destroy(mg);
     return s;
   }
@@ -776,7 +818,7 @@ static nh_status precond(nh_mg mg, const double* r, double* z) {
     cur = out;
   }
   const int64_t n = mg->L[0].n;
-  ST(nh_jacobian_apply(mg->fine, NH_F64, mg->lz1, mg->lw));  // lw = J z1
+  ST(nh_jacobian_apply(mg->fine, mg->p64, mg->lz1, mg->lw));  // lw = J z1
   bool accept = false;
   if (mg->o.learned_accept == 1) {
     // energy-optimal step: a = z1.r / z1.J z1; the A-norm of the error drops iff z1.r > 0
@@ -837,13 +879,13 @@ static nh_status fcg(nh_mg mg, const double* b, double* x, double rtol, int maxi
   nh_op A = mg->fine;
   const int64_t n = mg->L[0].n;
   double *r = mg->fr, *z = mg->fz, *p = mg->fp, *q = mg->fq;
-  ST(nh_jacobian_apply(A, NH_F64, x, r));
+  ST(nh_jacobian_apply(A, mg->p64, x, r));
   CK(kv_axpby<double>(st, n, 1.0, b, -1.0, r));  // r = b - A x
   mg->ctx->launches++;
   ST(record_pair(mg, col, r, x));
   ST(precond(mg, r, z));
   CK(cudaMemcpyAsync(p, z, 8 * n, cudaMemcpyDeviceToDevice, st));
-  ST(nh_jacobian_apply(A, NH_F64, p, q));
+  ST(nh_jacobian_apply(A, mg->p64, p, q));
   double nrm0 = 0.0;
   ST(norm == 0 ? dot(mg, n, r, z, S_FRR) : dot(mg, n, r, r, S_FRR));
   ST(read_sc(mg, S_FRR, 1, &nrm0));
@@ -872,7 +914,7 @@ static nh_status fcg(nh_mg mg, const double* b, double* x, double rtol, int maxi
     ST(dot(mg, n, z, q, S_FZQ));
     CK(kv_xpby_dev<double>(st, n, z, p, mg->sc, S_FZQ, S_FPQ, -1.0));  // p = z - (z.q / p.q) p
     mg->ctx->launches++;
-    ST(nh_jacobian_apply(A, NH_F64, p, q));
+    ST(nh_jacobian_apply(A, mg->p64, p, q));
   }
   *its_out = k;
   *rel_out = nrm / nrm0;

@@ -220,19 +220,39 @@ cudaError_t assemble_q(cudaStream_t st, int64_t ne, int nx, int ny, int nz, cons
   return cudaGetLastError();
 }
 
+// Zero the stencil entries that multiply constrained components (the dropped
+// columns of the Dirichlet convention), so that applies need no mask lookups.
+__global__ void k_mask_cols(int Nx, int Ny, int Nz, const uint8_t* __restrict__ bc, double* __restrict__ A) {
+  const int64_t nn = (int64_t)Nx * Ny * Nz;
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const int I = (int)(n % Nx), J = (int)((n / Nx) % Ny), K = (int)(n / ((int64_t)Nx * Ny));
+  for (int s = 0; s < 27; s++) {
+    const int I2 = I + s % 3 - 1, J2 = J + (s / 3) % 3 - 1, K2 = K + s / 9 - 1;
+    if (I2 < 0 || I2 >= Nx || J2 < 0 || J2 >= Ny || K2 < 0 || K2 >= Nz) continue;
+    const unsigned mb = bc[I2 + (int64_t)Nx * (J2 + (int64_t)Ny * K2)];
+    for (int c2 = 0; c2 < 3; c2++)
+      if ((mb >> c2) & 1u)
+        for (int c = 0; c < 3; c++) A[((int64_t)s * 9 + 3 * c + c2) * nn + n] = 0.0;
+  }
+}
+
 }  // namespace
 
 cudaError_t ks_assemble_q1(int Q, cudaStream_t st, int64_t ne, int nx, int ny, int nz, const uint8_t* bc,
                            const double* qd, int64_t qstride, int layout, const Tab1D* tab, double* A) {
-  (void)bc;
+  cudaError_t e = cudaErrorInvalidValue;
   switch (Q) {
-    case 2: return assemble_q<2>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A);
-    case 3: return assemble_q<3>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A);
-    case 4: return assemble_q<4>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A);
-    case 5: return assemble_q<5>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A);
-    case 6: return assemble_q<6>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A);
+    case 2: e = assemble_q<2>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
+    case 3: e = assemble_q<3>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
+    case 4: e = assemble_q<4>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
+    case 5: e = assemble_q<5>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
+    case 6: e = assemble_q<6>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
   }
-  return cudaErrorInvalidValue;
+  if (e != cudaSuccess) return e;
+  const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  k_mask_cols<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(nx + 1, ny + 1, nz + 1, bc, A);
+  return cudaGetLastError();
 }
 
 cudaError_t ks_apply(cudaStream_t st, int Nx, int Ny, int Nz, const uint8_t* bc, const double* A, const double* x,
@@ -241,6 +261,217 @@ cudaError_t ks_apply(cudaStream_t st, int Nx, int Ny, int Nz, const uint8_t* bc,
   if (nn == 0) return cudaSuccess;
   k_apply<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Nx, Ny, Nz, bc, A, x, y);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Coarse Jacobi-PCG in one cooperative launch
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kPcgThreads = 256;
+constexpr unsigned kGridSpin = 1u << 24;  // polls per grid barrier before giving up
+
+// Barrier over all blocks of a cooperative launch: arrival counter plus a
+// generation word; the last block to arrive resets the counter and advances the
+// generation.  A wait that outlives kGridSpin polls sets *err and returns false
+// (the caller leaves the kernel; the host sees NH_ERR_TIMEOUT).
+__device__ bool grid_sync_bounded(unsigned* count, unsigned* gen, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    ok = 1;
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned it = 0;
+      while (*vgen == g) {
+        if (++it > kGridSpin) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// fixed-order block sum (every block that calls it with the same inputs gets
+// the same bits)
+__device__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += sh[i];
+    sh[32] = s;
+  }
+  __syncthreads();
+  s = sh[32];
+  __syncthreads();
+  return s;
+}
+
+// sum of the grid's partials, same order in every block
+__device__ double grid_total(const double* part, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(&part[i]);
+  return block_sum(v, sh);
+}
+
+// Row (n, c) of the stencil times v.  Constrained columns are zero in the
+// stored stencil and so are the entries of neighbours outside the lattice, so
+// every neighbour index is clamped into the lattice and all 81 loads are
+// unconditional.
+__device__ __forceinline__ double stencil_row(int Nx, int Ny, int Nz, int64_t nn, int64_t n, int c,
+                                              const double* __restrict__ A, const double* v) {
+  const int I = (int)(n % Nx), J = (int)((n / Nx) % Ny), K = (int)(n / ((int64_t)Nx * Ny));
+  double acc = 0.0;
+#pragma unroll
+  for (int s = 0; s < 27; s++) {
+    const int I2 = min(max(I + s % 3 - 1, 0), Nx - 1), J2 = min(max(J + (s / 3) % 3 - 1, 0), Ny - 1),
+              K2 = min(max(K + s / 9 - 1, 0), Nz - 1);
+    const int64_t m = I2 + (int64_t)Nx * (J2 + (int64_t)Ny * K2);
+    const double* As = A + ((int64_t)s * 9 + 3 * c) * nn + n;
+    acc += As[0] * __ldcg(&v[3 * m]) + As[nn] * __ldcg(&v[3 * m + 1]) + As[2 * nn] * __ldcg(&v[3 * m + 2]);
+  }
+  return acc;
+}
+
+// One thread per DoF row, component-major (t = c n_nodes + n) so that a warp's
+// stencil loads are coalesced; grid-stride over the 3 n_nodes rows.
+__global__ void __launch_bounds__(kPcgThreads) k_pcg(KsPcg a) {
+  __shared__ double sh[33];
+  const int64_t nn = (int64_t)a.Nx * a.Ny * a.Nz, nr = 3 * nn;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double* part1 = a.part;
+  double* part2 = a.part + gridDim.x;
+  unsigned* cnt = a.bar;
+  unsigned* gen = a.bar + 1;
+  // r = b - A x (warm) or b (x = 0); z = D^-1 r; p = z
+  double loc = 0.0;
+  for (int64_t t = t0; t < nr; t += stride) {
+    const int c = (int)(t / nn);
+    const int64_t n = t - c * nn, i = 3 * n + c;
+    double rv;
+    if (a.warm) {
+      const bool fixed = (a.bc[n] >> c) & 1u;
+      rv = a.b[i] - (fixed ? a.x[i] : stencil_row(a.Nx, a.Ny, a.Nz, nn, n, c, a.A, a.x));
+    } else {
+      a.x[i] = 0.0;
+      rv = a.b[i];
+    }
+    const double zv = a.dinv[i] * rv;
+    a.r[i] = rv;
+    a.z[i] = zv;
+    a.p[i] = zv;
+    loc += rv * zv;
+  }
+  double s = block_sum(loc, sh);
+  if (threadIdx.x == 0) part1[blockIdx.x] = s;
+  if (!grid_sync_bounded(cnt, gen, a.err)) return;
+  double rz = grid_total(part1, sh), rz0;
+  int k = 0, bad = 0;
+  bool done = false;
+  if (a.warm) {
+    done = sqrt(fabs(rz)) <= a.rtol * a.ref;
+    rz0 = a.ref * a.ref;
+  } else {
+    rz0 = rz;
+    done = !(rz0 > 0.0);
+  }
+  while (!done && k < a.maxit) {
+    // q = A p, p . q
+    loc = 0.0;
+    for (int64_t t = t0; t < nr; t += stride) {
+      const int c = (int)(t / nn);
+      const int64_t n = t - c * nn, i = 3 * n + c;
+      const double pv = a.p[i];
+      const double qv = ((a.bc[n] >> c) & 1u) ? pv : stencil_row(a.Nx, a.Ny, a.Nz, nn, n, c, a.A, a.p);
+      a.q[i] = qv;
+      loc += pv * qv;
+    }
+    s = block_sum(loc, sh);
+    if (threadIdx.x == 0) part1[blockIdx.x] = s;
+    if (!grid_sync_bounded(cnt, gen, a.err)) return;
+    const double alpha = rz / grid_total(part1, sh);
+    // x += alpha p, r -= alpha q, z = D^-1 r, r . z
+    loc = 0.0;
+    for (int64_t t = t0; t < nr; t += stride) {
+      const int c = (int)(t / nn);
+      const int64_t i = 3 * (t - c * nn) + c;
+      a.x[i] += alpha * a.p[i];
+      const double rv = a.r[i] - alpha * a.q[i];
+      const double zv = a.dinv[i] * rv;
+      a.r[i] = rv;
+      a.z[i] = zv;
+      loc += rv * zv;
+    }
+    s = block_sum(loc, sh);
+    if (threadIdx.x == 0) part2[blockIdx.x] = s;
+    if (!grid_sync_bounded(cnt, gen, a.err)) return;
+    const double rzn = grid_total(part2, sh);
+    k++;
+    if (!isfinite(rzn)) {
+      bad = 1;
+      break;
+    }
+    if (sqrt(fabs(rzn)) <= a.rtol * sqrt(rz0)) break;
+    const double beta = rzn / rz;
+    rz = rzn;
+    for (int64_t t = t0; t < nr; t += stride) {
+      const int c = (int)(t / nn);
+      const int64_t i = 3 * (t - c * nn) + c;
+      a.p[i] = a.z[i] + beta * a.p[i];
+    }
+    if (!grid_sync_bounded(cnt, gen, a.err)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.out[0] = (double)k;
+    a.out[1] = (double)bad;
+  }
+}
+
+}  // namespace
+
+int ks_pcg_max_blocks() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (dev < 0 || dev >= 64) return 0;
+  if (!cached[dev]) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kPcgThreads, 0) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cached[dev] = per_sm * sms;
+  }
+  return cached[dev];
+}
+
+cudaError_t ks_pcg(cudaStream_t st, const KsPcg& a) {
+  const int64_t nn = (int64_t)a.Nx * a.Ny * a.Nz;
+  const int maxb = ks_pcg_max_blocks();
+  if (maxb <= 0) return cudaErrorInvalidConfiguration;
+  int64_t blocks = (3 * nn + kPcgThreads - 1) / kPcgThreads;
+  if (blocks > maxb) blocks = maxb;
+  if (blocks < 1) blocks = 1;
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  KsPcg args = a;
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3((unsigned)blocks), dim3(kPcgThreads), params, 0, st);
 }
 
 cudaError_t ks_diag(cudaStream_t st, int64_t nn, const uint8_t* bc, const double* A, double* d) {

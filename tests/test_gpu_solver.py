@@ -40,7 +40,7 @@ def host(t):
 
 class Problem:
     def __init__(self, ctx, n, p, levels, E=None, perturb=0.1, seed=3, mixed=0, assembled=1, coarse_rtol=1e-14,
-                 amp=0.04):
+                 amp=0.04, fp64_kind=0):
         from paper_2204_01722_b300 import nh
         self.nh, self.ctx = nh, ctx
         q = p + 1
@@ -55,7 +55,8 @@ class Problem:
         nh.nh_space_set_dirichlet(ctx, self.space, self.masks[0])
         self.op = nh.nh_op_create(ctx, self.space, 0.3, E)
         self.opts = nh.nh_mg_default_opts(ctx, self.op, level_p=levels, mixed=mixed, coarse_assembled=assembled,
-                                          coarse_rtol=coarse_rtol, coarse_maxit=5000, seed=SEED)
+                                          coarse_rtol=coarse_rtol, coarse_maxit=5000, seed=SEED,
+                                          fp64_kind=fp64_kind)
         self.mg = nh.nh_mg_create(ctx, self.op, self.opts)
 
     def setup(self, u=None):
@@ -123,11 +124,12 @@ def test_mixed_vcycle_close_to_fp64(nhctx):
     P32.close()
 
 
-@pytest.mark.parametrize("mixed", [0, 1])
-def test_linear_solve_matches_direct(nhctx, mixed):
+@pytest.mark.parametrize("mixed,fp64_kind", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_linear_solve_matches_direct(nhctx, mixed, fp64_kind):
+    """fp64_kind 1: outer FCG, Lanczos and FP64 smoothers in float-float arithmetic."""
     import scipy.sparse.linalg as spla
     ctx, _ = nhctx
-    P = Problem(ctx, (3, 3, 2), 3, (3, 2, 1), mixed=mixed, coarse_rtol=1e-3)
+    P = Problem(ctx, (3, 3, 2), 3, (3, 2, 1), mixed=mixed, coarse_rtol=1e-3, fp64_kind=fp64_kind)
     P.setup()
     st = fem.qp_state(P.sps[0], P.mat, P.u)
     J = fem.assemble(P.sps[0], fem.element_matrices(P.sps[0], st), P.masks[0])
@@ -141,14 +143,15 @@ def test_linear_solve_matches_direct(nhctx, mixed):
     P.close()
 
 
-@pytest.mark.parametrize("n,p,levels,steps,mixed,delta", [((4, 4, 4), 2, (2, 1), 1, 0, 0.01),
-                                                          ((2, 2, 3), 4, (4, 2, 1), 2, 0, 0.05),
-                                                          ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05),
-                                                          ((3, 2, 2), 3, (3, 2, 1), 1, 1, 0.03)])
-def test_newton_solve_matches_oracle(nhctx, n, p, levels, steps, mixed, delta):
+@pytest.mark.parametrize("n,p,levels,steps,mixed,delta,kind", [((4, 4, 4), 2, (2, 1), 1, 0, 0.01, 0),
+                                                               ((2, 2, 3), 4, (4, 2, 1), 2, 0, 0.05, 0),
+                                                               ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 0),
+                                                               ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 1),
+                                                               ((3, 2, 2), 3, (3, 2, 1), 1, 1, 0.03, 0)])
+def test_newton_solve_matches_oracle(nhctx, n, p, levels, steps, mixed, delta, kind):
     """Uniaxial compression (x = 0 clamped, x = 1 pushed by delta), load-stepped."""
     ctx, _ = nhctx
-    P = Problem(ctx, n, p, levels, mixed=mixed, coarse_rtol=1e-3)
+    P = Problem(ctx, n, p, levels, mixed=mixed, coarse_rtol=1e-3, fp64_kind=kind)
     P.opts.load_steps = steps
     P.nh.nh_mg_destroy(P.mg)
     P.mg = P.nh.nh_mg_create(ctx, P.op, P.opts)
