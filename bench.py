@@ -54,6 +54,12 @@ def n_dof_of(p, n):
     return 3 * (p * n + 1) ** 3
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per apply launch from the ncu
+# capture summarised in profiles/ (small case, scaled to the full launch by
+# elements); reset to None whenever the kernel changes.
+NCU_TRAFFIC = {("f64", 3, 48): 1.203e9}
+
+
 def apply_bytes(p, n, wbytes, S=17, bc_byte=True):
     """Algorithmic bytes of one apply: stored quadrature data, du read, y written,
     int32 element map, and (FP64 kernels) one Dirichlet-bit byte per node; the
@@ -404,6 +410,8 @@ def main():
                     help="dram bytes per apply from an ncu capture of this kernel (reported as is)")
     args = ap.parse_args()
     args.n = args.n or DEFAULT_N[args.p]
+    if args.traffic is None:
+        args.traffic = NCU_TRAFFIC.get((args.prec, args.p, args.n))
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
