@@ -205,8 +205,10 @@ typedef struct {
                               1 = energy decrease with the optimal step a = z1.r / z1.J z1, i.e. z1.r > 0 */
   int learned_mode;        /* where a network set by nh_mg_set_learned acts:
                               1 = outer FCG stage (predicts the fine error at the vertices);
-                              2 = coarse warm start (predicts A_c^-1 r_c; the coarsest PCG starts from it
-                                  when it lowers the coarse residual, else from zero) */
+                              2 = coarse warm start (predicts y ~ A_c^-1 r_c; the coarsest PCG starts
+                                  from a y, a = y.r_c / y.A_c y the step that minimises the A-norm
+                                  error along y, when a > 0 and that start at least halves the
+                                  residual's natural norm, else from zero) */
   int fp64_kind;           /* arithmetic of the FP64-accurate matrix-free applies (outer FCG, Lanczos,
                               FP64 smoothers): 0 = native FP64 (NH_F64), 1 = float-float (NH_F64X) */
 } nh_mg_opts;

@@ -15,12 +15,18 @@
 
 // elements per block of the fused element kernels (about 128 threads, Q*Q per element)
 __host__ __device__ constexpr int nh_epb(int Q) { return (128 / (Q * Q)) > 0 ? 128 / (Q * Q) : 1; }
-// Blocked FP32 quadrature data: per batch of EPB elements, Q z-planes, each
-// [S][EPB][Q^2] padded to a multiple of 4 floats (16 bytes, for the bulk copies).
+// Blocked FP32 quadrature data: per batch of EPB elements, Q z-planes of
+// NP = EPB Q^2 points, each plane padded to a multiple of 4 floats (16 bytes, for
+// the bulk copies).  Within a plane, point p (element-major, then y, x) keeps its
+// first 4 (S/4) scalars as S/4 contiguous 16-byte chunks at [p][S/4][4], chunk k
+// in slot (k + nh_f32_rot(S, p)) mod S/4 -- a per-point rotation that puts the 8
+// lanes of one 16-byte shared load on distinct banks -- and its last S mod 4
+// scalars at [NP][S mod 4] after all points' chunks.
 __host__ __device__ constexpr long long nh_f32_plane_floats(int Q, int S) {
   return ((long long)S * nh_epb(Q) * Q * Q + 3) / 4 * 4;
 }
 __host__ __device__ constexpr long long nh_f32_batch_floats(int Q, int S) { return (long long)Q * nh_f32_plane_floats(Q, S); }
+__host__ __device__ constexpr int nh_f32_rot(int S, int p) { return S / 4 == 4 ? ((p & 7) >> 1) : ((p & 7) >> 2); }
 
 // ---- 1-D tables ---------------------------------------------------------------
 // Host-side tabulations in double; kernels receive them by value as kernel

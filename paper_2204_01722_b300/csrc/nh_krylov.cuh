@@ -40,7 +40,8 @@ cudaError_t ks_diag(cudaStream_t st, int64_t nn, const uint8_t* bc, const double
 // launch (all blocks co-resident, bounded grid barriers, convergence tested on
 // the device).  Solves A x = b from x = 0 (warm = 0) or from the given x
 // (warm = 1, tolerance relative to ref = sqrt(b . D^-1 b)); stops when
-// sqrt(r . z) <= rtol sqrt(r0 . z0) or after maxit iterations.  Work vectors
+// sqrt(r . z) <= rtol sqrt(r0 . z0) (tested every 4 iterations) or after maxit
+// iterations.  Work vectors
 // r, z, p, q of 3 n_nodes doubles; part: 2 * ks_pcg_max_blocks() doubles;
 // bar: 2 unsigned; out[0] = iterations, out[1] = 1 if a residual was not finite.
 struct KsPcg {

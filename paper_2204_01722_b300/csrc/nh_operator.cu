@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 #pragma unroll
     for (int qz = 0; qz < Q; qz++) {
       mbar_wait_bounded(&bar[qz & 1], (qz >> 1) & 1, err);
-      const float* qe = qs + (qz & 1) * PL + el * Q2 + v * Q + u;  // [S][EPB][Q^2]
+      const float* qp = qs + (qz & 1) * PL;  // this plane's slot
       float g[3][3], f[3][3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -513,7 +513,20 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
         g[c][2] = gz[c][qz];
       }
       if (live) {
-        pointwise<LAYOUT, float>(qe, (int64_t)EPB * Q2, g, f);
+        // this point's scalars: S/4 rotated 16-byte chunks, then the remainder
+        constexpr int NC = S / 4, R = S - 4 * NC, NP = EPB * Q2;
+        float qv[S];
+#pragma unroll
+        for (int k = 0; k < NC; k++) {
+          const float4 c4 = *reinterpret_cast<const float4*>(qp + t * 4 * NC + ((k + nh_f32_rot(S, t)) % NC) * 4);
+          qv[4 * k] = c4.x;
+          qv[4 * k + 1] = c4.y;
+          qv[4 * k + 2] = c4.z;
+          qv[4 * k + 3] = c4.w;
+        }
+#pragma unroll
+        for (int j = 0; j < R; j++) qv[4 * NC + j] = qp[NP * 4 * NC + t * R + j];
+        nhpw::pointwise_ld<LAYOUT, float>([&](int i) { return qv[i]; }, g, f);
       } else {
 #pragma unroll
         for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.f;

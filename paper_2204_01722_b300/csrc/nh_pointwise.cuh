@@ -16,15 +16,15 @@ namespace nhpw {
 // W sigma = G (W tau) + W lambda tr(G) I + W (mu - lambda log J) (G + G^T),
 // f = W sigma (grad_x xi)^T.  Stored: grad_x xi (9, row d = xi_d), W tau
 // (00, 11, 22, 12, 02, 01), W lambda, W (mu - lambda log J).
-template <typename T>
-__device__ __forceinline__ void pw_current(const T* __restrict__ q, int64_t s, const T (&g)[3][3],
-                                           T (&f)[3][3]) {
+// ld(i) returns stored scalar i of the point
+template <typename T, typename LD>
+__device__ __forceinline__ void pw_current_ld(LD ld, const T (&g)[3][3], T (&f)[3][3]) {
   T X[3][3];
 #pragma unroll
-  for (int i = 0; i < 9; i++) X[i / 3][i % 3] = q[i * s];
-  const T t00 = q[9 * s], t11 = q[10 * s], t22 = q[11 * s];
-  const T t12 = q[12 * s], t02 = q[13 * s], t01 = q[14 * s];
-  const T wl = q[15 * s], wm = q[16 * s];
+  for (int i = 0; i < 9; i++) X[i / 3][i % 3] = ld(i);
+  const T t00 = ld(9), t11 = ld(10), t22 = ld(11);
+  const T t12 = ld(12), t02 = ld(13), t01 = ld(14);
+  const T wl = ld(15), wm = ld(16);
   const T tau[3][3] = {{t00, t01, t02}, {t01, t11, t12}, {t02, t12, t22}};
   T G[3][3];
 #pragma unroll
@@ -52,17 +52,16 @@ __device__ __forceinline__ void pw_current(const T* __restrict__ q, int64_t s, c
 // W dS = W lambda (C^-1 : dE) C^-1 + 2 (W mu - W lambda log J) C^-1 dE C^-1,
 // W dP = dF (W S) + F (W dS), f = W dP (grad_X xi)^T.  Stored: grad_X xi (9),
 // H = grad_X u (9), C^-1 (00, 11, 22, 12, 02, 01), W mu, W lambda log J, W lambda.
-template <typename T>
-__device__ __forceinline__ void pw_initial(const T* __restrict__ q, int64_t s, const T (&g)[3][3],
-                                           T (&f)[3][3]) {
+template <typename T, typename LD>
+__device__ __forceinline__ void pw_initial_ld(LD ld, const T (&g)[3][3], T (&f)[3][3]) {
   T R[3][3], F[3][3];
 #pragma unroll
-  for (int i = 0; i < 9; i++) R[i / 3][i % 3] = q[i * s];
+  for (int i = 0; i < 9; i++) R[i / 3][i % 3] = ld(i);
 #pragma unroll
-  for (int i = 0; i < 9; i++) F[i / 3][i % 3] = q[(9 + i) * s] + (i % 4 == 0 ? T(1) : T(0));
-  const T c00 = q[18 * s], c11 = q[19 * s], c22 = q[20 * s];
-  const T c12 = q[21 * s], c02 = q[22 * s], c01 = q[23 * s];
-  const T wmu = q[24 * s], wll = q[25 * s], wl = q[26 * s];
+  for (int i = 0; i < 9; i++) F[i / 3][i % 3] = ld(9 + i) + (i % 4 == 0 ? T(1) : T(0));
+  const T c00 = ld(18), c11 = ld(19), c22 = ld(20);
+  const T c12 = ld(21), c02 = ld(22), c01 = ld(23);
+  const T wmu = ld(24), wll = ld(25), wl = ld(26);
   const T Ci[3][3] = {{c00, c01, c02}, {c01, c11, c12}, {c02, c12, c22}};
   T dF[3][3];
 #pragma unroll
@@ -115,12 +114,18 @@ __device__ __forceinline__ void pw_initial(const T* __restrict__ q, int64_t s, c
     for (int d = 0; d < 3; d++) f[c][d] = dP[c][0] * R[d][0] + dP[c][1] * R[d][1] + dP[c][2] * R[d][2];
 }
 
+template <int LAYOUT, typename T, typename LD>
+__device__ __forceinline__ void pointwise_ld(LD ld, const T (&g)[3][3], T (&f)[3][3]) {
+  if (LAYOUT == NH_LAYOUT_CURRENT)
+    pw_current_ld<T>(ld, g, f);
+  else
+    pw_initial_ld<T>(ld, g, f);
+}
+
+// scalars of the point at q, scalar i at q[i s]
 template <int LAYOUT, typename T>
 __device__ __forceinline__ void pointwise(const T* __restrict__ q, int64_t s, const T (&g)[3][3], T (&f)[3][3]) {
-  if (LAYOUT == NH_LAYOUT_CURRENT)
-    pw_current<T>(q, s, g, f);
-  else
-    pw_initial<T>(q, s, g, f);
+  pointwise_ld<LAYOUT, T>([&](int i) { return q[i * s]; }, g, f);
 }
 
 }  // namespace nhpw

@@ -744,22 +744,36 @@ nh_status coarse_solve(nh_mg mg, Level& l) {
       CK(kn_from_net(st, l.nn, mg->nout, scale, x));
       CK(kv_mask_zero<double>(st, l.nn, l.space->bc, x));
       mg->ctx->launches += 2;
-      // natural norms of b and of the warm-start residual
-      double *r = l.w[0], *z = l.w[1];
-      ST(level_apply(mg, l, NH_F64, x, r));
-      CK(kv_axpby<double>(st, l.n, 1.0, b, -1.0, r));
-      CK(kv_mul<double>(st, l.n, l.dinv64, r, z));
-      mg->ctx->launches += 2;
-      double rz = 0.0, bb = 0.0;
-      ST(dot_host(mg, l.n, r, z, &rz));
+      // Scale the prediction y by the step that minimises the A-norm error along
+      // it, a = y.b / y.A y (||x* - a y||_A <= ||x*||_A), and start the coarse
+      // PCG from a y only if that at least halves the residual's natural norm:
+      // a start that helps little would make the coarse solve, and so the
+      // preconditioner, depend on r_c nonlinearly for no gain.
+      double *ay = l.w[0], *z = l.w[1], *rw = l.w[2];
+      ST(level_apply(mg, l, NH_F64, x, ay));
+      double yb = 0.0, yay = 0.0, bb = 0.0;
+      ST(dot_host(mg, l.n, x, b, &yb));
+      ST(dot_host(mg, l.n, x, ay, &yay));
       CK(kv_mul<double>(st, l.n, l.dinv64, b, z));
       mg->ctx->launches++;
       ST(dot_host(mg, l.n, b, z, &bb));
-      if (isfinite(rz) && rz < bb) {
-        ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its, true, sqrt(bb)));
-        mg->coarse_its += its;
-        mg->acc++;
-        return NH_OK;
+      if (isfinite(yb) && isfinite(yay) && yb > 0.0 && yay > 0.0) {
+        const double a = yb / yay;
+        CK(cudaMemcpyAsync(rw, b, sizeof(double) * l.n, cudaMemcpyDeviceToDevice, st));
+        CK(kv_axpby<double>(st, l.n, -a, ay, 1.0, rw));  // r = b - a A y
+        CK(kv_mul<double>(st, l.n, l.dinv64, rw, z));
+        mg->ctx->launches += 2;
+        double rz = 0.0;
+        ST(dot_host(mg, l.n, rw, z, &rz));
+        if (isfinite(rz) && rz < 0.25 * bb) {
+          CK(kv_axpby<double>(st, l.n, a, x, 0.0, z));  // x = a y
+          CK(cudaMemcpyAsync(x, z, sizeof(double) * l.n, cudaMemcpyDeviceToDevice, st));
+          mg->ctx->launches++;
+          ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its, true, sqrt(bb)));
+          mg->coarse_its += its;
+          mg->acc++;
+          return NH_OK;
+        }
       }
       mg->rej++;
     }

@@ -269,6 +269,7 @@ cudaError_t ks_apply(cudaStream_t st, int Nx, int Ny, int Nz, const uint8_t* bc,
 namespace {
 
 constexpr int kPcgThreads = 256;
+constexpr int kCheck = 4;  // convergence test period (iterations)
 constexpr unsigned kGridSpin = 1u << 24;  // polls per grid barrier before giving up
 
 // Barrier over all blocks of a cooperative launch: arrival counter plus a
@@ -428,7 +429,8 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg(KsPcg a) {
       bad = 1;
       break;
     }
-    if (sqrt(fabs(rzn)) <= a.rtol * sqrt(rz0)) break;
+    // tested every kCheck iterations, as the host-driven loop does
+    if ((k % kCheck == 0 || k == a.maxit) && sqrt(fabs(rzn)) <= a.rtol * sqrt(rz0)) break;
     const double beta = rzn / rz;
     rz = rzn;
     for (int64_t t = t0; t < nr; t += stride) {

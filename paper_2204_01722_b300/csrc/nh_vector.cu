@@ -49,20 +49,21 @@ __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ x, float* __r
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (float)x[i];
 }
 
-// FP32 quadrature data per batch of EPB elements as Q z-planes of
-// [S][EPB][Q^2 (y, x)], each padded to PL floats: one plane is one bulk copy,
-// and the z-line threads of a warp (consecutive elements, then y, x) read
-// consecutive words.
+// FP32 quadrature data per batch of EPB elements as Q z-planes (one bulk copy
+// each), points in the order of the z-line threads of a block, scalars in
+// rotated 16-byte chunks plus a remainder array (see nh_f32_plane_floats).
 __global__ void k_f32_blocked(int Q, int EPB, int S, long long PL, int64_t ne, const double* __restrict__ qd,
                               float* __restrict__ qdf) {
-  const int Q2 = Q * Q, Q3 = Q2 * Q;
+  const int Q2 = Q * Q, Q3 = Q2 * Q, NP = EPB * Q2, NC = S / 4, R = S - 4 * NC;
   const int64_t n = (int64_t)S * ne * Q3;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int64_t s = i / (ne * Q3), r = i - s * ne * Q3;
-    const int64_t e = r / Q3;
-    const int q = (int)(r - e * Q3), qz = q / Q2, qyx = q - qz * Q2;
-    qdf[((e / EPB) * Q + qz) * PL + (s * EPB + e % EPB) * Q2 + qyx] = (float)qd[i];
+    const int s = (int)(i / (ne * Q3));
+    const int64_t r = i - s * ne * Q3, e = r / Q3;
+    const int q = (int)(r - e * Q3), qz = q / Q2, p = (int)(e % EPB) * Q2 + (q - qz * Q2);
+    const int64_t pos = s < 4 * NC ? (int64_t)p * 4 * NC + (((s >> 2) + nh_f32_rot(S, p)) % NC) * 4 + (s & 3)
+                                   : (int64_t)NP * 4 * NC + (int64_t)p * R + (s - 4 * NC);
+    qdf[((e / EPB) * Q + qz) * PL + pos] = (float)qd[i];
   }
 }
 
