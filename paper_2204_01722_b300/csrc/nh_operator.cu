@@ -96,6 +96,13 @@ __device__ __forceinline__ int sidx(int c, int k, int j, int i) {
 
 using nhpw::pointwise;
 
+// Float-float pointwise stage as one out-of-line copy: inlined once per
+// quadrature plane, the double-single code overflows the instruction cache.
+template <int LAYOUT>
+__device__ __noinline__ void pointwise_ff(const ff* q, int64_t s, const ff (&g)[3][3], ff (&f)[3][3]) {
+  pointwise<LAYOUT, ff>(q, s, g, f);
+}
+
 // s + a * b as one fused operation: FMA for float and double; for float-float
 // the product's error terms and the running sum share one renormalisation.
 __device__ __forceinline__ float madd(float s, float a, float b) { return s + a * b; }
@@ -271,7 +278,10 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<T, Q>())
     T g[3][3], f[3][3];
     colloc_grad<P, Q, T>(a, b, qk, tab, bC, U, g);
     if (live) {
-      pointwise<LAYOUT, T>(qe + qk * Q2, qstride, g, f);
+      if constexpr (std::is_same<T, ff>::value)
+        pointwise_ff<LAYOUT>(qe + qk * Q2, qstride, g, f);
+      else
+        pointwise<LAYOUT, T>(qe + qk * Q2, qstride, g, f);
     } else {
 #pragma unroll
       for (int i = 0; i < 9; i++) f[i / 3][i % 3] = T(0);

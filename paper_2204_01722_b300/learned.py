@@ -145,7 +145,8 @@ def main():
         for name in ("plain_fp64", "mixed", "mixed_learned"):
             sel = [r for r in rows if r["solver"] == name]
             res[name] = {k: float(np.mean([r[k] for r in sel])) for k in
-                         ("seconds", "krylov_its", "newton_its", "vcycles", "learned_accepted", "learned_rejected")}
+                         ("seconds", "krylov_its", "newton_its", "vcycles", "coarse_its", "learned_accepted",
+                          "learned_rejected")}
             res[name]["converged"] = all(r["status"] == 0 for r in sel)
         nh.nh_net_destroy(net)
         nh.nh_destroy(ctx)
