@@ -179,3 +179,61 @@ def test_collected_targets(nhctx):
     nh.nh_mg_destroy(mg)
     nh.nh_op_destroy(op)
     nh.nh_space_destroy(s)
+
+
+def test_trained_network_gain(nhctx):
+    """What a trained coarse warm start gains on the problem it was trained for:
+    a network trained on the coarse (r_c, A_c^-1 r_c) pairs that p-MG solves of
+    one small inclusion problem generate, then used in learned_mode 2 on
+    held-out right-hand sides.  Training must lower the loss; the learned solve
+    must reach the same solution; its coarse PCG iterations are reported against
+    plain p-MG.  A warm start is only taken when it halves the coarse residual,
+    so the learned solve may not cost more than plain p-MG beyond the spread of
+    FCG iteration counts that atomic-scatter rounding causes (10%)."""
+    import scipy.sparse.linalg as spla
+    ctx, stream = nhctx
+    from paper_2204_01722_b300 import nh
+    from paper_2204_01722_b300 import learned as L
+    n, p = 4, 2
+    s, op, mg, sp, mask, J, nd, _ = _problem(ctx, n, p, mode=2)
+    Nv = n + 1
+    X = sp.node_coords()
+
+    def rhs(seed):
+        b = inputs.normal_vector(nd, seed=seed) if seed % 2 == 0 else inputs.smooth_field(X, 1.0, seed=seed).ravel()
+        b[mask] = 0.0
+        return b
+
+    F, T = [], []
+    for j in range(16):
+        f = torch.zeros((8, 4, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
+        t = torch.zeros((8, 3, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
+        k = nh.nh_mg_collect(ctx, mg, torch.from_numpy(rhs(100 + j)).cuda(), 8, f, t)
+        F.append(f[:k])
+        T.append(t[:k])
+    feats, tgts = torch.cat(F).contiguous(), torch.cat(T).contiguous()
+    net = nh.nh_net_create(ctx, Nv, 2, (8, 16), bf16=True, seed=3)
+    hist = L.train(ctx, net, feats, tgts, epochs=120, lr=3e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    Jc = J.tocsc()
+    out = {}
+    for name, use in (("plain", False), ("learned", True)):
+        nh.nh_mg_set_learned(ctx, mg, net if use else None)
+        its, acc = 0, 0
+        for j in range(4):
+            b = rhs(900 + j)
+            x = torch.zeros(nd, dtype=torch.float64, device="cuda")
+            rep = nh.nh_linear_solve(ctx, mg, torch.from_numpy(b).cuda(), x, rtol=1e-10, maxit=300, norm=1)
+            assert rel(x.cpu().numpy(), spla.spsolve(Jc, b)) < 1e-6
+            its += rep.coarse_its
+            acc += rep.learned_accepted
+        out[name] = (its, acc)
+    msg = (f"coarse PCG iterations on 4 held-out right-hand sides: plain {out['plain'][0]}, learned "
+           f"{out['learned'][0]} ({out['learned'][1]} warm starts taken); training loss {hist[0]:.3f} -> {hist[-1]:.3f}")
+    print(msg)
+    assert out["learned"][0] <= 1.1 * out["plain"][0], msg
+    nh.nh_mg_set_learned(ctx, mg, None)
+    nh.nh_net_destroy(net)
+    nh.nh_mg_destroy(mg)
+    nh.nh_op_destroy(op)
+    nh.nh_space_destroy(s)
