@@ -361,11 +361,31 @@ struct LineLayout {
   }
 };
 
+// Atomic add of v[K..N) to y[K..N), y + K - A 16-byte aligned when K = 0 (A = the
+// run's start modulo 4 floats): 16-byte vector atomics where aligned, 8-byte or
+// single ones at the ends; the sequence is fixed at compile time per alignment.
+template <int A, int K, int N>
+__device__ __forceinline__ void red_run(float* y, const float (&v)[N]) {
+  if constexpr (K < N) {
+    constexpr int al = (A + K) & 3;
+    if constexpr (al == 0 && K + 4 <= N) {
+      atomicAdd(reinterpret_cast<float4*>(y + K), make_float4(v[K], v[K + 1], v[K + 2], v[K + 3]));
+      red_run<A, K + 4, N>(y, v);
+    } else if constexpr ((al & 1) == 0 && K + 2 <= N) {
+      atomicAdd(reinterpret_cast<float2*>(y + K), make_float2(v[K], v[K + 1]));
+      red_run<A, K + 2, N>(y, v);
+    } else {
+      atomicAdd(y + K, v[K]);
+      red_run<A, K + 1, N>(y, v);
+    }
+  }
+}
+
 template <int P, int Q, int LAYOUT>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     k_jacobian_apply_f32l(int64_t ne, const unsigned* __restrict__ emapb, const float* __restrict__ qdb,
                           const KTab<P, Q, float> tab, const float* __restrict__ du, float* __restrict__ y, int lift,
-                          int* __restrict__ err) {
+                          int vec_ok, int* __restrict__ err) {
   using L = LineLayout<Q>;
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   constexpr int S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
@@ -639,17 +659,38 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
         o[c][i] = s;
       }
     }
+    // the line's P nodes consecutive and unconstrained (box meshes away from
+    // Dirichlet faces): their 3P values are one contiguous run of y
+    const unsigned n0 = nid[0] & kNodeMask;
+    bool run = vec_ok != 0;
 #pragma unroll
-    for (int i = 0; i < P; i++) {
-      const int64_t n = nid[i] & kNodeMask;
-      const unsigned m = nid[i] >> kNodeBits;
+    for (int i = 0; i < P; i++) run = run && nid[i] == n0 + (unsigned)i;
+    if (run) {
+      float v[3 * P];
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        const int64_t dof = 3 * n + c;
-        if ((m >> c) & 1u) {
-          if (!lift) y[dof] = du[dof];  // identity row; every writer stores the same value
-        } else {
-          atomicAdd(&y[dof], o[c][i]);
+      for (int i = 0; i < P; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) v[3 * i + c] = o[c][i];
+      float* yr = y + 3 * (int64_t)n0;
+      switch ((3u * n0) & 3u) {
+        case 0: red_run<0, 0, 3 * P>(yr, v); break;
+        case 1: red_run<1, 0, 3 * P>(yr, v); break;
+        case 2: red_run<2, 0, 3 * P>(yr, v); break;
+        default: red_run<3, 0, 3 * P>(yr, v); break;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < P; i++) {
+        const int64_t n = nid[i] & kNodeMask;
+        const unsigned m = nid[i] >> kNodeBits;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const int64_t dof = 3 * n + c;
+          if ((m >> c) & 1u) {
+            if (!lift) y[dof] = du[dof];  // identity row; every writer stores the same value
+          } else {
+            atomicAdd(&y[dof], o[c][i]);
+          }
         }
       }
     }
@@ -1033,7 +1074,8 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   cudaError_t e = prep<k_jacobian_apply_f32l<P, Q, LAYOUT>>(smem);
   if (e != cudaSuccess) return e;
   k_jacobian_apply_f32l<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
-      A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift, A.err);
+      A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift,
+      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, A.err);
   return cudaGetLastError();
 }
 
