@@ -350,6 +350,7 @@ static OpArgs base_args(nh_op op) {
   OpArgs a;
   memset(&a, 0, sizeof(a));
   a.ne = op->space->ne;
+  a.nx = op->space->nx;
   a.emap = op->space->emap;
   a.emapb = op->space->emapb;
   a.bc = op->space->bc;

@@ -148,6 +148,7 @@ struct OpArgs {
   int store;           // setup: write quadrature data
   int resid;           // setup: compute residual
   int lift;            // apply: keep constrained inputs, leave constrained rows zero
+  int nx;              // elements along x of the (box) space
   int* err;            // device error flag for bounded waits
   const Tab1D* tab;
 };

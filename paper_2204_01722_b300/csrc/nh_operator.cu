@@ -385,13 +385,14 @@ template <int P, int Q, int LAYOUT>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     k_jacobian_apply_f32l(int64_t ne, const unsigned* __restrict__ emapb, const float* __restrict__ qdb,
                           const KTab<P, Q, float> tab, const float* __restrict__ du, float* __restrict__ y, int lift,
-                          int vec_ok, int* __restrict__ err) {
+                          int vec_ok, int rows_ok, int* __restrict__ err) {
   using L = LineLayout<Q>;
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   constexpr int S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
   constexpr long long BS = nh_f32_batch_floats(Q, S), PL = nh_f32_plane_floats(Q, S);
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[2];
+  __shared__ unsigned srun[EPB * P * P];        // start node of each node line's run (or ~0)
   float* qs = reinterpret_cast<float*>(smraw);  // two plane slots [2][PL]
   const int t = threadIdx.x;
   const int el = t / Q2, r = t - el * Q2;
@@ -644,8 +645,11 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     }
   }
   __syncthreads();
-  if (live && node_line) {  // x-lines over nodes (j = u, k = v): B_I^T along x, E^T
-    float o[3][P];
+  // x-lines over nodes (j = u, k = v): B_I^T along x
+  float o[3][P];
+  unsigned n0 = 0;
+  bool run = false;
+  if (node_line) {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       float w[Q];
@@ -661,10 +665,66 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     }
     // the line's P nodes consecutive and unconstrained (box meshes away from
     // Dirichlet faces): their 3P values are one contiguous run of y
-    const unsigned n0 = nid[0] & kNodeMask;
-    bool run = vec_ok != 0;
+    n0 = nid[0] & kNodeMask;
+    run = live && vec_ok != 0;
 #pragma unroll
     for (int i = 0; i < P; i++) run = run && nid[i] == n0 + (unsigned)i;
+    if (rows_ok) srun[(el * P + v) * P + u] = run ? n0 : 0xffffffffu;
+  }
+  // E^T.  When the block's elements follow one another along x (rows_ok: the
+  // box has a multiple of EPB elements along x) and every line is such a run,
+  // each (j, k) row of the block is one contiguous run of
+  // RN = EPB (P - 1) + 1 nodes: the rows are summed in shared memory (shared
+  // element faces added once) and reduced into y by the bulk-copy engine.
+  constexpr int RN = EPB * (P - 1) + 1, RL = 3 * RN, RS = (RL + 6) / 4 * 4;
+  static_assert(P * P * RS <= L::block_floats(EPB), "row buffer fits the work area");
+  bool chain = false;
+  unsigned first = 0;
+  if (rows_ok) {  // uniform: the barriers below are taken by all threads or none
+    __syncthreads();
+    chain = true;
+    if (node_line) {
+      first = srun[v * P + u];
+      chain = first != 0xffffffffu && srun[(el * P + v) * P + u] == first + (unsigned)(el * (P - 1));
+    }
+    chain = __syncthreads_and(chain) != 0;
+  }
+  if (chain) {
+    float* Rr = qs + 2 * PL + (v * P + u) * RS + ((3u * first) & 3u);  // node x, component c at 3 x + c
+    if (node_line) {
+#pragma unroll
+      for (int i = 1; i < P; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) Rr[3 * (el * (P - 1) + i) + c] = o[c][i];
+      if (el == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) Rr[c] = o[c][0];
+      }
+    }
+    __syncthreads();
+    if (node_line && el > 0) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) Rr[3 * el * (P - 1) + c] += o[c][0];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // shared writes -> bulk-copy reads
+    __syncthreads();
+    if (node_line && el == 0) {
+      float* g = y + 3 * (int64_t)first;
+      const int h = (int)((4u - ((3u * first) & 3u)) & 3u);  // floats before a 16-byte boundary
+      const int mid = (RL - h) / 4 * 4;
+      for (int k = 0; k < h; k++) atomicAdd(g + k, Rr[k]);
+      if (mid > 0) {
+        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(g + h),
+                     "r"(smem_u32(Rr + h)), "r"((unsigned)(mid * 4))
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+      for (int k = h + mid; k < RL; k++) atomicAdd(g + k, Rr[k]);
+      if (mid > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+    return;
+  }
+  if (live && node_line) {
     if (run) {
       float v[3 * P];
 #pragma unroll
@@ -1075,7 +1135,7 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   k_jacobian_apply_f32l<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
       A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift,
-      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, A.err);
+      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, ((uintptr_t)A.out & 15) == 0 && A.nx % EPB == 0 ? 1 : 0, A.err);
   return cudaGetLastError();
 }
 

@@ -112,6 +112,22 @@ def test_jacobian_apply_fp32(nhctx, n, p, layout):
     c.close()
 
 
+@pytest.mark.parametrize("n,p,mask", [((16, 2, 1), 3, "none"), ((24, 2, 2), 3, "uniaxial"), ((14, 1, 2), 2, "none"),
+                                      ((10, 2, 1), 4, "none"), ((10, 1, 2), 4, "uniaxial")])
+def test_jacobian_apply_fp32_block_rows(nhctx, n, p, mask):
+    """FP32 apply on boxes whose x-element count is a multiple of the kernel's
+    elements per block, so the block-row scatter (rows summed in shared memory,
+    reduced into y by bulk copies) is taken wherever a row has no Dirichlet node."""
+    ctx, _ = nhctx
+    c = Case(ctx, n, p, mask=mask, seed=17)
+    du = inputs.normal_vector(c.sp.n_dof, seed=18)
+    y = torch.empty(c.sp.n_dof, dtype=torch.float32, device="cuda")
+    c.nh.nh_jacobian_apply(ctx, c.op, dev(du, torch.float32), y)
+    ref = fem.jacobian_apply(c.sp, c.state, du.astype(np.float32).astype(np.float64), c.mask)
+    assert rel(host(y), ref) < TOL32
+    c.close()
+
+
 def test_jacobian_apply_inclusions_and_empty_mask(nhctx):
     """Per-element modulus with contrast 1e3 and no Dirichlet DoFs."""
     ctx, _ = nhctx
