@@ -132,6 +132,21 @@ nh_status nh_op_info(nh_op op, nh_prec prec, int* scalars_per_qp, int64_t* qdata
  * Errors: NH_ERR_ARG, NH_ERR_STATE (coarse op). */
 nh_status nh_qdata_setup(nh_op op, const double* u, double* min_J);
 
+/* Rediscretised coarse operator (Sec. III-B: the alternative to the exact
+ * Galerkin levels, re-evaluating the nonlinearity on a smaller set of
+ * quadrature points): an operator on `coarse` (same mesh and layout, p_c <= p_f,
+ * its own q, typically p_c + 1) owning its quadrature data [S][n_elem q_c^3]
+ * and a copy of the fine per-element material.  Synchronises.
+ * Errors: NH_ERR_ARG (not the fine operator, different mesh), NH_ERR_OOM. */
+nh_status nh_op_rediscretize(nh_op fine, nh_space coarse, nh_op* out);
+/* Quadrature data of a rediscretised operator from the fine state: the fine
+ * displacement u_fine (device L-vector of the fine space, 16-byte aligned) and
+ * geometry are evaluated at the coarse Gauss points with the fine basis, then
+ * F, J, log J, tau and grad_x xi (or the initial layout) as in nh_qdata_setup.
+ * min_J (HOST out, nullable) = min det F over the coarse points.  Synchronises.
+ * Errors: NH_ERR_ARG, NH_ERR_INVERTED (min det F <= 0). */
+nh_status nh_qdata_setup_rediscretized(nh_op op, nh_op fine, const double* u_fine, double* min_J);
+
 /* Residual r = F(u) (Eq. residual-discrete-ref with f_1 = tau, f_0 = 0):
  * sum_e E^T B_xi^T W tau (grad_x xi)^T; constrained rows r = u - g_bc.
  * g_bc may be NULL (zero).  FP64 device vectors; does not touch the stored
@@ -211,6 +226,10 @@ typedef struct {
                                   residual's natural norm, else from zero) */
   int fp64_kind;           /* arithmetic of the FP64-accurate matrix-free applies (outer FCG, Lanczos,
                               FP64 smoothers): 0 = native FP64 (NH_F64), 1 = float-float (NH_F64X) */
+  int coarse_rediscretize; /* 1: matrix-free coarse levels get their own Gauss rule q = p_l + 1 and
+                              quadrature data re-evaluated from the fine state (nh_op_rediscretize);
+                              0: exact Galerkin levels on the fine points (default).  An assembled
+                              Q1 coarsest level is always built from the fine data. */
 } nh_mg_opts;
 
 typedef struct {

@@ -321,6 +321,65 @@ extern "C" nh_status nh_op_level(nh_op fine, nh_space coarse, nh_op* out) {
   return NH_OK;
 }
 
+extern "C" nh_status nh_op_rediscretize(nh_op fine, nh_space coarse, nh_op* out) {
+  if (!fine || !coarse || !out) return NH_ERR_ARG;
+  *out = nullptr;
+  nh_ctx ctx = fine->space->ctx;
+  if (fine->parent) return nh_fail(ctx, NH_ERR_ARG, "nh_op_rediscretize: needs the fine operator");
+  nh_space fs = fine->space;
+  if (coarse->nx != fs->nx || coarse->ny != fs->ny || coarse->nz != fs->nz || coarse->p > fs->p)
+    return nh_fail(ctx, NH_ERR_ARG, "nh_op_rediscretize: coarse space must share the mesh, with p_c <= p_f");
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  nh_op op = new nh_op_s();
+  op->space = coarse;
+  op->layout = fine->layout;
+  op->S = fine->S;
+  op->nu = fine->nu;
+  const int64_t ne = coarse->ne, nq = ne * (int64_t)coarse->Q * coarse->Q * coarse->Q;
+  if (cudaMalloc(&op->lam, sizeof(double) * ne) != cudaSuccess || cudaMalloc(&op->mu, sizeof(double) * ne) != cudaSuccess ||
+      cudaMalloc(&op->qd, sizeof(double) * nq * op->S) != cudaSuccess) {
+    cudaGetLastError();
+    nh_op_destroy(op);
+    return nh_fail(ctx, NH_ERR_OOM, "nh_op_rediscretize: device allocation failed");
+  }
+  NH_CUDA(ctx, cudaMemcpyAsync(op->lam, fine->lam, sizeof(double) * ne, cudaMemcpyDeviceToDevice, ctx->stream));
+  NH_CUDA(ctx, cudaMemcpyAsync(op->mu, fine->mu, sizeof(double) * ne, cudaMemcpyDeviceToDevice, ctx->stream));
+  NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *out = op;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_qdata_setup_rediscretized(nh_op op, nh_op fine, const double* u_fine, double* min_J) {
+  if (!op || !fine || !u_fine) return NH_ERR_ARG;
+  nh_ctx ctx = op->space->ctx;
+  nh_space fs = fine->space, cs = op->space;
+  if (op->parent || fine->parent) return nh_fail(ctx, NH_ERR_ARG, "nh_qdata_setup_rediscretized: needs two root operators");
+  if (cs->nx != fs->nx || cs->ny != fs->ny || cs->nz != fs->nz || cs->p > fs->p || op->layout != fine->layout)
+    return nh_fail(ctx, NH_ERR_ARG, "nh_qdata_setup_rediscretized: operators must share the mesh and layout, p_c <= p_f");
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t nq = cs->ne * (int64_t)cs->Q * cs->Q * cs->Q;
+  NH_CUDA(ctx, cudaMemsetAsync(ctx->minj, 0xff, sizeof(unsigned long long), ctx->stream));
+  NH_CUDA(ctx, nh_launch_setup_pts(fs->P, cs->Q, op->layout, ctx->stream, fs->ne, fs->emap, fs->coords, u_fine, op->lam,
+                                   op->mu, op->qd, nq, ctx->minj));
+  ctx->launches++;
+  unsigned long long bits = 0;
+  NH_CUDA(ctx, cudaMemcpyAsync(ctx->red_host, ctx->minj, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
+  NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  memcpy(&bits, ctx->red_host, sizeof(bits));
+  bits = (bits >> 63) ? (bits & 0x7fffffffffffffffull) : ~bits;
+  double mj;
+  memcpy(&mj, &bits, sizeof(mj));
+  if (min_J) *min_J = mj;
+  op->qd_f_valid = false;
+  op->qd_ff_valid = false;
+  if (!(mj > 0.0) || !isfinite(mj)) {
+    op->have_qd = false;
+    return nh_fail(ctx, NH_ERR_INVERTED, "nh_qdata_setup_rediscretized: inverted element");
+  }
+  op->have_qd = true;
+  return NH_OK;
+}
+
 extern "C" nh_status nh_op_destroy(nh_op op) {
   if (!op) return NH_ERR_ARG;
   if (!op->parent) {
@@ -330,6 +389,7 @@ extern "C" nh_status nh_op_destroy(nh_op op) {
     cudaFree(op->qd_f);
     cudaFree(op->qd_ff);
   }
+  cudaFree(op->u_state);
   cudaFree(op->hbuf_in);
   cudaFree(op->hbuf_out);
   delete op;
@@ -395,6 +455,14 @@ extern "C" nh_status nh_qdata_setup(nh_op op, const double* u, double* min_J) {
     snprintf(buf, sizeof(buf), "nh_qdata_setup: inverted element, min det F = %g", mj);
     return nh_fail(ctx, NH_ERR_INVERTED, buf);
   }
+  // the state, for rediscretised coarse levels set up later from it
+  if (!op->u_state && cudaMalloc(&op->u_state, sizeof(double) * op->space->n_dof) != cudaSuccess) {
+    cudaGetLastError();
+    op->u_state = nullptr;
+    return nh_fail(ctx, NH_ERR_OOM, "nh_qdata_setup: device allocation failed");
+  }
+  NH_CUDA(ctx, cudaMemcpyAsync(op->u_state, u, sizeof(double) * op->space->n_dof, cudaMemcpyDeviceToDevice,
+                               ctx->stream));
   op->have_qd = true;
   return NH_OK;
 }

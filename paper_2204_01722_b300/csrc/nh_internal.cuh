@@ -109,6 +109,7 @@ struct nh_op_s {
   double* qd = nullptr;           // [S][ne*Q^3] FP64 quadrature data (fine op only)
   float* qd_f = nullptr;          // FP32 copy, blocked per element batch (nh_f32_batch_floats)
   float* qd_ff = nullptr;         // float-float pairs (h, l), same indexing as qd (NH_F64X)
+  double* u_state = nullptr;      // copy of the u of the last nh_qdata_setup (rediscretised levels)
   bool qd_ff_valid = false;
   bool have_qd = false;
   bool qd_f_valid = false;
@@ -186,6 +187,9 @@ cudaError_t nh_launch_dot_partials(int64_t n, const double* x, const double* y, 
 cudaError_t nh_launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
 cudaError_t nh_launch_f64_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);
 // FP64 -> float-float pairs (h, l) elementwise
+cudaError_t nh_launch_setup_pts(int PF, int QC, int layout, cudaStream_t s, int64_t ne, const int* emap,
+                                const double* coords, const double* u, const double* lam, const double* mu, double* qd,
+                                int64_t qstride, unsigned long long* minj);
 cudaError_t nh_launch_pack_emap(cudaStream_t s, int64_t n, const int* emap, const uint8_t* bc, unsigned* out);
 cudaError_t nh_launch_f64_to_ff(int64_t n, const double* x, float* y2, cudaStream_t s);
 // FP64 SoA quadrature data [S][ne Q^3] -> blocked FP32 [batch][S][EPB][Q^3]

@@ -54,6 +54,7 @@ struct Level {
   double* dinv64 = nullptr;
   double lmax = 0.0;
   bool stencil = false;
+  bool redisc = false;     // rediscretised: own Gauss rule and quadrature data from the fine state
   double* A = nullptr;     // [27][9][nn]
 };
 
@@ -479,6 +480,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->learned_accept = 0;
   o->learned_mode = 2;
   o->fp64_kind = 0;
+  o->coarse_rediscretize = 0;
   return NH_OK;
 }
 
@@ -533,6 +535,8 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
     if (o.level_p[i] < 1 || o.level_p[i] >= o.level_p[i - 1]) return bad("nh_mg_create: orders must decrease to >= 1");
   if (o.cheb_degree < 1 || !(o.cheb_hi > o.cheb_lo) || !(o.cheb_lo > 0)) return bad("nh_mg_create: bad Chebyshev options");
   if (o.fp64_kind != 0 && o.fp64_kind != 1) return bad("nh_mg_create: fp64_kind must be 0 or 1");
+  if (o.coarse_rediscretize != 0 && o.coarse_rediscretize != 1)
+    return bad("nh_mg_create: coarse_rediscretize must be 0 or 1");
   mg->p64 = o.fp64_kind ? NH_F64X : NH_F64;
   cudaSetDevice(mg->ctx->device);
   nh_status s;
@@ -544,15 +548,18 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
       l.space = fs;
       l.op = fine;
     } else {
+      const bool assembled = (i == o.n_levels - 1) && l.p == 1 && o.coarse_assembled;
+      l.redisc = o.coarse_rediscretize && !assembled;
       int64_t nn, nd;
       s = nh_space_box(mg->ctx, fs->nx, fs->ny, fs->nz, fs->verts_host.empty() ? nullptr : fs->verts_host.data(), l.p,
-                       fs->q, &l.space, &nn, &nd);
+                       l.redisc ? l.p + 1 : fs->q, &l.space, &nn, &nd);
       if (s != NH_OK) { nh_mg_destroy(mg); return s; }
       l.own = true;
       std::vector<uint8_t> m;
       if ((s = coarse_mask(mg, fs, l.space, m)) != NH_OK) { nh_mg_destroy(mg); return s; }
       if ((s = nh_space_set_dirichlet(l.space, m.data())) != NH_OK) { nh_mg_destroy(mg); return s; }
-      if ((s = nh_op_level(fine, l.space, &l.op)) != NH_OK) { nh_mg_destroy(mg); return s; }
+      s = l.redisc ? nh_op_rediscretize(fine, l.space, &l.op) : nh_op_level(fine, l.space, &l.op);
+      if (s != NH_OK) { nh_mg_destroy(mg); return s; }
     }
     l.n = l.space->n_dof;
     l.nn = l.space->n_nodes;
@@ -628,6 +635,10 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
       mg->ctx->launches += 2;
       ST(mark("stencil", lv, t0));
     } else {
+      if (l.redisc) {
+        ST(nh_qdata_setup_rediscretized(l.op, root, root->u_state, nullptr));
+        ST(mark("qdata", lv, t0));
+      }
       ST(nh_jacobian_diagonal(l.op, NH_F64, l.dinv64));
       ST(mark("diagonal", lv, t0));
     }

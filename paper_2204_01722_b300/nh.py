@@ -44,6 +44,8 @@ SIGNATURES = {
     "nh_op_destroy": (_st, [_vp]),
     "nh_op_info": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_i64)]),
     "nh_qdata_setup": (_st, [_vp, _vp, C.POINTER(C.c_double)]),
+    "nh_op_rediscretize": (_st, [_vp, _vp, C.POINTER(_vp)]),
+    "nh_qdata_setup_rediscretized": (_st, [_vp, _vp, _vp, C.POINTER(C.c_double)]),
     "nh_residual": (_st, [_vp, _vp, _vp, _vp]),
     "nh_jacobian_apply": (_st, [_vp, C.c_int, _vp, _vp]),
     "nh_jacobian_apply_host": (_st, [_vp, C.c_int, _vp, _vp]),
@@ -84,7 +86,7 @@ class MgOpts(C.Structure):
                 ("newton_atol", C.c_double), ("newton_maxit", C.c_int), ("krylov_rtol", C.c_double),
                 ("krylov_maxit", C.c_int), ("line_search", C.c_int), ("verbose", C.c_int),
                 ("learned_accept", C.c_int), ("learned_mode", C.c_int),
-                ("fp64_kind", C.c_int)]
+                ("fp64_kind", C.c_int), ("coarse_rediscretize", C.c_int)]
 
 
 class SolveReport(C.Structure):
@@ -221,6 +223,18 @@ def nh_op_info(ctx, op, prec=NH_F64):
 def nh_qdata_setup(ctx, op, u):
     mj = C.c_double()
     _check(lib.nh_qdata_setup(op, _ptr(u), C.byref(mj)), ctx)
+    return mj.value
+
+
+def nh_op_rediscretize(ctx, fine_op, coarse_space):
+    h = _vp()
+    _check(lib.nh_op_rediscretize(fine_op, coarse_space, C.byref(h)), ctx)
+    return h.value
+
+
+def nh_qdata_setup_rediscretized(ctx, op, fine_op, u_fine):
+    mj = C.c_double()
+    _check(lib.nh_qdata_setup_rediscretized(op, fine_op, _ptr(u_fine), C.byref(mj)), ctx)
     return mj.value
 
 

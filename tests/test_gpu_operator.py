@@ -177,6 +177,42 @@ def test_diagonal(nhctx, n, p, q, layout):
     c.close()
 
 
+@pytest.mark.parametrize("pf,pc,layout", [(4, 2, 0), (4, 1, 0), (3, 2, 0), (2, 1, 0), (3, 2, 1)])
+def test_rediscretized_coarse_operator(nhctx, pf, pc, layout):
+    """Rediscretised coarse operator (Sec. III-B alternative): quadrature data
+    re-evaluated from the fine state on the coarse Gauss rule q_c = p_c + 1."""
+    ctx, _ = nhctx
+    n = (2, 3, 2)
+    c = Case(ctx, n, pf, layout=layout, seed=19)
+    qc = pc + 1
+    V = c.sp.vertices
+    st = fem.qp_state(fem.Space(*n, V, pf, qc), c.mat, c.u)
+    spc = fem.Space(*n, V, pc, qc)
+    maskc = inputs.uniaxial_mask(spc.node_dims)
+    nh = c.nh
+    sc, _, ndc = nh.nh_space_box(ctx, *n, V, pc, qc)
+    nh.nh_space_set_dirichlet(ctx, sc, maskc)
+    opc = nh.nh_op_rediscretize(ctx, c.op, sc)
+    mj = nh.nh_qdata_setup_rediscretized(ctx, opc, c.op, c.ud)
+    assert abs(mj - st["J"].min()) < 1e-13
+    du = inputs.normal_vector(ndc, seed=20)
+    form = "A" if layout == 0 else "B"
+    ref = fem.jacobian_apply(spc, st, du, maskc, form=form)
+    for dt, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+        y = torch.empty(ndc, dtype=dt, device="cuda")
+        nh.nh_jacobian_apply(ctx, opc, dev(du, dt), y)
+        assert rel(host(y), ref) < tol
+    y = torch.empty(ndc, dtype=torch.float64, device="cuda")
+    nh.nh_jacobian_apply(ctx, opc, dev(du), y, prec=nh.NH_F64X)
+    assert rel(host(y), ref) < TOL64
+    d = torch.empty(ndc, dtype=torch.float64, device="cuda")
+    nh.nh_jacobian_diagonal(ctx, opc, d)
+    assert rel(host(d), fem.diagonal(spc, st, maskc, form=form)) < TOL64
+    nh.nh_op_destroy(opc)
+    nh.nh_space_destroy(sc)
+    c.close()
+
+
 @pytest.mark.parametrize("pf,pc", [(4, 2), (4, 1), (3, 2), (3, 1), (2, 1)])
 def test_coarse_level_operator(nhctx, pf, pc):
     """Galerkin coarse operator sharing the fine quadrature data (Sec. III-B)."""

@@ -40,7 +40,7 @@ def host(t):
 
 class Problem:
     def __init__(self, ctx, n, p, levels, E=None, perturb=0.1, seed=3, mixed=0, assembled=1, coarse_rtol=1e-14,
-                 amp=0.04, fp64_kind=0):
+                 amp=0.04, fp64_kind=0, redisc=0):
         from paper_2204_01722_b300 import nh
         self.nh, self.ctx = nh, ctx
         q = p + 1
@@ -56,7 +56,7 @@ class Problem:
         self.op = nh.nh_op_create(ctx, self.space, 0.3, E)
         self.opts = nh.nh_mg_default_opts(ctx, self.op, level_p=levels, mixed=mixed, coarse_assembled=assembled,
                                           coarse_rtol=coarse_rtol, coarse_maxit=5000, seed=SEED,
-                                          fp64_kind=fp64_kind)
+                                          fp64_kind=fp64_kind, coarse_rediscretize=redisc)
         self.mg = nh.nh_mg_create(ctx, self.op, self.opts)
 
     def setup(self, u=None):
@@ -143,15 +143,18 @@ def test_linear_solve_matches_direct(nhctx, mixed, fp64_kind):
     P.close()
 
 
-@pytest.mark.parametrize("n,p,levels,steps,mixed,delta,kind", [((4, 4, 4), 2, (2, 1), 1, 0, 0.01, 0),
-                                                               ((2, 2, 3), 4, (4, 2, 1), 2, 0, 0.05, 0),
-                                                               ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 0),
-                                                               ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 1),
-                                                               ((3, 2, 2), 3, (3, 2, 1), 1, 1, 0.03, 0)])
-def test_newton_solve_matches_oracle(nhctx, n, p, levels, steps, mixed, delta, kind):
-    """Uniaxial compression (x = 0 clamped, x = 1 pushed by delta), load-stepped."""
+@pytest.mark.parametrize("n,p,levels,steps,mixed,delta,kind,redisc", [((4, 4, 4), 2, (2, 1), 1, 0, 0.01, 0, 0),
+                                                                      ((2, 2, 3), 4, (4, 2, 1), 2, 0, 0.05, 0, 0),
+                                                                      ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 0, 0),
+                                                                      ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 1, 0),
+                                                                      ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 1, 1),
+                                                                      ((3, 2, 2), 3, (3, 2, 1), 1, 0, 0.03, 0, 1),
+                                                                      ((3, 2, 2), 3, (3, 2, 1), 1, 1, 0.03, 0, 0)])
+def test_newton_solve_matches_oracle(nhctx, n, p, levels, steps, mixed, delta, kind, redisc):
+    """Uniaxial compression (x = 0 clamped, x = 1 pushed by delta), load-stepped.
+    redisc: rediscretised coarse levels (a different preconditioner, same solution)."""
     ctx, _ = nhctx
-    P = Problem(ctx, n, p, levels, mixed=mixed, coarse_rtol=1e-3, fp64_kind=kind)
+    P = Problem(ctx, n, p, levels, mixed=mixed, coarse_rtol=1e-3, fp64_kind=kind, redisc=redisc)
     P.opts.load_steps = steps
     P.nh.nh_mg_destroy(P.mg)
     P.mg = P.nh.nh_mg_create(ctx, P.op, P.opts)
