@@ -309,11 +309,11 @@ def run_nh(args):
 # solve time to relative residual 1e-8, plain FP64 p-MG vs the chosen solver
 # ---------------------------------------------------------------------------
 def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusions=False, learned=None):
-    """Load-stepped Newton-Krylov p-MG solve of uniaxial compression; returns the
-    reports of the plain FP64 solver, of mixed precision (FP32 on the p > 1
-    levels), of mixed precision with the FP64-accurate applies in float-float
-    arithmetic, and of the chosen one: that plus rediscretised p > 1 coarse
-    levels (their own Gauss rule, quadrature data from the fine state)."""
+    """Load-stepped p-MG solves of uniaxial compression; returns the reports of
+    plain FP64 Newton-Krylov p-MG (the judge), FP64 L-BFGS with the V-cycle as
+    initial inverse Hessian, Newton-Krylov with the faster V-cycle (FP32 on the
+    p > 1 levels, FP64-accurate applies in float-float, rediscretised coarse
+    levels), and the chosen solver: L-BFGS with that V-cycle."""
     from paper_2204_01722_b300 import inputs
     V = inputs.box_vertices(n, n, n)
     sp, nn, nd = nh.nh_space_box(ctx, n, n, n, V, p, p + 1)
@@ -323,10 +323,11 @@ def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusion
     op = nh.nh_op_create(ctx, sp, NU, E, 1.0)
     g = torch.from_numpy(inputs.uniaxial_bc((N, N, N), delta)).cuda()
     out = {}
-    for name, mixed, kind, redisc in (("plain_fp64", 0, 0, 0), ("mixed", 1, 0, 0), ("mixed_ff", 1, 1, 0),
-                                      ("chosen_mixed_ff_rediscretized", 1, 1, 1)):
+    for name, mixed, kind, redisc, nl in (("plain_fp64", 0, 0, 0, 0), ("lbfgs_fp64", 0, 0, 0, 1),
+                                          ("newton_mixed_ff_rediscretized", 1, 1, 1, 0),
+                                          ("chosen_lbfgs_mixed_ff_rediscretized", 1, 1, 1, 1)):
         o = nh.nh_mg_default_opts(ctx, op, mixed=mixed, load_steps=steps, fp64_kind=kind,
-                                  coarse_rediscretize=redisc)
+                                  coarse_rediscretize=redisc, nonlinear=nl)
         mg = nh.nh_mg_create(ctx, op, o)
         u = torch.zeros(nd, dtype=torch.float64, device="cuda")
         rep = nh.nh_solve(ctx, mg, g, u, check=False)
@@ -338,7 +339,8 @@ def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusion
     out["workload"] = (f"Q{p} on {n}^3 ({nd} DoF), {'inclusions E 1e3/1, ' if inclusions else ''}"
                        f"{int(delta * 100)}% uniaxial compression in {steps} load steps, p-MG "
                        f"{p}->2->1, Chebyshev(3)-Jacobi, Q1 coarse Jacobi-PCG 1e-3, FCG 1e-3, Newton to 1e-8")
-    out["speedup"] = round(out["plain_fp64"]["seconds"] / max(out["chosen_mixed_ff_rediscretized"]["seconds"], 1e-9), 3)
+    out["speedup"] = round(out["plain_fp64"]["seconds"] / max(out["chosen_lbfgs_mixed_ff_rediscretized"]["seconds"],
+                                                              1e-9), 3)
     return out
 
 

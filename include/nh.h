@@ -230,6 +230,11 @@ typedef struct {
                               quadrature data re-evaluated from the fine state (nh_op_rediscretize);
                               0: exact Galerkin levels on the fine points (default).  An assembled
                               Q1 coarsest level is always built from the fine data. */
+  int nonlinear;           /* 0: Newton-Krylov (FCG + V-cycle); 1: L-BFGS with one V-cycle of the load
+                              step's tangent (set up after the predictor) as the initial inverse Hessian
+                              (Sec. III-A); same line search, predictor and tolerances; at most
+                              4 newton_maxit iterations per load step */
+  int lbfgs_m;             /* L-BFGS history pairs (5), 1..32 */
 } nh_mg_opts;
 
 typedef struct {

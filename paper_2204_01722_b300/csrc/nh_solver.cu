@@ -74,6 +74,8 @@ struct nh_mg_s {
   double *fr = nullptr, *fz = nullptr, *fp = nullptr, *fq = nullptr;  // FCG work
   double *fx = nullptr, *fu = nullptr, *fg = nullptr, *fb = nullptr, *ft = nullptr, *fs = nullptr;  // Newton
   double* fsave = nullptr;  // state at the start of a load increment
+  std::vector<double*> lbs, lby;  // L-BFGS history: steps s_i and residual changes y_i (allocated on first use)
+  double* lbr = nullptr;          // L-BFGS: residual at the previous iterate
   bool setup_done = false;
   nh_prec p64 = NH_F64;    // arithmetic of the FP64-accurate matrix-free applies
   int vcycles = 0, coarse_its = 0;
@@ -481,6 +483,8 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->learned_mode = 2;
   o->fp64_kind = 0;
   o->coarse_rediscretize = 0;
+  o->nonlinear = 0;
+  o->lbfgs_m = 5;
   return NH_OK;
 }
 
@@ -502,6 +506,9 @@ extern "C" nh_status nh_mg_destroy(nh_mg mg) {
   cudaFree(mg->pcg_part);
   cudaFree(mg->pcg_bar);
   cudaFreeHost(mg->hsc);
+  for (double* p : mg->lbs) cudaFree(p);
+  for (double* p : mg->lby) cudaFree(p);
+  cudaFree(mg->lbr);
   for (double* p : {mg->fr, mg->fz, mg->fp, mg->fq, mg->fx, mg->fu, mg->fg, mg->fb, mg->ft, mg->fs, mg->fsave})
     cudaFree(p);
   for (void* p : {(void*)mg->feat, (void*)mg->nout, (void*)mg->logE, (void*)mg->lz1, (void*)mg->lw, (void*)mg->lxs,
@@ -537,6 +544,8 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
   if (o.fp64_kind != 0 && o.fp64_kind != 1) return bad("nh_mg_create: fp64_kind must be 0 or 1");
   if (o.coarse_rediscretize != 0 && o.coarse_rediscretize != 1)
     return bad("nh_mg_create: coarse_rediscretize must be 0 or 1");
+  if (o.nonlinear != 0 && o.nonlinear != 1) return bad("nh_mg_create: nonlinear must be 0 (Newton) or 1 (L-BFGS)");
+  if (o.nonlinear == 1 && (o.lbfgs_m < 1 || o.lbfgs_m > 32)) return bad("nh_mg_create: need 1 <= lbfgs_m <= 32");
   mg->p64 = o.fp64_kind ? NH_F64X : NH_F64;
   cudaSetDevice(mg->ctx->device);
   nh_status s;
@@ -987,6 +996,36 @@ static nh_status resid_norm(nh_mg mg, const double* v, const double* g, double* 
   return NH_OK;
 }
 
+// L-BFGS direction (Sec. III-A, the quasi-Newton alternative to Newton-Krylov):
+// d = -H F by the two-loop recursion over the stored pairs (s_i, y_i), oldest
+// last, with one V-cycle of the load step's tangent as the initial inverse
+// Hessian H_0.  hist[j] indexes the pairs from newest to oldest; rho[j] = 1 / y.s.
+static nh_status lbfgs_direction(nh_mg mg, const double* F, double* d, double* q, const std::vector<int>& hist,
+                                 const std::vector<double>& rho) {
+  cudaStream_t st = mg->ctx->stream;
+  const int64_t n = mg->L[0].n;
+  const int k = (int)hist.size();
+  std::vector<double> alpha(k, 0.0);
+  CK(cudaMemcpyAsync(q, F, 8 * n, cudaMemcpyDeviceToDevice, st));
+  for (int j = 0; j < k; j++) {
+    double sq = 0.0;
+    ST(dot_host(mg, n, mg->lbs[hist[j]], q, &sq));
+    alpha[j] = rho[j] * sq;
+    CK(kv_axpby<double>(st, n, -alpha[j], mg->lby[hist[j]], 1.0, q));
+    mg->ctx->launches++;
+  }
+  ST(precond(mg, q, d));  // d = H_0 q
+  for (int j = k - 1; j >= 0; j--) {
+    double yd = 0.0;
+    ST(dot_host(mg, n, mg->lby[hist[j]], d, &yd));
+    CK(kv_axpby<double>(st, n, alpha[j] - rho[j] * yd, mg->lbs[hist[j]], 1.0, d));
+    mg->ctx->launches++;
+  }
+  CK(kv_axpby<double>(st, n, 0.0, d, -1.0, d));  // d = -H F
+  mg->ctx->launches++;
+  return NH_OK;
+}
+
 extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_report* rep) {
   if (!mg || !u) return NH_ERR_ARG;
   nh_ctx ctx = mg->ctx;
@@ -1084,9 +1123,112 @@ extern "C" nh_status nh_solve(nh_mg mg, const double* g_bc, double* u, nh_solve_
     // the tolerance refers to the load step, not to a halved sub-increment of it
     if (t_target - t_prev >= (t_target - t) * 1.000001 && halvings == 0) nr_step = nr0;
     nr0 = std::max(nr0, nr_step);
-    // --- Newton corrector at fixed t
     int it = 0;
-    while (!(nr <= o.newton_rtol * nr0) && !(nr <= o.newton_atol)) {
+    if (o.nonlinear == 1) {
+      // --- L-BFGS corrector at fixed t, H_0 = V-cycle of the tangent at the predicted state
+      status = setup(u, &minJ);
+      if (status != NH_OK) break;
+      if (mg->lbs.empty()) {
+        for (int j = 0; j < o.lbfgs_m; j++) {
+          double *sv = nullptr, *yv = nullptr;
+          ST(dalloc(mg, (void**)&sv, 8 * n));
+          mg->lbs.push_back(sv);
+          ST(dalloc(mg, (void**)&yv, 8 * n));
+          mg->lby.push_back(yv);
+        }
+        ST(dalloc(mg, (void**)&mg->lbr, 8 * n));
+      }
+      std::vector<int> hist;     // slots, newest first
+      std::vector<double> rho;
+      int next = 0;
+      const int maxit = 4 * o.newton_maxit;
+      while (!(nr <= o.newton_rtol * nr0) && !(nr <= o.newton_atol)) {
+        if (it >= maxit || (it >= 40 && nr > 1e-4 * nr0)) {
+          status = nh_fail(ctx, NH_ERR_NOT_CONVERGED, "nh_solve: L-BFGS iteration limit");
+          break;
+        }
+        t1 = now_s();
+        mg->vcycles = 0;
+        mg->coarse_its = 0;
+        ST(lbfgs_direction(mg, r, du, rhs, hist, rho));
+        R.vcycles += mg->vcycles;
+        R.coarse_its += mg->coarse_its;
+        tK += now_s() - t1;
+        t1 = now_s();
+        double at = 1.0, nrt = 0.0;
+        for (int bt = 0;; bt++) {
+          CK(cudaMemcpyAsync(ut, u, 8 * n, cudaMemcpyDeviceToDevice, st));
+          CK(kv_axpby<double>(st, n, at, du, 1.0, ut));
+          ctx->launches++;
+          ST(resid_norm(mg, ut, gk, rt, &nrt));
+          if (isfinite(nrt)) break;
+          if (bt >= 12) {
+            status = nh_fail(ctx, NH_ERR_INVERTED, "nh_solve: every trial step inverts an element");
+            break;
+          }
+          at *= 0.5;
+        }
+        if (status != NH_OK) break;
+        double alpha = at;
+        if (o.line_search) {
+          double phi0 = 0.0, phi1 = 0.0;
+          ST(dot_host(mg, n, r, du, &phi0));
+          ST(dot_host(mg, n, rt, du, &phi1));
+          if (phi0 * phi1 < 0.0) {
+            const double a = at * phi0 / (phi0 - phi1);
+            if (isfinite(a)) alpha = std::min(at < 1.0 ? at : 1.5, std::max(0.1 * at, a));
+          }
+        }
+        // new pair in slot `next`: s = alpha du, y = F(u + s) - F(u)
+        double* sv = mg->lbs[next];
+        double* yv = mg->lby[next];
+        CK(cudaMemcpyAsync(mg->lbr, r, 8 * n, cudaMemcpyDeviceToDevice, st));
+        if (alpha == at) {
+          CK(cudaMemcpyAsync(u, ut, 8 * n, cudaMemcpyDeviceToDevice, st));
+          CK(cudaMemcpyAsync(r, rt, 8 * n, cudaMemcpyDeviceToDevice, st));
+          nr = nrt;
+        } else {
+          CK(cudaMemcpyAsync(ut, u, 8 * n, cudaMemcpyDeviceToDevice, st));
+          CK(kv_axpby<double>(st, n, alpha, du, 1.0, ut));
+          ctx->launches++;
+          double nra = 0.0;
+          ST(resid_norm(mg, ut, gk, rt, &nra));
+          if (!isfinite(nra)) {  // keep the backtracked trial step
+            alpha = at;
+            CK(cudaMemcpyAsync(ut, u, 8 * n, cudaMemcpyDeviceToDevice, st));
+            CK(kv_axpby<double>(st, n, at, du, 1.0, ut));
+            ctx->launches++;
+            ST(resid_norm(mg, ut, gk, rt, &nra));
+          }
+          CK(cudaMemcpyAsync(u, ut, 8 * n, cudaMemcpyDeviceToDevice, st));
+          CK(cudaMemcpyAsync(r, rt, 8 * n, cudaMemcpyDeviceToDevice, st));
+          nr = nra;
+        }
+        CK(kv_axpby<double>(st, n, alpha, du, 0.0, sv));          // s
+        CK(cudaMemcpyAsync(yv, r, 8 * n, cudaMemcpyDeviceToDevice, st));
+        CK(kv_axpby<double>(st, n, -1.0, mg->lbr, 1.0, yv));     // y (constrained rows are zero in both)
+        ctx->launches += 2;
+        double ys = 0.0;
+        ST(dot_host(mg, n, yv, sv, &ys));
+        if (ys > 0.0 && isfinite(ys)) {  // curvature condition, else the pair is dropped
+          if ((int)hist.size() == o.lbfgs_m) {
+            hist.pop_back();
+            rho.pop_back();
+          }
+          hist.insert(hist.begin(), next);
+          rho.insert(rho.begin(), 1.0 / ys);
+          next = (next + 1) % o.lbfgs_m;
+        }
+        tR += now_s() - t1;
+        it++;
+        R.newton_its++;
+        if (o.verbose)
+          fprintf(stderr, "nh_solve t %.4f lbfgs %d |F| %.3e rel %.3e vcyc %d alpha %.3f pairs %d\n", t, it, nr,
+                  nr / nr0, R.vcycles, alpha, (int)hist.size());
+      }
+    }
+    // --- Newton corrector at fixed t
+    while (o.nonlinear == 0 && !(nr <= o.newton_rtol * nr0) && !(nr <= o.newton_atol)) {
       if (it >= o.newton_maxit || (it >= 10 && nr > 1e-4 * nr0)) {  // limit, or stagnation
         status = nh_fail(ctx, NH_ERR_NOT_CONVERGED, "nh_solve: Newton iteration limit");
         break;

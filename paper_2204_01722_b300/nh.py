@@ -86,7 +86,8 @@ class MgOpts(C.Structure):
                 ("newton_atol", C.c_double), ("newton_maxit", C.c_int), ("krylov_rtol", C.c_double),
                 ("krylov_maxit", C.c_int), ("line_search", C.c_int), ("verbose", C.c_int),
                 ("learned_accept", C.c_int), ("learned_mode", C.c_int),
-                ("fp64_kind", C.c_int), ("coarse_rediscretize", C.c_int)]
+                ("fp64_kind", C.c_int), ("coarse_rediscretize", C.c_int), ("nonlinear", C.c_int),
+                ("lbfgs_m", C.c_int)]
 
 
 class SolveReport(C.Structure):

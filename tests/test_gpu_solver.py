@@ -40,7 +40,7 @@ def host(t):
 
 class Problem:
     def __init__(self, ctx, n, p, levels, E=None, perturb=0.1, seed=3, mixed=0, assembled=1, coarse_rtol=1e-14,
-                 amp=0.04, fp64_kind=0, redisc=0):
+                 amp=0.04, fp64_kind=0, redisc=0, nonlinear=0):
         from paper_2204_01722_b300 import nh
         self.nh, self.ctx = nh, ctx
         q = p + 1
@@ -56,7 +56,7 @@ class Problem:
         self.op = nh.nh_op_create(ctx, self.space, 0.3, E)
         self.opts = nh.nh_mg_default_opts(ctx, self.op, level_p=levels, mixed=mixed, coarse_assembled=assembled,
                                           coarse_rtol=coarse_rtol, coarse_maxit=5000, seed=SEED,
-                                          fp64_kind=fp64_kind, coarse_rediscretize=redisc)
+                                          fp64_kind=fp64_kind, coarse_rediscretize=redisc, nonlinear=nonlinear)
         self.mg = nh.nh_mg_create(ctx, self.op, self.opts)
 
     def setup(self, u=None):
@@ -143,18 +143,22 @@ def test_linear_solve_matches_direct(nhctx, mixed, fp64_kind):
     P.close()
 
 
-@pytest.mark.parametrize("n,p,levels,steps,mixed,delta,kind,redisc", [((4, 4, 4), 2, (2, 1), 1, 0, 0.01, 0, 0),
-                                                                      ((2, 2, 3), 4, (4, 2, 1), 2, 0, 0.05, 0, 0),
-                                                                      ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 0, 0),
-                                                                      ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 1, 0),
-                                                                      ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 1, 1),
-                                                                      ((3, 2, 2), 3, (3, 2, 1), 1, 0, 0.03, 0, 1),
-                                                                      ((3, 2, 2), 3, (3, 2, 1), 1, 1, 0.03, 0, 0)])
-def test_newton_solve_matches_oracle(nhctx, n, p, levels, steps, mixed, delta, kind, redisc):
+@pytest.mark.parametrize("n,p,levels,steps,mixed,delta,kind,redisc,nl", [((4, 4, 4), 2, (2, 1), 1, 0, 0.01, 0, 0, 0),
+                                                                         ((2, 2, 3), 4, (4, 2, 1), 2, 0, 0.05, 0, 0, 0),
+                                                                         ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 0, 0, 0),
+                                                                         ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 1, 0, 0),
+                                                                         ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 1, 1, 0),
+                                                                         ((3, 2, 2), 3, (3, 2, 1), 1, 0, 0.03, 0, 1, 0),
+                                                                         ((3, 2, 2), 3, (3, 2, 1), 1, 1, 0.03, 0, 0, 0),
+                                                                         ((4, 4, 4), 2, (2, 1), 1, 0, 0.01, 0, 0, 1),
+                                                                         ((2, 2, 3), 4, (4, 2, 1), 2, 1, 0.05, 1, 1, 1),
+                                                                         ((3, 2, 2), 3, (3, 2, 1), 1, 0, 0.03, 0, 0, 1)])
+def test_newton_solve_matches_oracle(nhctx, n, p, levels, steps, mixed, delta, kind, redisc, nl):
     """Uniaxial compression (x = 0 clamped, x = 1 pushed by delta), load-stepped.
-    redisc: rediscretised coarse levels (a different preconditioner, same solution)."""
+    redisc: rediscretised coarse levels (a different preconditioner, same solution);
+    nl = 1: L-BFGS with the V-cycle as initial inverse Hessian instead of Newton-Krylov."""
     ctx, _ = nhctx
-    P = Problem(ctx, n, p, levels, mixed=mixed, coarse_rtol=1e-3, fp64_kind=kind, redisc=redisc)
+    P = Problem(ctx, n, p, levels, mixed=mixed, coarse_rtol=1e-3, fp64_kind=kind, redisc=redisc, nonlinear=nl)
     P.opts.load_steps = steps
     P.nh.nh_mg_destroy(P.mg)
     P.mg = P.nh.nh_mg_create(ctx, P.op, P.opts)
@@ -162,7 +166,7 @@ def test_newton_solve_matches_oracle(nhctx, n, p, levels, steps, mixed, delta, k
     u = torch.zeros(P.nd, dtype=torch.float64, device="cuda")
     rep = P.nh.nh_solve(ctx, P.mg, dev(g), u)
     assert rep.rel_residual <= 1e-8 or rep.abs_residual <= 1e-13
-    assert rep.newton_its <= 12 * steps
+    assert rep.newton_its <= (12 if nl == 0 else 60) * steps
     # oracle: Newton with a direct solver, same load steps
     uo = np.zeros(P.nd)
     for k in range(1, steps + 1):
