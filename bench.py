@@ -313,7 +313,8 @@ def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusion
     plain FP64 Newton-Krylov p-MG (the judge), FP64 L-BFGS with the V-cycle as
     initial inverse Hessian, Newton-Krylov with the faster V-cycle (FP32 on the
     p > 1 levels, FP64-accurate applies in float-float, rediscretised coarse
-    levels), and the chosen solver: L-BFGS with that V-cycle."""
+    levels), and the chosen solver: L-BFGS with that V-cycle and the geometric
+    multigrid coarse solve."""
     from paper_2204_01722_b300 import inputs
     V = inputs.box_vertices(n, n, n)
     sp, nn, nd = nh.nh_space_box(ctx, n, n, n, V, p, p + 1)
@@ -323,11 +324,11 @@ def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusion
     op = nh.nh_op_create(ctx, sp, NU, E, 1.0)
     g = torch.from_numpy(inputs.uniaxial_bc((N, N, N), delta)).cuda()
     out = {}
-    for name, mixed, kind, redisc, nl in (("plain_fp64", 0, 0, 0, 0), ("lbfgs_fp64", 0, 0, 0, 1),
-                                          ("newton_mixed_ff_rediscretized", 1, 1, 1, 0),
-                                          ("chosen_lbfgs_mixed_ff_rediscretized", 1, 1, 1, 1)):
+    for name, mixed, kind, redisc, nl, cs in (("plain_fp64", 0, 0, 0, 0, 0), ("lbfgs_fp64", 0, 0, 0, 1, 0),
+                                              ("newton_mixed_ff_rediscretized", 1, 1, 1, 0, 0),
+                                              ("chosen_lbfgs_mixed_ff_rediscretized_hmg", 1, 1, 1, 1, 1)):
         o = nh.nh_mg_default_opts(ctx, op, mixed=mixed, load_steps=steps, fp64_kind=kind,
-                                  coarse_rediscretize=redisc, nonlinear=nl)
+                                  coarse_rediscretize=redisc, nonlinear=nl, coarse_solver=cs)
         mg = nh.nh_mg_create(ctx, op, o)
         u = torch.zeros(nd, dtype=torch.float64, device="cuda")
         rep = nh.nh_solve(ctx, mg, g, u, check=False)
@@ -339,8 +340,8 @@ def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusion
     out["workload"] = (f"Q{p} on {n}^3 ({nd} DoF), {'inclusions E 1e3/1, ' if inclusions else ''}"
                        f"{int(delta * 100)}% uniaxial compression in {steps} load steps, p-MG "
                        f"{p}->2->1, Chebyshev(3)-Jacobi, Q1 coarse Jacobi-PCG 1e-3, FCG 1e-3, Newton to 1e-8")
-    out["speedup"] = round(out["plain_fp64"]["seconds"] / max(out["chosen_lbfgs_mixed_ff_rediscretized"]["seconds"],
-                                                              1e-9), 3)
+    out["speedup"] = round(out["plain_fp64"]["seconds"] /
+                           max(out["chosen_lbfgs_mixed_ff_rediscretized_hmg"]["seconds"], 1e-9), 3)
     return out
 
 

@@ -235,6 +235,11 @@ typedef struct {
                               (Sec. III-A); same line search, predictor and tolerances; at most
                               4 newton_maxit iterations per load step */
   int lbfgs_m;             /* L-BFGS history pairs (5), 1..32 */
+  int coarse_solver;       /* assembled Q1 coarsest level: 0 = Jacobi-PCG (one cooperative kernel);
+                              1 = PCG with a geometric multigrid V-cycle on the vertex lattice (Galerkin
+                              P^T A P stencils, damped Jacobi, exact solve on 3^3 nodes), used when the
+                              lattice halves evenly down to 3 nodes per direction and the coarsest
+                              stencil is positive definite, else Jacobi-PCG */
 } nh_mg_opts;
 
 typedef struct {

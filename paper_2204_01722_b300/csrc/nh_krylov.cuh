@@ -57,4 +57,21 @@ struct KsPcg {
   int* err;
 };
 int ks_pcg_max_blocks();
+
+// Geometric multigrid on the Q1 vertex lattice (nh_hmg.cu): coarse Dirichlet bits
+// (node 2I of the finer lattice), Galerkin coarse stencil P^T A P, damped Jacobi
+// sweep, residual, restriction P^T, prolongation x_f += P x_c, dense x = M b.
+cudaError_t hm_coarse_bc(cudaStream_t st, int Nfx, int Nfy, int Ncx, int Ncy, int Ncz, const uint8_t* bcf,
+                         uint8_t* bcc);
+cudaError_t hm_rap(cudaStream_t st, int Nfx, int Nfy, int Nfz, int Ncx, int Ncy, int Ncz, const uint8_t* bcf,
+                   const uint8_t* bcc, const double* Af, double* Ac);
+cudaError_t hm_jacobi(cudaStream_t st, int Nx, int Ny, int Nz, const uint8_t* bc, const double* A, const double* dinv,
+                      const double* b, const double* xin, double* xout, double omega, int zero_in);
+cudaError_t hm_resid(cudaStream_t st, int Nx, int Ny, int Nz, const uint8_t* bc, const double* A, const double* b,
+                     const double* x, double* r);
+cudaError_t hm_restrict(cudaStream_t st, int Nfx, int Nfy, int Nfz, int Ncx, int Ncy, int Ncz, const uint8_t* bcf,
+                        const uint8_t* bcc, const double* rf, double* bcv);
+cudaError_t hm_prolong_add(cudaStream_t st, int Nfx, int Nfy, int Nfz, int Ncx, int Ncy, int Ncz, const uint8_t* bcf,
+                           const uint8_t* bcc, const double* xc, double* xf);
+cudaError_t hm_dense_mv(cudaStream_t st, int n, const double* M, const double* b, double* x);
 cudaError_t ks_pcg(cudaStream_t st, const KsPcg& a);

@@ -58,6 +58,15 @@ struct Level {
   double* A = nullptr;     // [27][9][nn]
 };
 
+// one lattice of the geometric multigrid on the assembled Q1 level
+struct HLevel {
+  int Nx = 0, Ny = 0, Nz = 0;
+  int64_t nn = 0;
+  uint8_t* bc = nullptr;
+  double *A = nullptr, *dinv = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+  bool own = false;  // level 0 borrows the p-multigrid's stencil, bits and diagonal
+};
+
 }  // namespace
 
 struct nh_mg_s {
@@ -68,6 +77,10 @@ struct nh_mg_s {
   double* sc = nullptr;    // device scalars
   double* part = nullptr;  // dot partials
   double* hsc = nullptr;   // pinned host mirror
+  std::vector<HLevel> H;           // geometric multigrid on the assembled Q1 level (coarse_solver 1)
+  bool hmg_ok = false;             // its current setup succeeded (else the coarse solve is Jacobi-PCG)
+  double* Hinv = nullptr;          // dense inverse on the coarsest lattice
+  int Hn = 0;
   double* pcg_part = nullptr;      // coarse cooperative PCG: block partials
   unsigned* pcg_bar = nullptr;     // its grid barrier words
   // FCG / Newton work (fine, FP64)
@@ -485,6 +498,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->coarse_rediscretize = 0;
   o->nonlinear = 0;
   o->lbfgs_m = 5;
+  o->coarse_solver = 0;
   return NH_OK;
 }
 
@@ -505,6 +519,15 @@ extern "C" nh_status nh_mg_destroy(nh_mg mg) {
   cudaFree(mg->part);
   cudaFree(mg->pcg_part);
   cudaFree(mg->pcg_bar);
+  for (HLevel& h : mg->H) {
+    if (h.own) {
+      cudaFree(h.bc);
+      cudaFree(h.A);
+      cudaFree(h.dinv);
+    }
+    for (double* p : {h.x, h.b, h.r, h.t}) cudaFree(p);
+  }
+  cudaFree(mg->Hinv);
   cudaFreeHost(mg->hsc);
   for (double* p : mg->lbs) cudaFree(p);
   for (double* p : mg->lby) cudaFree(p);
@@ -546,6 +569,7 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
     return bad("nh_mg_create: coarse_rediscretize must be 0 or 1");
   if (o.nonlinear != 0 && o.nonlinear != 1) return bad("nh_mg_create: nonlinear must be 0 (Newton) or 1 (L-BFGS)");
   if (o.nonlinear == 1 && (o.lbfgs_m < 1 || o.lbfgs_m > 32)) return bad("nh_mg_create: need 1 <= lbfgs_m <= 32");
+  if (o.coarse_solver != 0 && o.coarse_solver != 1) return bad("nh_mg_create: coarse_solver must be 0 or 1");
   mg->p64 = o.fp64_kind ? NH_F64X : NH_F64;
   cudaSetDevice(mg->ctx->device);
   nh_status s;
@@ -613,9 +637,204 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
     return NH_ERR_OOM;
   }
   cudaMemset(mg->sc, 0, sizeof(double) * S_LEN);
+  // geometric multigrid for an assembled Q1 coarsest level: halve the lattice while
+  // every direction has an even number of cells, down to 3 nodes per direction
+  Level& lc = mg->L.back();
+  if (o.coarse_solver == 1 && lc.stencil) {
+    HLevel h0;
+    h0.Nx = lc.space->Nx;
+    h0.Ny = lc.space->Ny;
+    h0.Nz = lc.space->Nz;
+    h0.nn = lc.nn;
+    h0.bc = lc.space->bc;
+    h0.A = lc.A;
+    h0.dinv = lc.dinv64;
+    mg->H.push_back(h0);
+    auto even = [](int N) { return N >= 5 && (N - 1) % 2 == 0; };
+    while (even(mg->H.back().Nx) && even(mg->H.back().Ny) && even(mg->H.back().Nz)) {
+      const HLevel& f = mg->H.back();
+      HLevel c;
+      c.Nx = (f.Nx - 1) / 2 + 1;
+      c.Ny = (f.Ny - 1) / 2 + 1;
+      c.Nz = (f.Nz - 1) / 2 + 1;
+      c.nn = (int64_t)c.Nx * c.Ny * c.Nz;
+      c.own = true;
+      mg->H.push_back(c);
+      HLevel& cc = mg->H.back();
+      if ((s = dalloc(mg, (void**)&cc.bc, cc.nn)) != NH_OK || (s = dalloc(mg, (void**)&cc.A, 8 * 243 * cc.nn)) != NH_OK ||
+          (s = dalloc(mg, (void**)&cc.dinv, 8 * 3 * cc.nn)) != NH_OK) {
+        nh_mg_destroy(mg);
+        return s;
+      }
+    }
+    for (HLevel& h : mg->H)
+      for (double** v : {&h.x, &h.b, &h.r, &h.t})
+        if ((s = dalloc(mg, (void**)v, 8 * 3 * h.nn)) != NH_OK) { nh_mg_destroy(mg); return s; }
+    if (mg->H.size() < 2 || mg->H.back().nn > 216) {
+      // no usable hierarchy (odd cell counts or a large coarsest lattice): Jacobi-PCG
+      for (HLevel& h : mg->H) {
+        if (h.own) {
+          cudaFree(h.bc);
+          cudaFree(h.A);
+          cudaFree(h.dinv);
+        }
+        for (double* p : {h.x, h.b, h.r, h.t}) cudaFree(p);
+      }
+      mg->H.clear();
+    } else {
+      mg->Hn = (int)(3 * mg->H.back().nn);
+      if ((s = dalloc(mg, (void**)&mg->Hinv, 8 * (size_t)mg->Hn * mg->Hn)) != NH_OK) { nh_mg_destroy(mg); return s; }
+    }
+  }
   *out = mg;
   return NH_OK;
 }
+
+// ---- geometric multigrid on the assembled Q1 level ------------------------------
+// Galerkin stencils down the lattice hierarchy, Jacobi diagonals, and the dense
+// inverse of the coarsest stencil (constrained rows identity; Cholesky on the host).
+static nh_status hmg_setup(nh_mg mg) {
+  cudaStream_t st = mg->ctx->stream;
+  for (size_t l = 1; l < mg->H.size(); l++) {
+    HLevel &f = mg->H[l - 1], &c = mg->H[l];
+    CK(hm_coarse_bc(st, f.Nx, f.Ny, c.Nx, c.Ny, c.Nz, f.bc, c.bc));
+    CK(hm_rap(st, f.Nx, f.Ny, f.Nz, c.Nx, c.Ny, c.Nz, f.bc, c.bc, f.A, c.A));
+    CK(ks_diag(st, c.nn, c.bc, c.A, c.dinv));
+    CK(kv_recip<double>(st, 3 * c.nn, c.dinv));
+    mg->ctx->launches += 4;
+  }
+  const HLevel& L = mg->H.back();
+  const int n = mg->Hn;
+  std::vector<double> A((size_t)243 * L.nn), D((size_t)n * n, 0.0);
+  std::vector<uint8_t> bc((size_t)L.nn);
+  CK(cudaMemcpyAsync(A.data(), L.A, 8 * A.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(bc.data(), L.bc, bc.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int64_t I = 0; I < L.nn; I++) {
+    const int x = (int)(I % L.Nx), y = (int)((I / L.Nx) % L.Ny), z = (int)(I / ((int64_t)L.Nx * L.Ny));
+    for (int c = 0; c < 3; c++) {
+      const int64_t row = 3 * I + c;
+      if ((bc[I] >> c) & 1u) {
+        D[row * n + row] = 1.0;
+        continue;
+      }
+      for (int s = 0; s < 27; s++) {
+        const int x2 = x + s % 3 - 1, y2 = y + (s / 3) % 3 - 1, z2 = z + s / 9 - 1;
+        if (x2 < 0 || x2 >= L.Nx || y2 < 0 || y2 >= L.Ny || z2 < 0 || z2 >= L.Nz) continue;
+        const int64_t J = x2 + (int64_t)L.Nx * (y2 + (int64_t)L.Ny * z2);
+        for (int cp = 0; cp < 3; cp++)
+          if (!((bc[J] >> cp) & 1u)) D[row * n + 3 * J + cp] += A[((size_t)s * 9 + 3 * c + cp) * L.nn + I];
+      }
+    }
+  }
+  // Cholesky D = C C^T, then the inverse column by column
+  std::vector<double> C((size_t)n * n, 0.0), Inv((size_t)n * n, 0.0);
+  for (int j = 0; j < n; j++) {
+    double d = D[(size_t)j * n + j];
+    for (int k = 0; k < j; k++) d -= C[(size_t)j * n + k] * C[(size_t)j * n + k];
+    if (!(d > 0.0)) {  // indefinite tangent (e.g. past a limit point): no SPD V-cycle this time
+      mg->hmg_ok = false;
+      return NH_OK;
+    }
+    const double cjj = sqrt(d);
+    C[(size_t)j * n + j] = cjj;
+    for (int i = j + 1; i < n; i++) {
+      double v = 0.5 * (D[(size_t)i * n + j] + D[(size_t)j * n + i]);
+      for (int k = 0; k < j; k++) v -= C[(size_t)i * n + k] * C[(size_t)j * n + k];
+      C[(size_t)i * n + j] = v / cjj;
+    }
+  }
+  std::vector<double> w(n);
+  for (int e = 0; e < n; e++) {
+    for (int i = 0; i < n; i++) {  // C w = e_e
+      double v = (i == e) ? 1.0 : 0.0;
+      for (int k = 0; k < i; k++) v -= C[(size_t)i * n + k] * w[k];
+      w[i] = v / C[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; i--) {  // C^T x = w
+      double v = w[i];
+      for (int k = i + 1; k < n; k++) v -= C[(size_t)k * n + i] * Inv[(size_t)k * n + e];
+      Inv[(size_t)i * n + e] = v / C[(size_t)i * n + i];
+    }
+  }
+  CK(cudaMemcpyAsync(mg->Hinv, Inv.data(), 8 * Inv.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  mg->hmg_ok = true;
+  return NH_OK;
+}
+
+namespace {
+constexpr double kHOmega = 0.6;  // Jacobi damping
+constexpr int kHSweeps = 2;      // pre- and post-smoothing sweeps
+
+// x = M_l b: one symmetric V-cycle from lattice l (x, b of that lattice's size)
+nh_status hvcycle(nh_mg mg, size_t l, const double* b, double* x) {
+  cudaStream_t st = mg->ctx->stream;
+  HLevel& h = mg->H[l];
+  if (l + 1 == mg->H.size()) {
+    CK(hm_dense_mv(st, mg->Hn, mg->Hinv, b, x));
+    mg->ctx->launches++;
+    return NH_OK;
+  }
+  HLevel& c = mg->H[l + 1];
+  const size_t bytes = 8 * 3 * (size_t)h.nn;
+  CK(hm_jacobi(st, h.Nx, h.Ny, h.Nz, h.bc, h.A, h.dinv, b, x, x, kHOmega, 1));
+  for (int s = 1; s < kHSweeps; s++) {
+    CK(hm_jacobi(st, h.Nx, h.Ny, h.Nz, h.bc, h.A, h.dinv, b, x, h.t, kHOmega, 0));
+    CK(cudaMemcpyAsync(x, h.t, bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  CK(hm_resid(st, h.Nx, h.Ny, h.Nz, h.bc, h.A, b, x, h.r));
+  CK(hm_restrict(st, h.Nx, h.Ny, h.Nz, c.Nx, c.Ny, c.Nz, h.bc, c.bc, h.r, c.b));
+  mg->ctx->launches += 1 + kHSweeps + 1;
+  ST(hvcycle(mg, l + 1, c.b, c.x));
+  CK(hm_prolong_add(st, h.Nx, h.Ny, h.Nz, c.Nx, c.Ny, c.Nz, h.bc, c.bc, c.x, x));
+  for (int s = 0; s < kHSweeps; s++) {
+    CK(hm_jacobi(st, h.Nx, h.Ny, h.Nz, h.bc, h.A, h.dinv, b, x, h.t, kHOmega, 0));
+    CK(cudaMemcpyAsync(x, h.t, bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  mg->ctx->launches += 1 + kHSweeps;
+  return NH_OK;
+}
+
+// PCG on the assembled Q1 level with the geometric V-cycle as preconditioner
+// (symmetric: same damped Jacobi sweeps before and after, P^T restriction,
+// exact coarsest solve); stops on sqrt(r.z) <= rtol sqrt(r0.z0).
+nh_status hmg_pcg(nh_mg mg, Level& l, const double* b, double* x, double rtol, int maxit, int* its) {
+  cudaStream_t st = mg->ctx->stream;
+  const int64_t n = l.n;
+  double *r = l.w[0], *z = l.w[1], *p = l.w[2], *q = l.w[3];
+  CK(cudaMemsetAsync(x, 0, 8 * n, st));
+  CK(cudaMemcpyAsync(r, b, 8 * n, cudaMemcpyDeviceToDevice, st));
+  ST(hvcycle(mg, 0, r, z));
+  double rz = 0.0;
+  ST(dot_host(mg, n, r, z, &rz));
+  const double rz0 = rz;
+  int k = 0;
+  if (rz0 > 0.0) {
+    CK(cudaMemcpyAsync(p, z, 8 * n, cudaMemcpyDeviceToDevice, st));
+    while (k < maxit) {
+      ST(level_apply(mg, l, NH_F64, p, q));
+      double pq = 0.0;
+      ST(dot_host(mg, n, p, q, &pq));
+      const double a = rz / pq;
+      CK(kv_axpby<double>(st, n, a, p, 1.0, x));
+      CK(kv_axpby<double>(st, n, -a, q, 1.0, r));
+      mg->ctx->launches += 2;
+      ST(hvcycle(mg, 0, r, z));
+      double rzn = 0.0;
+      ST(dot_host(mg, n, r, z, &rzn));
+      k++;
+      if (!isfinite(rzn)) return nh_fail(mg->ctx, NH_ERR_NAN, "coarse multigrid PCG: non-finite residual");
+      if (sqrt(fabs(rzn)) <= rtol * sqrt(rz0)) break;
+      CK(kv_axpby<double>(st, n, 1.0, z, rzn / rz, p));
+      mg->ctx->launches++;
+      rz = rzn;
+    }
+  }
+  *its = k;
+  return NH_OK;
+}
+}  // namespace
 
 extern "C" nh_status nh_mg_setup(nh_mg mg) {
   if (!mg) return NH_ERR_ARG;
@@ -662,6 +881,10 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
       ST(mark("lanczos", lv, t0));
     }
     lv++;
+  }
+  if (!mg->H.empty()) {
+    ST(hmg_setup(mg));
+    ST(mark("h-mg", lv, t0));
   }
   CK(cudaStreamSynchronize(st));
   mg->setup_done = true;
@@ -798,7 +1021,10 @@ nh_status coarse_solve(nh_mg mg, Level& l) {
       mg->rej++;
     }
   }
-  ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
+  if (mg->hmg_ok && &l == &mg->L.back())
+    ST(hmg_pcg(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, &its));
+  else
+    ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
   mg->coarse_its += its;
   return NH_OK;
 }
