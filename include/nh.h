@@ -160,7 +160,10 @@ nh_status nh_residual(nh_op op, const double* u, const double* g_bc, double* r);
  * alias.  Errors: NH_ERR_ARG, NH_ERR_STATE (no quadrature data yet). */
 nh_status nh_jacobian_apply(nh_op op, nh_prec prec, const void* du, void* y);
 /* Same, with HOST du_host and y_host (pinned memory recommended): copies in,
- * applies, copies out through library-owned device buffers; synchronises. */
+ * applies, copies out through library-owned device buffers; synchronises.  The
+ * apply runs in up to 8 chunks of z-layers of the box: a chunk's du node layers
+ * are uploaded on one copy stream while the previous chunk computes, and node
+ * layers that no later chunk touches are downloaded on another. */
 nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* du_host, void* y_host);
 
 /* Diagonal of the assembled Jacobian for Jacobi smoothing (Sec. III-B):

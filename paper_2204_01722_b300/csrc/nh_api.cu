@@ -102,6 +102,9 @@ extern "C" nh_status nh_destroy(nh_ctx c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : c->ev_chunk) cudaEventDestroy(ev);
+  if (c->s_in) cudaStreamDestroy(c->s_in);
+  if (c->s_out) cudaStreamDestroy(c->s_out);
   cudaFree(c->red);
   cudaFree(c->minj);
   cudaFree(c->dev_err);
@@ -588,12 +591,49 @@ nh_status nh_jacobian_apply_lift(nh_op op, const double* x, double* y) {
   return NH_OK;
 }
 
+// Launch the apply for elements [e0, e1) of op's space (arguments offset into
+// the element maps and quadrature data; y must have been zeroed).
+static nh_status launch_apply_range(nh_op op, nh_prec prec, const void* du, void* y, int64_t e0, int64_t e1,
+                                    cudaStream_t s) {
+  nh_ctx ctx = op->space->ctx;
+  nh_op root = op->parent ? op->parent : op;
+  nh_space sp = op->space;
+  const int64_t P3 = (int64_t)sp->P * sp->P * sp->P, Q3 = (int64_t)sp->Q * sp->Q * sp->Q;
+  OpArgs a = base_args(op);
+  a.ne = e1 - e0;
+  a.emap = sp->emap + e0 * P3;
+  a.emapb = sp->emapb + e0 * P3;
+  a.in = du;
+  a.out = y;
+  a.prec = prec;
+  if (prec == NH_F64) {
+    a.qd = root->qd + e0 * Q3;
+  } else if (prec == NH_F64X) {
+    a.qd = root->qd_ff + 2 * e0 * Q3;
+  } else {
+    const int epb = nh_epb(sp->Q);
+    a.qd = root->qd_f + (e0 / epb) * nh_f32_batch_floats(sp->Q, root->S);
+  }
+  NH_CUDA(ctx, nh_launch_apply(sp->P, sp->Q, prec, a, s));
+  ctx->launches++;
+  return NH_OK;
+}
+
+// Host vectors in and out.  On the box mesh the elements of z-layers [z0, z1)
+// need du on node layers [z0 p, z1 p] only, a contiguous range of the L-vector,
+// and leave y final on the layers below z1 p: the apply runs in chunks of
+// z-layers with the upload of the next chunk and the download of finished node
+// layers on two copy streams, overlapping the transfers with the kernels.
 extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* du_h, void* y_h) {
   if (!op || !du_h || !y_h) return NH_ERR_ARG;
   nh_ctx ctx = op->space->ctx;
+  nh_op root = op->parent ? op->parent : op;
+  nh_space sp = op->space;
   if (prec != NH_F64 && prec != NH_F32 && prec != NH_F64X)
     return nh_fail(ctx, NH_ERR_ARG, "nh_jacobian_apply_host: bad precision");
-  const size_t bytes = (prec == NH_F32 ? 4 : 8) * (size_t)op->space->n_dof;
+  if (!root->have_qd) return nh_fail(ctx, NH_ERR_STATE, "nh_jacobian_apply_host: call nh_qdata_setup first");
+  const size_t w = prec == NH_F32 ? 4 : 8;
+  const size_t bytes = w * (size_t)sp->n_dof;
   NH_CUDA(ctx, cudaSetDevice(ctx->device));
   if (op->hbuf_bytes < bytes) {
     NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -605,10 +645,69 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
     NH_CUDA(ctx, cudaMalloc(&op->hbuf_out, bytes));
     op->hbuf_bytes = bytes;
   }
-  NH_CUDA(ctx, cudaMemcpyAsync(op->hbuf_in, du_h, bytes, cudaMemcpyHostToDevice, ctx->stream));
-  nh_status st = nh_jacobian_apply(op, prec, op->hbuf_in, op->hbuf_out);
-  if (st != NH_OK) return st;
-  NH_CUDA(ctx, cudaMemcpyAsync(y_h, op->hbuf_out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  if (prec == NH_F32) {
+    nh_status st = ensure_f32(root);
+    if (st != NH_OK) return st;
+  } else if (prec == NH_F64X) {
+    nh_status st = ensure_ff(root);
+    if (st != NH_OK) return st;
+  }
+  if (!ctx->s_in) {
+    NH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
+    NH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
+  }
+  // chunks of z-layers; with FP32 each chunk starts on a kernel batch of EPB elements
+  const int64_t nxy = (int64_t)sp->nx * sp->ny, lay = (int64_t)sp->Nx * sp->Ny * 3;  // elements, DoF per layer
+  int64_t step = 1;
+  if (prec == NH_F32) {
+    const int64_t epb = nh_epb(sp->Q);
+    int64_t g = epb, r = nxy % epb;
+    while (r) {
+      const int64_t t2 = g % r;
+      g = r;
+      r = t2;
+    }
+    step = epb / g;  // layers per aligned boundary
+  }
+  const int64_t nsteps = (sp->nz + step - 1) / step;
+  const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(8, nsteps));
+  while (ctx->ev_chunk.size() < 2 * (size_t)nch) {
+    cudaEvent_t e;
+    NH_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->ev_chunk.push_back(e);
+  }
+  const char* hin = static_cast<const char*>(du_h);
+  char* hout = static_cast<char*>(y_h);
+  char* din = static_cast<char*>(op->hbuf_in);
+  char* dout = static_cast<char*>(op->hbuf_out);
+  // y = 0 on the compute stream, ordered before every chunk's kernel
+  NH_CUDA(ctx, cudaMemsetAsync(dout, 0, bytes, ctx->stream));
+  NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[0], ctx->stream));
+  NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_chunk[0], 0));  // hbuf reuse after earlier work
+  int64_t up = 0, down = 0;                                          // DoF uploaded / downloaded so far
+  for (int c = 0; c < nch; c++) {
+    const int64_t z0 = std::min<int64_t>(sp->nz, nsteps * c / nch * step);
+    const int64_t z1 = c + 1 == nch ? sp->nz : std::min<int64_t>(sp->nz, nsteps * (c + 1) / nch * step);
+    if (z1 <= z0) continue;
+    const int64_t need = std::min<int64_t>(sp->n_dof, (z1 * sp->p + 1) * lay);
+    if (need > up) {
+      NH_CUDA(ctx, cudaMemcpyAsync(din + w * up, hin + w * up, w * (need - up), cudaMemcpyHostToDevice, ctx->s_in));
+      up = need;
+    }
+    NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c], ctx->s_in));
+    NH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_chunk[2 * c], 0));
+    nh_status st = launch_apply_range(op, prec, din, dout, z0 * nxy, z1 * nxy, ctx->stream);
+    if (st != NH_OK) return st;
+    NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c + 1], ctx->stream));
+    const int64_t fin = c + 1 == nch ? sp->n_dof : std::min<int64_t>(sp->n_dof, z1 * sp->p * lay);
+    if (fin > down) {
+      NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_chunk[2 * c + 1], 0));
+      NH_CUDA(ctx, cudaMemcpyAsync(hout + w * down, dout + w * down, w * (fin - down), cudaMemcpyDeviceToHost,
+                                   ctx->s_out));
+      down = fin;
+    }
+  }
+  NH_CUDA(ctx, cudaStreamSynchronize(ctx->s_out));
   NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return NH_OK;
 }

@@ -79,6 +79,9 @@ struct nh_ctx_s {
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;   // 2 per recorded launch
   size_t ev_used = 0;
+  // host-buffer apply pipeline: upload and download streams, per-chunk events
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  std::vector<cudaEvent_t> ev_chunk;  // 2 per chunk (uploaded, computed)
 };
 
 struct nh_space_s {

@@ -150,6 +150,26 @@ def test_single_element_and_host_apply(nhctx):
     c.close()
 
 
+@pytest.mark.parametrize("n,p", [((3, 4, 11), 2), ((8, 2, 9), 3), ((2, 2, 7), 4)])
+def test_host_apply_pipelined(nhctx, n, p):
+    """nh_jacobian_apply_host in chunks of z-layers (upload, kernel, download of
+    finished node layers overlapped on three streams) equals the oracle, in each
+    precision; FP32 chunks start on kernel batches."""
+    ctx, _ = nhctx
+    c = Case(ctx, n, p, seed=23)
+    du = inputs.normal_vector(c.sp.n_dof, seed=24)
+    ref = fem.jacobian_apply(c.sp, c.state, du, c.mask)
+    for prec, dt, tol in ((c.nh.NH_F64, np.float64, TOL64), (c.nh.NH_F64X, np.float64, TOL64),
+                          (c.nh.NH_F32, np.float32, TOL32)):
+        x = torch.from_numpy(du.astype(dt)).pin_memory()
+        y = torch.empty_like(x).pin_memory()
+        c.nh.nh_jacobian_apply_host(ctx, c.op, x, y, prec=prec)
+        r = ref if dt == np.float64 else fem.jacobian_apply(c.sp, c.state, du.astype(np.float32).astype(np.float64),
+                                                             c.mask)
+        assert rel(y.numpy(), r) < tol
+    c.close()
+
+
 @pytest.mark.parametrize("n,p,q", [((3, 2, 4), 2, 3), ((2, 3, 2), 4, 5), ((3, 2, 2), 1, 3)])
 def test_residual(nhctx, n, p, q):
     ctx, _ = nhctx
