@@ -190,6 +190,20 @@ def kernel_ms(nh, ctx, case, prec, steps):
     return tot / max(k, 1)
 
 
+def replica_max(dist, value, device):
+    """Max over the ranks of a per-rank time: the slowest replica times the job."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, repeats, seconds):
+    """Units per second over all replicas, in billions (GDoF/s for DoF)."""
+    return world * units_per_rank * repeats / seconds / 1e9
+
+
 def run_nh(args):
     import torch
     from paper_2204_01722_b300 import nh
@@ -218,11 +232,8 @@ def run_nh(args):
         clocks = ClockSampler(gpu_index)
         ms, launches = time_applies(nh, torch, ctx, stream, case, args.prec, args.steps, args.warmup, barrier)
         clk = clocks.stop()
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        value = world * case.nd * args.steps / (ms_max * 1e-3) / 1e9
+        ms_max = replica_max(dist, ms, "cuda")
+        value = whole_job_rate(world, case.nd, args.steps, ms_max * 1e-3)
         # roofline of the apply kernel alone (CUDA events around each launch)
         kms = kernel_ms(nh, ctx, case, args.prec, args.steps)
         hbm, hbm_src = peaks()
@@ -251,10 +262,7 @@ def run_nh(args):
         for _ in range(ek):
             nh.nh_jacobian_apply_host(ctx, case.op, hin, hout, prec=PREC[args.prec])
         te = time.perf_counter() - t0
-        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": round(world * case.nd * ek / float(tt.item()) / 1e9, 4), "unit": "GDoF/s",
+        e2e = {"value": round(whole_job_rate(world, case.nd, ek, replica_max(dist, te, "cuda")), 4), "unit": "GDoF/s",
                "h2d_bytes_per_step": int(case.nd * np.dtype(dt).itemsize),
                "d2h_bytes_per_step": int(case.nd * np.dtype(dt).itemsize),
                "entry_point": "nh_jacobian_apply_host (pinned host du, y)"}
