@@ -82,6 +82,14 @@ nh_status nh_destroy(nh_ctx ctx);
 const char* nh_last_error(nh_ctx ctx);
 /* Block until the context stream is idle; returns any latched device error. */
 nh_status nh_sync(nh_ctx ctx);
+/* Failure-detection test hook (no counterpart in the paper): launches a kernel
+ * whose bounded wait cannot complete -- kind 0: an mbarrier that no copy
+ * arrives on (the wait of the FP32 apply's staged loads); kind 1: a grid
+ * barrier that one block of a cooperative launch skips (the coarse PCG's
+ * barrier) -- with a short poll limit.  The wait gives up, sets the device error
+ * flag and the kernel returns; the next nh_sync returns NH_ERR_TIMEOUT and clears
+ * the flag, and the context stays usable.  Errors: NH_ERR_ARG (kind). */
+nh_status nh_debug_wait_timeout(nh_ctx ctx, int kind);
 /* Number of kernels this context has launched since creation. */
 int64_t nh_launch_count(nh_ctx ctx);
 

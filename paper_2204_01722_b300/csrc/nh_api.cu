@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "nh_internal.cuh"
+#include "nh_krylov.cuh"
 
 // ---------------------------------------------------------------------------
 // errors
@@ -111,6 +112,23 @@ extern "C" nh_status nh_destroy(nh_ctx c) {
   cudaFreeHost(c->red_host);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_debug_wait_timeout(nh_ctx c, int kind) {
+  if (!c || (kind != 0 && kind != 1)) return NH_ERR_ARG;
+  NH_CUDA(c, cudaSetDevice(c->device));
+  if (kind == 0) {
+    NH_CUDA(c, nh_launch_wait_timeout_mbar(c->stream, c->dev_err));
+  } else {
+    unsigned* bar = nullptr;
+    NH_CUDA(c, cudaMalloc(&bar, 2 * sizeof(unsigned)));
+    cudaError_t e = ks_wait_timeout_grid(c->stream, bar, c->dev_err);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(bar);
+    NH_CUDA(c, e);
+  }
+  c->launches++;
   return NH_OK;
 }
 

@@ -193,6 +193,7 @@ cudaError_t nh_launch_f64_to_f32(int64_t n, const double* x, float* y, cudaStrea
 cudaError_t nh_launch_setup_pts(int PF, int QC, int layout, cudaStream_t s, int64_t ne, const int* emap,
                                 const double* coords, const double* u, const double* lam, const double* mu, double* qd,
                                 int64_t qstride, unsigned long long* minj);
+cudaError_t nh_launch_wait_timeout_mbar(cudaStream_t s, int* err);
 cudaError_t nh_launch_pack_emap(cudaStream_t s, int64_t n, const int* emap, const uint8_t* bc, unsigned* out);
 cudaError_t nh_launch_f64_to_ff(int64_t n, const double* x, float* y2, cudaStream_t s);
 // FP64 SoA quadrature data [S][ne Q^3] -> blocked FP32 [batch][S][EPB][Q^3]

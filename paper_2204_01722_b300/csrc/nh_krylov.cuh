@@ -57,6 +57,8 @@ struct KsPcg {
   int* err;
 };
 int ks_pcg_max_blocks();
+// failure-detection test: a cooperative launch whose grid barrier one block skips
+cudaError_t ks_wait_timeout_grid(cudaStream_t st, unsigned* bar, int* err);
 
 // Geometric multigrid on the Q1 vertex lattice (nh_hmg.cu): coarse Dirichlet bits
 // (node 2I of the finer lattice), Galerkin coarse stencil P^T A P, damped Jacobi

@@ -95,6 +95,22 @@ __device__ __forceinline__ int sidx(int c, int k, int j, int i) {
   return ((c * Q + k) * Q + j) * Q + i;
 }
 
+#if NH_P_INST == 2
+// Failure-detection test: an mbarrier that no copy or thread ever completes; the
+// bounded wait gives up after `limit` polls and sets the error flag.
+__global__ void k_wait_timeout_mbar(int* err, unsigned limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  for (unsigned it = 0; !mbar_try_wait(&bar, 0); it++) {
+    if (it >= limit) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      break;
+    }
+  }
+}
+#endif
+
 using nhpw::pointwise;
 
 // Float-float pointwise stage as one out-of-line copy: inlined once per
@@ -1130,6 +1146,13 @@ cudaError_t diag_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
 }
 
 }  // namespace
+
+#if NH_P_INST == 2
+cudaError_t nh_launch_wait_timeout_mbar(cudaStream_t s, int* err) {
+  k_wait_timeout_mbar<<<1, 32, 0, s>>>(err, 1u << 12);
+  return cudaGetLastError();
+}
+#endif
 
 #define NH_CAT2(a, b) a##b
 #define NH_CAT(a, b) NH_CAT2(a, b)

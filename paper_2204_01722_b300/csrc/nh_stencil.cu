@@ -276,7 +276,7 @@ constexpr unsigned kGridSpin = 1u << 24;  // polls per grid barrier before givin
 // generation word; the last block to arrive resets the counter and advances the
 // generation.  A wait that outlives kGridSpin polls sets *err and returns false
 // (the caller leaves the kernel; the host sees NH_ERR_TIMEOUT).
-__device__ bool grid_sync_bounded(unsigned* count, unsigned* gen, int* err) {
+__device__ bool grid_sync_bounded(unsigned* count, unsigned* gen, int* err, unsigned limit = kGridSpin) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -291,7 +291,7 @@ __device__ bool grid_sync_bounded(unsigned* count, unsigned* gen, int* err) {
     } else {
       unsigned it = 0;
       while (*vgen == g) {
-        if (++it > kGridSpin) {
+        if (++it > limit) {
           atomicExch(err, 1);
           ok = 0;
           break;
@@ -446,7 +446,22 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg(KsPcg a) {
   }
 }
 
+// Failure-detection test: block 1 never reaches the barrier, so block 0's
+// bounded wait expires after `limit` polls and sets the error flag.
+__global__ void k_wait_timeout_grid(unsigned* bar, int* err, unsigned limit) {
+  if (blockIdx.x == 1) return;
+  grid_sync_bounded(bar, bar + 1, err, limit);
+}
+
 }  // namespace
+
+cudaError_t ks_wait_timeout_grid(cudaStream_t st, unsigned* bar, int* err) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  unsigned limit = 1u << 16;
+  void* params[] = {&bar, &err, &limit};
+  return cudaLaunchCooperativeKernel((const void*)k_wait_timeout_grid, dim3(2), dim3(32), params, 0, st);
+}
 
 int ks_pcg_max_blocks() {
   static int cached[64] = {0};

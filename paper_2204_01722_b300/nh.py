@@ -44,6 +44,7 @@ SIGNATURES = {
     "nh_op_destroy": (_st, [_vp]),
     "nh_op_info": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_i64)]),
     "nh_qdata_setup": (_st, [_vp, _vp, C.POINTER(C.c_double)]),
+    "nh_debug_wait_timeout": (_st, [_vp, C.c_int]),
     "nh_op_rediscretize": (_st, [_vp, _vp, C.POINTER(_vp)]),
     "nh_qdata_setup_rediscretized": (_st, [_vp, _vp, _vp, C.POINTER(C.c_double)]),
     "nh_residual": (_st, [_vp, _vp, _vp, _vp]),
@@ -167,6 +168,10 @@ def nh_last_error(ctx):
 
 def nh_sync(ctx):
     _check(lib.nh_sync(ctx), ctx)
+
+
+def nh_debug_wait_timeout(ctx, kind):
+    _check(lib.nh_debug_wait_timeout(ctx, int(kind)), ctx)
 
 
 def nh_launch_count(ctx):
