@@ -693,7 +693,10 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
   // each (j, k) row of the block is one contiguous run of
   // RN = EPB (P - 1) + 1 nodes: the rows are summed in shared memory (shared
   // element faces added once) and reduced into y by the bulk-copy engine.
-  constexpr int RN = EPB * (P - 1) + 1, RL = 3 * RN, RS = (RL + 6) / 4 * 4;
+  // Row pitch RS: a multiple of 4 floats (16-byte aligned bulk sources) with RS / 4
+  // odd, so that the rows of 8 consecutive lines start on distinct bank quads.
+  constexpr int RN = EPB * (P - 1) + 1, RL = 3 * RN, RS0 = (RL + 6) / 4 * 4;
+  constexpr int RS = (RS0 / 4) % 2 ? RS0 : RS0 + 4;
   static_assert(P * P * RS <= L::block_floats(EPB), "row buffer fits the work area");
   bool chain = false;
   unsigned first = 0;
