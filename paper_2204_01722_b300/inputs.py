@@ -14,6 +14,11 @@ seeded numpy generators.  Recipes:
 * ``inclusion_modulus``: per-element Young's modulus from seeded spheres
   (centres uniform in the box, radius U(rmin, rmax) elements) added until the
   element-centroid volume fraction reaches ``vf``; E = contrast inside, 1 outside.
+  With ``gap=None`` spheres may overlap (clusters form; at vf = 0.3 the stiff
+  phase is near percolation).  With ``gap=g`` the spheres are disjoint with at
+  least g elements between surfaces: radii are drawn up front, sorted
+  largest first, and each is placed at the first of up to 2000 uniform centre
+  draws that keeps the gap (``inclusion_spheres`` returns the centres and radii).
 """
 import numpy as np
 
@@ -105,19 +110,49 @@ def all_faces_mask(node_dims):
     return np.repeat(b, 3)
 
 
-def inclusion_modulus(nx, ny, nz, seed=0, vf=0.3, rmin=2.0, rmax=6.0, contrast=1e3):
-    rng = np.random.default_rng(seed)
+def _element_centroids(nx, ny, nz):
     cx = (np.arange(nx) + 0.5) / nx
     cy = (np.arange(ny) + 0.5) / ny
     cz = (np.arange(nz) + 0.5) / nz
     Z, Y, X = np.meshgrid(cz, cy, cx, indexing="ij")
-    C = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+
+def inclusion_spheres(nx, ny, nz, seed=0, vf=0.3, rmin=2.0, rmax=6.0, gap=None):
+    """Returns (centres [m, 3], radii [m], inside [ne] bool) in unit-box units."""
+    rng = np.random.default_rng(seed)
+    C = _element_centroids(nx, ny, nz)
     h = 1.0 / max(nx, ny, nz)
     inside = np.zeros(C.shape[0], dtype=bool)
-    for _ in range(100000):
+    cs, rs = [], []
+    if gap is None:
+        for _ in range(100000):
+            if inside.mean() >= vf:
+                break
+            c = rng.uniform(0.0, 1.0, size=3)
+            r = rng.uniform(rmin, rmax) * h
+            inside |= np.sum((C - c) ** 2, axis=1) <= r * r
+            cs.append(c)
+            rs.append(r)
+        return np.array(cs).reshape(-1, 3), np.array(rs), inside
+    radii, vol = [], 0.0
+    while vol < 2.0 * vf:
+        radii.append(rng.uniform(rmin, rmax) * h)
+        vol += 4.0 / 3.0 * np.pi * radii[-1] ** 3
+    for r in sorted(radii, reverse=True):
         if inside.mean() >= vf:
             break
-        c = rng.uniform(0.0, 1.0, size=3)
-        r = rng.uniform(rmin, rmax) * h
-        inside |= np.sum((C - c) ** 2, axis=1) <= r * r
+        for _ in range(2000):
+            c = rng.uniform(0.0, 1.0, size=3)
+            if cs and np.any(np.linalg.norm(np.array(cs) - c, axis=1) < np.array(rs) + r + gap * h):
+                continue
+            cs.append(c)
+            rs.append(r)
+            inside |= np.sum((C - c) ** 2, axis=1) <= r * r
+            break
+    return np.array(cs).reshape(-1, 3), np.array(rs), inside
+
+
+def inclusion_modulus(nx, ny, nz, seed=0, vf=0.3, rmin=2.0, rmax=6.0, contrast=1e3, gap=None):
+    _, _, inside = inclusion_spheres(nx, ny, nz, seed=seed, vf=vf, rmin=rmin, rmax=rmax, gap=gap)
     return np.where(inside, contrast, 1.0)
