@@ -156,6 +156,31 @@ class Case:
         self.nh.nh_space_destroy(self.space)
 
 
+class HexCase(Case):
+    """The same workload on the unstructured-mesh path (`nh_space_hex`): every
+    element's local frame a random cube rotation; ``shuffled`` also permutes the
+    vertex ids and the element order (no locality left in the element map)."""
+
+    def __init__(self, nh, torch, ctx, p, n, shuffled):
+        self.nh, self.ctx, self.p, self.n = nh, ctx, p, n
+        from paper_2204_01722_b300 import inputs
+        V = inputs.box_vertices(n, n, n, perturb=PERTURB, seed=SEED)
+        Vh, H = inputs.hex_mesh_from_box(n, n, n, V, seed=SEED, permute=shuffled)
+        self.space, self.nn, self.nd = nh.nh_space_hex(ctx, Vh, H, p, p + 1)
+        X = nh.nh_space_coords(ctx, self.space, self.nn)
+        m = np.zeros((self.nn, 3), dtype=bool)
+        m[X[:, 0] < 1e-12, :] = True
+        m[X[:, 0] > 1.0 - 1e-12, 0] = True
+        nh.nh_space_set_dirichlet(ctx, self.space, m.ravel())
+        self.op = nh.nh_op_create(ctx, self.space, NU, None, 1.0, 0)
+        u = inputs.smooth_field(X, AMP, seed=SEED + 1).ravel()
+        self.minJ = nh.nh_qdata_setup(ctx, self.op, torch.from_numpy(u).cuda())
+        self.du64 = torch.from_numpy(inputs.normal_vector(self.nd, seed=SEED + 2)).cuda()
+        self.du32 = self.du64.float()
+        self.y64 = torch.empty_like(self.du64)
+        self.y32 = torch.empty_like(self.du32)
+
+
 def time_applies(nh, torch, ctx, stream, case, prec, steps, warmup, barrier):
     du, y = case.vecs(prec)
     for _ in range(warmup):
@@ -269,7 +294,7 @@ def run_nh(args):
         minJ = case.minJ
         nd = case.nd
         case.close()
-        sweep = []
+        sweep, hexes = [], []
         if args.sweep and rank == 0:
             for sp_ in (2, 3, 4):
                 c = Case(nh, torch, ctx, sp_, DEFAULT_N[sp_])
@@ -287,6 +312,16 @@ def run_nh(args):
                                   "alu_frac": round(tfl / (FP64_PEAK_TFLOPS if pr == "f64" else FP32_PEAK_TFLOPS), 4)})
                     if pr == "f64x":  # ALU peak of float-float: FP32 pipe / ~15 instructions per FP64 op
                         sweep[-1]["alu_frac"] = None
+                c.close()
+            for shuffled in (False, True):
+                c = HexCase(nh, torch, ctx, 3, DEFAULT_N[3], shuffled)
+                for pr in ("f64", "f32"):
+                    kernel_ms(nh, ctx, c, pr, 5)
+                    k = kernel_ms(nh, ctx, c, pr, 20)
+                    hexes.append({"mesh": "unstructured path, rotated element frames" +
+                                          (", shuffled ids and elements" if shuffled else ", box element order"),
+                                  "p": 3, "n": c.n, "n_dof": c.nd, "prec": pr,
+                                  "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4)})
                 c.close()
         solve = run_solves(nh, torch, ctx, stream) if (args.solve and rank == 0) else None
         nh.nh_destroy(ctx)
@@ -306,6 +341,8 @@ def run_nh(args):
             out["cpu_baseline"] = oracle_baseline(p, n, args.cpu_seconds)
         if sweep:
             out["sweep"] = sweep
+        if hexes:
+            out["hex"] = hexes
         if solve:
             out["solve"] = solve
         print(json.dumps(out), flush=True)

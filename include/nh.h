@@ -107,6 +107,23 @@ int64_t nh_launch_count(nh_ctx ctx);
  * a second copy of E), NH_ERR_OOM. */
 nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const double* vertex_xyz,
                        int p, int q, nh_space* out, int64_t* n_nodes, int64_t* n_dof);
+/* Unstructured conforming hexahedral mesh with a trilinear geometry (Sec. II-B:
+ * the element restriction E of a general mesh; the paper's Schwarz-P and
+ * extruded meshes are of this kind).  xyz: HOST [nv][3] vertex coordinates;
+ * hex8: HOST [ne][8] vertex ids, vertex v of an element at the corner
+ * (v & 1, (v >> 1) & 1, v >> 2) of the reference cube (tensor order; VTK's
+ * hexahedron order 0 1 2 3 4 5 6 7 is 0 1 3 2 4 5 7 6 here).  p, q as for
+ * nh_space_box.  Node numbering: vertices, edge, face and element interiors
+ * identified by their global vertex ids (edges numbered from the smaller id,
+ * faces in a frame anchored at their smallest corner id), ids handed out in
+ * order of first touch over the elements.  Validates: ids in range and distinct
+ * per element, a positive Jacobian at every corner, no face shared by more than
+ * two elements, and equal coordinates for every shared node (conformity).
+ * Spaces of lower order on the same xyz/hex8 are the p-multigrid levels.
+ * Synchronises.  Errors: NH_ERR_ARG (with the reason in nh_last_error),
+ * NH_ERR_UNSUPPORTED (orders, or 2^29 nodes), NH_ERR_OOM. */
+nh_status nh_space_hex(nh_ctx ctx, int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8, int p, int q,
+                       nh_space* out, int64_t* n_nodes, int64_t* n_dof);
 /* Node coordinates, HOST out [n_nodes][3]. */
 nh_status nh_space_coords(nh_space s, double* xyz_host);
 /* Dirichlet DoFs: HOST array [n_dof], nonzero = constrained.  Copied; synchronises. */

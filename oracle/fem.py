@@ -81,6 +81,12 @@ class Space:
         vk, vj, vi = np.meshgrid([0, 1], [0, 1], [0, 1], indexing="ij")
         vi, vj, vk = vi.ravel(), vj.ravel(), vk.ravel()  # v = vi + 2 vj + 4 vk
         self.elem_verts = (ex[:, None] + vi) + (nx + 1) * ((ey[:, None] + vj) + (ny + 1) * (ez[:, None] + vk))
+        self._setup_basis()
+
+    def _setup_basis(self):
+        p, q = self.p, self.q
+        vk, vj, vi = np.meshgrid([0, 1], [0, 1], [0, 1], indexing="ij")
+        vi, vj, vk = vi.ravel(), vj.ravel(), vk.ravel()  # v = vi + 2 vj + 4 vk
         self._vsign = np.stack([2 * vi - 1, 2 * vj - 1, 2 * vk - 1], axis=1).astype(np.float64)  # [8, 3]
 
         B1, D1, xg, wg = basis.tabulate(p, q)
@@ -92,7 +98,7 @@ class Space:
         self.wq = kron3(wg[:, None], wg[:, None], wg[:, None]).ravel()  # [Q^3]
         qk, qj, qi = np.meshgrid(xg, xg, xg, indexing="ij")
         self.xi_q = np.stack([qi.ravel(), qj.ravel(), qk.ravel()], axis=1)  # [Q^3, 3]
-        self.xnodes, _ = basis.gauss_lobatto(P)
+        self.xnodes, _ = basis.gauss_lobatto(self.P)
 
     # -- trilinear geometry ---------------------------------------------------
     def trilinear(self, xi):
@@ -163,6 +169,54 @@ class Space:
         y = np.zeros((self.n_nodes, 3))
         np.add.at(y, self.elem_nodes.ravel(), ye.reshape(-1, 3))
         return y
+
+
+class HexSpace(Space):
+    """Continuous Q_p space on an unstructured conforming hexahedral mesh
+    (the element restriction E of a general mesh, Sec. II-B).
+
+    ``hex8[e, v]`` is the vertex at corner (v & 1, (v >> 1) & 1, v >> 2) of the
+    reference cube.  Global nodes are found by coordinates: every element's
+    trilinear image of the GLL lattice is computed and points that coincide
+    (within 1e-9 of the mesh extent) are one node, numbered in order of first
+    appearance.  This uses no mesh topology, so it checks a topological
+    numbering independently.
+    """
+
+    def __init__(self, vertices, hex8, p, q):
+        from scipy.spatial import cKDTree
+
+        self.nx = self.ny = self.nz = None
+        self.p, self.P, self.q = p, p + 1, q
+        self.vertices = np.asarray(vertices, dtype=np.float64).reshape(-1, 3)
+        self.elem_verts = np.asarray(hex8, dtype=np.int64).reshape(-1, 8)
+        self.ne = self.elem_verts.shape[0]
+        self._setup_basis()
+        k, j, i = np.meshgrid(self.xnodes, self.xnodes, self.xnodes, indexing="ij")
+        N, _ = self.trilinear(np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1))
+        Xe = np.einsum("mv,evi->emi", N, self.vertices[self.elem_verts]).reshape(-1, 3)
+        tol = 1e-9 * max(np.ptp(self.vertices, axis=0).max(), 1e-300)
+        parent = np.arange(Xe.shape[0])
+
+        def root(a):
+            while parent[a] != a:
+                parent[a] = parent[parent[a]]
+                a = parent[a]
+            return a
+
+        for a, b in cKDTree(Xe).query_pairs(tol):
+            ra, rb = root(a), root(b)
+            if ra != rb:
+                parent[max(ra, rb)] = min(ra, rb)
+        roots = np.array([root(a) for a in range(Xe.shape[0])])
+        uniq, first = np.unique(roots, return_index=True)
+        order = np.argsort(first)                       # number by first appearance
+        rank = np.empty(len(uniq), dtype=np.int64)
+        rank[order] = np.arange(len(uniq))
+        self.elem_nodes = rank[np.searchsorted(uniq, roots)].reshape(self.ne, -1)
+        self.n_nodes = len(uniq)
+        self.n_dof = 3 * self.n_nodes
+        self.node_dims = None
 
 
 def unit_cube_vertices(nx, ny, nz):

@@ -153,6 +153,8 @@ extern "C" int64_t nh_launch_count(nh_ctx c) { return c ? c->launches : -1; }
 // ---------------------------------------------------------------------------
 // spaces
 // ---------------------------------------------------------------------------
+static nh_status space_upload(nh_ctx ctx, nh_space s, const std::vector<int>& emap, const std::vector<double>& mult);
+
 extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const double* vxyz, int p, int q,
                                   nh_space* out, int64_t* n_nodes, int64_t* n_dof) {
   if (!ctx || !out) return NH_ERR_ARG;
@@ -218,6 +220,18 @@ extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const doub
               for (int d = 0; d < 3; d++) s->coords_host[3 * nid + d] = X[d];
             }
       }
+  nh_status st = space_upload(ctx, s, emap, mult);
+  if (st != NH_OK) return st;
+  *out = s;
+  if (n_nodes) *n_nodes = nn;
+  if (n_dof) *n_dof = 3 * nn;
+  return NH_OK;
+}
+
+// device copies of a space's element restriction, coordinates and inverse
+// multiplicities; frees the space on failure
+static nh_status space_upload(nh_ctx ctx, nh_space s, const std::vector<int>& emap, const std::vector<double>& mult) {
+  const int64_t nn = s->n_nodes;
   std::vector<double> im(nn);
   std::vector<float> imf(nn);
   for (int64_t n = 0; n < nn; n++) {
@@ -233,20 +247,62 @@ extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const doub
   if (e1 || e2 || e3 || e4 || e5 || e6) {
     cudaGetLastError();
     nh_space_destroy(s);
-    return nh_fail(ctx, NH_ERR_OOM, "nh_space_box: device allocation failed");
+    return nh_fail(ctx, NH_ERR_OOM, "space: device allocation failed");
   }
-  NH_CUDA(ctx, cudaMemcpy(s->emap, emap.data(), sizeof(int) * emap.size(), cudaMemcpyHostToDevice));
-  NH_CUDA(ctx, cudaMemcpy(s->coords, s->coords_host.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice));
-  NH_CUDA(ctx, cudaMemset(s->bc, 0, nn));
-  NH_CUDA(ctx, cudaMemcpy(s->inv_mult, im.data(), sizeof(double) * nn, cudaMemcpyHostToDevice));
-  NH_CUDA(ctx, cudaMemcpy(s->inv_mult_f, imf.data(), sizeof(float) * nn, cudaMemcpyHostToDevice));
-  NH_CUDA(ctx, cudaDeviceSynchronize());
-  NH_CUDA(ctx, nh_launch_pack_emap(ctx->stream, (int64_t)emap.size(), s->emap, s->bc, s->emapb));
-  NH_CUDA(ctx, cudaDeviceSynchronize());
+  cudaError_t e = cudaMemcpy(s->emap, emap.data(), sizeof(int) * emap.size(), cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(s->coords, s->coords_host.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemset(s->bc, 0, nn);
+  if (!e) e = cudaMemcpy(s->inv_mult, im.data(), sizeof(double) * nn, cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(s->inv_mult_f, imf.data(), sizeof(float) * nn, cudaMemcpyHostToDevice);
+  if (!e) e = cudaDeviceSynchronize();
+  if (!e) e = nh_launch_pack_emap(ctx->stream, (int64_t)emap.size(), s->emap, s->bc, s->emapb);
+  if (!e) e = cudaDeviceSynchronize();
+  if (e) {
+    nh_space_destroy(s);
+    return nh_cuda_check(ctx, e, "space upload");
+  }
+  return NH_OK;
+}
+
+extern "C" nh_status nh_space_hex(nh_ctx ctx, int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8, int p,
+                                  int q, nh_space* out, int64_t* n_nodes, int64_t* n_dof) {
+  if (!ctx || !out || !xyz || !hex8) return NH_ERR_ARG;
+  *out = nullptr;
+  if (nv < 8 || ne < 1 || ne > INT32_MAX / 8) return nh_fail(ctx, NH_ERR_ARG, "nh_space_hex: need nv >= 8 and ne >= 1");
+  if (p < 1 || p > 4 || q < p + 1 || q > NH_MAXQ)
+    return nh_fail(ctx, NH_ERR_UNSUPPORTED, "nh_space_hex: need 1 <= p <= 4 and p+1 <= q <= 6");
+  std::vector<int> emap;
+  std::vector<double> coords;
+  int64_t nn = 0;
+  const std::string msg = nh_hex_numbering(nv, xyz, ne, hex8, p, emap, coords, nn);
+  if (!msg.empty())
+    return nh_fail(ctx, msg.find("too large") != std::string::npos ? NH_ERR_UNSUPPORTED : NH_ERR_ARG,
+                   "nh_space_hex: " + msg);
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  nh_space s = new nh_space_s();
+  s->ctx = ctx;
+  s->hex = true;
+  s->p = p; s->q = q; s->P = p + 1; s->Q = q;
+  s->ne = ne; s->n_nodes = nn; s->n_dof = 3 * nn;
+  nh_tabulate(p, q, &s->tab);
+  s->verts_host.assign(xyz, xyz + 3 * (size_t)nv);
+  s->hex8_host.assign(hex8, hex8 + 8 * (size_t)ne);
+  s->coords_host = std::move(coords);
+  std::vector<double> mult((size_t)nn, 0.0);
+  for (int n : emap) mult[n] += 1.0;
+  s->emap_host = emap;
+  nh_status st = space_upload(ctx, s, emap, mult);
+  if (st != NH_OK) return st;
   *out = s;
   if (n_nodes) *n_nodes = nn;
   if (n_dof) *n_dof = 3 * nn;
   return NH_OK;
+}
+
+bool nh_same_mesh(nh_space a, nh_space b) {
+  if (a->hex != b->hex || a->ne != b->ne) return false;
+  if (a->hex) return a->hex8_host == b->hex8_host && a->verts_host == b->verts_host;
+  return a->nx == b->nx && a->ny == b->ny && a->nz == b->nz && a->verts_host == b->verts_host;
 }
 
 extern "C" nh_status nh_space_coords(nh_space s, double* xyz) {
@@ -329,8 +385,7 @@ extern "C" nh_status nh_op_level(nh_op fine, nh_space coarse, nh_op* out) {
   nh_op root = fine->parent ? fine->parent : fine;
   nh_space fs = root->space;
   nh_ctx ctx = fs->ctx;
-  if (coarse->nx != fs->nx || coarse->ny != fs->ny || coarse->nz != fs->nz || coarse->Q != fs->Q ||
-      coarse->p > fs->p)
+  if (!nh_same_mesh(coarse, fs) || coarse->Q != fs->Q || coarse->p > fs->p)
     return nh_fail(ctx, NH_ERR_ARG, "nh_op_level: coarse space must share the mesh and q, with p_c <= p_f");
   nh_op op = new nh_op_s();
   op->space = coarse;
@@ -348,7 +403,7 @@ extern "C" nh_status nh_op_rediscretize(nh_op fine, nh_space coarse, nh_op* out)
   nh_ctx ctx = fine->space->ctx;
   if (fine->parent) return nh_fail(ctx, NH_ERR_ARG, "nh_op_rediscretize: needs the fine operator");
   nh_space fs = fine->space;
-  if (coarse->nx != fs->nx || coarse->ny != fs->ny || coarse->nz != fs->nz || coarse->p > fs->p)
+  if (!nh_same_mesh(coarse, fs) || coarse->p > fs->p)
     return nh_fail(ctx, NH_ERR_ARG, "nh_op_rediscretize: coarse space must share the mesh, with p_c <= p_f");
   NH_CUDA(ctx, cudaSetDevice(ctx->device));
   nh_op op = new nh_op_s();
@@ -375,7 +430,7 @@ extern "C" nh_status nh_qdata_setup_rediscretized(nh_op op, nh_op fine, const do
   nh_ctx ctx = op->space->ctx;
   nh_space fs = fine->space, cs = op->space;
   if (op->parent || fine->parent) return nh_fail(ctx, NH_ERR_ARG, "nh_qdata_setup_rediscretized: needs two root operators");
-  if (cs->nx != fs->nx || cs->ny != fs->ny || cs->nz != fs->nz || cs->p > fs->p || op->layout != fine->layout)
+  if (!nh_same_mesh(cs, fs) || cs->p > fs->p || op->layout != fine->layout)
     return nh_fail(ctx, NH_ERR_ARG, "nh_qdata_setup_rediscretized: operators must share the mesh and layout, p_c <= p_f");
   NH_CUDA(ctx, cudaSetDevice(ctx->device));
   const int64_t nq = cs->ne * (int64_t)cs->Q * cs->Q * cs->Q;
@@ -674,6 +729,15 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
     NH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
     NH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
   }
+  if (sp->hex) {  // unstructured mesh: no layer ranges; one upload, one apply, one download
+    NH_CUDA(ctx, cudaMemcpyAsync(op->hbuf_in, du_h, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    NH_CUDA(ctx, cudaMemsetAsync(op->hbuf_out, 0, bytes, ctx->stream));
+    nh_status st = launch_apply_range(op, prec, op->hbuf_in, op->hbuf_out, 0, sp->ne, ctx->stream);
+    if (st != NH_OK) return st;
+    NH_CUDA(ctx, cudaMemcpyAsync(y_h, op->hbuf_out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return NH_OK;
+  }
   // chunks of z-layers; with FP32 each chunk starts on a kernel batch of EPB elements
   const int64_t nxy = (int64_t)sp->nx * sp->ny, lay = (int64_t)sp->Nx * sp->Ny * 3;  // elements, DoF per layer
   int64_t step = 1;
@@ -754,7 +818,7 @@ extern "C" nh_status nh_jacobian_diagonal(nh_op op, nh_prec prec, void* diag) {
 nh_status nh_transfer_internal(nh_space c, nh_space f, nh_prec prec, int dir, const void* in, void* out) {
   if (!c || !f || !in || !out) return NH_ERR_ARG;
   nh_ctx ctx = f->ctx;
-  if (c->nx != f->nx || c->ny != f->ny || c->nz != f->nz || c->p >= f->p)
+  if (!nh_same_mesh(c, f) || c->p >= f->p)
     return nh_fail(ctx, NH_ERR_ARG, "nh_prolong/nh_restrict: spaces must share the mesh with p_c < p_f");
   if (prec != NH_F64 && prec != NH_F32) return nh_fail(ctx, NH_ERR_ARG, "transfer: bad precision");
   if (in == (const void*)out) return nh_fail(ctx, NH_ERR_ARG, "transfer: in and out must not alias");

@@ -42,6 +42,12 @@ struct Tab1D {
 // 1-D rules and Lagrange tabulation (nh_basis.cu)
 void nh_gauss(int q, double* x, double* w);
 void nh_lobatto(int n, double* x);
+// Q_p element restriction and node coordinates of a conforming hexahedral mesh;
+// returns an error message, empty on success (nh_mesh.cu).
+std::string nh_hex_numbering(int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8, int p,
+                             std::vector<int>& emap, std::vector<double>& coords, int64_t& n_nodes);
+// true when two spaces discretise the same mesh (box dimensions and vertices, or hex connectivity)
+bool nh_same_mesh(nh_space a, nh_space b);
 void nh_lagrange(int n, const double* nodes, int m, const double* pts, double* val, double* der);
 void nh_tabulate(int p, int q, Tab1D* t);
 
@@ -93,7 +99,10 @@ struct nh_space_s {
   int* emap = nullptr;            // [ne][P^3] element restriction
   double* coords = nullptr;       // [n_nodes][3] device
   std::vector<double> coords_host;
-  std::vector<double> verts_host; // [(nx+1)(ny+1)(nz+1)][3], empty for the unit cube
+  std::vector<double> verts_host; // [(nx+1)(ny+1)(nz+1)][3], empty for the unit cube; hex: [nv][3]
+  bool hex = false;               // built by nh_space_hex (unstructured); nx = ny = nz = 0
+  std::vector<int64_t> hex8_host; // hex: [ne][8] vertex ids
+  std::vector<int> emap_host;     // hex: [ne][P^3] copy of emap (coarse Dirichlet masks)
   uint8_t* bc = nullptr;          // [n_nodes] bit c set = component c constrained (device)
   unsigned* emapb = nullptr;      // [ne][P^3] node id | constrained bits << 29 (FP32 apply)
   double* inv_mult = nullptr;     // [n_nodes] 1 / multiplicity

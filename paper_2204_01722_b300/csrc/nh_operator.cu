@@ -1078,7 +1078,7 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   k_jacobian_apply_f32l<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
       A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift,
-      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, ((uintptr_t)A.out & 15) == 0 && A.nx % EPB == 0 ? 1 : 0, A.err);
+      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, ((uintptr_t)A.out & 15) == 0 && A.nx > 0 && A.nx % EPB == 0 ? 1 : 0, A.err);
   return cudaGetLastError();
 }
 

@@ -420,9 +420,39 @@ nh_status vcycle_t(nh_mg mg, int lv) {
 
 // the coarse Dirichlet mask by faces: a face component is constrained on the
 // coarse space if it is constrained at every fine node of that face
+// Unstructured mesh: a coarse node lies on one entity of an element (vertex, or the
+// interior of an edge, face or the element); it is constrained in component c
+// when every fine node on the same entity of that element is.  For masks made of
+// whole boundary faces this is the box rule above, entity by entity.
+nh_status coarse_mask_hex(nh_space f, nh_space c, const std::vector<uint8_t>& fb, std::vector<uint8_t>& out) {
+  const int pf = f->p, pc = c->p, Pf = pf + 1, Pc = pc + 1;
+  out.assign((size_t)c->n_dof, 0);
+  for (int64_t e = 0; e < c->ne; e++)
+    for (int k = 0; k < Pc; k++)
+      for (int j = 0; j < Pc; j++)
+        for (int i = 0; i < Pc; i++) {
+          const int L[3] = {i, j, k};
+          int lo[3], hi[3];  // fine lattice range of the same entity
+          for (int d = 0; d < 3; d++) {
+            if (L[d] == 0) lo[d] = hi[d] = 0;
+            else if (L[d] == pc) lo[d] = hi[d] = pf;
+            else { lo[d] = 1; hi[d] = pf - 1; }
+          }
+          unsigned m = 7u;
+          for (int kk = lo[2]; kk <= hi[2]; kk++)
+            for (int jj = lo[1]; jj <= hi[1]; jj++)
+              for (int ii = lo[0]; ii <= hi[0]; ii++)
+                m &= fb[f->emap_host[(size_t)e * Pf * Pf * Pf + (kk * Pf + jj) * Pf + ii]];
+          const int64_t n = c->emap_host[(size_t)e * Pc * Pc * Pc + (k * Pc + j) * Pc + i];
+          for (int cc = 0; cc < 3; cc++) out[3 * n + cc] = (m >> cc) & 1u;
+        }
+  return NH_OK;
+}
+
 nh_status coarse_mask(nh_mg mg, nh_space f, nh_space c, std::vector<uint8_t>& out) {
   std::vector<uint8_t> fb((size_t)f->n_nodes);
   CK(cudaMemcpy(fb.data(), f->bc, f->n_nodes, cudaMemcpyDeviceToHost));
+  if (f->hex) return coarse_mask_hex(f, c, fb, out);
   const int dims_f[3] = {f->Nx, f->Ny, f->Nz}, dims_c[3] = {c->Nx, c->Ny, c->Nz};
   unsigned face[6];  // (axis, side) -> component bits constrained everywhere on that face
   for (int ax = 0; ax < 3; ax++)
@@ -481,7 +511,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->lanczos_iters = 10;
   o->coarse_rtol = 1e-3;
   o->coarse_maxit = 2000;
-  o->coarse_assembled = 1;
+  o->coarse_assembled = fine->space->hex ? 0 : 1;  // the assembled Q1 stencil needs the box lattice
   o->mixed = 0;
   o->seed = 12345;
   o->load_steps = 1;
@@ -570,6 +600,12 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
   if (o.nonlinear != 0 && o.nonlinear != 1) return bad("nh_mg_create: nonlinear must be 0 (Newton) or 1 (L-BFGS)");
   if (o.nonlinear == 1 && (o.lbfgs_m < 1 || o.lbfgs_m > 32)) return bad("nh_mg_create: need 1 <= lbfgs_m <= 32");
   if (o.coarse_solver != 0 && o.coarse_solver != 1) return bad("nh_mg_create: coarse_solver must be 0 or 1");
+  if (fs->hex && (o.coarse_assembled || o.coarse_solver)) {
+    delete mg;
+    return nh_fail(fine->space->ctx, NH_ERR_UNSUPPORTED,
+                   "nh_mg_create: the assembled Q1 stencil and the geometric coarse multigrid need a box mesh "
+                   "(set coarse_assembled = 0 and coarse_solver = 0 on nh_space_hex meshes)");
+  }
   mg->p64 = o.fp64_kind ? NH_F64X : NH_F64;
   cudaSetDevice(mg->ctx->device);
   nh_status s;
@@ -584,8 +620,12 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
       const bool assembled = (i == o.n_levels - 1) && l.p == 1 && o.coarse_assembled;
       l.redisc = o.coarse_rediscretize && !assembled;
       int64_t nn, nd;
-      s = nh_space_box(mg->ctx, fs->nx, fs->ny, fs->nz, fs->verts_host.empty() ? nullptr : fs->verts_host.data(), l.p,
-                       l.redisc ? l.p + 1 : fs->q, &l.space, &nn, &nd);
+      if (fs->hex)
+        s = nh_space_hex(mg->ctx, (int64_t)fs->verts_host.size() / 3, fs->verts_host.data(), fs->ne,
+                         fs->hex8_host.data(), l.p, l.redisc ? l.p + 1 : fs->q, &l.space, &nn, &nd);
+      else
+        s = nh_space_box(mg->ctx, fs->nx, fs->ny, fs->nz, fs->verts_host.empty() ? nullptr : fs->verts_host.data(),
+                         l.p, l.redisc ? l.p + 1 : fs->q, &l.space, &nn, &nd);
       if (s != NH_OK) { nh_mg_destroy(mg); return s; }
       l.own = true;
       std::vector<uint8_t> m;
@@ -1604,6 +1644,8 @@ extern "C" nh_status nh_mg_set_learned(nh_mg mg, nh_net net) {
     mg->net = nullptr;
     return NH_OK;
   }
+  if (mg->L[0].space->hex)
+    return nh_fail(mg->ctx, NH_ERR_UNSUPPORTED, "nh_mg_set_learned: the network runs on the box mesh's Q1 grid");
   CK(cudaSetDevice(mg->ctx->device));
   ST(learned_buffers(mg));
   if (nh_net_grid(net) != (int)mg->L.back().space->Nx)
@@ -1616,6 +1658,8 @@ extern "C" nh_status nh_mg_collect(nh_mg mg, const double* b, int max_pairs, flo
                                    int* n_pairs) {
   if (!mg || !b || !feats || !targets || !n_pairs || max_pairs < 1) return NH_ERR_ARG;
   if (!mg->setup_done) return nh_fail(mg->ctx, NH_ERR_STATE, "nh_mg_collect: call nh_mg_setup first");
+  if (mg->L[0].space->hex)
+    return nh_fail(mg->ctx, NH_ERR_UNSUPPORTED, "nh_mg_collect: pairs live on the box mesh's Q1 grid");
   CK(cudaSetDevice(mg->ctx->device));
   ST(learned_buffers(mg));
   nh_net keep = mg->net;

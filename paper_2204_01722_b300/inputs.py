@@ -11,6 +11,9 @@ seeded numpy generators.  Recipes:
 * ``normal_vector``: N(0, 1) entries.
 * ``uniaxial_mask`` / ``uniaxial_bc``: x = 0 face clamped (all components),
   x = 1 face has its x-component prescribed to -delta, the rest free.
+* ``hex_mesh_from_box``: the box mesh as vertex/connectivity arrays, with each
+  element's local frame a random cube rotation, shuffled vertex ids and element
+  order, and optionally a subset of the elements (an unstructured mesh).
 * ``inclusion_modulus``: per-element Young's modulus from seeded spheres
   (centres uniform in the box, radius U(rmin, rmax) elements) added until the
   element-centroid volume fraction reaches ``vf``; E = contrast inside, 1 outside.
@@ -108,6 +111,57 @@ def all_faces_mask(node_dims):
     I, J, K = lattice_index(node_dims)
     b = (I == 0) | (I == Nx - 1) | (J == 0) | (J == Ny - 1) | (K == 0) | (K == Nz - 1)
     return np.repeat(b, 3)
+
+
+def _proper_rotations():
+    """The 24 rotations of the reference cube as (axis permutation, flips) with determinant +1."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(3)):
+        sgn = np.linalg.det(np.eye(3)[list(perm)])
+        for flips in itertools.product((0, 1), repeat=3):
+            if sgn * (-1) ** sum(flips) > 0:
+                out.append((perm, flips))
+    return out
+
+
+def hex_mesh_from_box(nx, ny, nz, vertices=None, seed=0, reorient=True, permute=True, keep=None):
+    """The box mesh as an unstructured hexahedral mesh: (vertices [nv, 3], hex8 [ne, 8]).
+
+    hex8 rows are in tensor corner order (corner v at (v & 1, (v >> 1) & 1, v >> 2)).
+    ``reorient``: each element's local frame is a random one of the 24 cube
+    rotations, so shared edges and faces are seen in every relative orientation;
+    ``permute``: vertex ids and element order are shuffled; ``keep`` (bool [ne],
+    lexicographic box order): elements to keep, e.g. an L-shaped subset.
+    """
+    rng = np.random.default_rng(seed)
+    V = box_vertices(nx, ny, nz) if vertices is None else np.asarray(vertices, dtype=np.float64).reshape(-1, 3)
+    ez, ey, ex = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ex, ey, ez = ex.ravel(), ey.ravel(), ez.ravel()
+    corners = [(v & 1, (v >> 1) & 1, v >> 2) for v in range(8)]
+    H = np.stack([(ex + c[0]) + (nx + 1) * ((ey + c[1]) + (ny + 1) * (ez + c[2])) for c in corners], axis=1)
+    if keep is not None:
+        H = H[np.asarray(keep, dtype=bool)]
+    if reorient:
+        table = []
+        for perm, flips in _proper_rotations():
+            row = []
+            for cn in corners:                 # new local corner cn <- old corner c
+                c = [0, 0, 0]
+                for d in range(3):
+                    c[perm[d]] = cn[d] ^ flips[d]
+                row.append(c[0] + 2 * c[1] + 4 * c[2])
+            table.append(row)
+        table = np.array(table)
+        pick = rng.integers(len(table), size=H.shape[0])
+        H = np.take_along_axis(H, table[pick], axis=1)
+    if permute:
+        pv = rng.permutation(V.shape[0])     # old vertex i -> new id pv[i]
+        Vn = np.empty_like(V)
+        Vn[pv] = V
+        V, H = Vn, pv[H]
+        H = H[rng.permutation(H.shape[0])]
+    return V, H
 
 
 def _element_centroids(nx, ny, nz):

@@ -36,6 +36,8 @@ SIGNATURES = {
     "nh_launch_count": (_i64, [_vp]),
     "nh_space_box": (_st, [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(_vp),
                            C.POINTER(_i64), C.POINTER(_i64)]),
+    "nh_space_hex": (_st, [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int, C.c_int, C.POINTER(_vp),
+                           C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "nh_space_coords": (_st, [_vp, _vp]),
     "nh_space_set_dirichlet": (_st, [_vp, _vp]),
     "nh_space_destroy": (_st, [_vp]),
@@ -184,6 +186,18 @@ def nh_space_box(ctx, nx, ny, nz, vertices, p, q):
     nn, nd = _i64(), _i64()
     V = None if vertices is None else np.ascontiguousarray(vertices, dtype=np.float64)
     _check(lib.nh_space_box(ctx, nx, ny, nz, _ptr(V), p, q, C.byref(h), C.byref(nn), C.byref(nd)), ctx)
+    return h.value, nn.value, nd.value
+
+
+def nh_space_hex(ctx, vertices, hex8, p, q):
+    """Unstructured hexahedral mesh; vertices [nv, 3], hex8 [ne, 8] in tensor
+    corner order.  Returns (space, n_nodes, n_dof)."""
+    h = _vp()
+    nn, nd = _i64(), _i64()
+    V = np.ascontiguousarray(vertices, dtype=np.float64).reshape(-1, 3)
+    H = np.ascontiguousarray(hex8, dtype=np.int64).reshape(-1, 8)
+    _check(lib.nh_space_hex(ctx, V.shape[0], _ptr(V), H.shape[0], _ptr(H), p, q, C.byref(h), C.byref(nn),
+                            C.byref(nd)), ctx)
     return h.value, nn.value, nd.value
 
 
