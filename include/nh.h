@@ -195,6 +195,23 @@ nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* du_host, vo
  * diag[a,c] = sum_e sum_q sum_{d,d'} B_xi,d[q,a] D[q; c,d; c,d'] B_xi,d'[q,a];
  * 1 on constrained DoFs.  Device out [n_dof] of prec type. */
 nh_status nh_jacobian_diagonal(nh_op op, nh_prec prec, void* diag);
+/* Assembled operator on a Q1 (p = 1) space as 3x3 block rows (Sec. IV: the
+ * split-phase COO assembly that hands the coarse level to a sparse solver).
+ * Symbolic phase on the host: COO entry (e, a, b) couples the element's nodes a
+ * (row) and b (column); rows bucketed, columns sorted and made unique, every
+ * entry listed under its block slot.  Numeric phase on the device: one block of
+ * 64 threads per element computes its 8 x 8 blocks sum_q G_a^T D_q G_b from the
+ * operator's quadrature data (a coarse level: the fine data at the fine points,
+ * exact Galerkin), then one thread per slot entry sums the slot's COO entries
+ * in a fixed order (no atomics, reproducible).  Call with rowptr = NULL to get
+ * the block count in *nnzb; then with HOST arrays rowptr [n_nodes + 1] (int64),
+ * col [nnzb] (node ids, sorted per row) and val [nnzb][3][3] (row-major block,
+ * row component first).  Dirichlet convention applied: constrained rows are
+ * identity rows, constrained columns zero.  The p-multigrid uses the same
+ * assembly (kept on the device) for the Q1 level of nh_space_hex meshes.
+ * Synchronises.  Errors: NH_ERR_UNSUPPORTED (p != 1), NH_ERR_STATE (no
+ * quadrature data), NH_ERR_ARG, NH_ERR_OOM. */
+nh_status nh_op_assemble_q1(nh_op op, int64_t* nnzb, int64_t* rowptr, int* col, double* val);
 
 /* ---- p-multigrid transfer (Eq. mg_prolong) ----------------------------- */
 

@@ -812,6 +812,64 @@ extern "C" nh_status nh_jacobian_diagonal(nh_op op, nh_prec prec, void* diag) {
   return NH_OK;
 }
 
+// Assembled Q1 operator as 3x3 block rows (split-phase COO assembly of the
+// element matrices B^T D B at the operator's quadrature points).
+extern "C" nh_status nh_op_assemble_q1(nh_op op, int64_t* nnzb, int64_t* rowptr, int* col, double* val) {
+  if (!op || !nnzb) return NH_ERR_ARG;
+  nh_ctx ctx = op->space->ctx;
+  nh_op root = op->parent ? op->parent : op;
+  nh_space sp = op->space;
+  if (sp->p != 1) return nh_fail(ctx, NH_ERR_UNSUPPORTED, "nh_op_assemble_q1: needs an operator on a p = 1 space");
+  if (!root->have_qd) return nh_fail(ctx, NH_ERR_STATE, "nh_op_assemble_q1: call nh_qdata_setup first");
+  if (sp->Q != root->space->Q) return nh_fail(ctx, NH_ERR_ARG, "nh_op_assemble_q1: quadrature rule mismatch");
+  NH_CUDA(ctx, cudaSetDevice(ctx->device));
+  NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<int> emap((size_t)sp->ne * 8);
+  NH_CUDA(ctx, cudaMemcpy(emap.data(), sp->emap, sizeof(int) * emap.size(), cudaMemcpyDeviceToHost));
+  std::vector<int64_t> rp, js, pm;
+  std::vector<int> cl;
+  ks_coo_symbolic(sp->ne, sp->n_nodes, emap.data(), rp, cl, js, pm);
+  *nnzb = (int64_t)cl.size();
+  if (!rowptr || !col || !val) return NH_OK;  // size query
+  int64_t *d_js = nullptr, *d_pm = nullptr;
+  double *d_coo = nullptr, *d_val = nullptr;
+  auto release = [&]() {
+    cudaFree(d_js);
+    cudaFree(d_pm);
+    cudaFree(d_coo);
+    cudaFree(d_val);
+  };
+  cudaError_t e = cudaMalloc(&d_js, sizeof(int64_t) * js.size());
+  if (!e) e = cudaMalloc(&d_pm, sizeof(int64_t) * pm.size());
+  if (!e) e = cudaMalloc(&d_coo, sizeof(double) * 9 * pm.size());
+  if (!e) e = cudaMalloc(&d_val, sizeof(double) * 9 * cl.size());
+  if (!e) e = cudaMemcpy(d_js, js.data(), sizeof(int64_t) * js.size(), cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(d_pm, pm.data(), sizeof(int64_t) * pm.size(), cudaMemcpyHostToDevice);
+  const int64_t Q3 = (int64_t)sp->Q * sp->Q * sp->Q;
+  if (!e) e = ks_element_blocks_q1(sp->Q, ctx->stream, sp->ne, root->qd, root->space->ne * Q3, root->layout, &sp->tab,
+                                   d_coo);
+  if (!e) e = ks_coo_sum(ctx->stream, (int64_t)cl.size(), d_js, d_pm, d_coo, d_val);
+  if (!e) e = cudaMemcpyAsync(val, d_val, sizeof(double) * 9 * cl.size(), cudaMemcpyDeviceToHost, ctx->stream);
+  if (!e) e = cudaStreamSynchronize(ctx->stream);
+  std::vector<uint8_t> bc((size_t)sp->n_nodes);
+  if (!e) e = cudaMemcpy(bc.data(), sp->bc, sp->n_nodes, cudaMemcpyDeviceToHost);
+  release();
+  if (e) return nh_cuda_check(ctx, e, "nh_op_assemble_q1");
+  ctx->launches += 2;
+  // Dirichlet convention: constrained rows are identity rows, constrained columns dropped
+  for (int64_t n = 0; n < sp->n_nodes; n++)
+    for (int64_t s = rp[n]; s < rp[n + 1]; s++)
+      for (int c = 0; c < 3; c++)
+        for (int c2 = 0; c2 < 3; c2++) {
+          double& v = val[s * 9 + 3 * c + c2];
+          if ((bc[n] >> c) & 1u) v = (cl[s] == n && c == c2) ? 1.0 : 0.0;
+          else if ((bc[cl[s]] >> c2) & 1u) v = 0.0;
+        }
+  memcpy(rowptr, rp.data(), sizeof(int64_t) * rp.size());
+  memcpy(col, cl.data(), sizeof(int) * cl.size());
+  return NH_OK;
+}
+
 // ---------------------------------------------------------------------------
 // transfer
 // ---------------------------------------------------------------------------

@@ -35,6 +35,18 @@ cudaError_t ks_assemble_q1(int Q, cudaStream_t st, int64_t ne, int nx, int ny, i
 cudaError_t ks_apply(cudaStream_t st, int Nx, int Ny, int Nz, const uint8_t* bc, const double* A, const double* x,
                      double* y);
 cudaError_t ks_diag(cudaStream_t st, int64_t nn, const uint8_t* bc, const double* A, double* d);
+// general meshes: element 3x3 blocks of the Q1 operator at the fine points into
+// COO slots [ne][8][8][9]; symbolic phase; slot sums; block-row apply and diagonal
+cudaError_t ks_element_blocks_q1(int Q, cudaStream_t st, int64_t ne, const double* qd, int64_t qstride, int layout,
+                                 const Tab1D* tab, double* coo);
+void ks_coo_symbolic(int64_t ne, int64_t nn, const int* emap, std::vector<int64_t>& rowptr, std::vector<int>& col,
+                     std::vector<int64_t>& jstart, std::vector<int64_t>& perm);
+cudaError_t ks_coo_sum(cudaStream_t st, int64_t nnzb, const int64_t* jstart, const int64_t* perm, const double* coo,
+                       double* val);
+cudaError_t ks_bsr_apply(cudaStream_t st, int64_t nn, const int64_t* rowptr, const int* col, const double* val,
+                         const uint8_t* bc, const double* x, double* y);
+cudaError_t ks_bsr_diag(cudaStream_t st, int64_t nn, const int64_t* rowptr, const int* col, const double* val,
+                        const uint8_t* bc, double* d);
 
 // Jacobi-preconditioned CG on the assembled Q1 stencil in one cooperative
 // launch (all blocks co-resident, bounded grid barriers, convergence tested on

@@ -56,6 +56,12 @@ struct Level {
   bool stencil = false;
   bool redisc = false;     // rediscretised: own Gauss rule and quadrature data from the fine state
   double* A = nullptr;     // [27][9][nn]
+  // assembled Q1 level of an unstructured mesh: 3x3 block rows (split-phase COO assembly)
+  bool bsr = false;
+  int64_t nnzb = 0;
+  int64_t *rowptr = nullptr, *jstart = nullptr, *perm = nullptr;
+  int* col = nullptr;
+  double *coo = nullptr, *val = nullptr;
 };
 
 // one lattice of the geometric multigrid on the assembled Q1 level
@@ -148,6 +154,11 @@ nh_status level_apply(nh_mg mg, Level& l, nh_prec prec, const void* x, void* y) 
   if (l.stencil && prec == NH_F64) {
     CK(ks_apply(mg->ctx->stream, l.space->Nx, l.space->Ny, l.space->Nz, l.space->bc, l.A, (const double*)x,
                 (double*)y));
+    mg->ctx->launches++;
+    return NH_OK;
+  }
+  if (l.bsr && prec == NH_F64) {
+    CK(ks_bsr_apply(mg->ctx->stream, l.nn, l.rowptr, l.col, l.val, l.space->bc, (const double*)x, (double*)y));
     mg->ctx->launches++;
     return NH_OK;
   }
@@ -511,7 +522,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->lanczos_iters = 10;
   o->coarse_rtol = 1e-3;
   o->coarse_maxit = 2000;
-  o->coarse_assembled = fine->space->hex ? 0 : 1;  // the assembled Q1 stencil needs the box lattice
+  o->coarse_assembled = 1;
   o->mixed = 0;
   o->seed = 12345;
   o->load_steps = 1;
@@ -537,6 +548,8 @@ extern "C" nh_status nh_mg_destroy(nh_mg mg) {
   cudaStreamSynchronize(mg->ctx->stream);
   for (Level& l : mg->L) {
     for (void* p : {l.x, l.b, l.r, l.d, l.t, l.dinv, l.ct}) cudaFree(p);
+    for (void* p : {(void*)l.rowptr, (void*)l.col, (void*)l.jstart, (void*)l.perm, (void*)l.coo, (void*)l.val})
+      cudaFree(p);
     for (double* p : l.w) cudaFree(p);
     if (l.dinv64 != (double*)l.dinv) cudaFree(l.dinv64);
     cudaFree(l.A);
@@ -600,11 +613,11 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
   if (o.nonlinear != 0 && o.nonlinear != 1) return bad("nh_mg_create: nonlinear must be 0 (Newton) or 1 (L-BFGS)");
   if (o.nonlinear == 1 && (o.lbfgs_m < 1 || o.lbfgs_m > 32)) return bad("nh_mg_create: need 1 <= lbfgs_m <= 32");
   if (o.coarse_solver != 0 && o.coarse_solver != 1) return bad("nh_mg_create: coarse_solver must be 0 or 1");
-  if (fs->hex && (o.coarse_assembled || o.coarse_solver)) {
+  if (fs->hex && o.coarse_solver) {
     delete mg;
     return nh_fail(fine->space->ctx, NH_ERR_UNSUPPORTED,
-                   "nh_mg_create: the assembled Q1 stencil and the geometric coarse multigrid need a box mesh "
-                   "(set coarse_assembled = 0 and coarse_solver = 0 on nh_space_hex meshes)");
+                   "nh_mg_create: the geometric coarse multigrid needs a box mesh (coarse_solver = 0 on nh_space_hex "
+                   "meshes)");
   }
   mg->p64 = o.fp64_kind ? NH_F64X : NH_F64;
   cudaSetDevice(mg->ctx->device);
@@ -637,7 +650,32 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
     l.n = l.space->n_dof;
     l.nn = l.space->n_nodes;
     l.prec = (o.mixed && l.p > 1) ? NH_F32 : NH_F64;
-    l.stencil = (i == o.n_levels - 1) && l.p == 1 && o.coarse_assembled && o.n_levels > 1;
+    const bool asm_level = (i == o.n_levels - 1) && l.p == 1 && o.coarse_assembled && o.n_levels > 1;
+    l.stencil = asm_level && !fs->hex;
+    l.bsr = asm_level && fs->hex;
+    if (l.bsr) {  // symbolic phase on the host, once per hierarchy
+      std::vector<int64_t> rp, js, pm;
+      std::vector<int> cl;
+      ks_coo_symbolic(l.space->ne, l.nn, l.space->emap_host.data(), rp, cl, js, pm);
+      l.nnzb = (int64_t)cl.size();
+      if ((s = dalloc(mg, (void**)&l.rowptr, sizeof(int64_t) * rp.size())) != NH_OK ||
+          (s = dalloc(mg, (void**)&l.col, sizeof(int) * cl.size())) != NH_OK ||
+          (s = dalloc(mg, (void**)&l.jstart, sizeof(int64_t) * js.size())) != NH_OK ||
+          (s = dalloc(mg, (void**)&l.perm, sizeof(int64_t) * pm.size())) != NH_OK ||
+          (s = dalloc(mg, (void**)&l.coo, sizeof(double) * 9 * pm.size())) != NH_OK ||
+          (s = dalloc(mg, (void**)&l.val, sizeof(double) * 9 * cl.size())) != NH_OK) {
+        nh_mg_destroy(mg);
+        return s;
+      }
+      cudaError_t ce = cudaMemcpy(l.rowptr, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice);
+      if (!ce) ce = cudaMemcpy(l.col, cl.data(), sizeof(int) * cl.size(), cudaMemcpyHostToDevice);
+      if (!ce) ce = cudaMemcpy(l.jstart, js.data(), sizeof(int64_t) * js.size(), cudaMemcpyHostToDevice);
+      if (!ce) ce = cudaMemcpy(l.perm, pm.data(), sizeof(int64_t) * pm.size(), cudaMemcpyHostToDevice);
+      if (ce) {
+        nh_mg_destroy(mg);
+        return nh_cuda_check(fine->space->ctx, ce, "nh_mg_create: block-row pattern upload");
+      }
+    }
     const size_t wb = wsize(l.prec) * l.n;
     for (void** v : {&l.x, &l.b, &l.r, &l.d, &l.t, &l.dinv})
       if ((s = dalloc(mg, v, wb)) != NH_OK) { nh_mg_destroy(mg); return s; }
@@ -894,7 +932,15 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
   double t0 = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
   int lv = 0;
   for (Level& l : mg->L) {
-    if (l.stencil) {
+    if (l.bsr) {
+      const int Qf = root->space->Q;
+      const int64_t Q3 = (int64_t)Qf * Qf * Qf;
+      CK(ks_element_blocks_q1(Qf, st, l.space->ne, root->qd, root->space->ne * Q3, root->layout, &l.space->tab, l.coo));
+      CK(ks_coo_sum(st, l.nnzb, l.jstart, l.perm, l.coo, l.val));
+      CK(ks_bsr_diag(st, l.nn, l.rowptr, l.col, l.val, l.space->bc, l.dinv64));
+      mg->ctx->launches += 3;
+      ST(mark("coo", lv, t0));
+    } else if (l.stencil) {
       CK(cudaMemsetAsync(l.A, 0, sizeof(double) * 243 * l.nn, st));
       const int64_t Q3 = (int64_t)root->space->Q * root->space->Q * root->space->Q;
       CK(ks_assemble_q1(root->space->Q, st, l.space->ne, l.space->nx, l.space->ny, l.space->nz, l.space->bc, root->qd,

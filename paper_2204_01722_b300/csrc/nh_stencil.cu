@@ -9,6 +9,9 @@
 // stencil: for every node, one 3x3 block per lattice neighbour, stored
 // [27][9][n_nodes] so that one thread per node reads coalesced rows.
 // Valid for the structured box meshes of nh_space_box.
+#include <algorithm>
+#include <vector>
+
 #include "nh_krylov.cuh"
 #include "nh_pointwise.cuh"
 
@@ -26,7 +29,7 @@ struct Q1Tab {
 template <int Q, int LAYOUT>
 __global__ void __launch_bounds__(64)
     k_assemble(int64_t ne, int nx, int ny, const double* __restrict__ qd, int64_t qstride, const Q1Tab<Q> tb,
-               double* __restrict__ A, int64_t nn, int Nx, int Ny) {
+               double* __restrict__ A, int64_t nn, int Nx, int Ny, double* __restrict__ coo) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
   __shared__ double Dq[kQC][81];
   const int t = threadIdx.x;
@@ -71,6 +74,11 @@ __global__ void __launch_bounds__(64)
     __syncthreads();
   }
   // scatter into the stencil row of node a, neighbour offset b - a
+  if (coo) {  // general mesh: the block goes to its COO slot (e, a, b)
+#pragma unroll
+    for (int c = 0; c < 9; c++) coo[((e * 64) + a * 8 + b) * 9 + c] = K[c / 3][c % 3];
+    return;
+  }
   const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
   const int64_t na = (ex + ai) + Nx * ((ey + aj) + (int64_t)Ny * (ez + ak));
   const int s = (bi - ai + 1) + 3 * (bj - aj + 1) + 9 * (bk - ak + 1);
@@ -124,7 +132,7 @@ __global__ void k_diag(int64_t nn, const uint8_t* __restrict__ bc, const double*
 template <int Q>
 __global__ void __launch_bounds__(64)
     k_assemble_current(int64_t ne, int nx, int ny, const double* __restrict__ qd, int64_t qstride, const Q1Tab<Q> tb,
-                       double* __restrict__ A, int64_t nn, int Nx, int Ny) {
+                       double* __restrict__ A, int64_t nn, int Nx, int Ny, double* __restrict__ coo) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
   __shared__ double sa[kQC], sh[kQC];
   __shared__ double sx[kQC][8][3], sAg[kQC][8][3], sg[kQC][8][3];
@@ -192,6 +200,11 @@ __global__ void __launch_bounds__(64)
     }
     __syncthreads();
   }
+  if (coo) {  // general mesh: the block goes to its COO slot (e, a, b)
+#pragma unroll
+    for (int c = 0; c < 9; c++) coo[((e * 64) + a * 8 + b) * 9 + c] = K[c / 3][c % 3];
+    return;
+  }
   const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
   const int64_t na = (ex + ai) + Nx * ((ey + aj) + (int64_t)Ny * (ez + ak));
   const int s = (bi - ai + 1) + 3 * (bj - aj + 1) + 9 * (bk - ak + 1);
@@ -203,7 +216,7 @@ __global__ void __launch_bounds__(64)
 
 template <int Q>
 cudaError_t assemble_q(cudaStream_t st, int64_t ne, int nx, int ny, int nz, const double* qd, int64_t qstride,
-                       int layout, const Tab1D* tab, double* A) {
+                       int layout, const Tab1D* tab, double* A, double* coo = nullptr) {
   Q1Tab<Q> tb;
   for (int i = 0; i < Q; i++)
     for (int j = 0; j < 2; j++) {
@@ -214,9 +227,9 @@ cudaError_t assemble_q(cudaStream_t st, int64_t ne, int nx, int ny, int nz, cons
   const int64_t nn = (int64_t)Nx * Ny * (nz + 1);
   if (ne == 0) return cudaSuccess;
   if (layout == NH_LAYOUT_CURRENT)
-    k_assemble_current<Q><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny);
+    k_assemble_current<Q><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny, coo);
   else
-    k_assemble<Q, NH_LAYOUT_INITIAL><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny);
+    k_assemble<Q, NH_LAYOUT_INITIAL><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny, coo);
   return cudaGetLastError();
 }
 
@@ -237,7 +250,126 @@ __global__ void k_mask_cols(int Nx, int Ny, int Nz, const uint8_t* __restrict__ 
   }
 }
 
+// ---- general meshes: split-phase COO assembly into 3x3 block rows (BSR) --------
+// Numeric phase, second half: every block slot sums its COO entries, listed by
+// the symbolic phase in perm[jstart[s] .. jstart[s+1]) (fixed order: deterministic,
+// no atomics).
+__global__ void k_coo_sum(int64_t nnzb, const int64_t* __restrict__ jstart, const int64_t* __restrict__ perm,
+                          const double* __restrict__ coo, double* __restrict__ val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnzb * 9) return;
+  const int64_t s = i / 9;
+  const int c = (int)(i - s * 9);
+  double v = 0.0;
+  for (int64_t m = jstart[s]; m < jstart[s + 1]; m++) v += coo[perm[m] * 9 + c];
+  val[i] = v;
+}
+
+// y = M A M x + (I - M) x on the block rows, one thread per node
+__global__ void __launch_bounds__(256)
+    k_bsr_apply(int64_t nn, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                const double* __restrict__ val, const uint8_t* __restrict__ bc, const double* __restrict__ x,
+                double* __restrict__ y) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  double acc[3] = {0, 0, 0};
+  for (int64_t s = rowptr[n]; s < rowptr[n + 1]; s++) {
+    const int64_t m = col[s];
+    const unsigned mb = bc[m];
+    const double x0 = (mb & 1u) ? 0.0 : x[3 * m], x1 = (mb & 2u) ? 0.0 : x[3 * m + 1],
+                 x2 = (mb & 4u) ? 0.0 : x[3 * m + 2];
+    const double* v = val + s * 9;
+    acc[0] += v[0] * x0 + v[1] * x1 + v[2] * x2;
+    acc[1] += v[3] * x0 + v[4] * x1 + v[5] * x2;
+    acc[2] += v[6] * x0 + v[7] * x1 + v[8] * x2;
+  }
+  const unsigned mb = bc[n];
+  for (int c = 0; c < 3; c++) y[3 * n + c] = ((mb >> c) & 1u) ? x[3 * n + c] : acc[c];
+}
+
+__global__ void k_bsr_diag(int64_t nn, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ val, const uint8_t* __restrict__ bc, double* __restrict__ d) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  double dv[3] = {0, 0, 0};
+  for (int64_t s = rowptr[n]; s < rowptr[n + 1]; s++)
+    if (col[s] == n)
+      for (int c = 0; c < 3; c++) dv[c] = val[s * 9 + 4 * c];
+  const unsigned mb = bc[n];
+  for (int c = 0; c < 3; c++) d[3 * n + c] = ((mb >> c) & 1u) ? 1.0 : dv[c];
+}
+
 }  // namespace
+
+cudaError_t ks_element_blocks_q1(int Q, cudaStream_t st, int64_t ne, const double* qd, int64_t qstride, int layout,
+                                 const Tab1D* tab, double* coo) {
+  switch (Q) {
+    case 2: return assemble_q<2>(st, ne, 1, 1, 1, qd, qstride, layout, tab, nullptr, coo);
+    case 3: return assemble_q<3>(st, ne, 1, 1, 1, qd, qstride, layout, tab, nullptr, coo);
+    case 4: return assemble_q<4>(st, ne, 1, 1, 1, qd, qstride, layout, tab, nullptr, coo);
+    case 5: return assemble_q<5>(st, ne, 1, 1, 1, qd, qstride, layout, tab, nullptr, coo);
+    case 6: return assemble_q<6>(st, ne, 1, 1, 1, qd, qstride, layout, tab, nullptr, coo);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t ks_coo_sum(cudaStream_t st, int64_t nnzb, const int64_t* jstart, const int64_t* perm, const double* coo,
+                       double* val) {
+  if (nnzb == 0) return cudaSuccess;
+  k_coo_sum<<<(unsigned)((nnzb * 9 + 255) / 256), 256, 0, st>>>(nnzb, jstart, perm, coo, val);
+  return cudaGetLastError();
+}
+
+cudaError_t ks_bsr_apply(cudaStream_t st, int64_t nn, const int64_t* rowptr, const int* col, const double* val,
+                         const uint8_t* bc, const double* x, double* y) {
+  if (nn == 0) return cudaSuccess;
+  k_bsr_apply<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(nn, rowptr, col, val, bc, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t ks_bsr_diag(cudaStream_t st, int64_t nn, const int64_t* rowptr, const int* col, const double* val,
+                        const uint8_t* bc, double* d) {
+  if (nn == 0) return cudaSuccess;
+  k_bsr_diag<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(nn, rowptr, col, val, bc, d);
+  return cudaGetLastError();
+}
+
+// Symbolic phase (host): COO entry m = 64 e + 8 a + b couples node emap[8e + a]
+// (row) with node emap[8e + b] (column).  Rows are bucketed by a counting sort,
+// each row's columns sorted and made unique; every entry is listed under its
+// block slot (duplicates are summed by the numeric phase).
+void ks_coo_symbolic(int64_t ne, int64_t nn, const int* emap, std::vector<int64_t>& rowptr, std::vector<int>& col,
+                     std::vector<int64_t>& jstart, std::vector<int64_t>& perm) {
+  const int64_t nc = ne * 64;
+  std::vector<int64_t> cnt(nn + 1, 0), byrow(nc);
+  for (int64_t m = 0; m < nc; m++) cnt[emap[8 * (m / 64) + (m / 8) % 8] + 1]++;
+  for (int64_t n = 0; n < nn; n++) cnt[n + 1] += cnt[n];
+  std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+  for (int64_t m = 0; m < nc; m++) byrow[pos[emap[8 * (m / 64) + (m / 8) % 8]]++] = m;
+  rowptr.assign(nn + 1, 0);
+  col.clear();
+  jstart.clear();
+  perm.assign(nc, 0);
+  int64_t w = 0;
+  std::vector<std::pair<int, int64_t>> row;
+  for (int64_t n = 0; n < nn; n++) {
+    row.clear();
+    for (int64_t k = cnt[n]; k < cnt[n + 1]; k++) {
+      const int64_t m = byrow[k];
+      row.emplace_back(emap[8 * (m / 64) + m % 8], m);
+    }
+    std::sort(row.begin(), row.end());
+    for (size_t k = 0; k < row.size(); k++) {
+      if (k == 0 || row[k].first != row[k - 1].first) {
+        col.push_back(row[k].first);
+        jstart.push_back(w);
+      }
+      perm[w++] = row[k].second;
+    }
+    rowptr[n + 1] = (int64_t)col.size();
+  }
+  jstart.push_back(w);
+}
 
 cudaError_t ks_assemble_q1(int Q, cudaStream_t st, int64_t ne, int nx, int ny, int nz, const uint8_t* bc,
                            const double* qd, int64_t qstride, int layout, const Tab1D* tab, double* A) {

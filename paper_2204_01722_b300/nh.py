@@ -36,6 +36,7 @@ SIGNATURES = {
     "nh_launch_count": (_i64, [_vp]),
     "nh_space_box": (_st, [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(_vp),
                            C.POINTER(_i64), C.POINTER(_i64)]),
+    "nh_op_assemble_q1": (_st, [_vp, C.POINTER(C.c_int64), _vp, _vp, _vp]),
     "nh_space_hex": (_st, [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int, C.c_int, C.POINTER(_vp),
                            C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "nh_space_coords": (_st, [_vp, _vp]),
@@ -199,6 +200,17 @@ def nh_space_hex(ctx, vertices, hex8, p, q):
     _check(lib.nh_space_hex(ctx, V.shape[0], _ptr(V), H.shape[0], _ptr(H), p, q, C.byref(h), C.byref(nn),
                             C.byref(nd)), ctx)
     return h.value, nn.value, nd.value
+
+
+def nh_op_assemble_q1(ctx, op, n_nodes):
+    """Assembled Q1 operator: (rowptr [n_nodes + 1], col [nnzb], val [nnzb, 3, 3])."""
+    nb = C.c_int64()
+    _check(lib.nh_op_assemble_q1(op, C.byref(nb), None, None, None), ctx)
+    rp = np.empty(n_nodes + 1, dtype=np.int64)
+    cl = np.empty(nb.value, dtype=np.int32)
+    val = np.empty((nb.value, 3, 3))
+    _check(lib.nh_op_assemble_q1(op, C.byref(nb), _ptr(rp), _ptr(cl), _ptr(val)), ctx)
+    return rp, cl, val
 
 
 def nh_space_coords(ctx, space, n_nodes):

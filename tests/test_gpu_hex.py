@@ -146,17 +146,59 @@ def test_hex_transfers(nhctx):
     f.close()
 
 
-@pytest.mark.parametrize("mixed", [0, 1])
-def test_hex_linear_solve_matches_direct(nhctx, mixed):
-    """p-multigrid 3 -> 2 -> 1 on the unstructured mesh (matrix-free Galerkin Q1
-    level with Jacobi-PCG: the assembled stencil needs the box lattice)."""
+def bsr_to_csr(rp, cl, val, n_nodes):
+    import scipy.sparse as sps
+    rows = np.repeat(np.arange(n_nodes), np.diff(rp))
+    r = (3 * rows[:, None, None] + np.arange(3)[None, :, None]).repeat(3, 2)
+    c = (3 * cl.astype(np.int64)[:, None, None] + np.arange(3)[None, None, :]).repeat(3, 1)
+    return sps.coo_matrix((val.ravel(), (r.ravel(), c.ravel())), shape=(3 * n_nodes, 3 * n_nodes)).tocsr()
+
+
+@pytest.mark.parametrize("kind", ["rotated", "L"])
+def test_hex_assembled_q1_matches_oracle(nhctx, kind):
+    """Split-phase COO assembly of the Galerkin Q1 level (fine quadrature data at
+    the fine points) against the oracle's assembled element matrices."""
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    Vh, H = make_mesh(kind, (3, 3, 2), seed=13)
+    f = HexCase(ctx, Vh, H, 3, seed=14)
+    cs = fem.HexSpace(Vh, H, 1, 4)
+    csp, nn, _ = nh.nh_space_hex(ctx, Vh, H, 1, 4)
+    d, perm = cKDTree(cs.node_coords()).query(nh.nh_space_coords(ctx, csp, nn))
+    assert d.max() < 1e-12
+    cdp = (3 * perm[:, None] + np.arange(3)[None, :]).ravel()
+    Xc = cs.node_coords()
+    m = np.zeros((nn, 3), dtype=bool)
+    m[np.abs(Xc[:, 0] - Xc[:, 0].min()) < 1e-12, :] = True
+    m[np.abs(Xc[:, 0] - Xc[:, 0].max()) < 1e-12, 0] = True
+    mask_c = m.ravel()
+    nh.nh_space_set_dirichlet(ctx, csp, mask_c[cdp])
+    cop = nh.nh_op_level(ctx, f.op, csp)
+    rp, cl, val = nh.nh_op_assemble_q1(ctx, cop, nn)
+    assert np.all(np.diff(rp) > 0) and np.all(np.diff(cl[rp[0]:rp[1]]) > 0)
+    A = bsr_to_csr(rp, cl, val, nn)                      # library numbering
+    ref = fem.assemble(cs, fem.element_matrices(cs, f.state), mask_c)
+    P = np.zeros(3 * nn, dtype=np.int64)
+    P[cdp] = np.arange(3 * nn)                          # oracle dof -> library dof
+    A_o = A[P][:, P]
+    err = abs(A_o - ref).max()
+    assert err <= 1e-12 * abs(ref).max()
+    nh.nh_op_destroy(cop)
+    nh.nh_space_destroy(csp)
+    f.close()
+
+
+@pytest.mark.parametrize("mixed,assembled", [(0, 1), (1, 1), (0, 0)])
+def test_hex_linear_solve_matches_direct(nhctx, mixed, assembled):
+    """p-multigrid 3 -> 2 -> 1 on the unstructured mesh; the Q1 level assembled
+    by the split-phase COO path (block rows, Jacobi-PCG) or matrix-free."""
     import scipy.sparse.linalg as spla
     ctx, _ = nhctx
     Vh, H = make_mesh("L", (4, 3, 3), seed=10)
     c = HexCase(ctx, Vh, H, 3, amp=0.04, seed=11)
     nh = c.nh
-    opts = nh.nh_mg_default_opts(ctx, c.op, level_p=(3, 2, 1), mixed=mixed, coarse_rtol=1e-3, coarse_maxit=5000)
-    assert opts.coarse_assembled == 0
+    opts = nh.nh_mg_default_opts(ctx, c.op, level_p=(3, 2, 1), mixed=mixed, coarse_rtol=1e-3, coarse_maxit=5000,
+                                 coarse_assembled=assembled)
     mg = nh.nh_mg_create(ctx, c.op, opts)
     nh.nh_mg_setup(ctx, mg)
     J = fem.assemble(c.sp, fem.element_matrices(c.sp, c.state), c.mask)
@@ -190,7 +232,7 @@ def test_hex_mesh_errors(nhctx):
     assert status(Vh, H, p=5) == nh.NH_ERR_UNSUPPORTED
     sp, _, _ = nh.nh_space_hex(ctx, Vh, H, 2, 3)
     op = nh.nh_op_create(ctx, sp, 0.3)
-    opts = nh.nh_mg_default_opts(ctx, op, coarse_assembled=1)
+    opts = nh.nh_mg_default_opts(ctx, op, coarse_solver=1)      # geometric coarse MG needs the box lattice
     with pytest.raises(nh.NhError) as e:
         nh.nh_mg_create(ctx, op, opts)
     assert e.value.status == nh.NH_ERR_UNSUPPORTED
