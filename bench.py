@@ -294,7 +294,7 @@ def run_nh(args):
         minJ = case.minJ
         nd = case.nd
         case.close()
-        sweep, hexes = [], []
+        sweep, hexes, layouts = [], [], []
         if args.sweep and rank == 0:
             for sp_ in (2, 3, 4):
                 c = Case(nh, torch, ctx, sp_, DEFAULT_N[sp_])
@@ -312,6 +312,14 @@ def run_nh(args):
                                   "alu_frac": round(tfl / (FP64_PEAK_TFLOPS if pr == "f64" else FP32_PEAK_TFLOPS), 4)})
                     if pr == "f64x":  # ALU peak of float-float: FP32 pipe / ~15 instructions per FP64 op
                         sweep[-1]["alu_frac"] = None
+                c.close()
+            for lay, lname in ((1, "initial tuned (27 scalars)"), (2, "AD-style tape (32 scalars)")):
+                c = Case(nh, torch, ctx, 3, DEFAULT_N[3], layout=lay)
+                for pr in ("f64", "f32"):
+                    kernel_ms(nh, ctx, c, pr, 5)
+                    k = kernel_ms(nh, ctx, c, pr, 20)
+                    layouts.append({"layout": lname, "p": 3, "n": c.n, "n_dof": c.nd, "prec": pr,
+                                    "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4)})
                 c.close()
             for shuffled in (False, True):
                 c = HexCase(nh, torch, ctx, 3, DEFAULT_N[3], shuffled)
@@ -343,6 +351,8 @@ def run_nh(args):
             out["sweep"] = sweep
         if hexes:
             out["hex"] = hexes
+        if layouts:
+            out["layouts"] = layouts
         if solve:
             out["solve"] = solve
         print(json.dumps(out), flush=True)

@@ -68,8 +68,12 @@ typedef enum { NH_F64 = 0, NH_F32 = 1, NH_F64X = 2 } nh_prec;
  * initial-configuration data of Table different-storage "initial tuned" with
  * the material folded in (27 scalars): grad_X xi (9), H = grad_X u (9),
  * C^-1 (6), W mu, W lambda log J, W lambda; its Jacobian is
- * dP = dF S + F dS (Sec. V-E). */
-typedef enum { NH_LAYOUT_CURRENT = 0, NH_LAYOUT_INITIAL = 1 } nh_layout;
+ * dP = dF S + F dS (Sec. V-E).  NH_LAYOUT_TAPE is the AD-style storage of
+ * Table different-storage "initial AD": the residual's by-products kept for a
+ * split forward-mode tangent that performs no constitutive evaluation (32
+ * scalars): grad_X xi (9), H (9), W S (6), and the tangent's tape C^-1 (6),
+ * W lambda, 2 W (mu - lambda log J); the same Jacobian as NH_LAYOUT_INITIAL. */
+typedef enum { NH_LAYOUT_CURRENT = 0, NH_LAYOUT_INITIAL = 1, NH_LAYOUT_TAPE = 2 } nh_layout;
 
 /* ---- context ---------------------------------------------------------- */
 

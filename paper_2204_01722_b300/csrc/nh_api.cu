@@ -344,13 +344,13 @@ extern "C" nh_status nh_space_destroy(nh_space s) {
 // ---------------------------------------------------------------------------
 // operators
 // ---------------------------------------------------------------------------
-static int scalars_for(int layout) { return layout == NH_LAYOUT_CURRENT ? 17 : 27; }
+static int scalars_for(int layout) { return nh_layout_scalars(layout); }
 
 extern "C" nh_status nh_op_create(nh_space fine, double nu, const double* Epe, double E, int layout, nh_op* out) {
   if (!fine || !out) return NH_ERR_ARG;
   *out = nullptr;
   nh_ctx ctx = fine->ctx;
-  if (layout != NH_LAYOUT_CURRENT && layout != NH_LAYOUT_INITIAL)
+  if (layout != NH_LAYOUT_CURRENT && layout != NH_LAYOUT_INITIAL && layout != NH_LAYOUT_TAPE)
     return nh_fail(ctx, NH_ERR_UNSUPPORTED, "nh_op_create: unknown layout");
   if (!(nu > -1.0 && nu < 0.5)) return nh_fail(ctx, NH_ERR_ARG, "nh_op_create: need -1 < nu < 0.5");
   std::vector<double> lam(fine->ne), mu(fine->ne);

@@ -14,6 +14,9 @@
 #define NH_MAXQ 6   // Gauss points per direction
 
 // elements per block of the fused element kernels (about 128 threads, Q*Q per element)
+__host__ __device__ constexpr int nh_layout_scalars(int layout) {
+  return layout == NH_LAYOUT_CURRENT ? 17 : layout == NH_LAYOUT_INITIAL ? 27 : 32;
+}
 __host__ __device__ constexpr int nh_epb(int Q) { return (128 / (Q * Q)) > 0 ? 128 / (Q * Q) : 1; }
 // Blocked FP32 quadrature data: per batch of EPB elements, Q z-planes of
 // NP = EPB Q^2 points, each plane padded to a multiple of 4 floats (16 bytes, for

@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
                           int vec_ok, int rows_ok, int* __restrict__ err) {
   using L = LineLayout<Q>;
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
-  constexpr int S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
+  constexpr int S = nh_layout_scalars(LAYOUT);
   constexpr long long BS = nh_f32_batch_floats(Q, S), PL = nh_f32_plane_floats(Q, S);
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -1068,7 +1068,7 @@ cudaError_t apply_launch(const OpArgs& A, cudaStream_t s) {
 
 template <int P, int Q, int LAYOUT>
 cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
-  constexpr int EPB = epb_for(Q), S = LAYOUT == NH_LAYOUT_CURRENT ? 17 : 27;
+  constexpr int EPB = epb_for(Q), S = nh_layout_scalars(LAYOUT);
   const int threads = Q * Q * EPB;
   const int64_t blocks = (A.ne + EPB - 1) / EPB;
   if (blocks == 0) return cudaSuccess;
@@ -1085,13 +1085,16 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
 template <int P, int Q>
 cudaError_t apply_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
   if (prec == NH_F64)
-    return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, double, double, NH_LAYOUT_CURRENT>(A, s)
-                                         : apply_launch<P, Q, double, double, NH_LAYOUT_INITIAL>(A, s);
+    return A.layout == NH_LAYOUT_CURRENT   ? apply_launch<P, Q, double, double, NH_LAYOUT_CURRENT>(A, s)
+           : A.layout == NH_LAYOUT_INITIAL ? apply_launch<P, Q, double, double, NH_LAYOUT_INITIAL>(A, s)
+                                           : apply_launch<P, Q, double, double, NH_LAYOUT_TAPE>(A, s);
   if (prec == NH_F64X)
-    return A.layout == NH_LAYOUT_CURRENT ? apply_launch<P, Q, ff, double, NH_LAYOUT_CURRENT>(A, s)
-                                         : apply_launch<P, Q, ff, double, NH_LAYOUT_INITIAL>(A, s);
-  return A.layout == NH_LAYOUT_CURRENT ? apply_f32l_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
-                                       : apply_f32l_launch<P, Q, NH_LAYOUT_INITIAL>(A, s);
+    return A.layout == NH_LAYOUT_CURRENT   ? apply_launch<P, Q, ff, double, NH_LAYOUT_CURRENT>(A, s)
+           : A.layout == NH_LAYOUT_INITIAL ? apply_launch<P, Q, ff, double, NH_LAYOUT_INITIAL>(A, s)
+                                           : apply_launch<P, Q, ff, double, NH_LAYOUT_TAPE>(A, s);
+  return A.layout == NH_LAYOUT_CURRENT   ? apply_f32l_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
+         : A.layout == NH_LAYOUT_INITIAL ? apply_f32l_launch<P, Q, NH_LAYOUT_INITIAL>(A, s)
+                                         : apply_f32l_launch<P, Q, NH_LAYOUT_TAPE>(A, s);
 }
 
 template <int P, int Q, int LAYOUT>
@@ -1114,8 +1117,9 @@ cudaError_t setup_launch(const OpArgs& A, cudaStream_t s) {
 
 template <int P, int Q>
 cudaError_t setup_pq(const OpArgs& A, cudaStream_t s) {
-  return A.layout == NH_LAYOUT_CURRENT ? setup_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
-                                       : setup_launch<P, Q, NH_LAYOUT_INITIAL>(A, s);
+  return A.layout == NH_LAYOUT_CURRENT   ? setup_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
+         : A.layout == NH_LAYOUT_INITIAL ? setup_launch<P, Q, NH_LAYOUT_INITIAL>(A, s)
+                                         : setup_launch<P, Q, NH_LAYOUT_TAPE>(A, s);
 }
 
 template <int P, int Q, int LAYOUT, typename TO>
@@ -1144,8 +1148,11 @@ cudaError_t diag_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
   if (A.layout == NH_LAYOUT_CURRENT)
     return prec == NH_F64 ? diag_launch<P, Q, NH_LAYOUT_CURRENT, double>(A, s)
                           : diag_launch<P, Q, NH_LAYOUT_CURRENT, float>(A, s);
-  return prec == NH_F64 ? diag_launch<P, Q, NH_LAYOUT_INITIAL, double>(A, s)
-                        : diag_launch<P, Q, NH_LAYOUT_INITIAL, float>(A, s);
+  if (A.layout == NH_LAYOUT_INITIAL)
+    return prec == NH_F64 ? diag_launch<P, Q, NH_LAYOUT_INITIAL, double>(A, s)
+                          : diag_launch<P, Q, NH_LAYOUT_INITIAL, float>(A, s);
+  return prec == NH_F64 ? diag_launch<P, Q, NH_LAYOUT_TAPE, double>(A, s)
+                        : diag_launch<P, Q, NH_LAYOUT_TAPE, float>(A, s);
 }
 
 }  // namespace

@@ -114,12 +114,75 @@ __device__ __forceinline__ void pw_initial_ld(LD ld, const T (&g)[3][3], T (&f)[
     for (int d = 0; d < 3; d++) f[c][d] = dP[c][0] * R[d][0] + dP[c][1] * R[d][1] + dP[c][2] * R[d][2];
 }
 
+// AD-style tape (Sec. V-E, "initial AD" storage): the same dP = dF S + F dS with
+// W S stored by the residual evaluation and the tangent reading its tape, so no
+// constitutive function is evaluated: W dS = W lambda (C^-1 : dE) C^-1
+// + 2 W (mu - lambda log J) C^-1 dE C^-1.  Stored: grad_X xi (9), H (9),
+// W S (00, 11, 22, 12, 02, 01), C^-1 (same order), W lambda, 2 W (mu - lambda log J).
+template <typename T, typename LD>
+__device__ __forceinline__ void pw_tape_ld(LD ld, const T (&g)[3][3], T (&f)[3][3]) {
+  T R[3][3], F[3][3];
+#pragma unroll
+  for (int i = 0; i < 9; i++) R[i / 3][i % 3] = ld(i);
+#pragma unroll
+  for (int i = 0; i < 9; i++) F[i / 3][i % 3] = ld(9 + i) + (i % 4 == 0 ? T(1) : T(0));
+  const T s00 = ld(18), s11 = ld(19), s22 = ld(20), s12 = ld(21), s02 = ld(22), s01 = ld(23);
+  const T c00 = ld(24), c11 = ld(25), c22 = ld(26), c12 = ld(27), c02 = ld(28), c01 = ld(29);
+  const T wl = ld(30), two_m = ld(31);
+  const T WS[3][3] = {{s00, s01, s02}, {s01, s11, s12}, {s02, s12, s22}};
+  const T Ci[3][3] = {{c00, c01, c02}, {c01, c11, c12}, {c02, c12, c22}};
+  T dF[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int k = 0; k < 3; k++) dF[c][k] = g[c][0] * R[0][k] + g[c][1] * R[1][k] + g[c][2] * R[2][k];
+  T dE[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = k; l < 3; l++) {
+      const T a = F[0][k] * dF[0][l] + F[1][k] * dF[1][l] + F[2][k] * dF[2][l];
+      const T b = F[0][l] * dF[0][k] + F[1][l] * dF[1][k] + F[2][l] * dF[2][k];
+      dE[k][l] = T(0.5) * (a + b);
+      dE[l][k] = dE[k][l];
+    }
+  T trc = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) trc += Ci[k][l] * dE[k][l];
+  T CdE[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++) CdE[k][l] = Ci[k][0] * dE[0][l] + Ci[k][1] * dE[1][l] + Ci[k][2] * dE[2][l];
+  T WdS[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int l = 0; l < 3; l++)
+      WdS[k][l] = wl * trc * Ci[k][l] + two_m * (CdE[k][0] * Ci[0][l] + CdE[k][1] * Ci[1][l] + CdE[k][2] * Ci[2][l]);
+  T dP[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int K = 0; K < 3; K++)
+      dP[c][K] = dF[c][0] * WS[0][K] + dF[c][1] * WS[1][K] + dF[c][2] * WS[2][K] + F[c][0] * WdS[0][K] +
+                 F[c][1] * WdS[1][K] + F[c][2] * WdS[2][K];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int d = 0; d < 3; d++) f[c][d] = dP[c][0] * R[d][0] + dP[c][1] * R[d][1] + dP[c][2] * R[d][2];
+}
+
 template <int LAYOUT, typename T, typename LD>
 __device__ __forceinline__ void pointwise_ld(LD ld, const T (&g)[3][3], T (&f)[3][3]) {
   if (LAYOUT == NH_LAYOUT_CURRENT)
     pw_current_ld<T>(ld, g, f);
-  else
+  else if (LAYOUT == NH_LAYOUT_INITIAL)
     pw_initial_ld<T>(ld, g, f);
+  else
+    pw_tape_ld<T>(ld, g, f);
 }
 
 // scalars of the point at q, scalar i at q[i s]

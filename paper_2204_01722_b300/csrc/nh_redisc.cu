@@ -84,8 +84,10 @@ cudaError_t launch_pq(int layout, cudaStream_t s, int64_t ne, const int* emap, c
   const unsigned blocks = (unsigned)((n + 127) / 128);
   if (layout == NH_LAYOUT_CURRENT)
     k_setup_pts<PF, QC, NH_LAYOUT_CURRENT><<<blocks, 128, 0, s>>>(ne, emap, coords, u, lam, mu, tb, qd, qstride, minj);
-  else
+  else if (layout == NH_LAYOUT_INITIAL)
     k_setup_pts<PF, QC, NH_LAYOUT_INITIAL><<<blocks, 128, 0, s>>>(ne, emap, coords, u, lam, mu, tb, qd, qstride, minj);
+  else
+    k_setup_pts<PF, QC, NH_LAYOUT_TAPE><<<blocks, 128, 0, s>>>(ne, emap, coords, u, lam, mu, tb, qd, qstride, minj);
   return cudaGetLastError();
 }
 

@@ -84,6 +84,26 @@ __device__ __forceinline__ void nh_setup_point(const double (&gX)[3][3], const d
       qp[14 * qstride] = W * tau[0][1];
       qp[15 * qstride] = W * lam;
       qp[16 * qstride] = W * (mu - lam * logJ);
+    } else if (LAYOUT == NH_LAYOUT_TAPE) {
+      double Ci[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) Ci[i][j] = Fi[i][0] * Fi[j][0] + Fi[i][1] * Fi[j][1] + Fi[i][2] * Fi[j][2];
+      // S = mu I + (lambda log J - mu) C^-1, the residual's second Piola stress
+      const int ix[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+#pragma unroll
+      for (int i = 0; i < 9; i++) qp[i * qstride] = R[i / 3][i % 3];
+#pragma unroll
+      for (int i = 0; i < 9; i++) qp[(9 + i) * qstride] = H[i / 3][i % 3];
+#pragma unroll
+      for (int m = 0; m < 6; m++) {
+        const int i = ix[m][0], j = ix[m][1];
+        qp[(18 + m) * qstride] = W * ((lam * logJ - mu) * Ci[i][j] + (i == j ? mu : 0.0));
+        qp[(24 + m) * qstride] = Ci[i][j];
+      }
+      qp[30 * qstride] = W * lam;
+      qp[31 * qstride] = 2.0 * W * (mu - lam * logJ);
     } else {
       double Ci[3][3];
 #pragma unroll

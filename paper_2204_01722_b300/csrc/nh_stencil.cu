@@ -228,8 +228,10 @@ cudaError_t assemble_q(cudaStream_t st, int64_t ne, int nx, int ny, int nz, cons
   if (ne == 0) return cudaSuccess;
   if (layout == NH_LAYOUT_CURRENT)
     k_assemble_current<Q><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny, coo);
-  else
+  else if (layout == NH_LAYOUT_INITIAL)
     k_assemble<Q, NH_LAYOUT_INITIAL><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny, coo);
+  else
+    k_assemble<Q, NH_LAYOUT_TAPE><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny, coo);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "NH_OK", 1: "NH_ERR_ARG", 2: "NH_ERR_CUDA", 3: "NH_ERR_OOM", 
                 5: "NH_ERR_NOT_CONVERGED", 6: "NH_ERR_NAN", 7: "NH_ERR_TIMEOUT", 8: "NH_ERR_STATE",
                 9: "NH_ERR_UNSUPPORTED"}
 NH_F64, NH_F32, NH_F64X = 0, 1, 2
-NH_LAYOUT_CURRENT, NH_LAYOUT_INITIAL = 0, 1
+NH_LAYOUT_CURRENT, NH_LAYOUT_INITIAL, NH_LAYOUT_TAPE = 0, 1, 2
 
 _vp = C.c_void_p
 _i64 = C.c_int64

@@ -5,10 +5,11 @@
   case must still match to 1e-12 relative, so a change to the oracle's arithmetic
   shows up here.
 * The paper's table of Jacobian representations (Sec. V-E): the current
-  configuration stores 17 scalars per quadrature point and the tuned initial
-  configuration 26.  The test packs exactly those scalars from the oracle's state,
-  rebuilds the pointwise linearisation from the packed values alone and checks it
-  against the oracle's form A / form B, so each listed set is sufficient.
+  configuration stores 17 scalars per quadrature point, the tuned initial
+  configuration 26 and the AD one 31 (its tape taken as C^-1, 6 scalars).  The
+  test packs exactly those scalars from the oracle's state, rebuilds the pointwise
+  linearisation from the packed values and the (homogeneous) Lame constants alone
+  and checks it against the oracle's form A / form B, so each listed set suffices.
 """
 import os
 import sys
@@ -99,5 +100,30 @@ def test_initial_configuration_tuned_needs_26_scalars():
     dE = 0.5 * (np.swapaxes(F, -1, -2) @ dF + np.swapaxes(dF, -1, -2) @ F)
     dS = lam * np.einsum("...ij,...ij", Ci, dE)[..., None, None] * Ci + 2.0 * (mu - llj) * (Ci @ dE @ Ci)
     f = W[..., None, None] * ((dF @ S + F @ dS) @ np.swapaxes(D, -1, -2))
+    ref = fem.pointwise_B(st, g)
+    assert np.abs(f - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_initial_configuration_ad_needs_31_scalars():
+    """S comes from the residual evaluation; the tangent needs C^-1 (the tape) and
+    log J, which the tape also fixes: log J = -log det(C^-1) / 2."""
+    st, g, lam, mu = state_and_gradient()
+    Finv = st["Finv"]
+    Cinv = Finv @ np.swapaxes(Finv, -1, -2)
+    S, _ = fem.second_piola(st)
+    sh = st["W"].shape
+    packed = np.concatenate([st["dxidX"].reshape(sh + (9,)), st["W"][..., None], st["H"].reshape(sh + (9,)),
+                             pack_sym(S), pack_sym(Cinv)], axis=-1)
+    assert packed.shape[-1] == storage_table()["initial_AD"]
+    D = packed[..., 0:9].reshape(sh + (3, 3))
+    W = packed[..., 9]
+    F = I3 + packed[..., 10:19].reshape(sh + (3, 3))
+    Sp = unpack_sym(packed[..., 19:25])
+    Ci = unpack_sym(packed[..., 25:31])
+    logJ = (-0.5 * np.log(np.linalg.det(Ci)))[..., None, None]
+    dF = g @ D
+    dE = 0.5 * (np.swapaxes(F, -1, -2) @ dF + np.swapaxes(dF, -1, -2) @ F)
+    dS = lam * np.einsum("...ij,...ij", Ci, dE)[..., None, None] * Ci + 2.0 * (mu - lam * logJ) * (Ci @ dE @ Ci)
+    f = W[..., None, None] * ((dF @ Sp + F @ dS) @ np.swapaxes(D, -1, -2))
     ref = fem.pointwise_B(st, g)
     assert np.abs(f - ref).max() <= 1e-12 * np.abs(ref).max()

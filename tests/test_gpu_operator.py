@@ -71,7 +71,7 @@ class Case:
 
 @pytest.mark.parametrize("n,p,q", [((3, 2, 4), 1, 2), ((3, 2, 4), 2, 3), ((3, 3, 2), 3, 4), ((2, 3, 2), 4, 5),
                                    ((3, 2, 2), 2, 4), ((2, 2, 3), 3, 5), ((2, 2, 2), 4, 6), ((5, 4, 3), 2, 3)])
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 def test_jacobian_apply_fp64(nhctx, n, p, q, layout):
     ctx, _ = nhctx
     c = Case(ctx, n, p, q, layout=layout, seed=p + 10 * q)
@@ -86,7 +86,7 @@ def test_jacobian_apply_fp64(nhctx, n, p, q, layout):
 
 @pytest.mark.parametrize("n,p,q", [((3, 2, 4), 2, 3), ((3, 3, 2), 3, 4), ((2, 3, 2), 4, 5), ((2, 2, 3), 2, 4),
                                    ((4, 3, 3), 1, 2)])
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 def test_jacobian_apply_f64x(nhctx, n, p, q, layout):
     """Float-float arithmetic on the FP32 pipes, FP64 vectors: same 1e-12 bar as FP64."""
     ctx, _ = nhctx
@@ -100,7 +100,7 @@ def test_jacobian_apply_f64x(nhctx, n, p, q, layout):
 
 
 @pytest.mark.parametrize("n,p", [((3, 2, 4), 2), ((3, 3, 2), 3), ((2, 3, 2), 4)])
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 def test_jacobian_apply_fp32(nhctx, n, p, layout):
     ctx, _ = nhctx
     c = Case(ctx, n, p, layout=layout, seed=3)
@@ -183,7 +183,7 @@ def test_residual(nhctx, n, p, q):
 
 
 @pytest.mark.parametrize("n,p,q,layout", [((3, 2, 2), 2, 3, 0), ((2, 2, 3), 3, 4, 0), ((2, 2, 2), 4, 5, 0),
-                                          ((2, 3, 2), 2, 3, 1), ((2, 2, 2), 1, 3, 0)])
+                                          ((2, 3, 2), 2, 3, 1), ((2, 2, 2), 1, 3, 0), ((2, 2, 3), 3, 4, 2)])
 def test_diagonal(nhctx, n, p, q, layout):
     ctx, _ = nhctx
     c = Case(ctx, n, p, q, layout=layout, seed=12)
@@ -197,7 +197,7 @@ def test_diagonal(nhctx, n, p, q, layout):
     c.close()
 
 
-@pytest.mark.parametrize("pf,pc,layout", [(4, 2, 0), (4, 1, 0), (3, 2, 0), (2, 1, 0), (3, 2, 1)])
+@pytest.mark.parametrize("pf,pc,layout", [(4, 2, 0), (4, 1, 0), (3, 2, 0), (2, 1, 0), (3, 2, 1), (3, 1, 2)])
 def test_rediscretized_coarse_operator(nhctx, pf, pc, layout):
     """Rediscretised coarse operator (Sec. III-B alternative): quadrature data
     re-evaluated from the fine state on the coarse Gauss rule q_c = p_c + 1."""

@@ -40,7 +40,7 @@ def host(t):
 
 class Problem:
     def __init__(self, ctx, n, p, levels, E=None, perturb=0.1, seed=3, mixed=0, assembled=1, coarse_rtol=1e-14,
-                 amp=0.04, fp64_kind=0, redisc=0, nonlinear=0, coarse_solver=0):
+                 amp=0.04, fp64_kind=0, redisc=0, nonlinear=0, coarse_solver=0, layout=0):
         from paper_2204_01722_b300 import nh
         self.nh, self.ctx = nh, ctx
         q = p + 1
@@ -53,7 +53,7 @@ class Problem:
         self.u[self.masks[0]] = 0.0
         self.space, _, self.nd = nh.nh_space_box(ctx, *n, self.V, p, q)
         nh.nh_space_set_dirichlet(ctx, self.space, self.masks[0])
-        self.op = nh.nh_op_create(ctx, self.space, 0.3, E)
+        self.op = nh.nh_op_create(ctx, self.space, 0.3, E, 1.0, layout)
         self.opts = nh.nh_mg_default_opts(ctx, self.op, level_p=levels, mixed=mixed, coarse_assembled=assembled,
                                           coarse_rtol=coarse_rtol, coarse_maxit=5000, seed=SEED,
                                           fp64_kind=fp64_kind, coarse_rediscretize=redisc, nonlinear=nonlinear,
@@ -125,12 +125,13 @@ def test_mixed_vcycle_close_to_fp64(nhctx):
     P32.close()
 
 
-@pytest.mark.parametrize("mixed,fp64_kind", [(0, 0), (1, 0), (0, 1), (1, 1)])
-def test_linear_solve_matches_direct(nhctx, mixed, fp64_kind):
-    """fp64_kind 1: outer FCG, Lanczos and FP64 smoothers in float-float arithmetic."""
+@pytest.mark.parametrize("mixed,fp64_kind,layout", [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0), (1, 1, 2)])
+def test_linear_solve_matches_direct(nhctx, mixed, fp64_kind, layout):
+    """fp64_kind 1: outer FCG, Lanczos and FP64 smoothers in float-float arithmetic;
+    layout 2: the AD-style tape storage on every level and in the Q1 stencil."""
     import scipy.sparse.linalg as spla
     ctx, _ = nhctx
-    P = Problem(ctx, (3, 3, 2), 3, (3, 2, 1), mixed=mixed, coarse_rtol=1e-3, fp64_kind=fp64_kind)
+    P = Problem(ctx, (3, 3, 2), 3, (3, 2, 1), mixed=mixed, coarse_rtol=1e-3, fp64_kind=fp64_kind, layout=layout)
     P.setup()
     st = fem.qp_state(P.sps[0], P.mat, P.u)
     J = fem.assemble(P.sps[0], fem.element_matrices(P.sps[0], st), P.masks[0])
