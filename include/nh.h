@@ -128,6 +128,21 @@ nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const double* vertex_
  * NH_ERR_UNSUPPORTED (orders, or 2^29 nodes), NH_ERR_OOM. */
 nh_status nh_space_hex(nh_ctx ctx, int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8, int p, int q,
                        nh_space* out, int64_t* n_nodes, int64_t* n_dof);
+/* Host only, no device or context needed: the node numbering and coordinates
+ * nh_space_hex builds for (xyz, hex8, p), for inspection and mesh tooling.
+ * Writes *n_nodes; with emap (HOST [ne][(p+1)^3] int32) and coords (HOST
+ * [n_nodes][3]) non-NULL also the element map and the node coordinates (call
+ * first with both NULL to size them).  On failure err (if non-NULL) receives
+ * the reason, up to err_len bytes.  Errors: NH_ERR_ARG (invalid mesh),
+ * NH_ERR_UNSUPPORTED (p outside 1..4, or 2^29 nodes). */
+nh_status nh_hex_mesh_numbering(int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8, int p,
+                                int64_t* n_nodes, int* emap, double* coords, char* err, int64_t err_len);
+/* Host only: the 3x3 block-row pattern of the Q1 COO assembly (the symbolic
+ * phase of nh_op_assemble_q1) for an element map emap [ne][8] over n_nodes
+ * nodes.  Writes *nnzb; with rowptr (HOST [n_nodes + 1] int64) and col (HOST
+ * [nnzb] int32) non-NULL also the pattern, columns sorted per row.
+ * Errors: NH_ERR_ARG (ids outside [0, n_nodes)). */
+nh_status nh_q1_block_pattern(int64_t ne, int64_t n_nodes, const int* emap, int64_t* nnzb, int64_t* rowptr, int* col);
 /* Node coordinates, HOST out [n_nodes][3]. */
 nh_status nh_space_coords(nh_space s, double* xyz_host);
 /* Dirichlet DoFs: HOST array [n_dof], nonzero = constrained.  Copied; synchronises. */
@@ -199,7 +214,7 @@ nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* du_host, vo
  * diag[a,c] = sum_e sum_q sum_{d,d'} B_xi,d[q,a] D[q; c,d; c,d'] B_xi,d'[q,a];
  * 1 on constrained DoFs.  Device out [n_dof] of prec type. */
 nh_status nh_jacobian_diagonal(nh_op op, nh_prec prec, void* diag);
-/* Assembled operator on a Q1 (p = 1) space as 3x3 block rows (Sec. IV: the
+/* Assembled operator on a Q1 (p = 1) space as 3x3 block rows (Sec. III-D: the
  * split-phase COO assembly that hands the coarse level to a sparse solver).
  * Symbolic phase on the host: COO entry (e, a, b) couples the element's nodes a
  * (row) and b (column); rows bucketed, columns sorted and made unique, every

@@ -299,6 +299,38 @@ extern "C" nh_status nh_space_hex(nh_ctx ctx, int64_t nv, const double* xyz, int
   return NH_OK;
 }
 
+extern "C" nh_status nh_hex_mesh_numbering(int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8, int p,
+                                           int64_t* n_nodes, int* emap, double* coords, char* err, int64_t err_len) {
+  if (!xyz || !hex8 || !n_nodes || nv < 8 || ne < 1 || ne > INT32_MAX / 8) return NH_ERR_ARG;
+  if (p < 1 || p > 4) return NH_ERR_UNSUPPORTED;
+  std::vector<int> em;
+  std::vector<double> X;
+  int64_t nn = 0;
+  const std::string msg = nh_hex_numbering(nv, xyz, ne, hex8, p, em, X, nn);
+  if (!msg.empty()) {
+    if (err && err_len > 0) snprintf(err, (size_t)err_len, "%s", msg.c_str());
+    return msg.find("too large") != std::string::npos ? NH_ERR_UNSUPPORTED : NH_ERR_ARG;
+  }
+  *n_nodes = nn;
+  if (emap) memcpy(emap, em.data(), sizeof(int) * em.size());
+  if (coords) memcpy(coords, X.data(), sizeof(double) * X.size());
+  return NH_OK;
+}
+
+extern "C" nh_status nh_q1_block_pattern(int64_t ne, int64_t n_nodes, const int* emap, int64_t* nnzb, int64_t* rowptr,
+                                         int* col) {
+  if (!emap || !nnzb || ne < 0 || n_nodes < 1) return NH_ERR_ARG;
+  for (int64_t i = 0; i < 8 * ne; i++)
+    if (emap[i] < 0 || emap[i] >= n_nodes) return NH_ERR_ARG;
+  std::vector<int64_t> rp, js, pm;
+  std::vector<int> cl;
+  ks_coo_symbolic(ne, n_nodes, emap, rp, cl, js, pm);
+  *nnzb = (int64_t)cl.size();
+  if (rowptr) memcpy(rowptr, rp.data(), sizeof(int64_t) * rp.size());
+  if (col) memcpy(col, cl.data(), sizeof(int) * cl.size());
+  return NH_OK;
+}
+
 bool nh_same_mesh(nh_space a, nh_space b) {
   if (a->hex != b->hex || a->ne != b->ne) return false;
   if (a->hex) return a->hex8_host == b->hex8_host && a->verts_host == b->verts_host;

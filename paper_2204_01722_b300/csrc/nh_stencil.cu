@@ -4,7 +4,7 @@
 // fine quadrature data (exact Galerkin, Sec. III-B).  Applied matrix-free it
 // would stream the whole fine quadrature data per coarse apply, and the coarse
 // Jacobi-CG solve applies it hundreds of times per V-cycle.  Instead the
-// element matrices K_e = sum_q G_q^T D_q G_q (the B^T D B of Sec. III-C) are
+// element matrices K_e = sum_q G_q^T D_q G_q (the B^T D B of Sec. III-D) are
 // built once per quadrature-data setup and summed into a 27-point block
 // stencil: for every node, one 3x3 block per lattice neighbour, stored
 // [27][9][n_nodes] so that one thread per node reads coalesced rows.

@@ -37,6 +37,9 @@ SIGNATURES = {
     "nh_space_box": (_st, [_vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(_vp),
                            C.POINTER(_i64), C.POINTER(_i64)]),
     "nh_op_assemble_q1": (_st, [_vp, C.POINTER(C.c_int64), _vp, _vp, _vp]),
+    "nh_hex_mesh_numbering": (_st, [C.c_int64, _vp, C.c_int64, _vp, C.c_int, C.POINTER(C.c_int64), _vp, _vp,
+                                    C.c_char_p, C.c_int64]),
+    "nh_q1_block_pattern": (_st, [C.c_int64, C.c_int64, _vp, C.POINTER(C.c_int64), _vp, _vp]),
     "nh_space_hex": (_st, [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int, C.c_int, C.POINTER(_vp),
                            C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "nh_space_coords": (_st, [_vp, _vp]),
@@ -211,6 +214,38 @@ def nh_op_assemble_q1(ctx, op, n_nodes):
     val = np.empty((nb.value, 3, 3))
     _check(lib.nh_op_assemble_q1(op, C.byref(nb), _ptr(rp), _ptr(cl), _ptr(val)), ctx)
     return rp, cl, val
+
+
+def nh_hex_mesh_numbering(vertices, hex8, p):
+    """Host-only numbering of nh_space_hex: (emap [ne, (p+1)^3] int32, coords [n_nodes, 3]).
+    Raises NhError with the reason on an invalid mesh."""
+    V = np.ascontiguousarray(vertices, dtype=np.float64).reshape(-1, 3)
+    H = np.ascontiguousarray(hex8, dtype=np.int64).reshape(-1, 8)
+    nn = C.c_int64()
+    err = C.create_string_buffer(512)
+    st = lib.nh_hex_mesh_numbering(V.shape[0], _ptr(V), H.shape[0], _ptr(H), p, C.byref(nn), None, None, err, 512)
+    if st != NH_OK:
+        raise NhError(st, err.value.decode())
+    emap = np.empty((H.shape[0], (p + 1) ** 3), dtype=np.int32)
+    X = np.empty((nn.value, 3))
+    st = lib.nh_hex_mesh_numbering(V.shape[0], _ptr(V), H.shape[0], _ptr(H), p, C.byref(nn), _ptr(emap), _ptr(X),
+                                   err, 512)
+    if st != NH_OK:
+        raise NhError(st, err.value.decode())
+    return emap, X
+
+
+def nh_q1_block_pattern(emap, n_nodes):
+    """Host-only block-row pattern of the Q1 COO assembly: (rowptr [n_nodes + 1], col [nnzb])."""
+    E = np.ascontiguousarray(emap, dtype=np.int32).reshape(-1, 8)
+    nb = C.c_int64()
+    st = lib.nh_q1_block_pattern(E.shape[0], n_nodes, _ptr(E), C.byref(nb), None, None)
+    if st != NH_OK:
+        raise NhError(st, "nh_q1_block_pattern: invalid element map")
+    rp = np.empty(n_nodes + 1, dtype=np.int64)
+    cl = np.empty(nb.value, dtype=np.int32)
+    lib.nh_q1_block_pattern(E.shape[0], n_nodes, _ptr(E), C.byref(nb), _ptr(rp), _ptr(cl))
+    return rp, cl
 
 
 def nh_space_coords(ctx, space, n_nodes):
