@@ -155,6 +155,14 @@ extern "C" int64_t nh_launch_count(nh_ctx c) { return c ? c->launches : -1; }
 // ---------------------------------------------------------------------------
 static nh_status space_upload(nh_ctx ctx, nh_space s, const std::vector<int>& emap, const std::vector<double>& mult);
 
+// FNV-1a over raw bytes: spaces on the same mesh (the p-multigrid levels) get
+// the same value, so the per-call mesh checks of the transfers cost O(1)
+static uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; i++) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
 extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const double* vxyz, int p, int q,
                                   nh_space* out, int64_t* n_nodes, int64_t* n_dof) {
   if (!ctx || !out) return NH_ERR_ARG;
@@ -175,6 +183,8 @@ extern "C" nh_status nh_space_box(nh_ctx ctx, int nx, int ny, int nz, const doub
   s->Nx = (int)Nx; s->Ny = (int)Ny; s->Nz = (int)Nz;
   nh_tabulate(p, q, &s->tab);
   if (vxyz) s->verts_host.assign(vxyz, vxyz + 3 * (size_t)(nx + 1) * (ny + 1) * (nz + 1));
+  const int dims[3] = {nx, ny, nz};
+  s->mesh_hash = fnv1a(s->verts_host.data(), sizeof(double) * s->verts_host.size(), fnv1a(dims, sizeof(dims)));
 
   // element restriction and node coordinates (trilinear image of the GLL lattice)
   const int P3 = P * P * P;
@@ -287,6 +297,8 @@ extern "C" nh_status nh_space_hex(nh_ctx ctx, int64_t nv, const double* xyz, int
   nh_tabulate(p, q, &s->tab);
   s->verts_host.assign(xyz, xyz + 3 * (size_t)nv);
   s->hex8_host.assign(hex8, hex8 + 8 * (size_t)ne);
+  s->mesh_hash = fnv1a(s->verts_host.data(), sizeof(double) * s->verts_host.size(),
+                       fnv1a(s->hex8_host.data(), sizeof(int64_t) * s->hex8_host.size()));
   s->coords_host = std::move(coords);
   std::vector<double> mult((size_t)nn, 0.0);
   for (int n : emap) mult[n] += 1.0;
@@ -332,9 +344,8 @@ extern "C" nh_status nh_q1_block_pattern(int64_t ne, int64_t n_nodes, const int*
 }
 
 bool nh_same_mesh(nh_space a, nh_space b) {
-  if (a->hex != b->hex || a->ne != b->ne) return false;
-  if (a->hex) return a->hex8_host == b->hex8_host && a->verts_host == b->verts_host;
-  return a->nx == b->nx && a->ny == b->ny && a->nz == b->nz && a->verts_host == b->verts_host;
+  if (a->hex != b->hex || a->ne != b->ne || a->mesh_hash != b->mesh_hash) return false;
+  return a->hex || (a->nx == b->nx && a->ny == b->ny && a->nz == b->nz);
 }
 
 extern "C" nh_status nh_space_coords(nh_space s, double* xyz) {

@@ -117,7 +117,7 @@ def test_learned_stage_keeps_fcg_exact(nhctx, mode):
     x = torch.zeros(nd, dtype=torch.float64, device="cuda")
     # rtol and maxit leave room for the run-to-run spread of FCG(1) counts on this
     # high-contrast problem (the inexact coarse solve, with atomic-scatter rounding)
-    rep = nh.nh_linear_solve(ctx, mg, torch.from_numpy(b).cuda(), x, rtol=1e-9, maxit=600, norm=1)
+    rep = nh.nh_linear_solve(ctx, mg, torch.from_numpy(b).cuda(), x, rtol=1e-9, maxit=3000, norm=1)
     assert rep.learned_accepted + rep.learned_rejected == rep.vcycles
     assert rel(x.cpu().numpy(), spla.spsolve(J.tocsc(), b)) < 1e-6
     nh.nh_mg_set_learned(ctx, mg, None)
@@ -191,9 +191,10 @@ def test_trained_network_gain(nhctx):
     must reach the same solution and account for every coarse solve (warm start
     taken or refused); its coarse PCG iterations are reported against plain
     p-MG.  The counts are not compared: on this small high-contrast problem the
-    FCG iteration count of plain p-MG itself varies from run to run (64 to 101
-    observed), because atomic-scatter rounding moves the inexact coarse solve
-    across its every-4-iterations stopping test."""
+    FCG iteration count of plain p-MG itself varies from run to run (58 to 525
+    observed for one right-hand side), because atomic-scatter rounding moves the
+    inexact coarse solve across its every-4-iterations stopping test; hence the
+    generous iteration limit."""
     import scipy.sparse.linalg as spla
     ctx, stream = nhctx
     from paper_2204_01722_b300 import nh
@@ -227,7 +228,7 @@ def test_trained_network_gain(nhctx):
         for j in range(4):
             b = rhs(900 + j)
             x = torch.zeros(nd, dtype=torch.float64, device="cuda")
-            rep = nh.nh_linear_solve(ctx, mg, torch.from_numpy(b).cuda(), x, rtol=1e-9, maxit=600, norm=1)
+            rep = nh.nh_linear_solve(ctx, mg, torch.from_numpy(b).cuda(), x, rtol=1e-9, maxit=3000, norm=1)
             assert rel(x.cpu().numpy(), spla.spsolve(Jc, b)) < 1e-6
             its += rep.coarse_its
             acc += rep.learned_accepted
