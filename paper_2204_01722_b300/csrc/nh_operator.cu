@@ -32,6 +32,14 @@ __host__ __device__ constexpr int epb_for(int Q) { return nh_epb(Q); }
 // ~128 threads).  Measured on B300 (Q3 on 48^3): 2 blocks 2.97, 3 blocks 4.20,
 // 4 blocks 4.78 GDoF/s; for q = 5 three blocks beat four (4.32 vs 4.06), the
 // spills of a 128-register cap outweigh the extra warps.
+// FP32 block-row scatter: tried when every block lies in one row of elements (the
+// x-element count a multiple of the block's elements), or always (blocks that
+// straddle two rows fall back at run time) when NH_F32_ROWS_ANY or q <= 3.
+// Measured on B300 with rows straddled: q = 3 +0.9%, q = 5 -0.4%, q = 4 unchanged.
+#ifndef NH_F32_ROWS_ANY
+#define NH_F32_ROWS_ANY 0
+#endif
+
 #ifndef NH_FF_MIN_BLOCKS_SMALLQ
 #define NH_FF_MIN_BLOCKS_SMALLQ 4
 #endif
@@ -1078,7 +1086,7 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   k_jacobian_apply_f32l<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
       A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift,
-      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, ((uintptr_t)A.out & 15) == 0 && A.nx > 0 && A.nx % EPB == 0 ? 1 : 0, A.err);
+      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, ((uintptr_t)A.out & 15) == 0 && A.nx > 0 && (NH_F32_ROWS_ANY || Q <= 3 || A.nx % EPB == 0) ? 1 : 0, A.err);
   return cudaGetLastError();
 }
 
