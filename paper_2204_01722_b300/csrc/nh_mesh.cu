@@ -20,7 +20,6 @@
 
 #include <algorithm>
 #include <array>
-#include <map>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -29,10 +28,27 @@
 
 namespace {
 
+uint64_t mix(uint64_t h, uint64_t v) {  // splitmix64-style combine
+  h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  h ^= h >> 31;
+  h *= 0xbf58476d1ce4e5b9ull;
+  return h ^ (h >> 29);
+}
+
 struct EdgeHash {
-  size_t operator()(const std::pair<int64_t, int64_t>& k) const {
-    return std::hash<int64_t>()(k.first * 1000003 + k.second);
+  size_t operator()(const std::pair<int64_t, int64_t>& k) const { return (size_t)mix(mix(0, k.first), k.second); }
+};
+
+struct FaceHash {
+  size_t operator()(const std::array<int64_t, 4>& k) const {
+    return (size_t)mix(mix(mix(mix(0, k[0]), k[1]), k[2]), k[3]);
   }
+};
+
+// per face (sorted corner ids): elements using it, and the id of its first interior node
+struct FaceInfo {
+  int uses = 0;
+  int64_t base = -1;
 };
 
 // det of d X / d xi of the trilinear map at the corner (ci, cj, ck) in {0,1}^3
@@ -74,25 +90,33 @@ std::string nh_hex_numbering(int64_t nv, const double* xyz, int64_t ne, const in
                "(vertex v of an element sits at corner (v & 1, (v >> 1) & 1, v >> 2))";
   }
   // faces used by more than two elements make the mesh non-manifold
-  std::map<std::array<int64_t, 4>, int> face_use;
+  std::unordered_map<std::array<int64_t, 4>, FaceInfo, FaceHash> faces;
+  faces.reserve((size_t)(3.5 * ne) + 16);
   static const int kFace[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5}, {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
   for (int64_t e = 0; e < ne; e++)
     for (int f = 0; f < 6; f++) {
       std::array<int64_t, 4> k;
       for (int t = 0; t < 4; t++) k[t] = hex8[8 * e + kFace[f][t]];
       std::sort(k.begin(), k.end());
-      if (++face_use[k] > 2) return "a face is shared by more than two elements (element " + std::to_string(e) + ")";
+      if (++faces[k].uses > 2) return "a face is shared by more than two elements (element " + std::to_string(e) + ")";
     }
 
   std::vector<int64_t> vnode((size_t)nv, -1);
   std::unordered_map<std::pair<int64_t, int64_t>, int64_t, EdgeHash> edge_base;
-  std::map<std::array<int64_t, 4>, int64_t> face_base;
+  edge_base.reserve((size_t)(3.5 * ne) + 16);
   int64_t next = 0;
   emap.assign((size_t)ne * P3, 0);
   std::vector<int64_t> ids((size_t)P3);
+  // per element, each edge and face is looked up once: edge cache by (axis, the
+  // two fixed coordinates), face cache by (fixed axis, side) with its frame
+  int64_t ebase[12], fbase[6];
+  int fos[6], fot[6];
+  bool falong[6];
   for (int64_t e = 0; e < ne; e++) {
     const int64_t* hv = hex8 + 8 * e;
     int64_t interior = -1;
+    for (int c = 0; c < 12; c++) ebase[c] = -1;
+    for (int c = 0; c < 6; c++) fbase[c] = -1;
     for (int k = 0; k < P; k++)
       for (int j = 0; j < P; j++)
         for (int i = 0; i < P; i++) {
@@ -113,43 +137,56 @@ std::string nh_hex_numbering(int64_t nv, const double* xyz, int64_t ne, const in
             c0[ax] = 0;
             c1[ax] = p;
             const int64_t a = corner(c0), b = corner(c1);
-            const auto key = std::make_pair(std::min(a, b), std::max(a, b));
-            auto it = edge_base.find(key);
-            if (it == edge_base.end()) {
-              it = edge_base.emplace(key, next).first;
-              next += p - 1;
+            const int o1 = ax == 0 ? 1 : 0, o2 = ax == 2 ? 1 : 2;
+            const int slot = ax * 4 + (L[o1] == p) + 2 * (L[o2] == p);
+            if (ebase[slot] < 0) {
+              const auto key = std::make_pair(std::min(a, b), std::max(a, b));
+              auto it = edge_base.find(key);
+              if (it == edge_base.end()) {
+                it = edge_base.emplace(key, next).first;
+                next += p - 1;
+              }
+              ebase[slot] = it->second;
             }
             const int t = L[ax];  // 1 .. p-1 from local corner a
-            id = it->second + (a < b ? t - 1 : p - 1 - t);
+            id = ebase[slot] + (a < b ? t - 1 : p - 1 - t);
           } else if (nb == 1) {
             const int fx = bd[0] ? 0 : bd[1] ? 1 : 2;  // fixed axis
             const int sa = fx == 0 ? 1 : 0, ta = fx == 2 ? 1 : 2;  // free axes, increasing
-            int64_t cid[2][2];  // corner ids at (s, t) in {0, p}^2
-            for (int cs = 0; cs < 2; cs++)
-              for (int ct = 0; ct < 2; ct++) {
-                int c[3] = {L[0], L[1], L[2]};
-                c[sa] = cs * p;
-                c[ta] = ct * p;
-                cid[cs][ct] = corner(c);
-              }
-            std::array<int64_t, 4> key = {cid[0][0], cid[1][0], cid[0][1], cid[1][1]};
-            std::sort(key.begin(), key.end());
-            auto it = face_base.find(key);
-            if (it == face_base.end()) {
-              it = face_base.emplace(key, next).first;
-              next += (int64_t)(p - 1) * (p - 1);
-            }
-            int os = 0, ot = 0;  // origin: smallest corner id
-            for (int cs = 0; cs < 2; cs++)
-              for (int ct = 0; ct < 2; ct++)
-                if (cid[cs][ct] < cid[os][ot]) {
-                  os = cs;
-                  ot = ct;
+            const int slot = fx * 2 + (L[fx] == p);
+            if (fbase[slot] < 0) {
+              int64_t cid[2][2];  // corner ids at (s, t) in {0, p}^2
+              for (int cs = 0; cs < 2; cs++)
+                for (int ct = 0; ct < 2; ct++) {
+                  int c[3] = {L[0], L[1], L[2]};
+                  c[sa] = cs * p;
+                  c[ta] = ct * p;
+                  cid[cs][ct] = corner(c);
                 }
-            const bool first_along_s = cid[1 - os][ot] < cid[os][1 - ot];  // neighbour with the smaller id
+              std::array<int64_t, 4> key = {cid[0][0], cid[1][0], cid[0][1], cid[1][1]};
+              std::sort(key.begin(), key.end());
+              FaceInfo& fi = faces[key];
+              if (fi.base < 0) {
+                fi.base = next;
+                next += (int64_t)(p - 1) * (p - 1);
+              }
+              int os = 0, ot = 0;  // origin: smallest corner id
+              for (int cs = 0; cs < 2; cs++)
+                for (int ct = 0; ct < 2; ct++)
+                  if (cid[cs][ct] < cid[os][ot]) {
+                    os = cs;
+                    ot = ct;
+                  }
+              fbase[slot] = fi.base;
+              fos[slot] = os;
+              fot[slot] = ot;
+              falong[slot] = cid[1 - os][ot] < cid[os][1 - ot];  // neighbour with the smaller id
+            }
+            const int os = fos[slot], ot = fot[slot];
+            const bool first_along_s = falong[slot];
             const int ds = os ? p - L[sa] : L[sa], dt = ot ? p - L[ta] : L[ta];
             const int s1 = first_along_s ? ds : dt, t1 = first_along_s ? dt : ds;
-            id = it->second + (s1 - 1) + (int64_t)(p - 1) * (t1 - 1);
+            id = fbase[slot] + (s1 - 1) + (int64_t)(p - 1) * (t1 - 1);
           } else {
             if (interior < 0) {
               interior = next;
