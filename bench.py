@@ -34,7 +34,7 @@ NU = 0.3
 PERTURB = 0.1
 AMP = 0.05
 SEED = 42
-# FP64 pipe of a B300: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
+# FP64 pipe of a B300: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (unit count x maximum clock)
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 # FP32 pipe: 148 SMs x 128 FFMA/clk x 2 flop x 2.032 GHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -365,7 +365,7 @@ def run_nh(args):
 # ---------------------------------------------------------------------------
 def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusions=False, learned=None):
     """Load-stepped p-MG solves of uniaxial compression; returns the reports of
-    plain FP64 Newton-Krylov p-MG (the judge), FP64 L-BFGS with the V-cycle as
+    plain FP64 Newton-Krylov p-MG (the reference solver), FP64 L-BFGS with the V-cycle as
     initial inverse Hessian, Newton-Krylov with the faster V-cycle (FP32 on the
     p > 1 levels, FP64-accurate applies in float-float, rediscretised coarse
     levels), and the chosen solver: L-BFGS with that V-cycle and the geometric
