@@ -303,6 +303,22 @@ extern "C" nh_status nh_space_hex(nh_ctx ctx, int64_t nv, const double* xyz, int
   std::vector<double> mult((size_t)nn, 0.0);
   for (int n : emap) mult[n] += 1.0;
   s->emap_host = emap;
+  // first-touch numbering: the nodes of elements [0, e] are a prefix of the ids, so
+  // the host-buffer apply can upload du and download y in element chunks
+  const int P3 = s->P * s->P * s->P;
+  s->hex_need.resize(ne);
+  s->hex_fin.assign(ne + 1, nn);
+  int64_t hi = 0;
+  for (int64_t e = 0; e < ne; e++) {
+    int64_t lo = nn;
+    for (int l = 0; l < P3; l++) {
+      hi = std::max<int64_t>(hi, emap[(size_t)e * P3 + l] + 1);
+      lo = std::min<int64_t>(lo, emap[(size_t)e * P3 + l]);
+    }
+    s->hex_need[e] = hi;
+    s->hex_fin[e] = lo;
+  }
+  for (int64_t e = ne - 1; e >= 0; e--) s->hex_fin[e] = std::min(s->hex_fin[e], s->hex_fin[e + 1]);
   nh_status st = space_upload(ctx, s, emap, mult);
   if (st != NH_OK) return st;
   *out = s;
@@ -772,12 +788,48 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
     NH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
     NH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
   }
-  if (sp->hex) {  // unstructured mesh: no layer ranges; one upload, one apply, one download
-    NH_CUDA(ctx, cudaMemcpyAsync(op->hbuf_in, du_h, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    NH_CUDA(ctx, cudaMemsetAsync(op->hbuf_out, 0, bytes, ctx->stream));
-    nh_status st = launch_apply_range(op, prec, op->hbuf_in, op->hbuf_out, 0, sp->ne, ctx->stream);
-    if (st != NH_OK) return st;
-    NH_CUDA(ctx, cudaMemcpyAsync(y_h, op->hbuf_out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  if (sp->hex) {
+    // unstructured mesh in first-touch numbering: elements [e0, e1) read du on the
+    // node prefix [0, hex_need[e1 - 1]) and leave y final below hex_fin[e1]; chunks
+    // of elements (FP32: whole kernel batches) with the same three-stream overlap
+    const int64_t ne = sp->ne, al = prec == NH_F32 ? nh_epb(sp->Q) : 1;
+    const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(8, ne / al));
+    while (ctx->ev_chunk.size() < 2 * (size_t)nch) {
+      cudaEvent_t ev;
+      NH_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      ctx->ev_chunk.push_back(ev);
+    }
+    const char* hin = static_cast<const char*>(du_h);
+    char* hout = static_cast<char*>(y_h);
+    char* din = static_cast<char*>(op->hbuf_in);
+    char* dout = static_cast<char*>(op->hbuf_out);
+    NH_CUDA(ctx, cudaMemsetAsync(dout, 0, bytes, ctx->stream));
+    NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[0], ctx->stream));
+    NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_chunk[0], 0));
+    int64_t up = 0, down = 0;  // DoF uploaded / downloaded so far
+    for (int c = 0; c < nch; c++) {
+      const int64_t e0 = ne * c / nch / al * al;
+      const int64_t e1 = c + 1 == nch ? ne : ne * (c + 1) / nch / al * al;
+      if (e1 <= e0) continue;
+      const int64_t need = 3 * sp->hex_need[e1 - 1];
+      if (need > up) {
+        NH_CUDA(ctx, cudaMemcpyAsync(din + w * up, hin + w * up, w * (need - up), cudaMemcpyHostToDevice, ctx->s_in));
+        up = need;
+      }
+      NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c], ctx->s_in));
+      NH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_chunk[2 * c], 0));
+      nh_status st = launch_apply_range(op, prec, din, dout, e0, e1, ctx->stream);
+      if (st != NH_OK) return st;
+      NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c + 1], ctx->stream));
+      const int64_t fin = c + 1 == nch ? sp->n_dof : 3 * sp->hex_fin[e1];
+      if (fin > down) {
+        NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_chunk[2 * c + 1], 0));
+        NH_CUDA(ctx, cudaMemcpyAsync(hout + w * down, dout + w * down, w * (fin - down), cudaMemcpyDeviceToHost,
+                                     ctx->s_out));
+        down = fin;
+      }
+    }
+    NH_CUDA(ctx, cudaStreamSynchronize(ctx->s_out));
     NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return NH_OK;
   }

@@ -106,6 +106,8 @@ struct nh_space_s {
   bool hex = false;               // built by nh_space_hex (unstructured); nx = ny = nz = 0
   std::vector<int64_t> hex8_host; // hex: [ne][8] vertex ids
   std::vector<int> emap_host;     // hex: [ne][P^3] copy of emap (coarse Dirichlet masks)
+  std::vector<int64_t> hex_need;  // hex: 1 + largest node id of elements [0, e] (du prefix they read)
+  std::vector<int64_t> hex_fin;   // hex: smallest node id of elements [e, ne) (y below it is final)
   uint64_t mesh_hash = 0;         // FNV-1a of the mesh (dimensions or connectivity, and vertices)
   uint8_t* bc = nullptr;          // [n_nodes] bit c set = component c constrained (device)
   unsigned* emapb = nullptr;      // [ne][P^3] node id | constrained bits << 29 (FP32 apply)

@@ -85,7 +85,7 @@ class HexCase:
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_hex_jacobian_apply(nhctx, kind, p):
     ctx, _ = nhctx
-    Vh, H = make_mesh(kind, (3, 3, 2), seed=p)
+    Vh, H = make_mesh(kind, (6, 4, 3) if p <= 2 else (3, 3, 2), seed=p)
     c = HexCase(ctx, Vh, H, p, seed=p)
     nh = c.nh
     du = inputs.normal_vector(c.sp.n_dof, seed=9)
@@ -98,9 +98,14 @@ def test_hex_jacobian_apply(nhctx, kind, p):
         y = torch.empty(c.sp.n_dof, dtype=dtype, device="cuda")
         nh.nh_jacobian_apply(ctx, c.op, dev(c.to_lib(x), dtype), y, prec=prec)
         assert rel(c.to_oracle(host(y)), r) < tol, prec
+    # host buffers: chunks of elements over node prefixes (first-touch numbering)
     yh = np.empty(c.sp.n_dof)
     nh.nh_jacobian_apply_host(ctx, c.op, np.ascontiguousarray(c.to_lib(du)), yh)
     assert rel(c.to_oracle(yh), ref) < 1e-12
+    x32 = du.astype(np.float32)
+    yh32 = np.empty(c.sp.n_dof, dtype=np.float32)
+    nh.nh_jacobian_apply_host(ctx, c.op, np.ascontiguousarray(c.to_lib(x32)), yh32)
+    assert rel(c.to_oracle(yh32), fem.jacobian_apply(c.sp, c.state, x32.astype(np.float64), c.mask)) < 2e-5
     c.close()
 
 
