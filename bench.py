@@ -161,11 +161,13 @@ class HexCase(Case):
     element's local frame a random cube rotation; ``shuffled`` also permutes the
     vertex ids and the element order (no locality left in the element map)."""
 
-    def __init__(self, nh, torch, ctx, p, n, shuffled):
+    def __init__(self, nh, torch, ctx, p, n, shuffled, morton=False):
         self.nh, self.ctx, self.p, self.n = nh, ctx, p, n
         from paper_2204_01722_b300 import inputs
         V = inputs.box_vertices(n, n, n, perturb=PERTURB, seed=SEED)
         Vh, H = inputs.hex_mesh_from_box(n, n, n, V, seed=SEED, permute=shuffled)
+        if morton:  # elements reordered along the Z-order curve before numbering
+            H = H[nh.nh_hex_morton_order(Vh, H)]
         self.space, self.nn, self.nd = nh.nh_space_hex(ctx, Vh, H, p, p + 1)
         X = nh.nh_space_coords(ctx, self.space, self.nn)
         m = np.zeros((self.nn, 3), dtype=bool)
@@ -321,8 +323,8 @@ def run_nh(args):
                     layouts.append({"layout": lname, "p": 3, "n": c.n, "n_dof": c.nd, "prec": pr,
                                     "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4)})
                 c.close()
-            for shuffled in (False, True):
-                c = HexCase(nh, torch, ctx, 3, DEFAULT_N[3], shuffled)
+            for shuffled, morton in ((False, False), (True, False), (True, True)):
+                c = HexCase(nh, torch, ctx, 3, DEFAULT_N[3], shuffled, morton)
                 for pr in ("f64", "f32"):
                     kernel_ms(nh, ctx, c, pr, 5)
                     k = kernel_ms(nh, ctx, c, pr, 20)
@@ -335,7 +337,8 @@ def run_nh(args):
                         nh.nh_jacobian_apply_host(ctx, c.op, hin, hout, prec=PREC[pr])
                     te = (time.perf_counter() - t0) / 5
                     hexes.append({"mesh": "unstructured path, rotated element frames" +
-                                          (", shuffled ids and elements" if shuffled else ", box element order"),
+                                          (", shuffled ids and elements" if shuffled else ", box element order") +
+                                          (", then Z-order element order" if morton else ""),
                                   "p": 3, "n": c.n, "n_dof": c.nd, "prec": pr,
                                   "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4),
                                   "gdofs_e2e": round(c.nd / te / 1e9, 3)})

@@ -143,6 +143,13 @@ nh_status nh_hex_mesh_numbering(int64_t nv, const double* xyz, int64_t ne, const
  * [nnzb] int32) non-NULL also the pattern, columns sorted per row.
  * Errors: NH_ERR_ARG (ids outside [0, n_nodes)). */
 nh_status nh_q1_block_pattern(int64_t ne, int64_t n_nodes, const int* emap, int64_t* nnzb, int64_t* rowptr, int* col);
+/* Host only: an element order for locality.  perm (HOST [ne]) receives the
+ * elements sorted along a Z-order (Morton) curve through their centroids
+ * (21 bits per axis of the bounding box): perm[k] is the element to place k-th.
+ * Building the space from hex8 rows in that order (and per-element data in the
+ * same order) makes neighbouring elements, and through the first-touch
+ * numbering their nodes, neighbours in memory.  Errors: NH_ERR_ARG. */
+nh_status nh_hex_morton_order(int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8, int64_t* perm);
 /* Node coordinates, HOST out [n_nodes][3]. */
 nh_status nh_space_coords(nh_space s, double* xyz_host);
 /* Dirichlet DoFs: HOST array [n_dof], nonzero = constrained.  Copied; synchronises. */

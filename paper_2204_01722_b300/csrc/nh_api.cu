@@ -345,6 +345,15 @@ extern "C" nh_status nh_hex_mesh_numbering(int64_t nv, const double* xyz, int64_
   return NH_OK;
 }
 
+extern "C" nh_status nh_hex_morton_order(int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8,
+                                         int64_t* perm) {
+  if (!xyz || !hex8 || !perm || nv < 1 || ne < 1) return NH_ERR_ARG;
+  for (int64_t i = 0; i < 8 * ne; i++)
+    if (hex8[i] < 0 || hex8[i] >= nv) return NH_ERR_ARG;
+  nh_hex_morton(nv, xyz, ne, hex8, perm);
+  return NH_OK;
+}
+
 extern "C" nh_status nh_q1_block_pattern(int64_t ne, int64_t n_nodes, const int* emap, int64_t* nnzb, int64_t* rowptr,
                                          int* col) {
   if (!emap || !nnzb || ne < 0 || n_nodes < 1) return NH_ERR_ARG;

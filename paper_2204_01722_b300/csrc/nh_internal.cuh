@@ -51,6 +51,8 @@ std::string nh_hex_numbering(int64_t nv, const double* xyz, int64_t ne, const in
                              std::vector<int>& emap, std::vector<double>& coords, int64_t& n_nodes);
 // true when two spaces discretise the same mesh (box dimensions and vertices, or hex connectivity)
 bool nh_same_mesh(nh_space a, nh_space b);
+// Z-order of the elements by centroid: perm[k] = element placed k-th (nh_mesh.cu)
+void nh_hex_morton(int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8, int64_t* perm);
 void nh_lagrange(int n, const double* nodes, int m, const double* pts, double* val, double* der);
 void nh_tabulate(int p, int q, Tab1D* t);
 

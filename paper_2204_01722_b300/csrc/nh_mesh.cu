@@ -239,3 +239,41 @@ std::string nh_hex_numbering(int64_t nv, const double* xyz, int64_t ne, const in
   }
   return std::string();
 }
+
+// Z-order (Morton) ordering of the elements by centroid: centroids scaled to the
+// bounding box, 21 bits per axis interleaved into a 63-bit key, stable sort.
+// Elements close in space become close in order, and with first-touch numbering
+// so do their nodes.
+void nh_hex_morton(int64_t nv, const double* xyz, int64_t ne, const int64_t* hex8, int64_t* perm) {
+  (void)nv;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  std::vector<double> cen((size_t)3 * ne);
+  for (int64_t e = 0; e < ne; e++)
+    for (int d = 0; d < 3; d++) {
+      double s = 0.0;
+      for (int v = 0; v < 8; v++) s += xyz[3 * hex8[8 * e + v] + d];
+      cen[3 * e + d] = s / 8.0;
+      lo[d] = std::min(lo[d], s / 8.0);
+      hi[d] = std::max(hi[d], s / 8.0);
+    }
+  auto spread = [](uint64_t x) {  // 21 bits -> every third bit
+    x &= 0x1fffffull;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+  };
+  std::vector<std::pair<uint64_t, int64_t>> key((size_t)ne);
+  for (int64_t e = 0; e < ne; e++) {
+    uint64_t k = 0;
+    for (int d = 0; d < 3; d++) {
+      const double w = hi[d] > lo[d] ? (cen[3 * e + d] - lo[d]) / (hi[d] - lo[d]) : 0.0;
+      k |= spread((uint64_t)std::min(2097151.0, std::max(0.0, w * 2097151.0))) << d;
+    }
+    key[e] = {k, e};
+  }
+  std::stable_sort(key.begin(), key.end());
+  for (int64_t i = 0; i < ne; i++) perm[i] = key[i].second;
+}

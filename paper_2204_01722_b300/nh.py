@@ -39,6 +39,7 @@ SIGNATURES = {
     "nh_op_assemble_q1": (_st, [_vp, C.POINTER(C.c_int64), _vp, _vp, _vp]),
     "nh_hex_mesh_numbering": (_st, [C.c_int64, _vp, C.c_int64, _vp, C.c_int, C.POINTER(C.c_int64), _vp, _vp,
                                     C.c_char_p, C.c_int64]),
+    "nh_hex_morton_order": (_st, [C.c_int64, _vp, C.c_int64, _vp, _vp]),
     "nh_q1_block_pattern": (_st, [C.c_int64, C.c_int64, _vp, C.POINTER(C.c_int64), _vp, _vp]),
     "nh_space_hex": (_st, [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int, C.c_int, C.POINTER(_vp),
                            C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -233,6 +234,17 @@ def nh_hex_mesh_numbering(vertices, hex8, p):
     if st != NH_OK:
         raise NhError(st, err.value.decode())
     return emap, X
+
+
+def nh_hex_morton_order(vertices, hex8):
+    """Host-only Z-order of the elements by centroid: perm with hex8[perm] the reordered mesh."""
+    V = np.ascontiguousarray(vertices, dtype=np.float64).reshape(-1, 3)
+    H = np.ascontiguousarray(hex8, dtype=np.int64).reshape(-1, 8)
+    perm = np.empty(H.shape[0], dtype=np.int64)
+    st = lib.nh_hex_morton_order(V.shape[0], _ptr(V), H.shape[0], _ptr(H), _ptr(perm))
+    if st != NH_OK:
+        raise NhError(st, "nh_hex_morton_order: invalid mesh")
+    return perm
 
 
 def nh_q1_block_pattern(emap, n_nodes):

@@ -65,3 +65,17 @@ def test_q1_block_pattern(kind):
     assert got == ref and len(got) == len(cl)
     for r in range(X.shape[0]):
         assert np.all(np.diff(cl[rp[r]:rp[r + 1]]) > 0)
+
+
+def test_morton_order_restores_locality():
+    """A shuffled mesh reordered along the Z-order curve: perm is a permutation, and
+    with first-touch numbering an element's nodes span a small id range again."""
+    Vh, H = inputs.hex_mesh_from_box(12, 12, 12, inputs.box_vertices(12, 12, 12, perturb=0.1, seed=1), seed=2)
+    perm = nh.nh_hex_morton_order(Vh, H)
+    assert np.array_equal(np.sort(perm), np.arange(len(H)))
+
+    def spread(hh):
+        emap, _ = nh.nh_hex_mesh_numbering(Vh, hh, 2)
+        return np.median(emap.max(axis=1) - emap.min(axis=1))
+    s_shuffled, s_morton = spread(H), spread(H[perm])
+    assert s_morton * 5 < s_shuffled, (s_morton, s_shuffled)
