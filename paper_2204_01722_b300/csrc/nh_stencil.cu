@@ -514,10 +514,14 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg(KsPcg a) {
     a.p[i] = zv;
     loc += rv * zv;
   }
+  // the initial r . z goes through part2: its next writer (the update phase of
+  // the first iteration) runs only after the barrier that follows the first
+  // p . q, so no block can overwrite a partial that another is still reading
+  // (part1 is rewritten by the first p . q without a barrier in between)
   double s = block_sum(loc, sh);
-  if (threadIdx.x == 0) part1[blockIdx.x] = s;
+  if (threadIdx.x == 0) part2[blockIdx.x] = s;
   if (!grid_sync_bounded(cnt, gen, a.err)) return;
-  double rz = grid_total(part1, sh), rz0;
+  double rz = grid_total(part2, sh), rz0;
   int k = 0, bad = 0;
   bool done = false;
   if (a.warm) {
