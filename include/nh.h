@@ -276,7 +276,9 @@ typedef struct {
   int lanczos_iters;       /* CG/Lanczos steps for lambda_max on a rough seed (10) */
   double coarse_rtol;      /* coarsest-level Jacobi-PCG relative tolerance, natural norm (1e-3) */
   int coarse_maxit;        /* (2000) */
-  int coarse_assembled;    /* 1: a p = 1 coarsest level is assembled into a 27-point block stencil */
+  int coarse_assembled;    /* 1: a p = 1 coarsest level is assembled: a 27-point block stencil on
+                              nh_space_box meshes, COO-assembled 3x3 block rows (nh_op_assemble_q1)
+                              on nh_space_hex meshes; 0: applied matrix-free */
   int mixed;               /* 1: FP32 applies, smoothers and transfers on levels with p > 1 */
   uint64_t seed;           /* seed of the rough Lanczos start vector (splitmix64, uniform(-1, 1)) */
   int load_steps;          /* pseudo-time steps t_k = k / load_steps (1) */
@@ -310,7 +312,8 @@ typedef struct {
                               1 = PCG with a geometric multigrid V-cycle on the vertex lattice (Galerkin
                               P^T A P stencils, damped Jacobi, exact solve on 3^3 nodes), used when the
                               lattice halves evenly down to 3 nodes per direction and the coarsest
-                              stencil is positive definite, else Jacobi-PCG */
+                              stencil is positive definite, else Jacobi-PCG; box meshes only
+                              (NH_ERR_UNSUPPORTED from nh_mg_create on nh_space_hex meshes) */
 } nh_mg_opts;
 
 typedef struct {
