@@ -13,7 +13,13 @@ Prints ONE JSON line (rank 0).  N > 1 (torchrun) runs independent replicas,
 one per GPU: the operator has no exchange step on a single-GPU mesh, so the
 job value is the sum of all ranks' DoF over the slowest rank's time.
 The reference arm (--impl reference) times the plain FP64 CPU oracle on a
-bounded window of the same workload.
+bounded window of the same workload.  Besides the headline, the line carries the
+roofline of the timed kernel, the end-to-end rate through the host-buffer entry
+point, a sweep over Q2-Q4 and the three arithmetic paths, the unstructured-mesh
+and quadrature-layout variants, and the solve comparison (plain FP64 p-MG
+against the chosen solver).  Two further modes print their own line instead:
+--multiscale (mixed precision on Q3 64^3 with inclusions) and --hex-solve (the
+solve workload through the unstructured-mesh path).
 """
 import argparse
 import json
