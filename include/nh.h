@@ -424,14 +424,19 @@ nh_status nh_mg_collect(nh_mg mg, const double* b, int max_pairs, float* feats, 
  * elements, then a fixed-order sum), so repeated calls give identical results.
  * Scratch: a fixed 256 KiB array in the library's device image, held by every
  * GPU that loads the library until the process exits; n > NH_DOT_NOALLOC_MAX_N
- * returns NH_ERR_UNSUPPORTED.  The first call on each device looks up the
- * scratch address with that device current: make that first call before any
- * stream capture.  All calls share the one scratch array, which keeps the last
- * call's partial sums (no slot needs clearing: each call writes every slot it
- * reads); calls that can overlap on the GPU (two streams, two host threads)
- * race and must be serialised by the caller.
+ * returns NH_ERR_UNSUPPORTED.  The scratch address is per CUDA context: the
+ * first call in each context (the device's primary context, a fresh one after
+ * cudaDeviceReset, or a driver-API context of the caller's) looks it up with
+ * that context current and caches it under the context's id, so make that first
+ * call before any stream capture; a process that meets more than 64 contexts
+ * looks the address up on every call from then on.  All calls share the one
+ * scratch array, which keeps the last call's partial sums (no slot needs
+ * clearing: each call writes every slot it reads); calls that can overlap on
+ * the GPU (two streams, two host threads) race and must be serialised by the
+ * caller.
  * Errors: NH_ERR_ARG (n < 0, null or misaligned pointer), NH_ERR_UNSUPPORTED,
- * NH_ERR_CUDA (symbol lookup or launch failed). */
+ * NH_ERR_CUDA (symbol lookup or one of this call's two launches failed; an error
+ * left pending by earlier, unrelated work is neither reported nor cleared). */
 nh_status nh_dot_noalloc(void* cuda_stream, int64_t n, const double* x, const double* y, double* result);
 
 #ifdef __cplusplus

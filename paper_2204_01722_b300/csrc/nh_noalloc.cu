@@ -67,23 +67,82 @@ __global__ void __launch_bounds__(1024)
   if (threadIdx.x == 0) *out = s;
 }
 
-// Device address of g_dot_scratch, looked up once per device with that device current.
-std::mutex g_lock;
-double* g_addr[64] = {nullptr};
+// Device address of g_dot_scratch.  The address belongs to a CUDA context, not
+// to a device number: after cudaDeviceReset the primary context is new and the
+// module is loaded again, and a driver-API context of its own on the same device
+// holds another copy.  So the lookup is cached per context, keyed by the
+// driver's context id (unique within the process, never reused), and redone for
+// every context met.  The two driver calls are reached through the runtime's
+// entry-point query, so the library does not link libcuda.  When they cannot be
+// had, or the cache is full, the address is looked up on every call.
+typedef int (*ctx_get_current_fn)(void** ctx);
+typedef int (*ctx_get_id_fn)(void* ctx, unsigned long long* id);
 
-cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+struct Slot {
+  unsigned long long ctx_id;
+  double* addr;
+};
+
+std::mutex g_lock;
+bool g_fns_queried = false;
+ctx_get_current_fn g_get_current = nullptr;
+ctx_get_id_fn g_get_id = nullptr;
+constexpr int kSlots = 64;
+Slot g_slots[kSlots];
+int g_nslots = 0;
+
+cudaError_t lookup_symbol(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_dot_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  *out = static_cast<double*>(p);
+  return cudaSuccess;
+}
+
+// Id of the context current on this thread, or false if it cannot be had.
+bool current_ctx_id(unsigned long long* id) {
+  if (!g_get_current || !g_get_id) return false;
+  void* ctx = nullptr;
+  if (g_get_current(&ctx) != 0 || !ctx) return false;
+  return g_get_id(ctx, id) == 0;
+}
+
+cudaError_t scratch_for_current_context(double** out) {
   std::lock_guard<std::mutex> g(g_lock);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_dot_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double*>(p);
+  if (!g_fns_queried) {
+    g_fns_queried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_get_current = reinterpret_cast<ctx_get_current_fn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_get_id = reinterpret_cast<ctx_get_id_fn>(f);
   }
-  *out = g_addr[dev];
+  unsigned long long id = 0;
+  if (!current_ctx_id(&id)) {
+    // No context current yet (the runtime makes the primary one on its first
+    // call that needs it): look up, which creates it, then try the id again.
+    double* addr = nullptr;
+    const cudaError_t e = lookup_symbol(&addr);
+    if (e != cudaSuccess) return e;
+    *out = addr;
+    if (!current_ctx_id(&id)) return cudaSuccess;
+    if (g_nslots < kSlots) g_slots[g_nslots++] = Slot{id, addr};
+    return cudaSuccess;
+  }
+  for (int i = 0; i < g_nslots; ++i)
+    if (g_slots[i].ctx_id == id) {
+      *out = g_slots[i].addr;
+      return cudaSuccess;
+    }
+  double* addr = nullptr;
+  const cudaError_t e = lookup_symbol(&addr);
+  if (e != cudaSuccess) return e;
+  if (g_nslots < kSlots) g_slots[g_nslots++] = Slot{id, addr};
+  *out = addr;
   return cudaSuccess;
 }
 
@@ -96,12 +155,19 @@ extern "C" nh_status nh_dot_noalloc(void* cuda_stream, int64_t n, const double* 
   if (((uintptr_t)result % 8) || ((uintptr_t)x % 8) || ((uintptr_t)y % 8)) return NH_ERR_ARG;
   if (n > NH_DOT_NOALLOC_MAX_N) return NH_ERR_UNSUPPORTED;  // more partial sums than the scratch holds
   double* scratch = nullptr;
-  if (scratch_for_current_device(&scratch) != cudaSuccess) return NH_ERR_CUDA;
+  if (scratch_for_current_context(&scratch) != cudaSuccess) return NH_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  const int nb = (int)((n + kChunk - 1) / kChunk);
+  int nb = (int)((n + kChunk - 1) / kChunk);
   // Every partial slot that k_sum_chunks reads is written by k_dot_chunks of the
-  // same call, so nothing left by an earlier call needs clearing.
-  if (nb > 0) k_dot_chunks<<<nb, kThreads, 0, s>>>(n, x, y, scratch);
-  k_sum_chunks<<<1, 1024, 0, s>>>(scratch, nb, result);
-  return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
+  // same call, so nothing left by an earlier call needs clearing.  Each launch's
+  // own status is taken from cudaLaunchKernel, so an error left pending by
+  // unrelated earlier work is neither reported here nor cleared.
+  if (nb > 0) {
+    void* args[] = {&n, (void*)&x, (void*)&y, &scratch};
+    const cudaError_t e = cudaLaunchKernel((const void*)k_dot_chunks, dim3(nb), dim3(kThreads), args, 0, s);
+    if (e != cudaSuccess) return NH_ERR_CUDA;
+  }
+  void* args2[] = {&scratch, &nb, &result};
+  const cudaError_t e = cudaLaunchKernel((const void*)k_sum_chunks, dim3(1), dim3(1024), args2, 0, s);
+  return e == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }

@@ -19,10 +19,16 @@ def test_dot_noalloc_matches_dot(nhctx):
     ctx, stream = nhctx
     from paper_2204_01722_b300 import nh
     for n, seed in ((3_000_001, 1), (777, 5)):
-        x = torch.from_numpy(inputs.normal_vector(n, seed=seed)).cuda()
-        y = torch.from_numpy(inputs.normal_vector(n, seed=seed + 1)).cuda()
+        xh = inputs.normal_vector(n, seed=seed)
+        yh = inputs.normal_vector(n, seed=seed + 1)
+        x = torch.from_numpy(xh).cuda()
+        y = torch.from_numpy(yh).cuda()
         ref = nh.nh_dot(ctx, n, x, y)
-        scale = max(1.0, float(torch.linalg.norm(x)) * float(torch.linalg.norm(y)))
+        scale = max(1.0, float(np.linalg.norm(xh)) * float(np.linalg.norm(yh)))
+        # the allocating entry point itself agrees with a host sum computed apart
+        # from the library (math.fsum: correctly rounded)
+        import math
+        assert abs(ref - math.fsum((xh * yh).tolist())) <= 1e-12 * scale
         res = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
         nh.nh_dot_noalloc(stream.cuda_stream, n, x, y, res[0:1])
         nh.nh_dot_noalloc(stream.cuda_stream, n, x, y, res[1:2])
@@ -30,6 +36,8 @@ def test_dot_noalloc_matches_dot(nhctx):
         a, b = res.cpu().numpy()
         assert abs(a - ref) <= 1e-12 * scale
         assert abs(b - ref) <= 1e-12 * scale
+        exact = math.fsum((xh * yh).tolist())
+        assert abs(a - exact) <= 1e-12 * scale
         assert a == b          # fixed summation order
     # empty input gives 0; oversize n is refused before anything runs
     res = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
