@@ -387,7 +387,9 @@ def diagonal(space, state, mask=None, form="A"):
 def element_matrices(space, state, form="A"):
     """Element Jacobian matrices K[e, (l,c), (l',c')] (tiny meshes only)."""
     D = tangent(state, form)
-    K = np.einsum("dql,eqcdCD,Dqm->elcmC", space.Bxi, D, space.Bxi)
+    # K = sum_q B_xi^T D B_xi, the right product first: DB[e,q,c,d,m,C] = sum_D D[.., C, D] B_xi,D[q, m]
+    DB = np.einsum("eqcdCD,Dqm->eqcdmC", D, space.Bxi)
+    K = np.einsum("dql,eqcdmC->elcmC", space.Bxi, DB)
     P3 = space.P ** 3
     return K.reshape(space.ne, 3 * P3, 3 * P3)
 
