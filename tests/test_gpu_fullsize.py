@@ -1,15 +1,21 @@
 """Full-size parity in the launch configuration the benchmark times.
 
-Q3 on 48^3 elements (9,145,875 DoF) and Q2 on 74^3 / Q4 on 37^3 (~9.9 M DoF):
-the whole apply runs on the GPU; the oracle recomputes sampled outputs exactly
-from element windows.  A window is a 3x3x3 block of elements; every node that
-is not on a window face interior to the domain receives all of its element
-contributions from inside the window, so its value is complete and is
-compared with the GPU's.
+Q3 on 48^3 elements (9,145,875 DoF) and Q2 on 74^3 / Q4 on 37^3 (~9.9 M DoF),
+plus Q2 on 70^3 and Q4 on 35^3 (8.4 M DoF), whose x-element counts are
+multiples of the FP32 kernel's elements per block, so that its block-row
+scatter runs next to the uniaxial Dirichlet faces: the whole apply runs on the
+GPU in FP64, float-float and FP32; the oracle recomputes sampled outputs
+exactly from element windows.  A window is a 3x3x3 block of elements; every
+node that is not on a window face interior to the domain receives all of its
+element contributions from inside the window, so its value is complete and is
+compared with the GPU's, entry by entry against the sum of absolute
+contributions of that entry (|J| |du| on the window) and norm-wise over the
+window.
 """
 import numpy as np
 import pytest
 
+import parity
 from oracle import fem
 from paper_2204_01722_b300 import inputs
 
@@ -37,7 +43,7 @@ def window(V, n, e0, w, p, q):
     return sp, gid, ok
 
 
-@pytest.mark.parametrize("p,n", [(3, 48), (2, 74), (4, 37)])
+@pytest.mark.parametrize("p,n", [(3, 48), (2, 74), (4, 37), (2, 70), (4, 35)])
 def test_fullsize_sampled_parity(nhctx, p, n):
     ctx, _ = nhctx
     from paper_2204_01722_b300 import nh
@@ -59,11 +65,15 @@ def test_fullsize_sampled_parity(nhctx, p, n):
     du_d = torch.from_numpy(du).cuda()
     y = torch.empty(nd, dtype=torch.float64, device="cuda")
     nh.nh_jacobian_apply(ctx, op, du_d, y)
+    yx = torch.empty(nd, dtype=torch.float64, device="cuda")
+    nh.nh_jacobian_apply(ctx, op, du_d, yx, prec=nh.NH_F64X)
     y32 = torch.empty(nd, dtype=torch.float32, device="cuda")
     nh.nh_jacobian_apply(ctx, op, du_d.float(), y32)
     torch.cuda.current_stream().synchronize()
     yh = y.cpu().numpy().reshape(-1, 3)
+    yxh = yx.cpu().numpy().reshape(-1, 3)
     y32h = y32.double().cpu().numpy().reshape(-1, 3)
+    du32 = du.astype(np.float32).astype(np.float64)
     mat = None
     w = 3
     rng = np.random.default_rng(p)
@@ -77,11 +87,16 @@ def test_fullsize_sampled_parity(nhctx, p, n):
         mw = mask.reshape(-1, 3)[gid].ravel()
         st = fem.qp_state(sp, mat, uw)
         ref = fem.jacobian_apply(sp, st, dw, mw).reshape(-1, 3)
-        got = yh[gid]
+        sc = parity.jacobian_scale(sp, st, dw, mw).reshape(-1, 3)
+        d32 = du32.reshape(-1, 3)[gid].ravel()
+        ref32 = fem.jacobian_apply(sp, st, d32, mw).reshape(-1, 3)
+        sc32 = parity.jacobian_scale(sp, st, d32, mw).reshape(-1, 3)
         assert ok.sum() > 0
-        e64 = np.linalg.norm(got[ok] - ref[ok]) / np.linalg.norm(ref[ok])
-        e32 = np.linalg.norm(y32h[gid][ok] - ref[ok]) / np.linalg.norm(ref[ok])
-        assert e64 < TOL64, (e0, e64)
-        assert e32 < TOL32, (e0, e32)
+        for got, r, scl, tol, what in ((yh, ref, sc, TOL64, "FP64"), (yxh, ref, sc, TOL64, "float-float"),
+                                       (y32h, ref32, sc32, TOL32, "FP32")):
+            g = got[gid][ok]
+            e = np.linalg.norm(g - r[ok]) / np.linalg.norm(r[ok])
+            assert e < tol, (what, e0, e)
+            parity.check(g, r[ok], scl[ok], tol, f"{what} window at {e0}")
     nh.nh_op_destroy(op)
     nh.nh_space_destroy(s)

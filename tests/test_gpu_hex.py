@@ -6,12 +6,16 @@ matching coordinates), so vectors are carried across by node position.  Meshes:
 the perturbed box written as an unstructured mesh with every element's local
 frame a random cube rotation and ids and element order shuffled, and an L-shaped
 subset of it.  Tolerances as for the box: 1e-12 (FP64 and float-float), 2e-5
-(FP32), 1e-7 for a linear solve to 1e-11 against a sparse direct solve.
+(FP32), each both norm-wise and entry by entry against the sum of absolute
+contributions of the entry (``parity.check``); 1e-7 for a linear solve to 1e-11
+against a sparse direct solve (norm-wise, and per entry against the largest
+entry).
 """
 import numpy as np
 import pytest
 from scipy.spatial import cKDTree
 
+import parity
 from oracle import fem
 from paper_2204_01722_b300 import inputs
 
@@ -21,6 +25,13 @@ pytestmark = pytest.mark.gpu
 
 def rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def agree(got, ref, scale, tol, what=""):
+    got = np.asarray(got, dtype=np.float64).ravel()
+    e = rel(got, ref)
+    assert e < tol, f"{what}: norm-wise {e:.3e} >= {tol:.1e}"
+    parity.check(got, ref, scale, tol, what)
 
 
 def dev(x, dtype=torch.float64):
@@ -91,21 +102,23 @@ def test_hex_jacobian_apply(nhctx, kind, p):
     du = inputs.normal_vector(c.sp.n_dof, seed=9)
     ref = fem.jacobian_apply(c.sp, c.state, du, c.mask)
     assert abs(c.minJ - c.state["J"].min()) < 1e-13
+    sc = parity.jacobian_scale(c.sp, c.state, du, c.mask)
+    x32 = du.astype(np.float32)
+    ref32 = fem.jacobian_apply(c.sp, c.state, x32.astype(np.float64), c.mask)
+    sc32 = parity.jacobian_scale(c.sp, c.state, x32.astype(np.float64), c.mask)
     for prec, dtype, tol in ((nh.NH_F64, torch.float64, 1e-12), (nh.NH_F64X, torch.float64, 1e-12),
                              (nh.NH_F32, torch.float32, 2e-5)):
-        x = du.astype(np.float32).astype(np.float64) if dtype == torch.float32 else du
-        r = ref if dtype == torch.float64 else fem.jacobian_apply(c.sp, c.state, x, c.mask)
+        x, r, scl = (x32.astype(np.float64), ref32, sc32) if dtype == torch.float32 else (du, ref, sc)
         y = torch.empty(c.sp.n_dof, dtype=dtype, device="cuda")
         nh.nh_jacobian_apply(ctx, c.op, dev(c.to_lib(x), dtype), y, prec=prec)
-        assert rel(c.to_oracle(host(y)), r) < tol, prec
+        agree(c.to_oracle(host(y)), r, scl, tol, f"hex apply, prec {prec}")
     # host buffers: chunks of elements over node prefixes (first-touch numbering)
     yh = np.empty(c.sp.n_dof)
     nh.nh_jacobian_apply_host(ctx, c.op, np.ascontiguousarray(c.to_lib(du)), yh)
-    assert rel(c.to_oracle(yh), ref) < 1e-12
-    x32 = du.astype(np.float32)
+    agree(c.to_oracle(yh), ref, sc, 1e-12, "hex host apply FP64")
     yh32 = np.empty(c.sp.n_dof, dtype=np.float32)
     nh.nh_jacobian_apply_host(ctx, c.op, np.ascontiguousarray(c.to_lib(x32)), yh32)
-    assert rel(c.to_oracle(yh32), fem.jacobian_apply(c.sp, c.state, x32.astype(np.float64), c.mask)) < 2e-5
+    agree(c.to_oracle(yh32), ref32, sc32, 2e-5, "hex host apply FP32")
     c.close()
 
 
@@ -120,10 +133,12 @@ def test_hex_residual_and_diagonal(nhctx, kind):
     g[c.mask] = -0.01
     r = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
     nh.nh_residual(ctx, c.op, dev(c.to_lib(c.u)), dev(c.to_lib(g)), r)
-    assert rel(c.to_oracle(host(r)), fem.residual(c.sp, c.mat, c.u, c.mask, g)) < 1e-12
+    agree(c.to_oracle(host(r)), fem.residual(c.sp, c.mat, c.u, c.mask, g),
+          parity.residual_scale(c.sp, c.mat, c.u, c.mask, g), 1e-12, "hex residual")
     d = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
     nh.nh_jacobian_diagonal(ctx, c.op, d)
-    assert rel(c.to_oracle(host(d)), fem.diagonal(c.sp, c.state, c.mask)) < 1e-12
+    agree(c.to_oracle(host(d)), fem.diagonal(c.sp, c.state, c.mask), parity.diagonal_scale(c.sp, c.state, c.mask),
+          1e-12, "hex diagonal")
     c.close()
 
 
@@ -140,13 +155,14 @@ def test_hex_transfers(nhctx):
     uc = inputs.normal_vector(cs.n_dof, seed=8)
     uf = torch.empty(f.sp.n_dof, dtype=torch.float64, device="cuda")
     nh.nh_prolong(ctx, csp, f.space, dev(uc[cdp]), uf)
-    assert rel(f.to_oracle(host(uf)), fem.prolong(cs, f.sp, uc)) < 1e-12
+    agree(f.to_oracle(host(uf)), fem.prolong(cs, f.sp, uc), parity.prolong_scale(cs, f.sp, uc), 1e-12,
+          "hex prolongation")
     rf = inputs.normal_vector(f.sp.n_dof, seed=9)
     rc = torch.empty(cs.n_dof, dtype=torch.float64, device="cuda")
     nh.nh_restrict(ctx, f.space, csp, dev(f.to_lib(rf)), rc)
     out = np.empty(cs.n_dof)
     out[cdp] = host(rc)
-    assert rel(out, fem.restrict(f.sp, cs, rf)) < 1e-12
+    agree(out, fem.restrict(f.sp, cs, rf), parity.restrict_scale(f.sp, cs, rf), 1e-12, "hex restriction")
     nh.nh_space_destroy(csp)
     f.close()
 
@@ -211,7 +227,9 @@ def test_hex_linear_solve_matches_direct(nhctx, mixed, assembled):
     b[c.mask] = 0.0
     x = torch.zeros(c.sp.n_dof, dtype=torch.float64, device="cuda")
     rep = nh.nh_linear_solve(ctx, mg, dev(c.to_lib(b)), x, rtol=1e-11, maxit=300, norm=1)
-    assert rel(c.to_oracle(host(x)), spla.spsolve(J.tocsc(), b)) < 1e-7
+    ref = spla.spsolve(J.tocsc(), b)
+    assert rel(c.to_oracle(host(x)), ref) < 1e-7
+    parity.check_inf(c.to_oracle(host(x)), ref, 1e-7, "hex linear solve")
     assert rep.krylov_its < 150
     nh.nh_mg_destroy(mg)
     c.close()

@@ -13,6 +13,7 @@
 import numpy as np
 import pytest
 
+import parity
 from oracle import fem, learned
 from paper_2204_01722_b300 import inputs
 
@@ -59,7 +60,9 @@ def test_forward_and_gradient(nhctx, sample, bf16):
     gh = g.double().cpu().numpy()
     if not bf16:
         assert rel(y.double().cpu().numpy(), y_ref) < 2e-5
+        parity.check_inf(y.double().cpu().numpy(), y_ref, 2e-5, "FP32 forward")
         assert rel(gh, g_ref) < 2e-4
+        parity.check_inf(gh, g_ref, 2e-4, "FP32 gradient")
         assert abs(loss - learned.loss(th32, x32, t32, LEVELS, CH)) < 1e-5 * loss
     else:
         assert rel(y.double().cpu().numpy(), y_ref) < 3e-2

@@ -1,8 +1,11 @@
 """GPU parity: every operator entry point of libnh against the FP64 oracle on the
 same seeded inputs.
 
-Tolerances (relative, norm-wise: entries that nearly cancel make entry-wise
-checks meaningless, Sec. II-B sums many element contributions):
+Every result is checked twice: norm-wise (relative 2-norm) and entry by
+entry against the sum of absolute contributions of that entry
+(``parity.check``: |y_i - ref_i| <= tol * (|J| |du|)_i and the like), so that a
+wrong value in a few entries cannot hide under the norm of the whole vector.
+Tolerances, in both forms:
 * FP64 paths: 1e-12.
 * FP32 paths: 2e-5 -- unit roundoff 6e-8 times a few hundred rounded
   operations along the gather / six contraction stages / pointwise /
@@ -11,6 +14,7 @@ checks meaningless, Sec. II-B sums many element contributions):
 import numpy as np
 import pytest
 
+import parity
 from oracle import fem
 from paper_2204_01722_b300 import inputs
 
@@ -25,6 +29,14 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64).ravel()
     b = np.asarray(b, dtype=np.float64).ravel()
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def agree(got, ref, scale, tol, what=""):
+    """Norm-wise and entry-wise agreement (module docstring)."""
+    got = np.asarray(got, dtype=np.float64).ravel()
+    e = rel(got, ref)
+    assert e < tol, f"{what}: norm-wise {e:.3e} >= {tol:.1e}"
+    parity.check(got, ref, scale, tol, what)
 
 
 def dev(x, dtype=torch.float64):
@@ -78,8 +90,9 @@ def test_jacobian_apply_fp64(nhctx, n, p, q, layout):
     du = inputs.normal_vector(c.sp.n_dof, seed=7)
     y = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
     c.nh.nh_jacobian_apply(ctx, c.op, dev(du), y)
-    ref = fem.jacobian_apply(c.sp, c.state, du, c.mask, form="A" if layout == 0 else "B")
-    assert rel(host(y), ref) < TOL64
+    form = "A" if layout == 0 else "B"
+    ref = fem.jacobian_apply(c.sp, c.state, du, c.mask, form=form)
+    agree(host(y), ref, parity.jacobian_scale(c.sp, c.state, du, c.mask, form), TOL64, "FP64 apply")
     assert abs(c.minJ - c.state["J"].min()) < 1e-13
     c.close()
 
@@ -94,8 +107,9 @@ def test_jacobian_apply_f64x(nhctx, n, p, q, layout):
     du = inputs.normal_vector(c.sp.n_dof, seed=22)
     y = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
     c.nh.nh_jacobian_apply(ctx, c.op, dev(du), y, prec=c.nh.NH_F64X)
-    ref = fem.jacobian_apply(c.sp, c.state, du, c.mask, form="A" if layout == 0 else "B")
-    assert rel(host(y), ref) < TOL64
+    form = "A" if layout == 0 else "B"
+    ref = fem.jacobian_apply(c.sp, c.state, du, c.mask, form=form)
+    agree(host(y), ref, parity.jacobian_scale(c.sp, c.state, du, c.mask, form), TOL64, "float-float apply")
     c.close()
 
 
@@ -107,8 +121,9 @@ def test_jacobian_apply_fp32(nhctx, n, p, layout):
     du = inputs.normal_vector(c.sp.n_dof, seed=8)
     y = torch.empty(c.sp.n_dof, dtype=torch.float32, device="cuda")
     c.nh.nh_jacobian_apply(ctx, c.op, dev(du, torch.float32), y)
-    ref = fem.jacobian_apply(c.sp, c.state, du.astype(np.float32).astype(np.float64), c.mask)
-    assert rel(host(y), ref) < TOL32
+    du32 = du.astype(np.float32).astype(np.float64)
+    ref = fem.jacobian_apply(c.sp, c.state, du32, c.mask)
+    agree(host(y), ref, parity.jacobian_scale(c.sp, c.state, du32, c.mask), TOL32, "FP32 apply")
     c.close()
 
 
@@ -123,8 +138,9 @@ def test_jacobian_apply_fp32_block_rows(nhctx, n, p, mask):
     du = inputs.normal_vector(c.sp.n_dof, seed=18)
     y = torch.empty(c.sp.n_dof, dtype=torch.float32, device="cuda")
     c.nh.nh_jacobian_apply(ctx, c.op, dev(du, torch.float32), y)
-    ref = fem.jacobian_apply(c.sp, c.state, du.astype(np.float32).astype(np.float64), c.mask)
-    assert rel(host(y), ref) < TOL32
+    du32 = du.astype(np.float32).astype(np.float64)
+    ref = fem.jacobian_apply(c.sp, c.state, du32, c.mask)
+    agree(host(y), ref, parity.jacobian_scale(c.sp, c.state, du32, c.mask), TOL32, "FP32 block-row apply")
     c.close()
 
 
@@ -136,7 +152,13 @@ def test_jacobian_apply_inclusions_and_empty_mask(nhctx):
     du = inputs.normal_vector(c.sp.n_dof, seed=9)
     y = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
     c.nh.nh_jacobian_apply(ctx, c.op, dev(du), y)
-    assert rel(host(y), fem.jacobian_apply(c.sp, c.state, du)) < TOL64
+    agree(host(y), fem.jacobian_apply(c.sp, c.state, du), parity.jacobian_scale(c.sp, c.state, du), TOL64,
+          "FP64 apply, inclusions")
+    y32 = torch.empty(c.sp.n_dof, dtype=torch.float32, device="cuda")
+    c.nh.nh_jacobian_apply(ctx, c.op, dev(du, torch.float32), y32)
+    du32 = du.astype(np.float32).astype(np.float64)
+    agree(host(y32), fem.jacobian_apply(c.sp, c.state, du32), parity.jacobian_scale(c.sp, c.state, du32), TOL32,
+          "FP32 apply, inclusions")
     c.close()
 
 
@@ -146,7 +168,8 @@ def test_single_element_and_host_apply(nhctx):
     du = inputs.normal_vector(c.sp.n_dof, seed=1)
     yh = np.empty(c.sp.n_dof)
     c.nh.nh_jacobian_apply_host(ctx, c.op, du, yh)
-    assert rel(yh, fem.jacobian_apply(c.sp, c.state, du, c.mask)) < TOL64
+    agree(yh, fem.jacobian_apply(c.sp, c.state, du, c.mask), parity.jacobian_scale(c.sp, c.state, du, c.mask), TOL64,
+          "host apply, one element")
     c.close()
 
 
@@ -158,15 +181,14 @@ def test_host_apply_pipelined(nhctx, n, p):
     ctx, _ = nhctx
     c = Case(ctx, n, p, seed=23)
     du = inputs.normal_vector(c.sp.n_dof, seed=24)
-    ref = fem.jacobian_apply(c.sp, c.state, du, c.mask)
     for prec, dt, tol in ((c.nh.NH_F64, np.float64, TOL64), (c.nh.NH_F64X, np.float64, TOL64),
                           (c.nh.NH_F32, np.float32, TOL32)):
         x = torch.from_numpy(du.astype(dt)).pin_memory()
         y = torch.empty_like(x).pin_memory()
         c.nh.nh_jacobian_apply_host(ctx, c.op, x, y, prec=prec)
-        r = ref if dt == np.float64 else fem.jacobian_apply(c.sp, c.state, du.astype(np.float32).astype(np.float64),
-                                                             c.mask)
-        assert rel(y.numpy(), r) < tol
+        xin = du.astype(dt).astype(np.float64)
+        agree(y.numpy(), fem.jacobian_apply(c.sp, c.state, xin, c.mask),
+              parity.jacobian_scale(c.sp, c.state, xin, c.mask), tol, f"pipelined host apply, prec {prec}")
     c.close()
 
 
@@ -178,7 +200,7 @@ def test_residual(nhctx, n, p, q):
     r = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
     c.nh.nh_residual(ctx, c.op, c.ud, dev(g), r)
     ref = fem.residual(c.sp, c.mat, c.u, c.mask, g)
-    assert rel(host(r), ref) < TOL64
+    agree(host(r), ref, parity.residual_scale(c.sp, c.mat, c.u, c.mask, g), TOL64, "residual")
     c.close()
 
 
@@ -189,11 +211,13 @@ def test_diagonal(nhctx, n, p, q, layout):
     c = Case(ctx, n, p, q, layout=layout, seed=12)
     d = torch.empty(c.sp.n_dof, dtype=torch.float64, device="cuda")
     c.nh.nh_jacobian_diagonal(ctx, c.op, d)
-    ref = fem.diagonal(c.sp, c.state, c.mask, form="A" if layout == 0 else "B")
-    assert rel(host(d), ref) < TOL64
+    form = "A" if layout == 0 else "B"
+    ref = fem.diagonal(c.sp, c.state, c.mask, form=form)
+    sc = parity.diagonal_scale(c.sp, c.state, c.mask, form)
+    agree(host(d), ref, sc, TOL64, "FP64 diagonal")
     d32 = torch.empty(c.sp.n_dof, dtype=torch.float32, device="cuda")
     c.nh.nh_jacobian_diagonal(ctx, c.op, d32)
-    assert rel(host(d32), ref) < TOL32
+    agree(host(d32), ref, sc, TOL32, "FP32 diagonal")
     c.close()
 
 
@@ -217,17 +241,20 @@ def test_rediscretized_coarse_operator(nhctx, pf, pc, layout):
     assert abs(mj - st["J"].min()) < 1e-13
     du = inputs.normal_vector(ndc, seed=20)
     form = "A" if layout == 0 else "B"
-    ref = fem.jacobian_apply(spc, st, du, maskc, form=form)
     for dt, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
         y = torch.empty(ndc, dtype=dt, device="cuda")
         nh.nh_jacobian_apply(ctx, opc, dev(du, dt), y)
-        assert rel(host(y), ref) < tol
+        xin = du if dt == torch.float64 else du.astype(np.float32).astype(np.float64)
+        agree(host(y), fem.jacobian_apply(spc, st, xin, maskc, form=form),
+              parity.jacobian_scale(spc, st, xin, maskc, form), tol, f"rediscretised apply {dt}")
     y = torch.empty(ndc, dtype=torch.float64, device="cuda")
     nh.nh_jacobian_apply(ctx, opc, dev(du), y, prec=nh.NH_F64X)
-    assert rel(host(y), ref) < TOL64
+    agree(host(y), fem.jacobian_apply(spc, st, du, maskc, form=form), parity.jacobian_scale(spc, st, du, maskc, form),
+          TOL64, "rediscretised float-float apply")
     d = torch.empty(ndc, dtype=torch.float64, device="cuda")
     nh.nh_jacobian_diagonal(ctx, opc, d)
-    assert rel(host(d), fem.diagonal(spc, st, maskc, form=form)) < TOL64
+    agree(host(d), fem.diagonal(spc, st, maskc, form=form), parity.diagonal_scale(spc, st, maskc, form), TOL64,
+          "rediscretised diagonal")
     nh.nh_op_destroy(opc)
     nh.nh_space_destroy(sc)
     c.close()
@@ -247,14 +274,20 @@ def test_coarse_level_operator(nhctx, pf, pc):
     nh.nh_space_set_dirichlet(ctx, sc, maskc)
     opc = nh.nh_op_level(ctx, c.op, sc)
     du = inputs.normal_vector(ndc, seed=3)
-    ref = fem.jacobian_apply(spc, c.state, du, maskc)
     for dt, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
         y = torch.empty(ndc, dtype=dt, device="cuda")
         nh.nh_jacobian_apply(ctx, opc, dev(du, dt), y)
-        assert rel(host(y), ref) < tol
+        xin = du if dt == torch.float64 else du.astype(np.float32).astype(np.float64)
+        agree(host(y), fem.jacobian_apply(spc, c.state, xin, maskc),
+              parity.jacobian_scale(spc, c.state, xin, maskc), tol, f"coarse-level apply {dt}")
+    y = torch.empty(ndc, dtype=torch.float64, device="cuda")
+    nh.nh_jacobian_apply(ctx, opc, dev(du), y, prec=nh.NH_F64X)
+    agree(host(y), fem.jacobian_apply(spc, c.state, du, maskc), parity.jacobian_scale(spc, c.state, du, maskc),
+          TOL64, "coarse-level float-float apply")
     d = torch.empty(ndc, dtype=torch.float64, device="cuda")
     nh.nh_jacobian_diagonal(ctx, opc, d)
-    assert rel(host(d), fem.diagonal(spc, c.state, maskc)) < TOL64
+    agree(host(d), fem.diagonal(spc, c.state, maskc), parity.diagonal_scale(spc, c.state, maskc), TOL64,
+          "coarse-level diagonal")
     nh.nh_op_destroy(opc)
     nh.nh_space_destroy(sc)
     c.close()
@@ -275,10 +308,12 @@ def test_prolong_restrict(nhctx, pc, pf):
     for dt, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
         out = torch.empty(ndf, dtype=dt, device="cuda")
         nh.nh_prolong(ctx, sc, sf, dev(uc, dt), out)
-        assert rel(host(out), fem.prolong(c, f, uc)) < tol
+        ucin = uc if dt == torch.float64 else uc.astype(np.float32).astype(np.float64)
+        agree(host(out), fem.prolong(c, f, ucin), parity.prolong_scale(c, f, ucin), tol, f"prolongation {dt}")
         outc = torch.empty(ndc, dtype=dt, device="cuda")
         nh.nh_restrict(ctx, sf, sc, dev(rf, dt), outc)
-        assert rel(host(outc), fem.restrict(f, c, rf)) < tol
+        rfin = rf if dt == torch.float64 else rf.astype(np.float32).astype(np.float64)
+        agree(host(outc), fem.restrict(f, c, rfin), parity.restrict_scale(f, c, rfin), tol, f"restriction {dt}")
     nh.nh_space_destroy(sc)
     nh.nh_space_destroy(sf)
 

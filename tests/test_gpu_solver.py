@@ -12,10 +12,13 @@ Tolerances:
 * linear solve to ||r|| <= 1e-11 ||b||: 1e-7 against a sparse direct solve.
 * nonlinear solve to ||F|| <= 1e-8 ||F_0||: 1e-6 against the oracle's Newton
   with a direct solver (both converged; iteration counts may differ).
+Each is checked norm-wise and entry by entry against the largest entry of the
+reference (``parity.check_inf``).
 """
 import numpy as np
 import pytest
 
+import parity
 from oracle import fem, solvers
 from paper_2204_01722_b300 import inputs
 
@@ -105,6 +108,7 @@ def test_lambda_and_vcycle(nhctx, n, p, levels, assembled):
     P.nh.nh_mg_vcycle(ctx, P.mg, dev(r), z)
     ref = solvers.vcycle(L, r, coarse_rtol=1e-14, coarse_maxit=5000)
     assert rel(host(z), ref) < 1e-8
+    parity.check_inf(host(z), ref, 1e-8, "V-cycle")
     P.close()
 
 
@@ -141,6 +145,7 @@ def test_linear_solve_matches_direct(nhctx, mixed, fp64_kind, layout):
     rep = P.nh.nh_linear_solve(ctx, P.mg, dev(b), x, rtol=1e-11, maxit=300, norm=1)
     ref = spla.spsolve(J.tocsc(), b)
     assert rel(host(x), ref) < 1e-7
+    parity.check_inf(host(x), ref, 1e-7, "linear solve")
     assert rep.krylov_its < 100
     P.close()
 
@@ -167,7 +172,9 @@ def test_geometric_coarse_multigrid(nhctx, E):
         rtol, tol = (1e-10, 1e-7) if E is None else (1e-8, 1e-5)
         rep = P.nh.nh_linear_solve(ctx, P.mg, dev(b), x, rtol=rtol, maxit=600, norm=1)
         J = fem.assemble(P.sps[0], fem.element_matrices(P.sps[0], st), P.masks[0])
-        assert rel(host(x), spla.spsolve(J.tocsc(), b)) < tol
+        ref = spla.spsolve(J.tocsc(), b)
+        assert rel(host(x), ref) < tol
+        parity.check_inf(host(x), ref, tol, f"linear solve, coarse solver {cs}")
         its[cs] = rep.coarse_its / max(rep.vcycles, 1)
         P.close()
     assert its[1] * 3 < its[0], its
@@ -205,4 +212,67 @@ def test_newton_solve_matches_oracle(nhctx, n, p, levels, steps, mixed, delta, k
     for k in range(1, steps + 1):
         uo, _ = solvers.newton_direct(P.sps[0], P.mat, uo, P.masks[0], g * k / steps, rtol=1e-12)
     assert rel(host(u), uo) < 1e-6
+    parity.check_inf(host(u), uo, 1e-6, "Newton solution")
+    P.close()
+
+
+def test_nan_right_hand_side_is_reported(nhctx):
+    """A NaN written into b from the host: the linear solve returns NH_ERR_NAN
+    (the first residual norm is not finite), the report carries that status,
+    and the same multigrid object then solves a clean system."""
+    import scipy.sparse.linalg as spla
+    ctx, _ = nhctx
+    P = Problem(ctx, (3, 2, 2), 2, (2, 1), coarse_rtol=1e-3)
+    P.setup()
+    nh = P.nh
+    b = inputs.normal_vector(P.nd, seed=31)
+    b[P.masks[0]] = 0.0
+    bad = b.copy()
+    bad[np.flatnonzero(~P.masks[0])[5]] = np.nan
+    x = torch.zeros(P.nd, dtype=torch.float64, device="cuda")
+    rep = nh.nh_linear_solve(ctx, P.mg, dev(bad), x, rtol=1e-10, maxit=50, norm=1, check=False)
+    assert rep.status == nh.NH_ERR_NAN
+    with pytest.raises(nh.NhError) as ei:
+        nh.nh_linear_solve(ctx, P.mg, dev(bad), torch.zeros_like(x), rtol=1e-10, maxit=50, norm=1)
+    assert ei.value.status == nh.NH_ERR_NAN
+    x = torch.zeros(P.nd, dtype=torch.float64, device="cuda")
+    nh.nh_linear_solve(ctx, P.mg, dev(b), x, rtol=1e-11, maxit=100, norm=1)
+    st = fem.qp_state(P.sps[0], P.mat, P.u)
+    J = fem.assemble(P.sps[0], fem.element_matrices(P.sps[0], st), P.masks[0])
+    assert rel(host(x), spla.spsolve(J.tocsc(), b)) < 1e-7
+    # a NaN in the boundary values of the nonlinear solve reaches the first Krylov solve
+    g = inputs.uniaxial_bc(P.sps[0].node_dims, 0.01)
+    g[np.flatnonzero(P.masks[0])[2]] = np.nan
+    rep = nh.nh_solve(ctx, P.mg, dev(g), torch.zeros(P.nd, dtype=torch.float64, device="cuda"), check=False)
+    assert rep.status == nh.NH_ERR_NAN
+    P.close()
+
+
+def test_not_converged_is_reported_with_the_report_filled(nhctx):
+    """Iteration limits: the linear solve with krylov maxit 1 and the nonlinear
+    solve with one Newton iteration per attempt return NH_ERR_NOT_CONVERGED with
+    the counts and the residual reached in the report."""
+    ctx, _ = nhctx
+    P = Problem(ctx, (3, 2, 2), 2, (2, 1), coarse_rtol=1e-3)
+    P.setup()
+    nh = P.nh
+    b = inputs.normal_vector(P.nd, seed=32)
+    b[P.masks[0]] = 0.0
+    x = torch.zeros(P.nd, dtype=torch.float64, device="cuda")
+    rep = nh.nh_linear_solve(ctx, P.mg, dev(b), x, rtol=1e-12, maxit=1, norm=1, check=False)
+    assert rep.status == nh.NH_ERR_NOT_CONVERGED
+    assert rep.krylov_its == 1 and rep.vcycles >= 1
+    assert 1e-12 < rep.rel_residual < 1.0
+    P.opts.newton_maxit = 1
+    P.opts.newton_rtol = 1e-15
+    P.opts.newton_atol = 0.0
+    P.opts.load_steps = 1
+    nh.nh_mg_destroy(P.mg)
+    P.mg = nh.nh_mg_create(ctx, P.op, P.opts)
+    g = inputs.uniaxial_bc(P.sps[0].node_dims, 0.01)
+    rep = nh.nh_solve(ctx, P.mg, dev(g), torch.zeros(P.nd, dtype=torch.float64, device="cuda"), check=False)
+    assert rep.status == nh.NH_ERR_NOT_CONVERGED
+    assert rep.newton_its >= 1 and rep.krylov_its >= 1
+    assert rep.rel_residual > 1e-14 and np.isfinite(rep.abs_residual)
+    assert "not" in nh.nh_last_error(ctx) or "limit" in nh.nh_last_error(ctx) or "halved" in nh.nh_last_error(ctx)
     P.close()

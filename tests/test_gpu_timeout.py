@@ -7,6 +7,7 @@ mbarriers) and an FP64 apply afterwards still match the oracle."""
 import numpy as np
 import pytest
 
+import parity
 from oracle import fem
 from paper_2204_01722_b300 import inputs
 
@@ -49,7 +50,11 @@ def test_bounded_wait_expires_and_context_survives(nhctx, kind):
     nh.nh_jacobian_apply(ctx, op, torch.as_tensor(du, dtype=torch.float32).cuda(), y32)
     nh.nh_sync(ctx)
     assert rel(y64.cpu().numpy(), ref) < 1e-12
-    ref32 = fem.jacobian_apply(sp, state, du.astype(np.float32).astype(np.float64), mask)
+    parity.check(y64.cpu().numpy(), ref, parity.jacobian_scale(sp, state, du, mask), 1e-12, "FP64 apply after expiry")
+    du32 = du.astype(np.float32).astype(np.float64)
+    ref32 = fem.jacobian_apply(sp, state, du32, mask)
     assert rel(y32.double().cpu().numpy(), ref32) < 2e-5
+    parity.check(y32.double().cpu().numpy(), ref32, parity.jacobian_scale(sp, state, du32, mask), 2e-5,
+                 "FP32 apply after expiry")
     nh.nh_op_destroy(op)
     nh.nh_space_destroy(space)
