@@ -95,3 +95,98 @@ def test_vcycle_preconditioned_cg_converges_fast():
     _, it_j, _ = solvers.cg_lanczos(levels[0]["A"], b, apply_M=lambda r: levels[0]["dinv"] * r,
                                     rtol=1e-8, maxit=2000, norm="l2")
     assert it_j > 2 * it
+
+
+def _spd(n, seed, lo=1.0, hi=50.0):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    return Q @ np.diag(np.linspace(lo, hi, n)) @ Q.T, rng
+
+
+def test_fcg_with_a_fixed_preconditioner_generates_the_pcg_iterates():
+    """FCG(1) with a fixed SPD preconditioner: the truncated A-orthogonalisation
+    is exact (CG's directions are A-conjugate), so its iterates are PCG's."""
+    A, rng = _spd(30, 2)
+    M = np.diag(rng.uniform(0.5, 2.0, 30))
+    b = rng.normal(size=30)
+    for k in range(1, 8):
+        x_f, _, _ = solvers.fcg(lambda v: A @ v, b, lambda v: M @ v, rtol=0.0, maxit=k)
+        x_c, _, _ = solvers.cg_lanczos(lambda v: A @ v, b, apply_M=lambda v: M @ v, rtol=0.0, maxit=k)
+        np.testing.assert_allclose(x_f, x_c, rtol=1e-11, atol=1e-12 * np.linalg.norm(x_c))
+
+
+def test_fcg_tolerates_a_varying_preconditioner():
+    """Alternating two different SPD preconditioners (plain PCG loses its
+    conjugacy): FCG(1) still converges to the solution."""
+    A, rng = _spd(40, 3, 1.0, 1e3)
+    M1 = np.diag(1.0 / np.diag(A))
+    M2 = np.linalg.inv(A + np.diag(rng.uniform(0, 50, 40)))
+    calls = [0]
+
+    def M(v):
+        calls[0] += 1
+        return (M1 if calls[0] % 2 else M2) @ v
+    b = rng.normal(size=40)
+    x, k, rel = solvers.fcg(lambda v: A @ v, b, M, rtol=1e-12, maxit=400)
+    assert rel <= 1e-12 and k < 400
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-10)
+
+
+def test_chebyshev_solve_closed_form_and_symmetry():
+    """x = q(M A) M b: on a diagonal problem with spectrum of M A inside [a, b]
+    the error after k steps is p_k(lambda) e_0 with the scaled Chebyshev
+    polynomial; on a general SPD problem the map b -> x is linear and
+    symmetric (M symmetric)."""
+    rng = np.random.default_rng(4)
+    n = 40
+    lam = np.sort(rng.uniform(0.05, 1.0, n))
+    d = rng.uniform(0.5, 2.0, n)
+    A = np.diag(lam * d)
+    Mv = lambda v: v / d          # noqa: E731  (M A = diag(lam))
+    xs = rng.normal(size=n)
+    a, bb = 0.04, 1.1
+    theta, delta = (bb + a) / 2, (bb - a) / 2
+    for k in (1, 2, 4, 9):
+        x = solvers.chebyshev_solve(lambda v: A @ v, Mv, A @ xs, a, bb, k)
+        Tk = np.polynomial.chebyshev.Chebyshev.basis(k)
+        pk = Tk((theta - lam) / delta) / Tk(theta / delta)
+        np.testing.assert_allclose(xs - x, pk * xs, atol=1e-12)
+    S, rng = _spd(25, 5)
+    dinv = 1.0 / np.diag(S)
+    Q = np.stack([solvers.chebyshev_solve(lambda v: S @ v, lambda v: dinv * v, e, 0.02, 1.5, 7) for e in np.eye(25)],
+                 axis=1)
+    np.testing.assert_allclose(Q, Q.T, atol=1e-12 * np.abs(Q).max())
+    assert np.linalg.eigvalsh(0.5 * (Q + Q.T)).min() > 0
+
+
+def test_lanczos_extremes():
+    """With as many steps as distinct eigenvalues the Ritz values are exact."""
+    rng = np.random.default_rng(6)
+    lam = np.array([0.3, 0.7, 1.1, 2.0, 5.0, 9.5])
+    A = np.diag(lam)
+    lo, hi = solvers.lanczos_extremes(lambda v: A @ v, lambda v: v.copy(), rng.uniform(-1, 1, 6), 6)
+    assert abs(lo - 0.3) < 1e-10 and abs(hi - 9.5) < 1e-10
+
+
+def test_newton_krylov_reaches_the_direct_newton_solution():
+    """The load-stepped inexact Newton-Krylov driver (FCG(1) to 1e-3 with a
+    Jacobi preconditioner, predictor, secant step) converges to the solution of
+    Newton with direct solves on every load step."""
+    n, p = (3, 2, 2), 2
+    V = inputs.box_vertices(*n, perturb=0.1, seed=3)
+    sp = fem.Space(*n, V, p, p + 1)
+    mat = fem.Material(1.0, 0.3, sp.ne)
+    mask = inputs.uniaxial_mask(sp.node_dims)
+    g = inputs.uniaxial_bc(sp.node_dims, 0.04)
+
+    def jacobi(st):
+        dinv = 1.0 / fem.diagonal(sp, st, mask)
+        return lambda v: dinv * v
+    u, hist = solvers.newton_krylov(sp, mat, mask, g, 2, jacobi)
+    uo = np.zeros(sp.n_dof)
+    for k in (1, 2):
+        uo, _ = solvers.newton_direct(sp, mat, uo, mask, g * k / 2, rtol=1e-13)
+    assert np.linalg.norm(u - uo) / np.linalg.norm(uo) < 1e-7
+    assert len(hist) == 2 and all(1 <= h[0] <= 8 for h in hist)
+    r = fem.residual(sp, mat, u, mask, g)
+    assert np.linalg.norm(r) < 1e-8 * np.linalg.norm(fem.residual(sp, mat, uo * 0.5, mask, g)) + 1e-12
