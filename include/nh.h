@@ -314,6 +314,17 @@ typedef struct {
                               lattice halves evenly down to 3 nodes per direction and the coarsest
                               stencil is positive definite, else Jacobi-PCG; box meshes only
                               (NH_ERR_UNSUPPORTED from nh_mg_create on nh_space_hex meshes) */
+  int coarse_fixed;        /* 0 (default): the coarsest solve is the PCG chosen by coarse_solver, stopped
+                              at coarse_rtol, so its work and result depend on the residual and the
+                              V-cycle is not a fixed operator.  k > 0: a fixed linear coarse solve
+                              instead -- k steps of Chebyshev semi-iteration (Saad, Alg. 12.1) on the
+                              coarsest level, preconditioned by its Jacobi diagonal (coarse_solver 0)
+                              or by one geometric V-cycle (coarse_solver 1), over [l_min, cheb_hi l_max]
+                              of the preconditioned operator, the extreme Ritz values of 20 (or
+                              2 lanczos_iters, at most 60) preconditioned Lanczos steps at setup.  The
+                              V-cycle is then a fixed symmetric positive definite operator (FCG(1)
+                              reduces to PCG), and the coarse solve has no reductions and no host
+                              synchronisation.  coarse_its counts k per coarse solve */
 } nh_mg_opts;
 
 typedef struct {

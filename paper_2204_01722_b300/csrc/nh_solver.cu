@@ -53,6 +53,7 @@ struct Level {
   double *w[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double* dinv64 = nullptr;
   double lmax = 0.0;
+  double cmin = 0.0, cmax = 0.0;  // coarsest level, fixed solve: Chebyshev interval of M A
   bool stencil = false;
   bool redisc = false;     // rediscretised: own Gauss rule and quadrature data from the fine state
   double* A = nullptr;     // [27][9][nn]
@@ -540,6 +541,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->nonlinear = 0;
   o->lbfgs_m = 5;
   o->coarse_solver = 0;
+  o->coarse_fixed = 0;
   return NH_OK;
 }
 
@@ -612,6 +614,7 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
     return bad("nh_mg_create: coarse_rediscretize must be 0 or 1");
   if (o.nonlinear != 0 && o.nonlinear != 1) return bad("nh_mg_create: nonlinear must be 0 (Newton) or 1 (L-BFGS)");
   if (o.nonlinear == 1 && (o.lbfgs_m < 1 || o.lbfgs_m > 32)) return bad("nh_mg_create: need 1 <= lbfgs_m <= 32");
+  if (o.coarse_fixed < 0 || o.coarse_fixed > 100000) return bad("nh_mg_create: need 0 <= coarse_fixed <= 100000");
   if (o.coarse_solver != 0 && o.coarse_solver != 1) return bad("nh_mg_create: coarse_solver must be 0 or 1");
   if (fs->hex && o.coarse_solver) {
     delete mg;
@@ -912,6 +915,113 @@ nh_status hmg_pcg(nh_mg mg, Level& l, const double* b, double* x, double rtol, i
   *its = k;
   return NH_OK;
 }
+
+// z = M r, the preconditioner of the fixed coarse solve: one geometric V-cycle
+// when that hierarchy is set up, else the Jacobi diagonal.
+nh_status coarse_prec(nh_mg mg, Level& l, const double* r, double* z) {
+  if (mg->hmg_ok && &l == &mg->L.back()) return hvcycle(mg, 0, r, z);
+  CK(kv_mul<double>(mg->ctx->stream, l.n, l.dinv64, r, z));
+  mg->ctx->launches++;
+  return NH_OK;
+}
+
+// Interval of the fixed coarse solve: extreme Ritz values of M A from m steps of
+// M-preconditioned CG on a seeded rough vector (the Lanczos tridiagonal of the
+// CG coefficients, as for the smoothers' lambda_max).  The upper end gets the
+// smoothers' margin cheb_hi: Chebyshev semi-iteration must not see eigenvalues
+// above its interval; below it (the Ritz value overestimates lambda_min) it only
+// damps less.
+nh_status coarse_bounds(nh_mg mg, Level& l) {
+  cudaStream_t st = mg->ctx->stream;
+  const int m = std::min(60, std::max(20, 2 * mg->o.lanczos_iters));
+  double *r = l.w[0], *z = l.w[1], *p = l.w[2], *q = l.w[3], *seed = l.w[4];
+  CK(kv_uniform(st, l.n, mg->o.seed, seed));
+  CK(kv_mask_zero<double>(st, l.nn, l.space->bc, seed));
+  mg->ctx->launches += 2;
+  CK(cudaMemcpyAsync(r, seed, 8 * l.n, cudaMemcpyDeviceToDevice, st));
+  ST(coarse_prec(mg, l, r, z));
+  CK(cudaMemcpyAsync(p, z, 8 * l.n, cudaMemcpyDeviceToDevice, st));
+  double rz = 0.0;
+  ST(dot_host(mg, l.n, r, z, &rz));
+  std::vector<double> al, be;
+  double alpha_prev = 1.0, beta_prev = 0.0;
+  for (int k = 0; k < m && rz > 0.0 && isfinite(rz); k++) {
+    ST(level_apply(mg, l, NH_F64, p, q));
+    double pq = 0.0;
+    ST(dot_host(mg, l.n, p, q, &pq));
+    if (!(pq > 0.0) || !isfinite(pq)) break;
+    const double alpha = rz / pq;
+    al.push_back(1.0 / alpha + (k > 0 ? beta_prev / alpha_prev : 0.0));
+    CK(kv_axpby<double>(st, l.n, -alpha, q, 1.0, r));
+    mg->ctx->launches++;
+    ST(coarse_prec(mg, l, r, z));
+    double rzn = 0.0;
+    ST(dot_host(mg, l.n, r, z, &rzn));
+    const double beta = rzn / rz;
+    be.push_back(sqrt(fabs(beta)) / alpha);
+    CK(kv_axpby<double>(st, l.n, 1.0, z, beta, p));  // p = z + beta p
+    mg->ctx->launches++;
+    alpha_prev = alpha;
+    beta_prev = beta;
+    rz = rzn;
+  }
+  if (al.empty()) return nh_fail(mg->ctx, NH_ERR_NAN, "coarse Lanczos: no positive curvature on the seed vector");
+  be.resize(al.size() - 1);
+  const double lmax = tridiag_max_eig(al, be);
+  std::vector<double> neg(al.size());
+  for (size_t i = 0; i < al.size(); i++) neg[i] = -al[i];
+  const double lmin = -tridiag_max_eig(neg, be);
+  if (!(lmax > 0.0) || !isfinite(lmax)) return nh_fail(mg->ctx, NH_ERR_NAN, "coarse Lanczos: lambda_max <= 0");
+  l.cmax = mg->o.cheb_hi * lmax;
+  l.cmin = (lmin > 0.0 && isfinite(lmin)) ? std::min(lmin, 0.5 * l.cmax) : 1e-3 * l.cmax;
+  return NH_OK;
+}
+
+// Fixed coarse solve: x = q(M A) M b after `degree` steps of Chebyshev
+// semi-iteration preconditioned by M over [cmin, cmax] (Saad, Iterative
+// Methods, Alg. 12.1), from x = 0, or from the given x (warm).  A fixed
+// polynomial: the map b -> x is linear, symmetric and positive definite, and
+// it needs no reduction and no host synchronisation.
+nh_status coarse_cheb(nh_mg mg, Level& l, const double* b, double* x, bool warm) {
+  cudaStream_t st = mg->ctx->stream;
+  const int64_t n = l.n;
+  double *r = l.w[0], *d = l.w[1], *z = l.w[2], *t = l.w[3];
+  const double theta = 0.5 * (l.cmax + l.cmin), delta = 0.5 * (l.cmax - l.cmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  const bool jac = !(mg->hmg_ok && &l == &mg->L.back());
+  if (warm) {
+    ST(level_apply(mg, l, NH_F64, x, t));
+    CK(cudaMemcpyAsync(r, b, 8 * n, cudaMemcpyDeviceToDevice, st));
+    CK(kv_axpby<double>(st, n, -1.0, t, 1.0, r));  // r = b - A x
+    mg->ctx->launches++;
+  } else {
+    CK(cudaMemcpyAsync(r, b, 8 * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(x, 0, 8 * n, st));
+  }
+  const int deg = std::max(1, mg->o.coarse_fixed);
+  for (int k = 0; k < deg; k++) {
+    double c1 = 0.0, c2 = 1.0 / theta;
+    if (k > 0) {
+      ST(level_apply(mg, l, NH_F64, d, t));
+      CK(kv_axpby<double>(st, n, -1.0, t, 1.0, r));  // r -= A d
+      mg->ctx->launches++;
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      c1 = rho_new * rho;
+      c2 = 2.0 * rho_new / delta;
+      rho = rho_new;
+    }
+    if (jac) {
+      CK(kv_cheb<double>(st, n, c1, c2, l.dinv64, r, d, x));  // d = c1 d + c2 D^-1 r; x += d
+      mg->ctx->launches++;
+    } else {
+      ST(coarse_prec(mg, l, r, z));
+      CK(kv_axpby<double>(st, n, c2, z, c1, d));  // d = c1 d + c2 M r
+      CK(kv_axpby<double>(st, n, 1.0, d, 1.0, x));
+      mg->ctx->launches += 2;
+    }
+  }
+  return NH_OK;
+}
 }  // namespace
 
 extern "C" nh_status nh_mg_setup(nh_mg mg) {
@@ -972,6 +1082,10 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
     ST(hmg_setup(mg));
     ST(mark("h-mg", lv, t0));
   }
+  if (mg->o.coarse_fixed > 0) {
+    ST(coarse_bounds(mg, mg->L.back()));
+    ST(mark("c-bounds", lv, t0));
+  }
   CK(cudaStreamSynchronize(st));
   mg->setup_done = true;
   return NH_OK;
@@ -989,8 +1103,11 @@ static nh_status vcycle_fp64(nh_mg mg, const double* r, double* z) {
   cudaStream_t st = mg->ctx->stream;
   Level& l = mg->L[0];
   if (mg->L.size() == 1) {
-    int its = 0;
-    ST(pcg64(mg, l, r, z, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
+    int its = mg->o.coarse_fixed;
+    if (mg->o.coarse_fixed > 0)
+      ST(coarse_cheb(mg, l, r, z, false));
+    else
+      ST(pcg64(mg, l, r, z, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
     mg->coarse_its += its;
     mg->vcycles++;
     return NH_OK;
@@ -1107,10 +1224,14 @@ nh_status coarse_solve(nh_mg mg, Level& l) {
       mg->rej++;
     }
   }
-  if (mg->hmg_ok && &l == &mg->L.back())
+  if (mg->o.coarse_fixed > 0) {
+    ST(coarse_cheb(mg, l, b, x, false));
+    its = mg->o.coarse_fixed;
+  } else if (mg->hmg_ok && &l == &mg->L.back()) {
     ST(hmg_pcg(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, &its));
-  else
+  } else {
     ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
+  }
   mg->coarse_its += its;
   return NH_OK;
 }

@@ -95,7 +95,7 @@ class MgOpts(C.Structure):
                 ("krylov_maxit", C.c_int), ("line_search", C.c_int), ("verbose", C.c_int),
                 ("learned_accept", C.c_int), ("learned_mode", C.c_int),
                 ("fp64_kind", C.c_int), ("coarse_rediscretize", C.c_int), ("nonlinear", C.c_int),
-                ("lbfgs_m", C.c_int), ("coarse_solver", C.c_int)]
+                ("lbfgs_m", C.c_int), ("coarse_solver", C.c_int), ("coarse_fixed", C.c_int)]
 
 
 class SolveReport(C.Structure):

@@ -43,7 +43,7 @@ def host(t):
 
 class Problem:
     def __init__(self, ctx, n, p, levels, E=None, perturb=0.1, seed=3, mixed=0, assembled=1, coarse_rtol=1e-14,
-                 amp=0.04, fp64_kind=0, redisc=0, nonlinear=0, coarse_solver=0, layout=0):
+                 amp=0.04, fp64_kind=0, redisc=0, nonlinear=0, coarse_solver=0, layout=0, coarse_fixed=0):
         from paper_2204_01722_b300 import nh
         self.nh, self.ctx = nh, ctx
         q = p + 1
@@ -60,7 +60,7 @@ class Problem:
         self.opts = nh.nh_mg_default_opts(ctx, self.op, level_p=levels, mixed=mixed, coarse_assembled=assembled,
                                           coarse_rtol=coarse_rtol, coarse_maxit=5000, seed=SEED,
                                           fp64_kind=fp64_kind, coarse_rediscretize=redisc, nonlinear=nonlinear,
-                                          coarse_solver=coarse_solver)
+                                          coarse_solver=coarse_solver, coarse_fixed=coarse_fixed)
         self.mg = nh.nh_mg_create(ctx, self.op, self.opts)
 
     def setup(self, u=None):
@@ -69,7 +69,9 @@ class Problem:
         self.nh.nh_mg_setup(self.ctx, self.mg)
 
     def oracle_levels(self, u=None):
-        st = fem.qp_state(self.sps[0], self.mat, self.u if u is None else u)
+        return self.oracle_levels_at(fem.qp_state(self.sps[0], self.mat, self.u if u is None else u))
+
+    def oracle_levels_at(self, st):
         levels = []
         for i, sp in enumerate(self.sps):
             m = self.masks[i]
@@ -83,6 +85,12 @@ class Problem:
                 c = self.sps[i + 1]
                 L["restrict"] = (lambda f, cc: (lambda v: fem.restrict(f, cc, v)))(sp, c)
                 L["prolong"] = (lambda f, cc: (lambda v: fem.prolong(cc, f, v)))(sp, c)
+            elif self.opts.coarse_fixed > 0:
+                # the fixed coarse solve's interval: extreme Ritz values of D^-1 A, upper end x cheb_hi
+                its = min(60, max(20, 2 * self.opts.lanczos_iters))
+                lo, hi = solvers.lanczos_extremes(A, (lambda d: (lambda v: d * v))(dinv), seed, its)
+                bnd = self.opts.cheb_hi * hi
+                L["cheb"] = (min(lo, 0.5 * bnd), bnd, self.opts.coarse_fixed)
             levels.append(L)
         return st, levels
 
@@ -275,4 +283,105 @@ def test_not_converged_is_reported_with_the_report_filled(nhctx):
     assert rep.newton_its >= 1 and rep.krylov_its >= 1
     assert rep.rel_residual > 1e-14 and np.isfinite(rep.abs_residual)
     assert "not" in nh.nh_last_error(ctx) or "limit" in nh.nh_last_error(ctx) or "halved" in nh.nh_last_error(ctx)
+    P.close()
+
+
+@pytest.mark.parametrize("n,p,levels", [((3, 2, 3), 4, (4, 2, 1)), ((4, 3, 3), 2, (2, 1))])
+def test_fixed_coarse_vcycle_matches_oracle(nhctx, n, p, levels):
+    """coarse_fixed: the coarsest solve is a fixed Jacobi-preconditioned
+    Chebyshev polynomial over the Ritz interval, so the V-cycle is a fixed
+    linear map; it equals the oracle's V-cycle with the same polynomial (bounds
+    from the same seeded Lanczos run: 1e-8 as for the near-exact coarse solve),
+    and is linear: V(r1 + 2 r2) = V(r1) + 2 V(r2)."""
+    ctx, _ = nhctx
+    P = Problem(ctx, n, p, levels, coarse_fixed=25)
+    P.setup()
+    _, L = P.oracle_levels()
+    r = inputs.normal_vector(P.nd, seed=10)
+    r[P.masks[0]] = 0.0
+    r2 = inputs.normal_vector(P.nd, seed=11)
+    r2[P.masks[0]] = 0.0
+    z = torch.empty(P.nd, dtype=torch.float64, device="cuda")
+    P.nh.nh_mg_vcycle(ctx, P.mg, dev(r), z)
+    ref = solvers.vcycle(L, r)
+    assert rel(host(z), ref) < 1e-8
+    parity.check_inf(host(z), ref, 1e-8, "V-cycle, fixed coarse solve")
+    z1, z2, z12 = (torch.empty(P.nd, dtype=torch.float64, device="cuda") for _ in range(3))
+    P.nh.nh_mg_vcycle(ctx, P.mg, dev(r2), z2)
+    P.nh.nh_mg_vcycle(ctx, P.mg, dev(r + 2.0 * r2), z12)
+    parity.check_inf(host(z12), host(z) + 2.0 * host(z2), 1e-12, "V-cycle linearity")
+    # symmetric: a.V(b) = b.V(a)
+    assert abs(r @ host(z2) - r2 @ host(z)) <= 1e-12 * np.linalg.norm(r) * np.linalg.norm(host(z2))
+    P.close()
+
+
+def test_fixed_coarse_solve_makes_fcg_repeatable(nhctx):
+    """4^3 Q2 contrast-100 inclusion problem, where the tolerance-stopped coarse
+    PCG made FCG(1) counts vary from run to run: with the fixed linear coarse
+    solve, 20 repeated solves take the same number of iterations and reach the
+    direct solution."""
+    import scipy.sparse.linalg as spla
+    ctx, _ = nhctx
+    n = (4, 4, 4)
+    E = inputs.inclusion_modulus(*n, seed=4, rmin=0.5, rmax=1.0, contrast=100.0)
+    P = Problem(ctx, n, 2, (2, 1), E=E, amp=0.03, seed=2, coarse_fixed=30)
+    P.setup()
+    st = fem.qp_state(P.sps[0], P.mat, P.u)
+    J = fem.assemble(P.sps[0], fem.element_matrices(P.sps[0], st), P.masks[0])
+    b = inputs.normal_vector(P.nd, seed=8)
+    b[P.masks[0]] = 0.0
+    ref = spla.spsolve(J.tocsc(), b)
+    counts = []
+    for _ in range(20):
+        x = torch.zeros(P.nd, dtype=torch.float64, device="cuda")
+        rep = P.nh.nh_linear_solve(ctx, P.mg, dev(b), x, rtol=1e-9, maxit=300, norm=1)
+        counts.append(rep.krylov_its)
+    assert len(set(counts)) == 1, counts
+    assert rel(host(x), ref) < 1e-7
+    parity.check_inf(host(x), ref, 1e-7, "linear solve, fixed coarse solve")
+    P.close()
+
+
+def test_fcg_iterates_match_oracle(nhctx):
+    """With the fixed coarse solve the preconditioner is a fixed operator: the
+    GPU's FCG(1) iterates x_k (k = 1..5 iterations) equal the oracle's FCG(1)
+    with the oracle's V-cycle."""
+    ctx, _ = nhctx
+    P = Problem(ctx, (3, 3, 2), 3, (3, 2, 1), coarse_fixed=20)
+    P.setup()
+    _, L = P.oracle_levels()
+    b = inputs.normal_vector(P.nd, seed=12)
+    b[P.masks[0]] = 0.0
+    A = L[0]["A"]
+    for k in range(1, 6):
+        x = torch.zeros(P.nd, dtype=torch.float64, device="cuda")
+        P.nh.nh_linear_solve(ctx, P.mg, dev(b), x, rtol=1e-30, maxit=k, norm=1, check=False)
+        xo, ko, _ = solvers.fcg(A, b, lambda v: solvers.vcycle(L, v), rtol=1e-30, maxit=k)
+        assert ko == k
+        assert rel(host(x), xo) < 1e-8, k
+        parity.check_inf(host(x), xo, 1e-8, f"FCG iterate {k}")
+    P.close()
+
+
+def test_newton_krylov_matches_oracle(nhctx):
+    """The load-stepped Newton-Krylov solve (predictor, FCG(1) to 1e-3 with the
+    V-cycle, secant step; Sec. III-A) against the oracle's, both with the fixed
+    coarse solve: the same Newton iteration counts (+-1 in all) and the same
+    solution (1e-6)."""
+    ctx, _ = nhctx
+    P = Problem(ctx, (3, 2, 2), 3, (3, 2, 1), coarse_fixed=20)
+    P.opts.load_steps = 2
+    P.nh.nh_mg_destroy(P.mg)
+    P.mg = P.nh.nh_mg_create(ctx, P.op, P.opts)
+    g = inputs.uniaxial_bc(P.sps[0].node_dims, 0.03)
+    u = torch.zeros(P.nd, dtype=torch.float64, device="cuda")
+    rep = P.nh.nh_solve(ctx, P.mg, dev(g), u)
+
+    def precond(st):
+        _, L = P.oracle_levels_at(st)
+        return lambda v: solvers.vcycle(L, v)
+    uo, hist = solvers.newton_krylov(P.sps[0], P.mat, P.masks[0], g, 2, precond)
+    assert abs(rep.newton_its - sum(h[0] for h in hist)) <= 1, (rep.newton_its, hist)
+    assert rel(host(u), uo) < 1e-6
+    parity.check_inf(host(u), uo, 1e-6, "Newton-Krylov solution")
     P.close()
