@@ -40,10 +40,15 @@ NU = 0.3
 PERTURB = 0.1
 AMP = 0.05
 SEED = 42
-# FP64 pipe of a B300: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (unit count x maximum clock)
+# Unit-count ALU peaks (148 SMs x DFMA or FFMA per clock x 2 flop x 2.032 GHz), used
+# only when the measured ones (nh_fma_peak, measured at the start of every run) are missing
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
-# FP32 pipe: 148 SMs x 128 FFMA/clk x 2 flop x 2.032 GHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# float-float: one FP64-accurate multiply-add (2 flops) costs 15 FP32 operations
+# (FMA TwoProduct with the cross terms, TwoSum, Fast2Sum), and the FP32 pipe issues
+# an add, a multiply or an FMA per lane per clock, so its ceiling in FP64 flops is
+# the FP32 FMA rate (2 flops per instruction) / 15
+FF_OPS_PER_FMA = 15
 DEFAULT_N = {2: 74, 3: 48, 4: 37}
 
 
@@ -237,6 +242,21 @@ def whole_job_rate(world, units_per_rank, repeats, seconds):
     return world * units_per_rank * repeats / seconds / 1e9
 
 
+def measure_alu_peaks(nh, ctx, gpu_index):
+    """FP64 and FP32 FMA throughput measured on this GPU (nh_fma_peak: FMA chains
+    on every SM, CUDA events), with the SM clock sampled meanwhile."""
+    clocks = ClockSampler(gpu_index)
+    f64, ms64 = nh.nh_fma_peak(ctx, 0, 16384)
+    f32, ms32 = nh.nh_fma_peak(ctx, 1, 1 << 20)
+    clk = clocks.stop()
+    return {"fp64_tflops": round(f64, 4), "fp32_tflops": round(f32, 3),
+            "float_float_tflops": round(f32 / FF_OPS_PER_FMA, 4), "fp64_ms": round(ms64, 2),
+            "fp32_ms": round(ms32, 2), "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
+            "how": "nh_fma_peak: 8 independent FMA chains per thread, 8 blocks of 256 threads per SM, one timed "
+                   "launch after a warm-up; float-float = FP32 / %d FP32 operations per FP64-accurate FMA"
+                   % FF_OPS_PER_FMA}
+
+
 def run_nh(args):
     import torch
     from paper_2204_01722_b300 import nh
@@ -261,6 +281,8 @@ def run_nh(args):
     with torch.cuda.stream(stream):
         ctx = nh.nh_create(local, stream.cuda_stream)
         p, n = args.p, args.n
+        alu = measure_alu_peaks(nh, ctx, gpu_index)
+        pk = {"f64": alu["fp64_tflops"], "f64x": alu["float_float_tflops"], "f32": alu["fp32_tflops"]}
         case = Case(nh, torch, ctx, p, n)
         clocks = ClockSampler(gpu_index)
         ms, launches = time_applies(nh, torch, ctx, stream, case, args.prec, args.steps, args.warmup, barrier)
@@ -274,9 +296,11 @@ def run_nh(args):
         S, _ = nh.nh_op_info(ctx, case.op)
         if args.prec in ("f64", "f64x"):
             ach = apply_flops(p, n) / (kms * 1e-3) / 1e12
-            roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                    "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": args.traffic,
-                    "peak_source": "FP64 pipe: 148 SM x 2 DFMA/clk x 2.032 GHz (unit count x max clock)",
+            src = ("measured FP64 DFMA throughput on this GPU (nh_fma_peak)" if args.prec == "f64" else
+                   "measured FP32 FFMA throughput on this GPU / %d (float-float FMA cost)" % FF_OPS_PER_FMA)
+            roof = {"bound": "alu", "achieved": round(ach, 4), "peak": pk[args.prec],
+                    "unit": "TFLOP/s", "frac": round(ach / pk[args.prec], 4), "traffic": args.traffic,
+                    "peak_source": src, "peak_unit_count": round(FP64_PEAK_TFLOPS, 4),
                     "kernel_ms": round(kms, 4), "hbm_frac": round(apply_bytes(p, n, wb, S) / (kms * 1e-3) / 1e9 / hbm, 4)}
         else:
             ach = apply_bytes(p, n, wb, S, bc_byte=False) / (kms * 1e-3) / 1e9
@@ -316,10 +340,8 @@ def run_nh(args):
                     sweep.append({"p": sp_, "n": c.n, "n_dof": c.nd, "prec": pr,
                                   "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4),
                                   "algorithmic_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
-                                  "tflops": round(tfl, 3),
-                                  "alu_frac": round(tfl / (FP64_PEAK_TFLOPS if pr == "f64" else FP32_PEAK_TFLOPS), 4)})
-                    if pr == "f64x":  # ALU peak of float-float: FP32 pipe / ~15 instructions per FP64 op
-                        sweep[-1]["alu_frac"] = None
+                                  "tflops": round(tfl, 3), "alu_frac": round(tfl / pk[pr], 4),
+                                  "traffic": NCU_TRAFFIC.get((pr, sp_, c.n))})
                 c.close()
             for lay, lname in ((1, "initial tuned (27 scalars)"), (2, "AD-style tape (32 scalars)")):
                 c = Case(nh, torch, ctx, 3, DEFAULT_N[3], layout=lay)
@@ -349,7 +371,25 @@ def run_nh(args):
                                   "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4),
                                   "gdofs_e2e": round(c.nd / te / 1e9, 3)})
                 c.close()
-        solve = run_solves(nh, torch, ctx, stream) if (args.solve and rank == 0) else None
+        scatter = []
+        if args.sweep and rank == 0:
+            # atomics against the eight-colour scatter (no atomics, eight launches), at
+            # sizes whose x-element count is a multiple of the FP32 kernel's elements per block
+            for sp_, n_ in ((2, 70), (3, 48), (4, 35)):
+                c = Case(nh, torch, ctx, sp_, n_)
+                for pr in ("f64", "f32"):
+                    row = {"p": sp_, "n": n_, "n_dof": c.nd, "prec": pr}
+                    for mode, key in ((0, "atomic"), (1, "colour8")):
+                        nh.nh_op_set_scatter(ctx, c.op, mode)
+                        kernel_ms(nh, ctx, c, pr, 5)
+                        k = kernel_ms(nh, ctx, c, pr, 20)
+                        row[key + "_ms"] = round(k, 4)
+                        row[key + "_gdofs"] = round(c.nd / (k * 1e-3) / 1e9, 3)
+                    nh.nh_op_set_scatter(ctx, c.op, 0)
+                    scatter.append(row)
+                c.close()
+        solve = run_solves(nh, torch, ctx, stream, repeats=args.solve_repeats) if (args.solve and rank == 0) else None
+        multi = multiscale_block(nh, torch, ctx, stream) if (args.multiscale_block and rank == 0) else None
         nh.nh_destroy(ctx)
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 4), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -362,17 +402,22 @@ def run_nh(args):
                           "min_det_F": minJ, "l2": "inputs larger than L2 (quadrature data %.2f GB)"
                                                    % (n ** 3 * (p + 1) ** 3 * S * wb / 1e9),
                           "parallelism": f"replicas x{world}"},
-               "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+               "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "alu_peaks": alu}
         if args.cpu_baseline:
-            out["cpu_baseline"] = oracle_baseline(p, n, args.cpu_seconds)
+            out["cpu_baseline"] = oracle_baseline_all_cores(p, n, args.cpu_seconds)
+            out["cpu_baseline_1core"] = oracle_baseline(p, n, args.cpu_seconds)
         if sweep:
             out["sweep"] = sweep
         if hexes:
             out["hex"] = hexes
         if layouts:
             out["layouts"] = layouts
+        if scatter:
+            out["scatter"] = scatter
         if solve:
             out["solve"] = solve
+        if multi:
+            out["multiscale"] = multi
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -381,38 +426,71 @@ def run_nh(args):
 # ---------------------------------------------------------------------------
 # solve time to relative residual 1e-8, plain FP64 p-MG vs the chosen solver
 # ---------------------------------------------------------------------------
-def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, inclusions=False, learned=None):
-    """Load-stepped p-MG solves of uniaxial compression; returns the reports of
-    plain FP64 Newton-Krylov p-MG (the reference solver), FP64 L-BFGS with the V-cycle as
-    initial inverse Hessian, Newton-Krylov with the faster V-cycle (FP32 on the
-    p > 1 levels, FP64-accurate applies in float-float, rediscretised coarse
-    levels), and the chosen solver: L-BFGS with that V-cycle and the geometric
-    multigrid coarse solve."""
+SOLVE_ARMS = (  # name, mixed, fp64_kind, coarse_rediscretize, nonlinear, coarse_solver, coarse_fixed
+    ("plain_fp64", 0, 0, 0, 0, 0, 0),
+    ("lbfgs_fp64", 0, 0, 0, 1, 0, 0),
+    ("newton_mixed_ff_rediscretized", 1, 1, 1, 0, 0, 0),
+    ("chosen_lbfgs_mixed_ff_rediscretized_hmg", 1, 1, 1, 1, 1, 0),
+    ("lbfgs_mixed_ff_rediscretized_hmg_fixed8", 1, 1, 1, 1, 1, 8),
+)
+
+
+def _report(rep):
+    return {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.as_dict().items()}
+
+
+def run_solves(nh, torch, ctx, stream, p=4, n=32, delta=0.10, steps=5, repeats=3):
+    """Load-stepped p-MG solves of uniaxial compression, per solver arm: plain
+    FP64 Newton-Krylov p-MG (the reference solver), FP64 L-BFGS with the V-cycle
+    as initial inverse Hessian, Newton-Krylov with the faster V-cycle (FP32 on
+    the p > 1 levels, FP64-accurate applies in float-float, rediscretised coarse
+    levels), the chosen solver (L-BFGS with that V-cycle and the geometric
+    multigrid coarse solve), and the same with the fixed coarse solve (8
+    Chebyshev steps preconditioned by the geometric V-cycle).  Each arm: one
+    discarded warm-up solve, then `repeats` timed solves, the arms' order rotated
+    from one repeat to the next; reported: the median run's report, its time, and
+    the spread of times and counts."""
     from paper_2204_01722_b300 import inputs
     V = inputs.box_vertices(n, n, n)
     sp, nn, nd = nh.nh_space_box(ctx, n, n, n, V, p, p + 1)
     N = p * n + 1
     nh.nh_space_set_dirichlet(ctx, sp, inputs.uniaxial_mask((N, N, N)))
-    E = inputs.inclusion_modulus(n, n, n, seed=SEED) if inclusions else None
-    op = nh.nh_op_create(ctx, sp, NU, E, 1.0)
+    op = nh.nh_op_create(ctx, sp, NU, None, 1.0)
     g = torch.from_numpy(inputs.uniaxial_bc((N, N, N), delta)).cuda()
-    out = {}
-    for name, mixed, kind, redisc, nl, cs in (("plain_fp64", 0, 0, 0, 0, 0), ("lbfgs_fp64", 0, 0, 0, 1, 0),
-                                              ("newton_mixed_ff_rediscretized", 1, 1, 1, 0, 0),
-                                              ("chosen_lbfgs_mixed_ff_rediscretized_hmg", 1, 1, 1, 1, 1)):
+    mgs = {}
+    for name, mixed, kind, redisc, nl, cs, fixed in SOLVE_ARMS:
         o = nh.nh_mg_default_opts(ctx, op, mixed=mixed, load_steps=steps, fp64_kind=kind,
-                                  coarse_rediscretize=redisc, nonlinear=nl, coarse_solver=cs)
-        mg = nh.nh_mg_create(ctx, op, o)
+                                  coarse_rediscretize=redisc, nonlinear=nl, coarse_solver=cs, coarse_fixed=fixed)
+        mgs[name] = nh.nh_mg_create(ctx, op, o)
+    runs = {name: [] for name in mgs}
+
+    def solve(name):
         u = torch.zeros(nd, dtype=torch.float64, device="cuda")
-        rep = nh.nh_solve(ctx, mg, g, u, check=False)
+        rep = nh.nh_solve(ctx, mgs[name], g, u, check=False)
         stream.synchronize()
-        out[name] = {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.as_dict().items()}
-        nh.nh_mg_destroy(mg)
+        return rep
+
+    for name in mgs:
+        solve(name)                                   # warm-up, discarded
+    names = list(mgs)
+    for r in range(repeats):
+        for name in names[r % len(names):] + names[:r % len(names)]:
+            runs[name].append(solve(name))
+    out = {}
+    for name, reps in runs.items():
+        secs = [x.seconds for x in reps]
+        med = sorted(range(len(reps)), key=lambda i: secs[i])[len(reps) // 2]
+        out[name] = _report(reps[med])
+        out[name].update(seconds_all=[round(x, 3) for x in secs],
+                         krylov_its_all=[x.krylov_its for x in reps], newton_its_all=[x.newton_its for x in reps])
+        nh.nh_mg_destroy(mgs[name])
     nh.nh_op_destroy(op)
     nh.nh_space_destroy(sp)
-    out["workload"] = (f"Q{p} on {n}^3 ({nd} DoF), {'inclusions E 1e3/1, ' if inclusions else ''}"
-                       f"{int(delta * 100)}% uniaxial compression in {steps} load steps, p-MG "
-                       f"{p}->2->1, Chebyshev(3)-Jacobi, Q1 coarse Jacobi-PCG 1e-3, FCG 1e-3, Newton to 1e-8")
+    out["workload"] = (f"Q{p} on {n}^3 ({nd} DoF), {int(delta * 100)}% uniaxial compression in {steps} load "
+                       f"steps, p-MG {p}->2->1, Chebyshev(3)-Jacobi, Q1 coarse Jacobi-PCG 1e-3 (plain), "
+                       f"FCG 1e-3, Newton to 1e-8")
+    out["protocol"] = (f"per arm one discarded warm-up solve, then the median of {repeats} solves; "
+                       f"arm order rotated between repeats")
     out["speedup"] = round(out["plain_fp64"]["seconds"] /
                            max(out["chosen_lbfgs_mixed_ff_rediscretized_hmg"]["seconds"], 1e-9), 3)
     return out
@@ -459,49 +537,61 @@ def run_hex_solves(args):
     print(json.dumps({"hex_solve": out}), flush=True)
 
 
-def run_multiscale(args):
+def multiscale_block(nh, torch, ctx, stream, p=3, n=64):
     """Mixed precision on the multiscale structure: Q3 on 64^3 elements (21.6 M DoF),
     per-element modulus from disjoint seeded spheres (volume fraction 0.3, radius
     2-6 elements, at least 2 elements between surfaces, contrast 1e3), 5% uniaxial
     compression in 5 load steps.  The chosen solver (L-BFGS, V-cycle with FP32
     applies/smoothers/transfers on p > 1 levels, float-float FP64-accurate fine
     residual path, rediscretised levels, geometric coarse multigrid) against the
-    same solver with FP64 levels; prints one JSON line with both reports, the
-    relative difference of the two displacement solutions and min det F."""
+    same solver with FP64 levels.  Each arm is warmed up by one load step of 0.5%
+    on the same operator, then timed once; returns both reports, the relative
+    difference of the two displacement solutions and min det F."""
+    from paper_2204_01722_b300 import inputs
+    out = {"workload": f"Q{p} on {n}^3, disjoint inclusions (vf 0.3, r 2-6 elements, gap >= 2 elements, "
+                       f"E 1e3/1), 5% uniaxial compression in 5 load steps, relative residual 1e-8",
+           "protocol": "per arm one warm-up solve (one load step of 0.5%), then one timed solve"}
+    V = inputs.box_vertices(n, n, n)
+    sp, nn, nd = nh.nh_space_box(ctx, n, n, n, V, p, p + 1)
+    N = p * n + 1
+    nh.nh_space_set_dirichlet(ctx, sp, inputs.uniaxial_mask((N, N, N)))
+    E = inputs.inclusion_modulus(n, n, n, seed=SEED, gap=2.0)
+    out["inclusion_fraction"] = round(float((E > 1.0).mean()), 4)
+    op = nh.nh_op_create(ctx, sp, NU, E, 1.0)
+    g = torch.from_numpy(inputs.uniaxial_bc((N, N, N), 0.05)).cuda()
+    sols = {}
+    for name, mixed, kind, redisc in (("chosen_mixed", 1, 1, 1), ("same_solver_fp64", 0, 0, 0)):
+        o = nh.nh_mg_default_opts(ctx, op, mixed=mixed, load_steps=1, fp64_kind=kind,
+                                  coarse_rediscretize=redisc, nonlinear=1, coarse_solver=1)
+        mg = nh.nh_mg_create(ctx, op, o)
+        u = torch.zeros(nd, dtype=torch.float64, device="cuda")
+        nh.nh_solve(ctx, mg, g * 0.1, u, check=False)
+        nh.nh_mg_destroy(mg)
+        o.load_steps = 5
+        mg = nh.nh_mg_create(ctx, op, o)
+        u = torch.zeros(nd, dtype=torch.float64, device="cuda")
+        rep = nh.nh_solve(ctx, mg, g, u, check=False)
+        stream.synchronize()
+        out[name] = _report(rep)
+        out[name]["min_det_F"] = float("%.4g" % nh.nh_qdata_setup(ctx, op, u))
+        sols[name] = u
+        nh.nh_mg_destroy(mg)
+    a, b = sols["chosen_mixed"], sols["same_solver_fp64"]
+    out["rel_diff_mixed_vs_fp64"] = float("%.4g" % (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item())
+    out["speedup"] = round(out["same_solver_fp64"]["seconds"] / max(out["chosen_mixed"]["seconds"], 1e-9), 3)
+    nh.nh_op_destroy(op)
+    nh.nh_space_destroy(sp)
+    return out
+
+
+def run_multiscale(args):
+    """The multiscale block alone, as its own JSON line."""
     import torch
-    from paper_2204_01722_b300 import inputs, nh
-    p, n = args.p, args.n
+    from paper_2204_01722_b300 import nh
     stream = torch.cuda.Stream()
     ctx = nh.nh_create(0, stream.cuda_stream)
-    out = {"workload": f"Q{p} on {n}^3, disjoint inclusions (vf 0.3, r 2-6 elements, gap >= 2 elements, "
-                       f"E 1e3/1), 5% uniaxial compression in 5 load steps, relative residual 1e-8"}
     with torch.cuda.stream(stream):
-        V = inputs.box_vertices(n, n, n)
-        sp, nn, nd = nh.nh_space_box(ctx, n, n, n, V, p, p + 1)
-        N = p * n + 1
-        nh.nh_space_set_dirichlet(ctx, sp, inputs.uniaxial_mask((N, N, N)))
-        E = inputs.inclusion_modulus(n, n, n, seed=SEED, gap=2.0)
-        out["inclusion_fraction"] = round(float((E > 1.0).mean()), 4)
-        op = nh.nh_op_create(ctx, sp, NU, E, 1.0)
-        g = torch.from_numpy(inputs.uniaxial_bc((N, N, N), 0.05)).cuda()
-        sols = {}
-        for name, mixed, kind, redisc in (("chosen_mixed", 1, 1, 1), ("same_solver_fp64", 0, 0, 0)):
-            o = nh.nh_mg_default_opts(ctx, op, mixed=mixed, load_steps=5, fp64_kind=kind,
-                                      coarse_rediscretize=redisc, nonlinear=1, coarse_solver=1)
-            mg = nh.nh_mg_create(ctx, op, o)
-            u = torch.zeros(nd, dtype=torch.float64, device="cuda")
-            rep = nh.nh_solve(ctx, mg, g, u, check=False)
-            stream.synchronize()
-            out[name] = {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in rep.as_dict().items()}
-            out[name]["min_det_F"] = float("%.4g" % nh.nh_qdata_setup(ctx, op, u))
-            sols[name] = u
-            nh.nh_mg_destroy(mg)
-            print(json.dumps({name: out[name]}), file=sys.stderr, flush=True)
-        a, b = sols["chosen_mixed"], sols["same_solver_fp64"]
-        out["rel_diff_mixed_vs_fp64"] = float("%.4g" % (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item())
-        out["speedup"] = round(out["same_solver_fp64"]["seconds"] / max(out["chosen_mixed"]["seconds"], 1e-9), 3)
-        nh.nh_op_destroy(op)
-        nh.nh_space_destroy(sp)
+        out = multiscale_block(nh, torch, ctx, stream, args.p, args.n)
     nh.nh_destroy(ctx)
     print(json.dumps({"multiscale": out}), flush=True)
 
@@ -514,13 +604,14 @@ class OracleWindow:
     workload (same p, q, material, perturbed mesh, displacement recipe), set up
     once; `time(seconds)` runs applies for at least that long (at least one)."""
 
-    def __init__(self, p, n, w=8):
+    def __init__(self, p, n, w=8, index=0):
         from oracle import fem
         from paper_2204_01722_b300 import inputs
         self.fem, self.p, self.n, self.w = fem, p, n, w
         V = inputs.box_vertices(n, n, n, perturb=PERTURB, seed=SEED).reshape(n + 1, n + 1, n + 1, 3)
         x0 = (n - w) // 2
-        sub = V[x0:x0 + w + 1, x0:x0 + w + 1, x0:x0 + w + 1].reshape(-1, 3)
+        z0 = (x0 + index * w) % (n - w + 1)   # window `index`: shifted along z
+        sub = V[z0:z0 + w + 1, x0:x0 + w + 1, x0:x0 + w + 1].reshape(-1, 3)
         self.sp = fem.Space(w, w, w, sub, p, p + 1)
         mat = fem.Material(1.0, NU, self.sp.ne)
         u = inputs.smooth_field(self.sp.node_coords(), AMP, seed=SEED + 1).ravel()
@@ -548,31 +639,78 @@ def oracle_baseline(p, n, seconds, w=8):
     return OracleWindow(p, n, w).time(seconds)
 
 
+def _oracle_worker(p, n, w, seconds, index, barrier, queue):
+    """One host core: its own window, applies for `seconds` once every core is ready."""
+    win = OracleWindow(p, n, w, index)
+    try:
+        barrier.wait(timeout=300)
+    except Exception:
+        queue.put((index, 0, 1.0, win.sp.n_dof))
+        return
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        win.fem.jacobian_apply(win.sp, win.st, win.du, win.mask)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    queue.put((index, reps, el, win.sp.n_dof))
+
+
+def oracle_baseline_all_cores(p, n, seconds, w=8):
+    """The oracle on every host core at once: one process per core (spawned, one
+    BLAS/OpenMP thread each), each applying the oracle on its own w^3-element
+    window of the workload for about `seconds`; the rate is all windows' DoF
+    over the slowest process's time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    mpc = mp.get_context("spawn")
+    barrier, queue = mpc.Barrier(cores), mpc.Queue()
+    procs = [mpc.Process(target=_oracle_worker, args=(p, n, w, seconds, i, barrier, queue)) for i in range(cores)]
+    for pr in procs:
+        pr.start()
+    res = [queue.get(timeout=600) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+    el = max(r[2] for r in res)
+    dofs = sum(r[1] * r[3] for r in res)
+    return {"value": round(dofs / el / 1e9, 6), "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes, one per host core, each running FP64 oracle applies on its own "
+                      f"{w}^3-element window (Q{p}) of the {n}^3 workload for {seconds:.0f} s; "
+                      f"{sum(r[1] for r in res)} applies in {el:.2f} s"}
+
+
 def run_reference(args):
-    """The oracle as the reference arm: set up once, W untimed applies, then K
-    steps of about cpu_seconds / K each (one apply at least, ~0.1 s at Q3), so
-    the whole run stays within a few minutes; the value is the median step."""
+    """The oracle as the reference arm: one step is one FP64 oracle apply on an
+    8^3-element window of the workload (~0.06 s at Q3), set up once; W untimed
+    steps, then K timed ones; the value is the window's DoF over the median step
+    and ms_per_step that median, so steps x ms_per_step is the time spent."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per = args.cpu_seconds / max(args.steps, 1)
     win = OracleWindow(args.p, args.n)
     for _ in range(args.warmup):
-        win.time(0.0)
-    vals, base, t0 = [], None, time.perf_counter()
+        win.fem.jacobian_apply(win.sp, win.st, win.du, win.mask)
+    times, t0 = [], time.perf_counter()
     for _ in range(args.steps):
-        base = win.time(per)
-        vals.append(base["value"])
+        t1 = time.perf_counter()
+        win.fem.jacobian_apply(win.sp, win.st, win.du, win.mask)
+        times.append(time.perf_counter() - t1)
     total = time.perf_counter() - t0
-    v = statistics.median(vals)
-    nd = n_dof_of(args.p, args.n)
+    step = statistics.median(times)
+    v = round(win.sp.n_dof / step / 1e9, 6)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(nd / (v * 1e9) * 1e3, 3), "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": round(step * 1e3, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"Jacobian apply, Q{args.p} (q={args.p + 1}) on {args.n}^3 hexahedra "
-                                  f"(oracle timed on a window)", "p": args.p, "n_dof": nd},
-           "cpu_baseline": dict(base, value=v, sample=f"{args.steps} steps of " + base["sample"] +
-                                f"; median step, {total:.1f} s in all"),
+           "config": {"workload": f"Jacobian apply, Q{args.p} (q={args.p + 1}) on a {win.w}^3-element window "
+                                  f"({win.sp.n_dof} DoF) of the {args.n}^3 hexahedra workload, plain FP64 CPU oracle",
+                      "p": args.p, "window_elements": win.w ** 3, "window_n_dof": win.sp.n_dof,
+                      "workload_n_dof": n_dof_of(args.p, args.n)},
+           "cpu_baseline": {"value": v, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} single applies on the {win.w}^3-element window, median step "
+                                      f"{step * 1e3:.1f} ms, {total:.1f} s in all, single-threaded numpy"},
            "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -590,6 +728,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-solve", dest="solve", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--solve-repeats", type=int, default=3)
+    ap.add_argument("--no-multiscale", dest="multiscale_block", action="store_false",
+                    help="skip the multiscale block of the default line")
     ap.add_argument("--hex-solve", action="store_true",
                     help="run the solve workload through the unstructured-mesh path instead of the bench")
     ap.add_argument("--multiscale", action="store_true",

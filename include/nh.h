@@ -247,6 +247,19 @@ nh_status nh_prolong(nh_space coarse, nh_space fine, nh_prec prec, const void* u
 /* rc = P^T rf (restriction = prolongation transposed, Sec. III-B). */
 nh_status nh_restrict(nh_space fine, nh_space coarse, nh_prec prec, const void* rf, void* rc);
 
+/* Scatter E^T of this operator's Jacobian applies (Sec. IV discusses the
+ * atomic writes among the operator overheads).  mode 0 (default): one launch,
+ * atomic scatter-add.  mode 1: eight launches, one per parity class of the box
+ * mesh's elements -- FP64 and float-float: elements classed by the parities of
+ * (ex, ey, ez); FP32: batches of the kernel's consecutive elements along x
+ * classed by the parities of (batch x, ey, ez) -- with plain read-modify-writes
+ * of y: no two elements (batches) of a class share a node, and within an FP32
+ * batch the rows are summed in shared memory or the elements take turns.
+ * Summation order is then fixed.  mode 1 needs a box mesh whose x-element count
+ * is a multiple of the FP32 kernel's elements per block (14, 8, 5 for q = 3, 4,
+ * 5), else NH_ERR_UNSUPPORTED.  Errors: NH_ERR_ARG. */
+nh_status nh_op_set_scatter(nh_op op, int mode);
+
 /* ---- kernel timing ----------------------------------------------------- */
 
 /* When on, every Jacobian-apply kernel launch on this context is bracketed by
@@ -255,6 +268,16 @@ nh_status nh_profile_enable(nh_ctx ctx, int on);
 /* Total device time (ms) and number of Jacobian-apply kernels recorded since
  * the last read; clears the record.  Synchronises. */
 nh_status nh_profile_read(nh_ctx ctx, double* total_ms, int64_t* launches);
+
+/* Measured FMA throughput of this GPU (not part of the method): a kernel in
+ * which every thread runs 8 independent fused multiply-add chains for `iters`
+ * steps on 8 resident 256-thread blocks per SM, timed with CUDA events on the
+ * context stream after one warm-up launch.  prec NH_F64 (DFMA) or NH_F32
+ * (FFMA); *tflops = 2 x FMAs / time, *ms (optional) = the timed launch.  It is
+ * the denominator of the FP64 and float-float applies' ALU rooflines.
+ * Allocates and frees a small output buffer; synchronises.
+ * Errors: NH_ERR_ARG (iters < 1, other prec), NH_ERR_CUDA. */
+nh_status nh_fma_peak(nh_ctx ctx, nh_prec prec, int64_t iters, double* tflops, double* ms);
 
 /* ---- vector kernels --------------------------------------------------- */
 
@@ -296,7 +319,20 @@ typedef struct {
                               2 = coarse warm start (predicts y ~ A_c^-1 r_c; the coarsest PCG starts
                                   from a y, a = y.r_c / y.A_c y the step that minimises the A-norm
                                   error along y, when a > 0 and that start at least halves the
-                                  residual's natural norm, else from zero) */
+                                  residual's natural norm, else from zero);
+                              3 = coarse post-correction: after the plain coarsest solve x1 (best with
+                                  coarse_fixed), predicts the error A_c^-1 r1 it leaves from the scaled
+                                  residual D_c^-1 r1, r1 = r_c - A_c x1, and adds a y,
+                                  a = y.r1 / y.A_c y, when y.r1 > 0 and
+                                  y.A_c y > 0 (the coarse A_c-norm error then strictly decreases);
+                              4 = learned coarse space, built at every nh_mg_setup: for learned_vectors
+                                  seeded probes r the network predicts the error A_c^-1 r1 that the plain
+                                  coarsest solve x1 leaves (r1 = r - A_c x1); these predictions,
+                                  A_c-orthonormalised, form W, and the coarsest solve becomes the two-level
+                                  balancing map x = W W^T b + (I - W W^T A_c) Q (I - A_c W W^T) b around
+                                  the plain coarsest solve Q: linear, symmetric positive definite, fixed
+                                  between setups.  With no network set, W is built from the probes' x1
+                                  (the same construction without the learned part) */
   int fp64_kind;           /* arithmetic of the FP64-accurate matrix-free applies (outer FCG, Lanczos,
                               FP64 smoothers): 0 = native FP64 (NH_F64), 1 = float-float (NH_F64X) */
   int coarse_rediscretize; /* 1: matrix-free coarse levels get their own Gauss rule q = p_l + 1 and
@@ -325,6 +361,7 @@ typedef struct {
                               V-cycle is then a fixed symmetric positive definite operator (FCG(1)
                               reduces to PCG), and the coarse solve has no reductions and no host
                               synchronisation.  coarse_its counts k per coarse solve */
+  int learned_vectors;     /* learned_mode 4: probes for the coarse space (32), 0..256 */
 } nh_mg_opts;
 
 typedef struct {
@@ -413,7 +450,13 @@ nh_status nh_mg_set_learned(nh_mg mg, nh_net net);
  * (x* - x_k injected at the vertex nodes, in the input's scaling).
  * learned_mode 2: runs FCG + V-cycle to krylov_rtol; at every coarsest solve
  * stores the input for the coarse right-hand side r_c and the target
- * A_c^-1 r_c (coarse PCG to 1e-9, in the input's scaling).  feats: device float
+ * A_c^-1 r_c (coarse PCG to 1e-9, in the input's scaling).
+ * learned_mode 3 and 4: runs FCG + V-cycle to krylov_rtol; at every coarsest
+ * solve stores the input for the residual r1 = r_c - A_c x1 left by the plain
+ * coarsest solve x1 (the network sees D_c^-1 r1, scaled to unit RMS, and
+ * log10 E) and the target A_c^-1 r1 (PCG to 1e-9) scaled to unit RMS: these
+ * modes use only the prediction's direction.  The V-cycle continues with x1.
+ * feats: device float
  * [max_pairs][4][N^3], targets [max_pairs][3][N^3]; *n_pairs = pairs written. */
 nh_status nh_mg_collect(nh_mg mg, const double* b, int max_pairs, float* feats, float* targets, int* n_pairs);
 

@@ -555,6 +555,9 @@ static OpArgs base_args(nh_op op) {
   memset(&a, 0, sizeof(a));
   a.ne = op->space->ne;
   a.nx = op->space->nx;
+  a.ny = op->space->ny;
+  a.nz = op->space->nz;
+  a.colour = -1;
   a.emap = op->space->emap;
   a.emapb = op->space->emapb;
   a.bc = op->space->bc;
@@ -688,9 +691,33 @@ extern "C" nh_status nh_jacobian_apply(nh_op op, nh_prec prec, const void* du, v
     ctx->ev_used += 2;
     NH_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
   }
-  NH_CUDA(ctx, nh_launch_apply(op->space->P, op->space->Q, prec, a, ctx->stream));
+  if (op->scatter == 1) {  // eight launches, one per parity class, no atomics
+    for (int c = 0; c < 8; c++) {
+      a.colour = c;
+      NH_CUDA(ctx, nh_launch_apply(op->space->P, op->space->Q, prec, a, ctx->stream));
+      ctx->launches++;
+    }
+  } else {
+    NH_CUDA(ctx, nh_launch_apply(op->space->P, op->space->Q, prec, a, ctx->stream));
+    ctx->launches++;
+  }
   if (ev) NH_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
-  ctx->launches++;
+  return NH_OK;
+}
+
+extern "C" nh_status nh_op_set_scatter(nh_op op, int mode) {
+  if (!op || (mode != 0 && mode != 1)) return NH_ERR_ARG;
+  nh_ctx ctx = op->space->ctx;
+  if (mode == 1) {
+    const nh_space s = op->space;
+    if (s->hex || s->nx <= 0)
+      return nh_fail(ctx, NH_ERR_UNSUPPORTED, "nh_op_set_scatter: the eight-colour scatter needs a box mesh");
+    if (s->nx % nh_epb(s->Q) != 0)
+      return nh_fail(ctx, NH_ERR_UNSUPPORTED,
+                     "nh_op_set_scatter: the eight-colour scatter needs an x-element count that is a multiple of "
+                     "the FP32 kernel's elements per block");
+  }
+  op->scatter = mode;
   return NH_OK;
 }
 

@@ -130,6 +130,7 @@ struct nh_op_s {
   float* qd_f = nullptr;          // FP32 copy, blocked per element batch (nh_f32_batch_floats)
   float* qd_ff = nullptr;         // float-float pairs (h, l), same indexing as qd (NH_F64X)
   double* u_state = nullptr;      // copy of the u of the last nh_qdata_setup (rediscretised levels)
+  int scatter = 0;                // E^T of the applies: 0 = atomic scatter-add, 1 = eight-colour passes
   bool qd_ff_valid = false;
   bool have_qd = false;
   bool qd_f_valid = false;
@@ -170,6 +171,8 @@ struct OpArgs {
   int resid;           // setup: compute residual
   int lift;            // apply: keep constrained inputs, leave constrained rows zero
   int nx;              // elements along x of the (box) space
+  int ny, nz;          // elements along y, z (box)
+  int colour;          // apply: -1 = atomic scatter; 0..7 = the parity class of the eight-colour scatter
   int* err;            // device error flag for bounded waits
   const Tab1D* tab;
 };

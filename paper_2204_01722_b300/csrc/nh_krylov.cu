@@ -163,9 +163,60 @@ __global__ void __launch_bounds__(1024) k_dotf(const double* __restrict__ part, 
   if (threadIdx.x == 0) *out = s;
 }
 
+// out[j] partials of W_j . v: block (c, j) sums chunk c of row j (rows of length n,
+// stride ldw); chunks of a row are summed afterwards in a fixed order
+constexpr int kMdChunks = 64;
+__global__ void __launch_bounds__(256)
+    k_multidot_part(int64_t n, const double* __restrict__ W, int64_t ldw, const double* __restrict__ v,
+                    double* __restrict__ part) {
+  const int j = blockIdx.y, c = blockIdx.x;
+  const int64_t len = (n + kMdChunks - 1) / kMdChunks, i0 = c * len, i1 = i0 + len < n ? i0 + len : n;
+  const double* w = W + (int64_t)j * ldw;
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(w[i], v[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[(int64_t)j * kMdChunks + c] = s;
+}
+
+__global__ void k_multidot_fin(int k, const double* __restrict__ part, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int c = 0; c < kMdChunks; c++) s += part[(int64_t)j * kMdChunks + c];
+  out[j] = s;
+}
+
+// y[i] += alpha sum_j c[j] W[j][i], k <= 256
+__global__ void k_gemv_rows(int64_t n, int k, const double* __restrict__ W, int64_t ldw, const double* __restrict__ c,
+                            double alpha, double* __restrict__ y) {
+  __shared__ double cs[256];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = alpha * c[j];
+  __syncthreads();
+  GRID_STRIDE(i, n) {
+    double s = 0.0;
+    for (int j = 0; j < k; j++) s = fma(cs[j], W[(int64_t)j * ldw + i], s);
+    y[i] += s;
+  }
+}
+
 }  // namespace
 
 // ---- launchers -------------------------------------------------------------------
+cudaError_t kv_multidot(cudaStream_t st, int k, int64_t n, const double* W, int64_t ldw, const double* v,
+                        double* part, double* out) {
+  if (k <= 0) return cudaSuccess;
+  k_multidot_part<<<dim3(kMdChunks, k), 256, 0, st>>>(n, W, ldw, v, part);
+  k_multidot_fin<<<(k + 127) / 128, 128, 0, st>>>(k, part, out);
+  return cudaGetLastError();
+}
+int kv_multidot_parts() { return kMdChunks; }
+cudaError_t kv_gemv_rows(cudaStream_t st, int64_t n, int k, const double* W, int64_t ldw, const double* c,
+                         double alpha, double* y) {
+  if (k <= 0) return cudaSuccess;
+  if (k > 256) return cudaErrorInvalidValue;
+  k_gemv_rows<<<grid_for(n), kT, 0, st>>>(n, k, W, ldw, c, alpha, y);
+  return cudaGetLastError();
+}
 #define L1(k, n, ...)                                     \
   do {                                                    \
     k<<<grid_for(n), kT, 0, st>>>(n, __VA_ARGS__);        \

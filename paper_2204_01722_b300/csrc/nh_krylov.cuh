@@ -27,6 +27,14 @@ cudaError_t kv_cheb(cudaStream_t st, int64_t n, double c1, double c2, const T* d
 cudaError_t kv_uniform(cudaStream_t st, int64_t n, uint64_t seed, double* v);
 template <typename TA, typename TB>
 cudaError_t kv_dot(cudaStream_t st, int64_t n, const TA* x, const TB* y, double* part, double* out);
+// out[j] = W_j . v for the k rows W_j = W + j ldw (length n), each summed in a
+// fixed order; part: k * kv_multidot_parts() doubles
+cudaError_t kv_multidot(cudaStream_t st, int k, int64_t n, const double* W, int64_t ldw, const double* v,
+                        double* part, double* out);
+int kv_multidot_parts();
+// y += alpha sum_j c[j] W_j, c a device vector of k <= 256 entries
+cudaError_t kv_gemv_rows(cudaStream_t st, int64_t n, int k, const double* W, int64_t ldw, const double* c,
+                         double alpha, double* y);
 
 // Assembled Q1 operator on a structured node lattice: 27 neighbour 3x3 blocks per
 // node, stored [27][9][n_nodes].

@@ -275,19 +275,26 @@ __device__ __forceinline__ void transpose_to_nodes(int a, int b, const KTab<P, Q
 // ---------------------------------------------------------------------------
 // T: arithmetic type (double, or ff for FP64-accurate float-float on the FP32
 // pipes); TV: type of the vectors du and y.
-template <int P, int Q, typename T, typename TV, int LAYOUT>
+template <int P, int Q, typename T, typename TV, int LAYOUT, bool COL = false>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<T, Q>())
     k_jacobian_apply(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
                      const T* __restrict__ qd, int64_t qstride, const KTab<P, Q, T> tab, const TV* __restrict__ du,
-                     TV* __restrict__ y, int lift) {
+                     TV* __restrict__ y, int lift, int colour, int nx, int ny, int nz) {
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int t = threadIdx.x;
   const int el = t / Q2, col = t - el * Q2;
   const int a = col % Q, b = col / Q;
-  const int64_t e = (int64_t)blockIdx.x * EPB + el;
-  const bool live = e < ne;
+  int64_t e = (int64_t)blockIdx.x * EPB + el;
+  bool live = e < ne;
+  if constexpr (COL) {  // eight-colour scatter: the launch covers the elements of one parity class
+    const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+    const int64_t cx = (nx - px + 1) / 2, cy = (ny - py + 1) / 2, cz = (nz - pz + 1) / 2;
+    live = e < cx * cy * cz;
+    const int64_t ix = e % cx, iy = (e / cx) % cy, iz = e / (cx * cy);
+    e = live ? (px + 2 * ix) + nx * ((py + 2 * iy) + (int64_t)ny * (pz + 2 * iz)) : 0;
+  }
   T* bA = sm + el * elem_stride<Q, T>();
   T* bB = bA + 3 * Q3;
   T* bC = bB + 3 * Q3;
@@ -331,6 +338,8 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<T, Q>())
         const int64_t dof = 3 * (int64_t)n + c;
         if ((m >> c) & 1u) {
           if (!lift) y[dof] = du[dof];  // identity row; every writer stores the same value
+        } else if constexpr (COL) {
+          y[dof] += (TV)out[c][k];  // no other element of this colour touches the node
         } else {
           atomicAdd(&y[dof], (TV)out[c][k]);
         }
@@ -406,11 +415,11 @@ __device__ __forceinline__ void red_run(float* y, const float (&v)[N]) {
   }
 }
 
-template <int P, int Q, int LAYOUT>
+template <int P, int Q, int LAYOUT, bool COL = false>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     k_jacobian_apply_f32l(int64_t ne, const unsigned* __restrict__ emapb, const float* __restrict__ qdb,
                           const KTab<P, Q, float> tab, const float* __restrict__ du, float* __restrict__ y, int lift,
-                          int vec_ok, int rows_ok, int* __restrict__ err) {
+                          int vec_ok, int rows_ok, int* __restrict__ err, int colour, int nbx, int ny, int nz) {
   using L = LineLayout<Q>;
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   constexpr int S = nh_layout_scalars(LAYOUT);
@@ -422,7 +431,18 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
   const int t = threadIdx.x;
   const int el = t / Q2, r = t - el * Q2;
   const int u = r % Q, v = r / Q;  // line coordinates of this thread
-  const int64_t e = (int64_t)blockIdx.x * EPB + el;
+  // batch of EPB consecutive elements: the block's index, or with the eight-colour
+  // scatter the colour's batch number blockIdx.x of batches classed by the parities
+  // of their (batch x, row y, row z) indices (rows of nbx batches; no two batches of
+  // a class share a node)
+  int64_t batch = blockIdx.x;
+  if constexpr (COL) {
+    const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+    const int64_t cx = (nbx - px + 1) / 2, cy = (ny - py + 1) / 2;
+    const int64_t ix = batch % cx, iy = (batch / cx) % cy, iz = batch / (cx * cy);
+    batch = (px + 2 * ix) + nbx * ((py + 2 * iy) + (int64_t)ny * (pz + 2 * iz));
+  }
+  const int64_t e = batch * EPB + el;
   const bool live = e < ne;
   float* A = qs + 2 * PL + L::elem(el);
   float* Bf = A + L::BUF;
@@ -431,7 +451,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     const unsigned bytes = (unsigned)(PL * sizeof(float));
     uint64_t* b = &bar[qz & 1];
     mbar_expect_tx(b, bytes);
-    const char* src = reinterpret_cast<const char*>(qdb + (int64_t)blockIdx.x * BS + qz * PL);
+    const char* src = reinterpret_cast<const char*>(qdb + batch * BS + qz * PL);
     char* dst = reinterpret_cast<char*>(qs + (qz & 1) * PL);
     for (unsigned off = 0; off < bytes; off += 16384u) {
       const unsigned chunk = bytes - off < 16384u ? bytes - off : 16384u;
@@ -734,6 +754,16 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 #pragma unroll
       for (int c = 0; c < 3; c++) Rr[3 * el * (P - 1) + c] += o[c][0];
     }
+    if constexpr (COL) {  // colour mode: the block's rows added to y by all threads, no atomics
+      __syncthreads();
+      constexpr int NR = P * P;
+      for (int k = t; k < NR * RL; k += Q2 * EPB) {
+        const int row = k / RL, off = k - row * RL;
+        const unsigned f = srun[row];
+        y[3 * (int64_t)f + off] += qs[2 * PL + row * RS + ((3u * f) & 3u) + off];
+      }
+      return;
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // shared writes -> bulk-copy reads
     __syncthreads();
     if (node_line && el == 0) {
@@ -749,6 +779,28 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       }
       for (int k = h + mid; k < RL; k++) atomicAdd(g + k, Rr[k]);
       if (mid > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+    return;
+  }
+  if constexpr (COL) {  // colour mode: the block's elements one after another (shared x-faces), no atomics
+    for (int rr = 0; rr < EPB; rr++) {
+      if (rr == el && live && node_line) {
+#pragma unroll
+        for (int i = 0; i < P; i++) {
+          const int64_t n = nid[i] & kNodeMask;
+          const unsigned m = nid[i] >> kNodeBits;
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const int64_t dof = 3 * n + c;
+            if ((m >> c) & 1u) {
+              if (!lift) y[dof] = du[dof];
+            } else {
+              y[dof] += o[c][i];
+            }
+          }
+        }
+      }
+      __syncthreads();
     }
     return;
   }
@@ -1067,10 +1119,22 @@ cudaError_t apply_launch(const OpArgs& A, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
   const size_t smem = (size_t)EPB * elem_stride<Q, T>() * sizeof(T);
   const KTab<P, Q, T> tab = make_ktab<P, Q, T>(*A.tab);
+  if (A.colour >= 0) {
+    const int px = A.colour & 1, py = (A.colour >> 1) & 1, pz = A.colour >> 2;
+    const int64_t ncol = (int64_t)((A.nx - px + 1) / 2) * ((A.ny - py + 1) / 2) * ((A.nz - pz + 1) / 2);
+    const int64_t grid = (ncol + EPB - 1) / EPB;
+    if (grid == 0) return cudaSuccess;
+    cudaError_t e = prep<k_jacobian_apply<P, Q, T, TV, LAYOUT, true>>(smem);
+    if (e != cudaSuccess) return e;
+    k_jacobian_apply<P, Q, T, TV, LAYOUT, true><<<(unsigned)grid, threads, smem, s>>>(
+        A.ne, A.emap, A.bc, (const T*)A.qd, A.qstride, tab, (const TV*)A.in, (TV*)A.out, A.lift, A.colour, A.nx, A.ny,
+        A.nz);
+    return cudaGetLastError();
+  }
   cudaError_t e = prep<k_jacobian_apply<P, Q, T, TV, LAYOUT>>(smem);
   if (e != cudaSuccess) return e;
   k_jacobian_apply<P, Q, T, TV, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
-      A.ne, A.emap, A.bc, (const T*)A.qd, A.qstride, tab, (const TV*)A.in, (TV*)A.out, A.lift);
+      A.ne, A.emap, A.bc, (const T*)A.qd, A.qstride, tab, (const TV*)A.in, (TV*)A.out, A.lift, -1, A.nx, A.ny, A.nz);
   return cudaGetLastError();
 }
 
@@ -1082,11 +1146,25 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
   const size_t smem = ((size_t)2 * nh_f32_plane_floats(Q, S) + (size_t)LineLayout<Q>::block_floats(EPB)) * sizeof(float);
   const KTab<P, Q, float> tab = make_ktab<P, Q, float>(*A.tab);
+  const int nbx = A.nx > 0 ? A.nx / EPB : 0;
+  if (A.colour >= 0) {  // batches must tile the rows: one block's elements lie in one row
+    if (A.nx <= 0 || A.nx % EPB != 0 || ((uintptr_t)A.out & 15) != 0) return cudaErrorInvalidValue;
+    const int px = A.colour & 1, py = (A.colour >> 1) & 1, pz = A.colour >> 2;
+    const int64_t grid = (int64_t)((nbx - px + 1) / 2) * ((A.ny - py + 1) / 2) * ((A.nz - pz + 1) / 2);
+    if (grid == 0) return cudaSuccess;
+    cudaError_t e = prep<k_jacobian_apply_f32l<P, Q, LAYOUT, true>>(smem);
+    if (e != cudaSuccess) return e;
+    k_jacobian_apply_f32l<P, Q, LAYOUT, true><<<(unsigned)grid, threads, smem, s>>>(
+        A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift, 1, 1, A.err, A.colour, nbx,
+        A.ny, A.nz);
+    return cudaGetLastError();
+  }
   cudaError_t e = prep<k_jacobian_apply_f32l<P, Q, LAYOUT>>(smem);
   if (e != cudaSuccess) return e;
   k_jacobian_apply_f32l<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
       A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift,
-      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, ((uintptr_t)A.out & 15) == 0 && A.nx > 0 && (NH_F32_ROWS_ANY || Q <= 3 || A.nx % EPB == 0) ? 1 : 0, A.err);
+      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, ((uintptr_t)A.out & 15) == 0 && A.nx > 0 && (NH_F32_ROWS_ANY || Q <= 3 || A.nx % EPB == 0) ? 1 : 0, A.err,
+      -1, nbx, A.ny, A.nz);
   return cudaGetLastError();
 }
 

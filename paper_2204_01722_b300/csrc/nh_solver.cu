@@ -103,6 +103,10 @@ struct nh_mg_s {
   nh_net net = nullptr;
   float *feat = nullptr, *nout = nullptr, *logE = nullptr;
   double *lz1 = nullptr, *lw = nullptr, *lxs = nullptr, *lx = nullptr, *lt = nullptr;
+  double *lc1 = nullptr, *lc2 = nullptr;  // coarse-sized: post-correction prediction, exact correction
+  // coarse space of learned_mode 4: Wk A_c-orthonormal coarse vectors W_j = W + j n_c
+  double *W = nullptr, *Wc = nullptr, *Wpart = nullptr;
+  int Wk = 0, Wcap = 0;
   int acc = 0, rej = 0;
   struct Collect* coll = nullptr;  // coarse-pair collection in progress
 };
@@ -375,6 +379,7 @@ nh_status vcycle_t(nh_mg mg, int lv);
 
 // x_lv = V-cycle(b_lv), dispatch on the level precision
 nh_status coarse_solve(nh_mg mg, Level& l);
+nh_status build_coarse_space(nh_mg mg);
 
 nh_status vcycle(nh_mg mg, int lv) {
   Level& l = mg->L[lv];
@@ -542,6 +547,7 @@ extern "C" nh_status nh_mg_default_opts(nh_op fine, nh_mg_opts* o) {
   o->lbfgs_m = 5;
   o->coarse_solver = 0;
   o->coarse_fixed = 0;
+  o->learned_vectors = 32;
   return NH_OK;
 }
 
@@ -579,6 +585,7 @@ extern "C" nh_status nh_mg_destroy(nh_mg mg) {
   cudaFree(mg->lbr);
   for (double* p : {mg->fr, mg->fz, mg->fp, mg->fq, mg->fx, mg->fu, mg->fg, mg->fb, mg->ft, mg->fs, mg->fsave})
     cudaFree(p);
+  for (void* p : {(void*)mg->lc1, (void*)mg->lc2, (void*)mg->W, (void*)mg->Wc, (void*)mg->Wpart}) cudaFree(p);
   for (void* p : {(void*)mg->feat, (void*)mg->nout, (void*)mg->logE, (void*)mg->lz1, (void*)mg->lw, (void*)mg->lxs,
                   (void*)mg->lx, (void*)mg->lt})
     cudaFree(p);
@@ -615,6 +622,8 @@ extern "C" nh_status nh_mg_create(nh_op fine, const nh_mg_opts* opts, nh_mg* out
   if (o.nonlinear != 0 && o.nonlinear != 1) return bad("nh_mg_create: nonlinear must be 0 (Newton) or 1 (L-BFGS)");
   if (o.nonlinear == 1 && (o.lbfgs_m < 1 || o.lbfgs_m > 32)) return bad("nh_mg_create: need 1 <= lbfgs_m <= 32");
   if (o.coarse_fixed < 0 || o.coarse_fixed > 100000) return bad("nh_mg_create: need 0 <= coarse_fixed <= 100000");
+  if (o.learned_mode < 1 || o.learned_mode > 4) return bad("nh_mg_create: learned_mode must be 1 to 4");
+  if (o.learned_vectors < 0 || o.learned_vectors > 256) return bad("nh_mg_create: need 0 <= learned_vectors <= 256");
   if (o.coarse_solver != 0 && o.coarse_solver != 1) return bad("nh_mg_create: coarse_solver must be 0 or 1");
   if (fs->hex && o.coarse_solver) {
     delete mg;
@@ -1024,6 +1033,8 @@ nh_status coarse_cheb(nh_mg mg, Level& l, const double* b, double* x, bool warm)
 }
 }  // namespace
 
+static nh_status learned_buffers(nh_mg mg);
+
 extern "C" nh_status nh_mg_setup(nh_mg mg) {
   if (!mg) return NH_ERR_ARG;
   nh_op root = mg->fine;
@@ -1085,6 +1096,13 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
   if (mg->o.coarse_fixed > 0) {
     ST(coarse_bounds(mg, mg->L.back()));
     ST(mark("c-bounds", lv, t0));
+  }
+  mg->Wk = 0;
+  if (mg->o.learned_mode == 4 && mg->o.learned_vectors > 0 && mg->L.size() >= 2 && mg->L.back().p == 1 &&
+      !mg->L[0].space->hex) {
+    ST(learned_buffers(mg));
+    ST(build_coarse_space(mg));
+    ST(mark("c-space", lv, t0));
   }
   CK(cudaStreamSynchronize(st));
   mg->setup_done = true;
@@ -1161,13 +1179,178 @@ nh_status coarse_features(nh_mg mg, const double* bc, float* feat, double* scale
   return NH_OK;
 }
 
-// coarsest solve: FP64 Jacobi-PCG (the coarsest level is always FP64), with the
-// learned warm start in learned_mode 2 and pair recording in collection mode
+// the coarsest solve without any learned stage: the fixed polynomial, or the PCG
+// chosen by coarse_solver to coarse_rtol
+nh_status coarse_plain(nh_mg mg, Level& l, const double* b, double* x, int* its) {
+  if (mg->o.coarse_fixed > 0) {
+    ST(coarse_cheb(mg, l, b, x, false));
+    *its = mg->o.coarse_fixed;
+  } else if (mg->hmg_ok && &l == &mg->L.back()) {
+    ST(hmg_pcg(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, its));
+  } else {
+    ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, its));
+  }
+  return NH_OK;
+}
+
+// learned post-correction (learned_mode 3): after the plain coarse solve x1,
+// the network predicts the error e1 = A_c^-1 r1 left by it from the residual
+// r1 = b - A_c x1, and x = x1 + a y with the step a = y.r1 / y.A_c y that
+// minimises the A_c-norm error along the prediction y.  Whenever y.r1 > 0 the
+// coarse error strictly decreases in the A_c-norm; otherwise x = x1 (rejected).
+nh_status coarse_post_correct(nh_mg mg, Level& l, const double* b, double* x) {
+  cudaStream_t st = mg->ctx->stream;
+  double *r1 = l.w[4], *y = mg->lc1, *ay = l.w[0];
+  ST(level_apply(mg, l, NH_F64, x, r1));
+  CK(kv_axpby<double>(st, l.n, 1.0, b, -1.0, r1));  // r1 = b - A x1
+  CK(kv_mul<double>(st, l.n, l.dinv64, r1, y));     // network input: D^-1 r1
+  mg->ctx->launches += 2;
+  double scale = 0.0;
+  ST(coarse_features(mg, y, mg->feat, &scale));
+  if (scale == 0.0) return NH_OK;
+  ST(nh_net_forward_internal(mg->net, mg->feat, mg->nout));
+  CK(kn_from_net(st, l.nn, mg->nout, scale, y));
+  CK(kv_mask_zero<double>(st, l.nn, l.space->bc, y));
+  mg->ctx->launches += 2;
+  ST(level_apply(mg, l, NH_F64, y, ay));
+  double yr = 0.0, yay = 0.0;
+  ST(dot_host(mg, l.n, y, r1, &yr));
+  ST(dot_host(mg, l.n, y, ay, &yay));
+  if (isfinite(yr) && isfinite(yay) && yr > 0.0 && yay > 0.0) {
+    CK(kv_axpby<double>(st, l.n, yr / yay, y, 1.0, x));
+    mg->ctx->launches++;
+    mg->acc++;
+  } else {
+    mg->rej++;
+  }
+  return NH_OK;
+}
+
+// learned_mode 4: a coarse space built once per setup.  For probe j (a seeded
+// uniform(-1, 1) coarse vector r, constrained entries zeroed) the plain coarse
+// solve gives x1 and leaves r1 = r - A_c x1; the network predicts the error
+// e1 = A_c^-1 r1 that remains, y_j = N(r1).  The y_j are A_c-orthonormalised
+// (classical Gram-Schmidt, twice), dropping any whose A_c-norm falls below
+// 1e-8 of its norm before the projection.  Without a network, y_j = x1 (the
+// plain solve's own output: the non-learned coarse space of the same size).
+nh_status build_coarse_space(nh_mg mg) {
+  Level& l = mg->L.back();
+  cudaStream_t st = mg->ctx->stream;
+  const int k = mg->o.learned_vectors;
+  mg->Wk = 0;
+  if (k <= 0) return NH_OK;
+  if (mg->Wcap < k) {
+    for (void* p : {(void*)mg->W, (void*)mg->Wc, (void*)mg->Wpart}) cudaFree(p);
+    mg->W = mg->Wc = mg->Wpart = nullptr;
+    mg->Wcap = 0;
+    ST(dalloc(mg, (void**)&mg->W, 8 * (size_t)k * l.n));
+    ST(dalloc(mg, (void**)&mg->Wc, 8 * 2 * (size_t)k));
+    ST(dalloc(mg, (void**)&mg->Wpart, 8 * (size_t)k * kv_multidot_parts()));
+    mg->Wcap = k;
+  }
+  double *r = l.w[4], *x1 = mg->lc1, *y = mg->lc2, *ay = l.w[0];
+  for (int j = 0; j < k; j++) {
+    CK(kv_uniform(st, l.n, mg->o.seed + 7919ull * (uint64_t)(j + 1), r));
+    CK(kv_mask_zero<double>(st, l.nn, l.space->bc, r));
+    mg->ctx->launches += 2;
+    int its = 0;
+    ST(coarse_plain(mg, l, r, x1, &its));
+    if (mg->net) {
+      ST(level_apply(mg, l, NH_F64, x1, ay));
+      CK(kv_axpby<double>(st, l.n, -1.0, ay, 1.0, r));  // r1 = r - A x1
+      CK(kv_mul<double>(st, l.n, l.dinv64, r, y));      // network input: D^-1 r1
+      mg->ctx->launches += 2;
+      double scale = 0.0;
+      ST(coarse_features(mg, y, mg->feat, &scale));
+      if (scale == 0.0) continue;
+      ST(nh_net_forward_internal(mg->net, mg->feat, mg->nout));
+      CK(kn_from_net(st, l.nn, mg->nout, scale, y));
+      CK(kv_mask_zero<double>(st, l.nn, l.space->bc, y));
+      mg->ctx->launches += 2;
+    } else {
+      CK(cudaMemcpyAsync(y, x1, 8 * l.n, cudaMemcpyDeviceToDevice, st));
+    }
+    ST(level_apply(mg, l, NH_F64, y, ay));
+    double e0 = 0.0;
+    ST(dot_host(mg, l.n, y, ay, &e0));
+    if (!(e0 > 0.0) || !isfinite(e0)) continue;
+    for (int pass = 0; pass < 2 && mg->Wk > 0; pass++) {
+      CK(kv_multidot(st, mg->Wk, l.n, mg->W, l.n, ay, mg->Wpart, mg->Wc));  // c = W^T A y
+      CK(kv_gemv_rows(st, l.n, mg->Wk, mg->W, l.n, mg->Wc, -1.0, y));      // y -= W c
+      mg->ctx->launches += 3;
+      ST(level_apply(mg, l, NH_F64, y, ay));
+    }
+    double e = 0.0;
+    ST(dot_host(mg, l.n, y, ay, &e));
+    if (!(e > 1e-8 * e0) || !isfinite(e)) continue;
+    CK(kv_axpby<double>(st, l.n, 1.0 / sqrt(e), y, 0.0, mg->W + (int64_t)mg->Wk * l.n));
+    mg->ctx->launches++;
+    mg->Wk++;
+  }
+  return NH_OK;
+}
+
+// Two-level coarse solve with the coarse space W (W^T A_c W = I) around the
+// plain coarse solve Q (balancing form):
+//   x = W W^T b + (I - W W^T A_c) Q (I - A_c W W^T) b,
+// symmetric positive definite for Q SPD, linear, and with no host synchronisation.
+nh_status coarse_two_level(nh_mg mg, Level& l, const double* b, double* x, int* its) {
+  cudaStream_t st = mg->ctx->stream;
+  const int k = mg->Wk;
+  double *v = l.w[4], *x1 = mg->lc1, *t = mg->lc2;
+  CK(kv_multidot(st, k, l.n, mg->W, l.n, b, mg->Wpart, mg->Wc));  // c = W^T b
+  CK(cudaMemsetAsync(x, 0, 8 * l.n, st));
+  CK(kv_gemv_rows(st, l.n, k, mg->W, l.n, mg->Wc, 1.0, x));      // x = y0 = W c
+  mg->ctx->launches += 3;
+  ST(level_apply(mg, l, NH_F64, x, t));
+  CK(cudaMemcpyAsync(v, b, 8 * l.n, cudaMemcpyDeviceToDevice, st));
+  CK(kv_axpby<double>(st, l.n, -1.0, t, 1.0, v));                // v = b - A y0
+  mg->ctx->launches++;
+  ST(coarse_plain(mg, l, v, x1, its));
+  ST(level_apply(mg, l, NH_F64, x1, t));
+  CK(kv_multidot(st, k, l.n, mg->W, l.n, t, mg->Wpart, mg->Wc + k));  // c2 = W^T A x1
+  CK(kv_axpby<double>(st, l.n, 1.0, x1, 1.0, x));
+  CK(kv_gemv_rows(st, l.n, k, mg->W, l.n, mg->Wc + k, -1.0, x));   // x = y0 + x1 - W c2
+  mg->ctx->launches += 4;
+  return NH_OK;
+}
+
+// coarsest solve (the coarsest level is always FP64), with the learned warm start
+// (learned_mode 2) or post-correction (learned_mode 3), and pair recording in
+// collection mode
 nh_status coarse_solve(nh_mg mg, Level& l) {
   cudaStream_t st = mg->ctx->stream;
   const double* b = (const double*)l.b;
   double* x = (double*)l.x;
   int its = 0;
+  if (mg->coll && mg->coll->n < mg->coll->max && mg->o.learned_mode == 3) {
+    // collection for the post-correction: the residual r1 the plain solve leaves
+    // and its exact correction A^-1 r1 (PCG to 1e-9); the V-cycle goes on with x1
+    ST(coarse_plain(mg, l, b, x, &its));
+    mg->coarse_its += its;
+    double *r1 = l.w[4], *e1 = mg->lc2;
+    ST(level_apply(mg, l, NH_F64, x, r1));
+    CK(kv_axpby<double>(st, l.n, 1.0, b, -1.0, r1));
+    CK(kv_mul<double>(st, l.n, l.dinv64, r1, e1));  // network input: D^-1 r1
+    mg->ctx->launches += 2;
+    double scale = 0.0;
+    float* f = mg->coll->feats + (int64_t)mg->coll->n * 4 * l.nn;
+    ST(coarse_features(mg, e1, f, &scale));
+    if (scale > 0.0) {
+      // target: the exact correction, scaled to unit RMS (only its direction is used)
+      int its2 = 0;
+      ST(pcg64(mg, l, r1, e1, 1e-9, 20000, false, &its2));
+      double ee = 0.0;
+      ST(dot_host(mg, l.n, e1, e1, &ee));
+      const double rms = sqrt(ee / (double)l.n);
+      if (rms > 0.0 && isfinite(rms)) {
+        CK(kn_to_channels(st, l.nn, e1, 1.0 / rms, mg->coll->tgts + (int64_t)mg->coll->n * 3 * l.nn));
+        mg->ctx->launches++;
+        mg->coll->n++;
+      }
+    }
+    return NH_OK;
+  }
   if (mg->coll && mg->coll->n < mg->coll->max) {
     // collection: tight solve, store (scaled b, scaled A^-1 b)
     ST(pcg64(mg, l, b, x, 1e-9, 20000, false, &its));
@@ -1179,6 +1362,16 @@ nh_status coarse_solve(nh_mg mg, Level& l) {
       mg->ctx->launches++;
       mg->coll->n++;
     }
+    mg->coarse_its += its;
+    return NH_OK;
+  }
+  if (mg->net && mg->o.learned_mode == 3) {
+    ST(coarse_plain(mg, l, b, x, &its));
+    mg->coarse_its += its;
+    return coarse_post_correct(mg, l, b, x);
+  }
+  if (mg->o.learned_mode == 4 && mg->Wk > 0) {
+    ST(coarse_two_level(mg, l, b, x, &its));
     mg->coarse_its += its;
     return NH_OK;
   }
@@ -1224,14 +1417,7 @@ nh_status coarse_solve(nh_mg mg, Level& l) {
       mg->rej++;
     }
   }
-  if (mg->o.coarse_fixed > 0) {
-    ST(coarse_cheb(mg, l, b, x, false));
-    its = mg->o.coarse_fixed;
-  } else if (mg->hmg_ok && &l == &mg->L.back()) {
-    ST(hmg_pcg(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, &its));
-  } else {
-    ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its));
-  }
+  ST(coarse_plain(mg, l, b, x, &its));
   mg->coarse_its += its;
   return NH_OK;
 }
@@ -1780,6 +1966,8 @@ static nh_status learned_buffers(nh_mg mg) {
   if ((s = dalloc(mg, (void**)&mg->nout, sizeof(float) * 3 * nc)) != NH_OK) return s;
   for (double** v : {&mg->lz1, &mg->lw, &mg->lxs, &mg->lx, &mg->lt})
     if ((s = dalloc(mg, (void**)v, 8 * n)) != NH_OK) return s;
+  for (double** v : {&mg->lc1, &mg->lc2})
+    if ((s = dalloc(mg, (void**)v, 8 * c.n)) != NH_OK) return s;
   // log10 E at the vertices: mean over the adjacent elements, E = 2 mu (1 + nu)
   nh_op root = mg->fine;
   std::vector<double> mu((size_t)fs->ne);
@@ -1835,7 +2023,7 @@ extern "C" nh_status nh_mg_collect(nh_mg mg, const double* b, int max_pairs, flo
   cudaStream_t st = mg->ctx->stream;
   int its = 0;
   double rel = 0.0;
-  if (mg->o.learned_mode == 2) {
+  if (mg->o.learned_mode == 2 || mg->o.learned_mode == 3) {
     Collect col{nullptr, feats, targets, max_pairs, 0};
     mg->coll = &col;
     CK(cudaMemsetAsync(mg->lx, 0, 8 * n, st));

@@ -5,14 +5,21 @@ driven through the C ABI (every step runs in libnh's kernels).
 
 Recipe (the defaults): Q_p on an n^3 unit cube with seeded spherical
 inclusions (volume fraction 0.3, radius 2-6 elements, stiffness contrast 1e3),
-x = 0 clamped, x = 1 pushed along x.  For every training layout the solver is
-first run to a deformed state (1% compression), then for a few right-hand sides
-(N(0,1) and smooth seeded fields) nh_mg_collect records (network input,
-target) pairs along the FCG + V-cycle iterations of J x = b.  The network
-(3 levels, 16/32/64 channels, BF16 weights and activations, FP32 accumulation)
-is trained by Adam on the mean relative squared error.  Evaluation solves the
-held-out layouts (load-stepped compression to 5%) with the chosen solver
-(mixed precision) with and without the learned stage, and with plain FP64 p-MG.
+x = 0 clamped, x = 1 pushed along x.  For every layout the state is first
+solved to 1% compression (L-BFGS with the mixed-precision V-cycle and the
+geometric coarse multigrid).  At that state the p-multigrid hierarchy
+p -> 2 -> 1 uses the fixed coarse solve (``coarse_fixed`` Chebyshev-Jacobi
+steps on the assembled Q1 level), and for a few right-hand sides (N(0,1) and
+smooth seeded fields) nh_mg_collect records, at every coarsest solve along the
+FCG + V-cycle iterations of J x = b, the residual r1 that fixed solve leaves
+and its exact correction A_c^-1 r1.  The network (4 levels, 16/32/48/64
+channels, BF16 weights and activations, FP32 accumulation) is trained by Adam
+on the mean relative squared error and then acts as the coarse post-correction
+(learned_mode 3).  Held-out layouts: the tangent system at 1% compression with
+an N(0,1) right-hand side is solved to ||r|| <= 1e-8 ||b|| by plain FP64 p-MG
+(Jacobi-PCG coarse solve to 1e-3, the paper's), the mixed-precision V-cycle with
+the fixed coarse solve, the same with the learned post-correction, and the
+mixed-precision V-cycle with the geometric coarse multigrid.
 """
 import argparse
 import json
@@ -35,7 +42,7 @@ def problem(ctx, n, p, seed, vf=0.3, rmin=2.0, rmax=6.0, contrast=1e3):
     op = nh.nh_op_create(ctx, sp, 0.3, E)
     g1 = torch.from_numpy(inputs.uniaxial_bc((N, N, N), 1.0)).cuda()
     X = nh.nh_space_coords(ctx, sp, nn)
-    return dict(space=sp, op=op, g1=g1, nd=nd, mask=mask, X=X)
+    return dict(space=sp, op=op, g1=g1, nd=nd, mask=mask, X=X, n=n, p=p)
 
 
 def close(pb, mg=None):
@@ -45,31 +52,59 @@ def close(pb, mg=None):
     nh.nh_space_destroy(pb["space"])
 
 
-def collect(ctx, stream, n, p, seeds, delta_state=0.01, rhs=3, pairs=8, mixed=1):
+def solve_state(ctx, pb, delta):
+    """Displacement at `delta` compression (one load step), by the chosen solver."""
     import torch
-    Nv = n + 1
+    o = nh.nh_mg_default_opts(ctx, pb["op"], mixed=1, fp64_kind=1, coarse_rediscretize=1, nonlinear=1,
+                              coarse_solver=1, load_steps=1)
+    mg = nh.nh_mg_create(ctx, pb["op"], o)
+    u = torch.zeros(pb["nd"], dtype=torch.float64, device="cuda")
+    rep = nh.nh_solve(ctx, mg, pb["g1"] * delta, u, check=False)
+    nh.nh_mg_destroy(mg)
+    nh.nh_qdata_setup(ctx, pb["op"], u)
+    return u, rep
+
+
+def rhs_vectors(pb, seed, k):
+    out = []
+    for j in range(k):
+        if j % 2 == 0:
+            b = inputs.normal_vector(pb["nd"], seed=1000 * seed + j)
+        else:
+            b = inputs.smooth_field(pb["X"], 1.0, seed=1000 * seed + j).ravel()
+        b[pb["mask"]] = 0.0
+        out.append(b)
+    return out
+
+
+VARIANTS = ("plain_fp64", "mixed_fixed", "mixed_fixed_space", "mixed_fixed_learned", "mixed_geometric")
+
+
+def variant_opts(ctx, pb, name, coarse_fixed, vectors=32):
+    kw = dict(plain_fp64=dict(),
+              mixed_fixed=dict(mixed=1, coarse_fixed=coarse_fixed, learned_mode=3),
+              mixed_fixed_space=dict(mixed=1, coarse_fixed=coarse_fixed, learned_mode=4, learned_vectors=vectors),
+              mixed_fixed_learned=dict(mixed=1, coarse_fixed=coarse_fixed, learned_mode=4, learned_vectors=vectors),
+              mixed_geometric=dict(mixed=1, coarse_solver=1))[name]
+    return nh.nh_mg_default_opts(ctx, pb["op"], **kw)
+
+
+def collect(ctx, stream, pb, seed, coarse_fixed, rhs=3, pairs=16):
+    """(network input, target) pairs of the post-correction at the current state."""
+    import torch
+    Nv = pb["n"] + 1
+    mg = nh.nh_mg_create(ctx, pb["op"], variant_opts(ctx, pb, "mixed_fixed", coarse_fixed))
+    nh.nh_mg_setup(ctx, mg)
     F, T = [], []
-    for s in seeds:
-        pb = problem(ctx, n, p, s)
-        mg = nh.nh_mg_create(ctx, pb["op"], nh.nh_mg_default_opts(ctx, pb["op"], mixed=mixed, load_steps=1))
-        u = torch.zeros(pb["nd"], dtype=torch.float64, device="cuda")
-        nh.nh_solve(ctx, mg, pb["g1"] * delta_state, u, check=False)
-        nh.nh_qdata_setup(ctx, pb["op"], u)
-        nh.nh_mg_setup(ctx, mg)
-        for j in range(rhs):
-            if j % 2 == 0:
-                b = inputs.normal_vector(pb["nd"], seed=1000 * s + j)
-            else:
-                b = inputs.smooth_field(pb["X"], 1.0, seed=1000 * s + j).ravel()
-            b[pb["mask"]] = 0.0
-            f = torch.zeros((pairs, 4, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
-            t = torch.zeros((pairs, 3, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
-            k = nh.nh_mg_collect(ctx, mg, torch.from_numpy(b).cuda(), pairs, f, t)
-            F.append(f[:k])
-            T.append(t[:k])
-        close(pb, mg)
+    for b in rhs_vectors(pb, seed, rhs):
+        f = torch.zeros((pairs, 4, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
+        t = torch.zeros((pairs, 3, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
+        k = nh.nh_mg_collect(ctx, mg, torch.from_numpy(b).cuda(), pairs, f, t)
+        F.append(f[:k])
+        T.append(t[:k])
+    nh.nh_mg_destroy(mg)
     stream.synchronize()
-    return torch.cat(F).contiguous(), torch.cat(T).contiguous()
+    return torch.cat(F), torch.cat(T)
 
 
 def train(ctx, net, feats, tgts, epochs=20, lr=1e-3, batch=4, seed=0):
@@ -90,23 +125,50 @@ def train(ctx, net, feats, tgts, epochs=20, lr=1e-3, batch=4, seed=0):
     return hist
 
 
-def evaluate(ctx, stream, n, p, seeds, delta=0.05, steps=5, nets=(("plain_fp64", 0, None),)):
+def validation_loss(ctx, net, feats, tgts):
+    """Mean relative squared error on held-out pairs (forward only)."""
     import torch
+    Nv = feats.shape[-1]
+    y = torch.empty((3, Nv, Nv, Nv), dtype=torch.float32, device="cuda")
+    errs = []
+    for i in range(feats.shape[0]):
+        nh.nh_net_forward(ctx, net, feats[i].contiguous(), y)
+        t = tgts[i]
+        errs.append(float(((y - t) ** 2).sum() / (t ** 2).sum()))
+    return float(np.mean(errs)) if errs else float("nan")
+
+
+def linear_eval(ctx, stream, pb, seed, net, coarse_fixed, vectors=(32,), rtol=1e-8, maxit=2000, repeats=1):
+    """Tangent solve J x = b at the current state, per solver variant: setup
+    (diagonals, Lanczos, coarse level, coarse space) and solve timed apart, each
+    the median over `repeats` runs after one discarded warm-up."""
+    import torch
+    b = torch.from_numpy(rhs_vectors(pb, 10 ** 6 + seed, 1)[0]).cuda()
     rows = []
-    for s in seeds:
-        pb = problem(ctx, n, p, s)
-        for name, mixed, net in nets:
-            mg = nh.nh_mg_create(ctx, pb["op"], nh.nh_mg_default_opts(ctx, pb["op"], mixed=mixed, load_steps=steps))
-            if net:
-                nh.nh_mg_set_learned(ctx, mg, net)
-            u = torch.zeros(pb["nd"], dtype=torch.float64, device="cuda")
-            rep = nh.nh_solve(ctx, mg, pb["g1"] * delta, u, check=False)
+    runs = [(name, k) for name in VARIANTS for k in (vectors if "space" in name or "learned" in name else (0,))]
+    for name, k in runs:
+        mg = nh.nh_mg_create(ctx, pb["op"], variant_opts(ctx, pb, name, coarse_fixed, k))
+        if name == "mixed_fixed_learned":
+            nh.nh_mg_set_learned(ctx, mg, net)
+        t_setup, t_solve, rep = [], [], None
+        for _ in range(repeats + 1):
             stream.synchronize()
-            d = rep.as_dict()
-            d.update(layout=s, solver=name)
-            rows.append(d)
-            nh.nh_mg_destroy(mg)
-        close(pb)
+            t0 = time.perf_counter()
+            nh.nh_mg_setup(ctx, mg)
+            stream.synchronize()
+            t1 = time.perf_counter()
+            x = torch.zeros(pb["nd"], dtype=torch.float64, device="cuda")
+            rep = nh.nh_linear_solve(ctx, mg, b, x, rtol=rtol, maxit=maxit, norm=1, check=False)
+            stream.synchronize()
+            t_setup.append(t1 - t0)
+            t_solve.append(time.perf_counter() - t1)
+        d = rep.as_dict()
+        d.update(layout=seed, solver=name if k == vectors[0] or k == 0 else f"{name}_{k}",
+                 t_setup=float(np.median(t_setup[1:])),
+                 seconds=float(np.median(t_solve[1:])))
+        d["total"] = d["t_setup"] + d["seconds"]
+        rows.append(d)
+        nh.nh_mg_destroy(mg)
     return rows
 
 
@@ -118,18 +180,32 @@ def main():
     ap.add_argument("--train", type=int, default=20)
     ap.add_argument("--test", type=int, default=5)
     ap.add_argument("--epochs", type=int, default=20)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--rhs", type=int, default=3)
-    ap.add_argument("--pairs", type=int, default=8)
-    ap.add_argument("--channels", default="16,32,64")
+    ap.add_argument("--pairs", type=int, default=16)
+    ap.add_argument("--coarse-fixed", type=int, default=30)
+    ap.add_argument("--channels", default="16,32,48,64")
+    ap.add_argument("--delta", type=float, default=0.01)
+    ap.add_argument("--repeats", type=int, default=1)
+    ap.add_argument("--vectors", default="32")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     stream = torch.cuda.Stream()
-    res = {}
+    res = dict(n=a.n, p=a.p, train_layouts=a.train, test_layouts=a.test, coarse_fixed=a.coarse_fixed,
+               channels=a.channels, delta=a.delta)
     with torch.cuda.stream(stream):
         ctx = nh.nh_create(0, stream.cuda_stream)
         t0 = time.perf_counter()
-        feats, tgts = collect(ctx, stream, a.n, a.p, range(1, a.train + 1), rhs=a.rhs, pairs=a.pairs)
+        F, T = [], []
+        for s in range(1, a.train + 1):
+            pb = problem(ctx, a.n, a.p, s)
+            solve_state(ctx, pb, a.delta)
+            f, t = collect(ctx, stream, pb, s, a.coarse_fixed, rhs=a.rhs, pairs=a.pairs)
+            F.append(f)
+            T.append(t)
+            close(pb)
+        feats, tgts = torch.cat(F).contiguous(), torch.cat(T).contiguous()
+        del F, T
         res["pairs"] = int(feats.shape[0])
         res["collect_s"] = time.perf_counter() - t0
         ch = [int(c) for c in a.channels.split(",")]
@@ -138,15 +214,28 @@ def main():
         res["loss"] = train(ctx, net, feats, tgts, epochs=a.epochs, lr=a.lr)
         stream.synchronize()
         res["train_s"] = time.perf_counter() - t0
+        print(json.dumps(dict(pairs=res["pairs"], collect_s=res["collect_s"], train_s=res["train_s"],
+                              loss=res["loss"])), flush=True)
         del feats, tgts
-        rows = evaluate(ctx, stream, a.n, a.p, range(101, 101 + a.test),
-                        nets=(("plain_fp64", 0, None), ("mixed", 1, None), ("mixed_learned", 1, net)))
+        rows, vloss = [], []
+        for s in range(101, 101 + a.test):
+            pb = problem(ctx, a.n, a.p, s)
+            _, rep = solve_state(ctx, pb, a.delta)
+            f, t = collect(ctx, stream, pb, s, a.coarse_fixed, rhs=1, pairs=a.pairs)
+            vloss.append(validation_loss(ctx, net, f, t))
+            del f, t
+            rows += linear_eval(ctx, stream, pb, s, net, a.coarse_fixed, [int(v) for v in a.vectors.split(",")],
+                                repeats=a.repeats)
+            close(pb)
+            if a.out:   # partial results after every held-out layout
+                with open(a.out, "w") as f:
+                    f.write(json.dumps(dict(res, eval=rows, heldout_loss=vloss)) + "\n")
+        res["heldout_loss"] = vloss
         res["eval"] = rows
-        for name in ("plain_fp64", "mixed", "mixed_learned"):
+        for name in sorted({r["solver"] for r in rows}):
             sel = [r for r in rows if r["solver"] == name]
             res[name] = {k: float(np.mean([r[k] for r in sel])) for k in
-                         ("seconds", "krylov_its", "newton_its", "vcycles", "coarse_its", "learned_accepted",
-                          "learned_rejected")}
+                         ("seconds", "t_setup", "total", "krylov_its", "vcycles", "coarse_its", "rel_residual")}
             res[name]["converged"] = all(r["status"] == 0 for r in sel)
         nh.nh_net_destroy(net)
         nh.nh_destroy(ctx)

@@ -82,6 +82,8 @@ SIGNATURES = {
     "nh_net_train_step": (_st, [_vp, C.c_int, _vp, _vp, C.c_float, C.POINTER(C.c_double)]),
     "nh_mg_set_learned": (_st, [_vp, _vp]),
     "nh_mg_collect": (_st, [_vp, _vp, C.c_int, _vp, _vp, C.POINTER(C.c_int)]),
+    "nh_fma_peak": (_st, [_vp, C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "nh_op_set_scatter": (_st, [_vp, C.c_int]),
 }
 
 
@@ -95,7 +97,8 @@ class MgOpts(C.Structure):
                 ("krylov_maxit", C.c_int), ("line_search", C.c_int), ("verbose", C.c_int),
                 ("learned_accept", C.c_int), ("learned_mode", C.c_int),
                 ("fp64_kind", C.c_int), ("coarse_rediscretize", C.c_int), ("nonlinear", C.c_int),
-                ("lbfgs_m", C.c_int), ("coarse_solver", C.c_int), ("coarse_fixed", C.c_int)]
+                ("lbfgs_m", C.c_int), ("coarse_solver", C.c_int), ("coarse_fixed", C.c_int),
+                ("learned_vectors", C.c_int)]
 
 
 class SolveReport(C.Structure):
@@ -372,6 +375,18 @@ def nh_dot_noalloc(stream, n, x, y, result):
     st = lib.nh_dot_noalloc(stream, n, _ptr(x), _ptr(y), _ptr(result))
     if st != NH_OK:
         raise NhError(st, "nh_dot_noalloc")
+
+
+def nh_op_set_scatter(ctx, op, mode):
+    """0 = atomic scatter-add, 1 = eight-colour passes without atomics."""
+    _check(lib.nh_op_set_scatter(op, mode), ctx)
+
+
+def nh_fma_peak(ctx, prec, iters):
+    """Measured FMA throughput (TFLOP/s) and the timed launch (ms)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib.nh_fma_peak(ctx, prec, iters, C.byref(tf), C.byref(ms)), ctx)
+    return tf.value, ms.value
 
 
 def nh_mg_default_opts(ctx, fine_op, **kw):

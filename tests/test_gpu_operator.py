@@ -369,3 +369,50 @@ def test_argument_errors(nhctx):
     assert ei.value.status == nh.NH_ERR_ARG
     nh.nh_op_destroy(op)
     nh.nh_space_destroy(s)
+
+
+def test_fma_peak_measurement(nhctx):
+    """nh_fma_peak: measured FP64 and FP32 FMA throughput, within the range a
+    B300 can give (unit counts at up to 2.032 GHz: 1.2 and 77 TFLOP/s)."""
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    f64, ms64 = nh.nh_fma_peak(ctx, nh.NH_F64, 2048)
+    f32, ms32 = nh.nh_fma_peak(ctx, nh.NH_F32, 1 << 16)
+    assert 0.2 < f64 < 1.3 and ms64 > 0
+    assert 10.0 < f32 < 80.0 and ms32 > 0
+    with pytest.raises(nh.NhError):
+        nh.nh_fma_peak(ctx, nh.NH_F64X, 10)
+
+
+@pytest.mark.parametrize("n,p,mask", [((14, 2, 3), 2, "uniaxial"), ((14, 3, 2), 2, "none"), ((8, 3, 2), 3, "uniaxial"),
+                                      ((8, 2, 3), 3, "none"), ((5, 3, 2), 4, "uniaxial"), ((10, 2, 2), 4, "none")])
+def test_eight_colour_scatter(nhctx, n, p, mask):
+    """nh_op_set_scatter(op, 1): eight launches, one per parity class of the
+    elements (FP32: of the kernel's element batches), plain read-modify-writes
+    instead of atomics.  Every precision equals the oracle as with atomics, and
+    two applies give bit-identical results (fixed summation order)."""
+    ctx, _ = nhctx
+    c = Case(ctx, n, p, mask=mask, seed=29)
+    c.nh.nh_op_set_scatter(ctx, c.op, 1)
+    du = inputs.normal_vector(c.sp.n_dof, seed=30)
+    du32 = du.astype(np.float32).astype(np.float64)
+    ref = fem.jacobian_apply(c.sp, c.state, du, c.mask)
+    ref32 = fem.jacobian_apply(c.sp, c.state, du32, c.mask)
+    sc = parity.jacobian_scale(c.sp, c.state, du, c.mask)
+    sc32 = parity.jacobian_scale(c.sp, c.state, du32, c.mask)
+    for prec, dt, r, scl, tol in ((c.nh.NH_F64, torch.float64, ref, sc, TOL64),
+                                  (c.nh.NH_F64X, torch.float64, ref, sc, TOL64),
+                                  (c.nh.NH_F32, torch.float32, ref32, sc32, TOL32)):
+        y1 = torch.empty(c.sp.n_dof, dtype=dt, device="cuda")
+        y2 = torch.empty(c.sp.n_dof, dtype=dt, device="cuda")
+        c.nh.nh_jacobian_apply(ctx, c.op, dev(du, dt), y1, prec=prec)
+        c.nh.nh_jacobian_apply(ctx, c.op, dev(du, dt), y2, prec=prec)
+        agree(host(y1), r, scl, tol, f"eight-colour scatter, prec {prec}")
+        assert torch.equal(y1, y2), prec
+    c.nh.nh_op_set_scatter(ctx, c.op, 0)
+    c.close()
+    c = Case(ctx, (7, 2, 2), 3, seed=29)
+    with pytest.raises(c.nh.NhError) as ei:     # 7 elements along x: not a multiple of 8
+        c.nh.nh_op_set_scatter(ctx, c.op, 1)
+    assert ei.value.status == c.nh.NH_ERR_UNSUPPORTED
+    c.close()
