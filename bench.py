@@ -17,9 +17,11 @@ bounded window of the same workload.  Besides the headline, the line carries the
 roofline of the timed kernel, the end-to-end rate through the host-buffer entry
 point, a sweep over Q2-Q4 and the three arithmetic paths, the unstructured-mesh
 and quadrature-layout variants, and the solve comparison (plain FP64 p-MG
-against the chosen solver).  Two further modes print their own line instead:
---multiscale (mixed precision on Q3 64^3 with inclusions) and --hex-solve (the
-solve workload through the unstructured-mesh path).
+against the chosen solver), the multiscale solve and the atomics-vs-colouring
+scatter timings.  Further modes print their own line instead: --multiscale (the
+multiscale solve alone), --hex-solve (the solve workload through the
+unstructured-mesh path) and --learned (the learned-coarse-space study on the
+inclusion configuration).
 """
 import argparse
 import json
@@ -68,7 +70,9 @@ def n_dof_of(p, n):
 # dram__bytes_read.sum + dram__bytes_write.sum per apply launch from the ncu
 # capture summarised in profiles/ (small case, scaled to the full launch by
 # elements); reset to None whenever the kernel changes.
-NCU_TRAFFIC = {("f64", 3, 48): 1.203e9}
+NCU_TRAFFIC = {("f64", 3, 48): 1.203e9,
+               ("f32", 2, 74): 9.06e8, ("f32", 3, 48): 6.08e8, ("f32", 4, 37): 5.67e8,
+               ("f64x", 3, 48): 1.208e9}
 
 
 def apply_bytes(p, n, wbytes, S=17, bc_byte=True):
@@ -735,11 +739,19 @@ def main():
                     help="run the solve workload through the unstructured-mesh path instead of the bench")
     ap.add_argument("--multiscale", action="store_true",
                     help="run the mixed-precision multiscale solve (Q3 on 64^3 by default) instead of the bench")
+    ap.add_argument("--learned", action="store_true",
+                    help="run the learned-coarse-space study (training on 20 inclusion layouts of Q3 on 64^3, "
+                         "3 held-out layouts; about 30 minutes) instead of the bench; prints its JSON line")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per apply from an ncu capture of this kernel (reported as is)")
     args = ap.parse_args()
     if args.hex_solve:
         run_hex_solves(args)
+        return
+    if args.learned:
+        from paper_2204_01722_b300 import learned
+        learned.main(["--n", str(args.n or 64), "--p", str(args.p), "--train", "20", "--test", "3", "--rhs", "1",
+                      "--pairs", "16", "--epochs", "10", "--coarse-fixed", "30", "--vectors", "32,128"])
         return
     if args.multiscale:
         args.n = args.n or 64

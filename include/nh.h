@@ -316,10 +316,10 @@ typedef struct {
                               1 = energy decrease with the optimal step a = z1.r / z1.J z1, i.e. z1.r > 0 */
   int learned_mode;        /* where a network set by nh_mg_set_learned acts:
                               1 = outer FCG stage (predicts the fine error at the vertices);
-                              2 = coarse warm start (predicts y ~ A_c^-1 r_c; the coarsest PCG starts
-                                  from a y, a = y.r_c / y.A_c y the step that minimises the A-norm
-                                  error along y, when a > 0 and that start at least halves the
-                                  residual's natural norm, else from zero);
+                              2 = coarse warm start (predicts y ~ A_c^-1 r_c; the coarsest PCG, or the
+                                  fixed polynomial with coarse_fixed, starts from a y, a = y.r_c / y.A_c y
+                                  the step that minimises the A-norm error along y, when a > 0 and that
+                                  start at least halves the residual's natural norm, else from zero);
                               3 = coarse post-correction: after the plain coarsest solve x1 (best with
                                   coarse_fixed), predicts the error A_c^-1 r1 it leaves from the scaled
                                   residual D_c^-1 r1, r1 = r_c - A_c x1, and adds a y,

@@ -60,6 +60,13 @@ __host__ __device__ constexpr int elem_stride() {
 // ---- TMA (1-D bulk copy) and mbarrier helpers -----------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// read-only global load that does not allocate in L1 (streamed data read once)
+__device__ __forceinline__ float ldg_stream(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -349,6 +356,202 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<T, Q>())
 }
 
 // ---------------------------------------------------------------------------
+// Float-float Jacobian action with the quadrature-plane loops rolled.  One
+// float-float multiply-add is 15 FP32 instructions, so the fully unrolled kernel
+// above is several times the instruction cache; here every loop over qk runs
+// one copy of its body (table coefficients indexed at run time from the
+// constant bank), the point values and z-fluxes live in shared memory instead
+// of qk-indexed registers, and the pointwise stage stays one out-of-line copy.
+// Element work area: [12][Q^3] ff (u values, x-, y-, z-fluxes / scratch).
+// ---------------------------------------------------------------------------
+#ifndef NH_FF_ROLLED
+#define NH_FF_ROLLED 1
+#endif
+
+// element stride in ff words, padded like elem_stride so that consecutive
+// elements of a warp start on different banks
+template <int Q>
+__host__ __device__ constexpr int ffr_stride() {
+  constexpr int base = 12 * Q * Q * Q, W = 16, want = (Q * Q) % W;
+  return Q * Q >= W ? base : base + ((want - base % W) % W + W) % W;
+}
+
+template <int P, int Q, int LAYOUT, bool COL = false>
+__global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<ff, Q>())
+    k_jacobian_apply_ffr(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
+                         const ff* __restrict__ qd, int64_t qstride, const KTab<P, Q, ff> tab,
+                         const double* __restrict__ du, double* __restrict__ y, int lift, int colour, int nx, int ny,
+                         int nz) {
+  constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  ff* sm = reinterpret_cast<ff*>(smraw);
+  const int t = threadIdx.x;
+  const int el = t / Q2, col = t - el * Q2;
+  const int a = col % Q, b = col / Q;
+  int64_t e = (int64_t)blockIdx.x * EPB + el;
+  bool live = e < ne;
+  if constexpr (COL) {
+    const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+    const int64_t cx = (nx - px + 1) / 2, cy = (ny - py + 1) / 2, cz = (nz - pz + 1) / 2;
+    live = e < cx * cy * cz;
+    const int64_t ix = e % cx, iy = (e / cx) % cy, iz = e / (cx * cy);
+    e = live ? (px + 2 * ix) + nx * ((py + 2 * iy) + (int64_t)ny * (pz + 2 * iz)) : 0;
+  }
+  ff* bA = sm + el * ffr_stride<Q>();  // [3][Q^3] each
+  ff* bB = bA + 3 * Q3;
+  ff* bC = bB + 3 * Q3;                 // point values
+  ff* bD = bC + 3 * Q3;                 // z-fluxes
+  // E and B_I along x: thread (a, b) < P owns node column (i = a, j = b) over k
+  int nid[P];
+  if (a < P && b < P) {
+    ff r[3][P];
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+      const int n = live ? __ldg(&emap[e * P3 + (k * P + b) * P + a]) : 0;
+      nid[k] = n;
+      const unsigned m = (!lift && live) ? (unsigned)__ldg(&bc[n]) : 0u;
+#pragma unroll
+      for (int c = 0; c < 3; c++) r[c][k] = (live && !((m >> c) & 1u)) ? ff(du[3 * (int64_t)n + c]) : ff(0);
+    }
+#pragma unroll 1
+    for (int qk = 0; qk < Q; qk++) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        ff s = ff(0);
+#pragma unroll
+        for (int k = 0; k < P; k++) s = madd(s, tab.B[qk][k], r[c][k]);
+        bA[sidx<Q>(c, qk, b, a)] = s;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < P; k++) nid[k] = 0;
+  }
+  __syncthreads();
+  if (a < P) {
+#pragma unroll 1
+    for (int qk = 0; qk < Q; qk++) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        ff s = ff(0);
+#pragma unroll
+        for (int j = 0; j < P; j++) s = madd(s, tab.B[b][j], bA[sidx<Q>(c, qk, j, a)]);
+        bB[sidx<Q>(c, qk, b, a)] = s;
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int qk = 0; qk < Q; qk++) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      ff s = ff(0);
+#pragma unroll
+      for (int i = 0; i < P; i++) s = madd(s, tab.B[a][i], bB[sidx<Q>(c, qk, b, i)]);
+      bC[sidx<Q>(c, qk, b, a)] = s;
+    }
+  }
+  __syncthreads();
+  // gradients, pointwise, fluxes: x-, y-flux to bA, bB; z-flux to bD
+  const ff* qe = qd + (live ? e : 0) * Q3 + b * Q + a;
+#pragma unroll 1
+  for (int qk = 0; qk < Q; qk++) {
+    ff g[3][3], f[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      ff gx = ff(0), gy = ff(0), gz = ff(0);
+#pragma unroll
+      for (int m = 0; m < Q; m++) {
+        gx = madd(gx, tab.D[a][m], bC[sidx<Q>(c, qk, b, m)]);
+        gy = madd(gy, tab.D[b][m], bC[sidx<Q>(c, qk, m, a)]);
+        gz = madd(gz, tab.D[qk][m], bC[sidx<Q>(c, m, b, a)]);
+      }
+      g[c][0] = gx;
+      g[c][1] = gy;
+      g[c][2] = gz;
+    }
+    if (live) {
+      pointwise_ff<LAYOUT>(qe + qk * Q2, qstride, g, f);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; i++) f[i / 3][i % 3] = ff(0);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      bA[sidx<Q>(c, qk, b, a)] = f[c][0];
+      bB[sidx<Q>(c, qk, b, a)] = f[c][1];
+      bD[sidx<Q>(c, qk, b, a)] = f[c][2];
+    }
+  }
+  __syncthreads();
+  // transposed collocated derivative, summed over the three directions -> bC
+#pragma unroll 1
+  for (int qk = 0; qk < Q; qk++) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      ff s = ff(0);
+#pragma unroll
+      for (int m = 0; m < Q; m++) {
+        s = madd(s, tab.D[m][a], bA[sidx<Q>(c, qk, b, m)]);
+        s = madd(s, tab.D[m][b], bB[sidx<Q>(c, qk, m, a)]);
+        s = madd(s, tab.D[m][qk], bD[sidx<Q>(c, m, b, a)]);
+      }
+      bC[sidx<Q>(c, qk, b, a)] = s;
+    }
+  }
+  __syncthreads();
+  if (a < P) {  // B_I^T along x
+#pragma unroll 1
+    for (int qk = 0; qk < Q; qk++) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        ff s = ff(0);
+#pragma unroll
+        for (int qi = 0; qi < Q; qi++) s = madd(s, tab.B[qi][a], bC[sidx<Q>(c, qk, b, qi)]);
+        bA[sidx<Q>(c, qk, b, a)] = s;
+      }
+    }
+  }
+  __syncthreads();
+  if (a < P && b < P) {  // B_I^T along y, then along z into the node column's registers
+    ff out[3][P];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int k = 0; k < P; k++) out[c][k] = ff(0);
+#pragma unroll 1
+    for (int qk = 0; qk < Q; qk++) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        ff w = ff(0);
+#pragma unroll
+        for (int qj = 0; qj < Q; qj++) w = madd(w, tab.B[qj][b], bA[sidx<Q>(c, qk, qj, a)]);
+#pragma unroll
+        for (int k = 0; k < P; k++) out[c][k] = madd(out[c][k], tab.B[qk][k], w);
+      }
+    }
+    if (live) {
+#pragma unroll
+      for (int k = 0; k < P; k++) {
+        const int n = nid[k];
+        const unsigned m = __ldg(&bc[n]);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const int64_t dof = 3 * (int64_t)n + c;
+          if ((m >> c) & 1u) {
+            if (!lift) y[dof] = du[dof];
+          } else if constexpr (COL) {
+            y[dof] += (double)out[c][k];
+          } else {
+            atomicAdd(&y[dof], (double)out[c][k]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP32 Jacobian action, line-parallel.  Each of an element's Q^2 threads owns one
 // 1-D line of the Q^3 (or P x Q^2 ...) lattice per stage -- an x-line (y, z), a
 // y-line (x, z) or a z-line (x, y) -- reads that line from shared memory once,
@@ -415,8 +618,19 @@ __device__ __forceinline__ void red_run(float* y, const float (&v)[N]) {
   }
 }
 
+#ifndef NH_F32_DIRECT_MINB
+#define NH_F32_DIRECT_MINB 1
+#endif
+#ifndef NH_F32_DIRECT_PF
+#define NH_F32_DIRECT_PF 1
+#endif
+#if NH_F32_DIRECT
+#define NH_F32L_BOUNDS(Q) __launch_bounds__(Q* Q* epb_for(Q), NH_F32_DIRECT_MINB)
+#else
+#define NH_F32L_BOUNDS(Q) __launch_bounds__(Q* Q* epb_for(Q))
+#endif
 template <int P, int Q, int LAYOUT, bool COL = false>
-__global__ void __launch_bounds__(Q* Q* epb_for(Q))
+__global__ void NH_F32L_BOUNDS(Q)
     k_jacobian_apply_f32l(int64_t ne, const unsigned* __restrict__ emapb, const float* __restrict__ qdb,
                           const KTab<P, Q, float> tab, const float* __restrict__ du, float* __restrict__ y, int lift,
                           int vec_ok, int rows_ok, int* __restrict__ err, int colour, int nbx, int ny, int nz) {
@@ -424,6 +638,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   constexpr int S = nh_layout_scalars(LAYOUT);
   constexpr long long BS = nh_f32_batch_floats(Q, S), PL = nh_f32_plane_floats(Q, S);
+  constexpr long long RING = NH_F32_DIRECT ? 0 : 2 * PL;  // floats of the plane ring in shared memory
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ unsigned srun[EPB * P * P];        // start node of each node line's run (or ~0)
@@ -444,7 +659,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
   }
   const int64_t e = batch * EPB + el;
   const bool live = e < ne;
-  float* A = qs + 2 * PL + L::elem(el);
+  float* A = qs + RING + L::elem(el);
   float* Bf = A + L::BUF;
   // z-plane qz of the batch's quadrature data -> slot qz & 1 (one bulk copy)
   auto issue_plane = [&](int qz) {
@@ -458,6 +673,17 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       bulk_g2s(dst + off, src + off, chunk, b);
     }
   };
+#if NH_F32_DIRECT
+  // plane 0 of this thread's point, loaded at the start so that it arrives
+  // during the interpolation stages
+  const float* qg = qdb + batch * BS + t;
+  float qv[S];
+  if constexpr (NH_F32_DIRECT_PF) {
+#pragma unroll
+    for (int k = 0; k < S; k++) qv[k] = ldg_stream(qg + k * nh_f32_npp(Q));
+  }
+  (void)issue_plane;
+#else
   if (t == 0) {
     mbar_init(&bar[0]);
     mbar_init(&bar[1]);
@@ -467,6 +693,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     issue_plane(0);
     issue_plane(1);
   }
+#endif
   // x-lines over nodes (j = u, k = v): gather and B_I along x
   const bool node_line = u < P && v < P;
   unsigned nid[P];
@@ -579,8 +806,21 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     float fz[3][Q];
 #pragma unroll
     for (int qz = 0; qz < Q; qz++) {
+#if NH_F32_DIRECT
+      float qn[S];  // the next plane's scalars, requested before this plane's work
+      if constexpr (NH_F32_DIRECT_PF) {
+        if (qz + 1 < Q) {
+#pragma unroll
+          for (int k = 0; k < S; k++) qn[k] = ldg_stream(qg + (qz + 1) * PL + k * nh_f32_npp(Q));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < S; k++) qv[k] = ldg_stream(qg + qz * PL + k * nh_f32_npp(Q));
+      }
+#else
       mbar_wait_bounded(&bar[qz & 1], (qz >> 1) & 1, err);
       const float* qp = qs + (qz & 1) * PL;  // this plane's slot
+#endif
       float g[3][3], f[3][3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -589,6 +829,9 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
         g[c][2] = gz[c][qz];
       }
       if (live) {
+#if NH_F32_DIRECT
+        nhpw::pointwise_ld<LAYOUT, float>([&](int i) { return qv[i]; }, g, f);
+#else
         // this point's scalars: S/4 rotated 16-byte chunks, then the remainder
         constexpr int NC = S / 4, R = S - 4 * NC, NP = EPB * Q2;
         float qv[S];
@@ -603,6 +846,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 #pragma unroll
         for (int j = 0; j < R; j++) qv[4 * NC + j] = qp[NP * 4 * NC + t * R + j];
         nhpw::pointwise_ld<LAYOUT, float>([&](int i) { return qv[i]; }, g, f);
+#endif
       } else {
 #pragma unroll
         for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.f;
@@ -613,10 +857,17 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
         Bf[L::ix(c, qz, v, u)] = f[c][1];
         fz[c][qz] = f[c][2];
       }
+#if NH_F32_DIRECT
+      if (NH_F32_DIRECT_PF && qz + 1 < Q) {
+#pragma unroll
+        for (int k = 0; k < S; k++) qv[k] = qn[k];
+      }
+#else
       if (qz + 2 < Q) {
         __syncthreads();
         if (t == 0) issue_plane(qz + 2);
       }
+#endif
     }
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -738,7 +989,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     chain = __syncthreads_and(chain) != 0;
   }
   if (chain) {
-    float* Rr = qs + 2 * PL + (v * P + u) * RS + ((3u * first) & 3u);  // node x, component c at 3 x + c
+    float* Rr = qs + RING + (v * P + u) * RS + ((3u * first) & 3u);  // node x, component c at 3 x + c
     if (node_line) {
 #pragma unroll
       for (int i = 1; i < P; i++)
@@ -760,7 +1011,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       for (int k = t; k < NR * RL; k += Q2 * EPB) {
         const int row = k / RL, off = k - row * RL;
         const unsigned f = srun[row];
-        y[3 * (int64_t)f + off] += qs[2 * PL + row * RS + ((3u * f) & 3u) + off];
+        y[3 * (int64_t)f + off] += qs[RING + row * RS + ((3u * f) & 3u) + off];
       }
       return;
     }
@@ -1139,12 +1390,41 @@ cudaError_t apply_launch(const OpArgs& A, cudaStream_t s) {
 }
 
 template <int P, int Q, int LAYOUT>
+cudaError_t apply_ffr_launch(const OpArgs& A, cudaStream_t s) {
+  constexpr int EPB = epb_for(Q);
+  const int threads = Q * Q * EPB;
+  const int64_t blocks = (A.ne + EPB - 1) / EPB;
+  if (blocks == 0) return cudaSuccess;
+  const size_t smem = (size_t)EPB * ffr_stride<Q>() * sizeof(ff);
+  const KTab<P, Q, ff> tab = make_ktab<P, Q, ff>(*A.tab);
+  if (A.colour >= 0) {
+    const int px = A.colour & 1, py = (A.colour >> 1) & 1, pz = A.colour >> 2;
+    const int64_t ncol = (int64_t)((A.nx - px + 1) / 2) * ((A.ny - py + 1) / 2) * ((A.nz - pz + 1) / 2);
+    const int64_t grid = (ncol + EPB - 1) / EPB;
+    if (grid == 0) return cudaSuccess;
+    cudaError_t e = prep<k_jacobian_apply_ffr<P, Q, LAYOUT, true>>(smem);
+    if (e != cudaSuccess) return e;
+    k_jacobian_apply_ffr<P, Q, LAYOUT, true><<<(unsigned)grid, threads, smem, s>>>(
+        A.ne, A.emap, A.bc, (const ff*)A.qd, A.qstride, tab, (const double*)A.in, (double*)A.out, A.lift, A.colour,
+        A.nx, A.ny, A.nz);
+    return cudaGetLastError();
+  }
+  cudaError_t e = prep<k_jacobian_apply_ffr<P, Q, LAYOUT>>(smem);
+  if (e != cudaSuccess) return e;
+  k_jacobian_apply_ffr<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
+      A.ne, A.emap, A.bc, (const ff*)A.qd, A.qstride, tab, (const double*)A.in, (double*)A.out, A.lift, -1, A.nx,
+      A.ny, A.nz);
+  return cudaGetLastError();
+}
+
+template <int P, int Q, int LAYOUT>
 cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   constexpr int EPB = epb_for(Q), S = nh_layout_scalars(LAYOUT);
   const int threads = Q * Q * EPB;
   const int64_t blocks = (A.ne + EPB - 1) / EPB;
   if (blocks == 0) return cudaSuccess;
-  const size_t smem = ((size_t)2 * nh_f32_plane_floats(Q, S) + (size_t)LineLayout<Q>::block_floats(EPB)) * sizeof(float);
+  const size_t smem = ((NH_F32_DIRECT ? 0 : (size_t)2 * nh_f32_plane_floats(Q, S)) +
+                       (size_t)LineLayout<Q>::block_floats(EPB)) * sizeof(float);
   const KTab<P, Q, float> tab = make_ktab<P, Q, float>(*A.tab);
   const int nbx = A.nx > 0 ? A.nx / EPB : 0;
   if (A.colour >= 0) {  // batches must tile the rows: one block's elements lie in one row
@@ -1174,6 +1454,10 @@ cudaError_t apply_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
     return A.layout == NH_LAYOUT_CURRENT   ? apply_launch<P, Q, double, double, NH_LAYOUT_CURRENT>(A, s)
            : A.layout == NH_LAYOUT_INITIAL ? apply_launch<P, Q, double, double, NH_LAYOUT_INITIAL>(A, s)
                                            : apply_launch<P, Q, double, double, NH_LAYOUT_TAPE>(A, s);
+  if (prec == NH_F64X && NH_FF_ROLLED)
+    return A.layout == NH_LAYOUT_CURRENT   ? apply_ffr_launch<P, Q, NH_LAYOUT_CURRENT>(A, s)
+           : A.layout == NH_LAYOUT_INITIAL ? apply_ffr_launch<P, Q, NH_LAYOUT_INITIAL>(A, s)
+                                           : apply_ffr_launch<P, Q, NH_LAYOUT_TAPE>(A, s);
   if (prec == NH_F64X)
     return A.layout == NH_LAYOUT_CURRENT   ? apply_launch<P, Q, ff, double, NH_LAYOUT_CURRENT>(A, s)
            : A.layout == NH_LAYOUT_INITIAL ? apply_launch<P, Q, ff, double, NH_LAYOUT_INITIAL>(A, s)

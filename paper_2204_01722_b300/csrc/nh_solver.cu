@@ -1408,7 +1408,12 @@ nh_status coarse_solve(nh_mg mg, Level& l) {
           CK(kv_axpby<double>(st, l.n, a, x, 0.0, z));  // x = a y
           CK(cudaMemcpyAsync(x, z, sizeof(double) * l.n, cudaMemcpyDeviceToDevice, st));
           mg->ctx->launches++;
-          ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its, true, sqrt(bb)));
+          if (mg->o.coarse_fixed > 0) {  // the fixed polynomial, started from a y
+            ST(coarse_cheb(mg, l, b, x, true));
+            its = mg->o.coarse_fixed;
+          } else {
+            ST(pcg64(mg, l, b, x, mg->o.coarse_rtol, mg->o.coarse_maxit, false, &its, true, sqrt(bb)));
+          }
           mg->coarse_its += its;
           mg->acc++;
           return NH_OK;

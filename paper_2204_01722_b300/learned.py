@@ -14,12 +14,14 @@ smooth seeded fields) nh_mg_collect records, at every coarsest solve along the
 FCG + V-cycle iterations of J x = b, the residual r1 that fixed solve leaves
 and its exact correction A_c^-1 r1.  The network (4 levels, 16/32/48/64
 channels, BF16 weights and activations, FP32 accumulation) is trained by Adam
-on the mean relative squared error and then acts as the coarse post-correction
-(learned_mode 3).  Held-out layouts: the tangent system at 1% compression with
-an N(0,1) right-hand side is solved to ||r|| <= 1e-8 ||b|| by plain FP64 p-MG
-(Jacobi-PCG coarse solve to 1e-3, the paper's), the mixed-precision V-cycle with
-the fixed coarse solve, the same with the learned post-correction, and the
-mixed-precision V-cycle with the geometric coarse multigrid.
+on the mean relative squared error; its predictions then span the learned
+coarse space (learned_mode 4).  Held-out layouts: the tangent system at 1%
+compression with an N(0,1) right-hand side is solved to ||r|| <= 1e-8 ||b|| by
+plain FP64 p-MG (Jacobi-PCG coarse solve to 1e-3, the paper's), the
+mixed-precision V-cycle with the fixed coarse solve, the same with a coarse
+space built without the network and with the learned coarse space (each size
+in --vectors), and the mixed-precision V-cycle with the geometric coarse
+multigrid; setup and solve are timed apart (median after a warm-up).
 """
 import argparse
 import json
@@ -172,7 +174,7 @@ def linear_eval(ctx, stream, pb, seed, net, coarse_fixed, vectors=(32,), rtol=1e
     return rows
 
 
-def main():
+def main(argv=None):
     import torch
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=64)
@@ -189,7 +191,7 @@ def main():
     ap.add_argument("--repeats", type=int, default=1)
     ap.add_argument("--vectors", default="32")
     ap.add_argument("--out", default=None)
-    a = ap.parse_args()
+    a = ap.parse_args(argv)
     stream = torch.cuda.Stream()
     res = dict(n=a.n, p=a.p, train_layouts=a.train, test_layouts=a.test, coarse_fixed=a.coarse_fixed,
                channels=a.channels, delta=a.delta)
