@@ -38,8 +38,10 @@ cudaError_t kv_gemv_rows(cudaStream_t st, int64_t n, int k, const double* W, int
 
 // Assembled Q1 operator on a structured node lattice: 27 neighbour 3x3 blocks per
 // node, stored [27][9][n_nodes].
+// f32: sum the element blocks in float-float arithmetic on the FP32 pipes (current layout;
+// the stencil stays FP64)
 cudaError_t ks_assemble_q1(int Q, cudaStream_t st, int64_t ne, int nx, int ny, int nz, const uint8_t* bc,
-                           const double* qd, int64_t qstride, int layout, const Tab1D* tab, double* A);
+                           const double* qd, int64_t qstride, int layout, const Tab1D* tab, double* A, int f32 = 0);
 cudaError_t ks_apply(cudaStream_t st, int Nx, int Ny, int Nz, const uint8_t* bc, const double* A, const double* x,
                      double* y);
 cudaError_t ks_diag(cudaStream_t st, int64_t nn, const uint8_t* bc, const double* A, double* d);

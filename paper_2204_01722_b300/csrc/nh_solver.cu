@@ -1064,8 +1064,9 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
     } else if (l.stencil) {
       CK(cudaMemsetAsync(l.A, 0, sizeof(double) * 243 * l.nn, st));
       const int64_t Q3 = (int64_t)root->space->Q * root->space->Q * root->space->Q;
+      // mixed precision: the element blocks are summed in float-float on the FP32 pipes
       CK(ks_assemble_q1(root->space->Q, st, l.space->ne, l.space->nx, l.space->ny, l.space->nz, l.space->bc, root->qd,
-                        root->space->ne * Q3, root->layout, &l.space->tab, l.A));
+                        root->space->ne * Q3, root->layout, &l.space->tab, l.A, mg->o.mixed ? 1 : 0));
       CK(ks_diag(st, l.nn, l.space->bc, l.A, l.dinv64));
       mg->ctx->launches += 2;
       ST(mark("stencil", lv, t0));

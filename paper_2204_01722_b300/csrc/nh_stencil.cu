@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "nh_ff.cuh"
 #include "nh_krylov.cuh"
 #include "nh_pointwise.cuh"
 
@@ -128,21 +129,25 @@ __global__ void k_diag(int64_t nn, const uint8_t* __restrict__ bc, const double*
 // so with g_a = grad_xi N_a and x_a = X^T g_a (the physical gradient)
 //   K_ab[c][c'] = sum_q delta_cc' g_a^T A g_b + a x_a,c x_b,c' + h x_a,c' x_b,c.
 // Per point, A and the 8 nodes' x_a and A g_a are formed once and shared by the
-// 64 (a, b) threads.
-template <int Q>
+// 64 (a, b) threads.  T: arithmetic of the per-point factors and of the sums over
+// the points: double, or float-float (ff) for the mixed-precision hierarchy --
+// FP64-accurate sums on the FP32 pipes, which issue 64 times the FP64 rate (plain
+// FP32 sums perturb the blocks enough, at stiffness contrast 1e3, to cost the
+// coarse solve 15% more iterations).
+template <int Q, typename T = double>
 __global__ void __launch_bounds__(64)
     k_assemble_current(int64_t ne, int nx, int ny, const double* __restrict__ qd, int64_t qstride, const Q1Tab<Q> tb,
                        double* __restrict__ A, int64_t nn, int Nx, int Ny, double* __restrict__ coo) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
-  __shared__ double sa[kQC], sh[kQC];
-  __shared__ double sx[kQC][8][3], sAg[kQC][8][3], sg[kQC][8][3];
+  __shared__ T sa[kQC], sh[kQC];
+  __shared__ T sx[kQC][8][3], sAg[kQC][8][3], sg[kQC][8][3];
   __shared__ double sA[kQC][6], sX[kQC][9];
   const int t = threadIdx.x;
   const int a = t & 7, b = t >> 3;
   const int64_t e = blockIdx.x;
   const int ai = a & 1, aj = (a >> 1) & 1, ak = a >> 2;
   const int bi = b & 1, bj = (b >> 1) & 1, bk = b >> 2;
-  double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  T K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   for (int q0 = 0; q0 < Q3; q0 += kQC) {
     // per point: X, a, h and A = X (W tau) X^T + h X X^T
     if (t < kQC && q0 + t < Q3) {
@@ -153,8 +158,8 @@ __global__ void __launch_bounds__(64)
       const double t12 = qp[12 * qstride], t02 = qp[13 * qstride], t01 = qp[14 * qstride];
       const double tau[3][3] = {{t00, t01, t02}, {t01, t11, t12}, {t02, t12, t22}};
       const double h = qp[16 * qstride];
-      sa[t] = qp[15 * qstride];
-      sh[t] = h;
+      sa[t] = (T)qp[15 * qstride];
+      sh[t] = (T)h;
       double XT[3][3];  // X (W tau)
       for (int d = 0; d < 3; d++)
         for (int k = 0; k < 3; k++) XT[d][k] = X[d][0] * tau[0][k] + X[d][1] * tau[1][k] + X[d][2] * tau[2][k];
@@ -181,28 +186,28 @@ __global__ void __launch_bounds__(64)
         const double* Am = sA[ql];
         const double As[3][3] = {{Am[0], Am[5], Am[4]}, {Am[5], Am[1], Am[3]}, {Am[4], Am[3], Am[2]}};
         for (int c = 0; c < 3; c++) {
-          sx[ql][nd][c] = X[0 * 3 + c] * g[0] + X[1 * 3 + c] * g[1] + X[2 * 3 + c] * g[2];
-          sAg[ql][nd][c] = As[c][0] * g[0] + As[c][1] * g[1] + As[c][2] * g[2];
-          sg[ql][nd][c] = g[c];
+          sx[ql][nd][c] = (T)(X[0 * 3 + c] * g[0] + X[1 * 3 + c] * g[1] + X[2 * 3 + c] * g[2]);
+          sAg[ql][nd][c] = (T)(As[c][0] * g[0] + As[c][1] * g[1] + As[c][2] * g[2]);
+          sg[ql][nd][c] = (T)g[c];
         }
       }
     }
     __syncthreads();
     for (int ql = 0; ql < kQC && q0 + ql < Q3; ql++) {
-      const double* xa = sx[ql][a];
-      const double* xb = sx[ql][b];
-      const double gAg = sAg[ql][a][0] * sg[ql][b][0] + sAg[ql][a][1] * sg[ql][b][1] + sAg[ql][a][2] * sg[ql][b][2];
-      const double wa = sa[ql], wh = sh[ql];
+      const T* xa = sx[ql][a];
+      const T* xb = sx[ql][b];
+      const T gAg = sAg[ql][a][0] * sg[ql][b][0] + sAg[ql][a][1] * sg[ql][b][1] + sAg[ql][a][2] * sg[ql][b][2];
+      const T wa = sa[ql], wh = sh[ql];
 #pragma unroll
       for (int c = 0; c < 3; c++)
 #pragma unroll
-        for (int cp = 0; cp < 3; cp++) K[c][cp] += (c == cp ? gAg : 0.0) + wa * xa[c] * xb[cp] + wh * xa[cp] * xb[c];
+        for (int cp = 0; cp < 3; cp++) K[c][cp] += (c == cp ? gAg : T(0)) + wa * xa[c] * xb[cp] + wh * xa[cp] * xb[c];
     }
     __syncthreads();
   }
   if (coo) {  // general mesh: the block goes to its COO slot (e, a, b)
 #pragma unroll
-    for (int c = 0; c < 9; c++) coo[((e * 64) + a * 8 + b) * 9 + c] = K[c / 3][c % 3];
+    for (int c = 0; c < 9; c++) coo[((e * 64) + a * 8 + b) * 9 + c] = (double)K[c / 3][c % 3];
     return;
   }
   const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
@@ -211,12 +216,12 @@ __global__ void __launch_bounds__(64)
 #pragma unroll
   for (int c = 0; c < 3; c++)
 #pragma unroll
-    for (int cp = 0; cp < 3; cp++) atomicAdd(&A[((int64_t)s * 9 + c * 3 + cp) * nn + na], K[c][cp]);
+    for (int cp = 0; cp < 3; cp++) atomicAdd(&A[((int64_t)s * 9 + c * 3 + cp) * nn + na], (double)K[c][cp]);
 }
 
 template <int Q>
 cudaError_t assemble_q(cudaStream_t st, int64_t ne, int nx, int ny, int nz, const double* qd, int64_t qstride,
-                       int layout, const Tab1D* tab, double* A, double* coo = nullptr) {
+                       int layout, const Tab1D* tab, double* A, double* coo = nullptr, int f32 = 0) {
   Q1Tab<Q> tb;
   for (int i = 0; i < Q; i++)
     for (int j = 0; j < 2; j++) {
@@ -226,7 +231,9 @@ cudaError_t assemble_q(cudaStream_t st, int64_t ne, int nx, int ny, int nz, cons
   const int Nx = nx + 1, Ny = ny + 1;
   const int64_t nn = (int64_t)Nx * Ny * (nz + 1);
   if (ne == 0) return cudaSuccess;
-  if (layout == NH_LAYOUT_CURRENT)
+  if (layout == NH_LAYOUT_CURRENT && f32)
+    k_assemble_current<Q, ff><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny, coo);
+  else if (layout == NH_LAYOUT_CURRENT)
     k_assemble_current<Q><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny, coo);
   else if (layout == NH_LAYOUT_INITIAL)
     k_assemble<Q, NH_LAYOUT_INITIAL><<<(unsigned)ne, 64, 0, st>>>(ne, nx, ny, qd, qstride, tb, A, nn, Nx, Ny, coo);
@@ -374,14 +381,14 @@ void ks_coo_symbolic(int64_t ne, int64_t nn, const int* emap, std::vector<int64_
 }
 
 cudaError_t ks_assemble_q1(int Q, cudaStream_t st, int64_t ne, int nx, int ny, int nz, const uint8_t* bc,
-                           const double* qd, int64_t qstride, int layout, const Tab1D* tab, double* A) {
+                           const double* qd, int64_t qstride, int layout, const Tab1D* tab, double* A, int f32) {
   cudaError_t e = cudaErrorInvalidValue;
   switch (Q) {
-    case 2: e = assemble_q<2>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
-    case 3: e = assemble_q<3>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
-    case 4: e = assemble_q<4>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
-    case 5: e = assemble_q<5>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
-    case 6: e = assemble_q<6>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A); break;
+    case 2: e = assemble_q<2>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A, nullptr, f32); break;
+    case 3: e = assemble_q<3>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A, nullptr, f32); break;
+    case 4: e = assemble_q<4>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A, nullptr, f32); break;
+    case 5: e = assemble_q<5>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A, nullptr, f32); break;
+    case 6: e = assemble_q<6>(st, ne, nx, ny, nz, qd, qstride, layout, tab, A, nullptr, f32); break;
   }
   if (e != cudaSuccess) return e;
   const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
