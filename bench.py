@@ -375,6 +375,22 @@ def run_nh(args):
                                   "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4),
                                   "gdofs_e2e": round(c.nd / te / 1e9, 3)})
                 c.close()
+        sizes = []
+        if args.sweep and rank == 0:
+            # the ~1 M and ~50 M DoF rows of the Q2-Q4 sweep (the ~10 M rows are `sweep`)
+            for sp_, n_ in ((2, 34), (2, 128), (3, 23), (3, 85), (4, 17), (4, 64)):
+                c = Case(nh, torch, ctx, sp_, n_)
+                Sx, _ = nh.nh_op_info(ctx, c.op)
+                for pr in ("f64", "f64x", "f32"):
+                    kernel_ms(nh, ctx, c, pr, 3)
+                    k = kernel_ms(nh, ctx, c, pr, 10)
+                    w_ = 4 if pr == "f32" else 8
+                    gbs = apply_bytes(sp_, n_, w_, Sx, bc_byte=pr != "f32") / (k * 1e-3) / 1e9
+                    tfl = apply_flops(sp_, n_) / (k * 1e-3) / 1e12
+                    sizes.append({"p": sp_, "n": n_, "n_dof": c.nd, "prec": pr,
+                                  "gdofs_kernel": round(c.nd / (k * 1e-3) / 1e9, 3), "kernel_ms": round(k, 4),
+                                  "hbm_frac": round(gbs / hbm, 4), "alu_frac": round(tfl / pk[pr], 4)})
+                c.close()
         scatter = []
         if args.sweep and rank == 0:
             # atomics against the eight-colour scatter (no atomics, eight launches), at
@@ -418,6 +434,8 @@ def run_nh(args):
             out["layouts"] = layouts
         if scatter:
             out["scatter"] = scatter
+        if sizes:
+            out["sweep_sizes"] = sizes
         if solve:
             out["solve"] = solve
         if multi:

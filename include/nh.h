@@ -219,7 +219,8 @@ nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* du_host, vo
 
 /* Diagonal of the assembled Jacobian for Jacobi smoothing (Sec. III-B):
  * diag[a,c] = sum_e sum_q sum_{d,d'} B_xi,d[q,a] D[q; c,d; c,d'] B_xi,d'[q,a];
- * 1 on constrained DoFs.  Device out [n_dof] of prec type. */
+ * 1 on constrained DoFs.  Device out [n_dof] of prec type, computed in that
+ * precision's arithmetic (NH_F32: FP32, from the FP64 quadrature data). */
 nh_status nh_jacobian_diagonal(nh_op op, nh_prec prec, void* diag);
 /* Assembled operator on a Q1 (p = 1) space as 3x3 block rows (Sec. III-D: the
  * split-phase COO assembly that hands the coarse level to a sparse solver).
@@ -313,7 +314,8 @@ typedef struct {
   int line_search;         /* 1: one secant step on F(u + a du)^T du = 0 (critical point) */
   int verbose;             /* 1: one line per Newton step on stderr */
   int learned_accept;      /* outer learned stage test: 0 = ||r - J z1||_2 < ||r||_2 (z1 as is);
-                              1 = energy decrease with the optimal step a = z1.r / z1.J z1, i.e. z1.r > 0 */
+                              1 = energy decrease with the optimal step a = z1.r / z1.J z1, i.e. z1.r > 0;
+                              learned_mode 4 without a network: 1 = exact coarse space (see there) */
   int learned_mode;        /* where a network set by nh_mg_set_learned acts:
                               1 = outer FCG stage (predicts the fine error at the vertices);
                               2 = coarse warm start (predicts y ~ A_c^-1 r_c; the coarsest PCG, or the
@@ -332,7 +334,9 @@ typedef struct {
                                   balancing map x = W W^T b + (I - W W^T A_c) Q (I - A_c W W^T) b around
                                   the plain coarsest solve Q: linear, symmetric positive definite, fixed
                                   between setups.  With no network set, W is built from the probes' x1
-                                  (the same construction without the learned part) */
+                                  (the same construction without the learned part), or, with
+                                  learned_accept = 1, from the exact errors A_c^-1 r1 (coarse PCG to
+                                  1e-9 per probe: the space a perfect network would give) */
   int fp64_kind;           /* arithmetic of the FP64-accurate matrix-free applies (outer FCG, Lanczos,
                               FP64 smoothers): 0 = native FP64 (NH_F64), 1 = float-float (NH_F64X) */
   int coarse_rediscretize; /* 1: matrix-free coarse levels get their own Gauss rule q = p_l + 1 and

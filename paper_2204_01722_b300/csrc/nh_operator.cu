@@ -43,9 +43,12 @@ __host__ __device__ constexpr int epb_for(int Q) { return nh_epb(Q); }
 #ifndef NH_FF_MIN_BLOCKS_SMALLQ
 #define NH_FF_MIN_BLOCKS_SMALLQ 4
 #endif
+// Rolled float-float kernel (Q2 / Q3 / Q4 GDoF/s on B300 with 3, 4, 5 blocks of
+// registers per SM): q = 3 6.08 / 6.08 / 6.40, q = 4 6.99 / 7.58 / 7.26, q = 5
+// 7.07 / 7.06 / 7.09 (2, 3, 4 blocks).
 template <typename T, int Q>
 __host__ __device__ constexpr int apply_min_blocks() {
-  return std::is_same<T, ff>::value ? (Q <= 4 ? NH_FF_MIN_BLOCKS_SMALLQ : 3) : 1;
+  return std::is_same<T, ff>::value ? (Q <= 3 ? 5 : Q == 4 ? NH_FF_MIN_BLOCKS_SMALLQ : 3) : 1;
 }
 
 // Shared-memory stride of one element's [9][Q^3] work area, padded so that the
@@ -1216,26 +1219,27 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
 // contracted direction by direction with the elementwise products of the 1-D
 // value/derivative tables (B.B, B.G, G.G).
 // ---------------------------------------------------------------------------
-template <int P, int Q>
+template <int P, int Q, typename T = double>
 struct DiagTab {
-  double BB[Q][P], BG[Q][P], GG[Q][P];
+  T BB[Q][P], BG[Q][P], GG[Q][P];
 };
 
 template <int P, int Q, int LAYOUT, typename TO>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     k_diagonal(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
-               const double* __restrict__ qd, int64_t qstride, const DiagTab<P, Q> dt, TO* __restrict__ diag) {
+               const double* __restrict__ qd, int64_t qstride, const DiagTab<P, Q, TO> dt, TO* __restrict__ diag) {
+  using T = TO;  // arithmetic in the output's precision (FP32 for the FP32 smoothers' diagonals)
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* sm = reinterpret_cast<double*>(smraw);
+  T* sm = reinterpret_cast<T*>(smraw);
   const int t = threadIdx.x;
   const int el = t / Q2, col = t - el * Q2;
   const int a = col % Q, b = col / Q;
   const int64_t e = (int64_t)blockIdx.x * EPB + el;
   const bool live = e < ne;
-  double* Dsm = sm + el * 11 * Q3;  // [9][Q][Q][Q]
-  double* s1 = Dsm + 9 * Q3;        // [P][Q][Q]
-  double* s2 = s1 + Q3;             // [P][P][Q]
+  T* Dsm = sm + el * 11 * Q3;  // [9][Q][Q][Q]
+  T* s1 = Dsm + 9 * Q3;        // [P][Q][Q]
+  T* s2 = s1 + Q3;             // [P][P][Q]
   const double* qe = qd + (live ? e : 0) * Q3 + b * Q + a;
 
   for (int c = 0; c < 3; c++) {
@@ -1243,21 +1247,21 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       if (LAYOUT == NH_LAYOUT_CURRENT) {
         // closed form of Eq. dtau's tangent block: D^c[d][d'] = A_dd' + (a + h) X_dc X_d'c,
         // A = X (W tau) X^T + h X X^T, a = W lambda, h = W (mu - lambda log J)
-        double Dc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        T Dc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         if (live) {
           const double* qp = qe + qk * Q2;
-          double X[3][3];
+          T X[3][3];
 #pragma unroll
-          for (int i = 0; i < 9; i++) X[i / 3][i % 3] = qp[i * qstride];
-          const double t00 = qp[9 * qstride], t11 = qp[10 * qstride], t22 = qp[11 * qstride];
-          const double t12 = qp[12 * qstride], t02 = qp[13 * qstride], t01 = qp[14 * qstride];
-          const double tau[3][3] = {{t00, t01, t02}, {t01, t11, t12}, {t02, t12, t22}};
-          const double wa = qp[15 * qstride], wh = qp[16 * qstride];
+          for (int i = 0; i < 9; i++) X[i / 3][i % 3] = (T)qp[i * qstride];
+          const T t00 = (T)qp[9 * qstride], t11 = (T)qp[10 * qstride], t22 = (T)qp[11 * qstride];
+          const T t12 = (T)qp[12 * qstride], t02 = (T)qp[13 * qstride], t01 = (T)qp[14 * qstride];
+          const T tau[3][3] = {{t00, t01, t02}, {t01, t11, t12}, {t02, t12, t22}};
+          const T wa = (T)qp[15 * qstride], wh = (T)qp[16 * qstride];
 #pragma unroll
           for (int d = 0; d < 3; d++)
 #pragma unroll
             for (int dp = 0; dp < 3; dp++) {
-              double v = (wa + wh) * X[d][c] * X[dp][c];
+              T v = (wa + wh) * X[d][c] * X[dp][c];
 #pragma unroll
               for (int k = 0; k < 3; k++)
                 v += (X[d][0] * tau[0][k] + X[d][1] * tau[1][k] + X[d][2] * tau[2][k] + wh * X[d][k]) * X[dp][k];
@@ -1272,33 +1276,34 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       }
 #pragma unroll
       for (int dp = 0; dp < 3; dp++) {
-        double g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, f[3][3];
-        g[c][dp] = 1.0;
+        T g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, f[3][3];
+        g[c][dp] = T(1);
         if (live) {
-          pointwise<LAYOUT, double>(qe + qk * Q2, qstride, g, f);
+          const double* qp = qe + qk * Q2;
+          nhpw::pointwise_ld<LAYOUT, T>([&](int i) { return (T)qp[i * qstride]; }, g, f);
         } else {
 #pragma unroll
-          for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.0;
+          for (int i = 0; i < 9; i++) f[i / 3][i % 3] = T(0);
         }
 #pragma unroll
         for (int d = 0; d < 3; d++) Dsm[((d * 3 + dp) * Q + qk) * Q2 + b * Q + a] = f[c][d];
       }
     }
     __syncthreads();
-    double acc[P];
+    T acc[P];
 #pragma unroll
-    for (int k = 0; k < P; k++) acc[k] = 0.0;
+    for (int k = 0; k < P; k++) acc[k] = T(0);
 #pragma unroll
     for (int pr = 0; pr < 9; pr++) {
       const int d = pr / 3, dp = pr % 3;
-      const double(*Mx)[P] = (d == 0 && dp == 0) ? dt.GG : ((d == 0 || dp == 0) ? dt.BG : dt.BB);
-      const double(*My)[P] = (d == 1 && dp == 1) ? dt.GG : ((d == 1 || dp == 1) ? dt.BG : dt.BB);
-      const double(*Mz)[P] = (d == 2 && dp == 2) ? dt.GG : ((d == 2 || dp == 2) ? dt.BG : dt.BB);
-      const double* F = Dsm + pr * Q3;
+      const T(*Mx)[P] = (d == 0 && dp == 0) ? dt.GG : ((d == 0 || dp == 0) ? dt.BG : dt.BB);
+      const T(*My)[P] = (d == 1 && dp == 1) ? dt.GG : ((d == 1 || dp == 1) ? dt.BG : dt.BB);
+      const T(*Mz)[P] = (d == 2 && dp == 2) ? dt.GG : ((d == 2 || dp == 2) ? dt.BG : dt.BB);
+      const T* F = Dsm + pr * Q3;
       // z: thread (qi=a, qj=b)
 #pragma unroll
       for (int k = 0; k < P; k++) {
-        double s = 0.0;
+        T s = T(0);
 #pragma unroll
         for (int qk = 0; qk < Q; qk++) s += Mz[qk][k] * F[qk * Q2 + b * Q + a];
         s1[(k * Q + b) * Q + a] = s;
@@ -1308,7 +1313,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       if (b < P) {
 #pragma unroll
         for (int k = 0; k < P; k++) {
-          double s = 0.0;
+          T s = T(0);
 #pragma unroll
           for (int qj = 0; qj < Q; qj++) s += My[qj][b] * s1[(k * Q + qj) * Q + a];
           s2[(k * P + b) * Q + a] = s;
@@ -1319,7 +1324,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
       if (a < P && b < P) {
 #pragma unroll
         for (int k = 0; k < P; k++) {
-          double s = 0.0;
+          T s = T(0);
 #pragma unroll
           for (int qi = 0; qi < Q; qi++) s += Mx[qi][a] * s2[(k * P + b) * Q + qi];
           acc[k] += s;
@@ -1498,8 +1503,8 @@ cudaError_t diag_launch(const OpArgs& A, cudaStream_t s) {
   const int threads = Q * Q * EPB;
   const int64_t blocks = (A.ne + EPB - 1) / EPB;
   if (blocks == 0) return cudaSuccess;
-  const size_t smem = (size_t)EPB * 11 * Q3 * sizeof(double);
-  DiagTab<P, Q> dt;
+  const size_t smem = (size_t)EPB * 11 * Q3 * sizeof(TO);
+  DiagTab<P, Q, TO> dt;
   for (int i = 0; i < Q; i++)
     for (int j = 0; j < P; j++) {
       dt.BB[i][j] = A.tab->B[i][j] * A.tab->B[i][j];

@@ -1075,7 +1075,13 @@ extern "C" nh_status nh_mg_setup(nh_mg mg) {
         ST(nh_qdata_setup_rediscretized(l.op, root, root->u_state, nullptr));
         ST(mark("qdata", lv, t0));
       }
-      ST(nh_jacobian_diagonal(l.op, NH_F64, l.dinv64));
+      if (l.prec == NH_F32) {  // FP32 smoother level: the diagonal in FP32 arithmetic
+        ST(nh_jacobian_diagonal(l.op, NH_F32, l.dinv));
+        CK((kv_convert<float, double>(st, l.n, (const float*)l.dinv, l.dinv64)));
+        mg->ctx->launches++;
+      } else {
+        ST(nh_jacobian_diagonal(l.op, NH_F64, l.dinv64));
+      }
       ST(mark("diagonal", lv, t0));
     }
     CK(kv_recip<double>(st, l.n, l.dinv64));
@@ -1233,7 +1239,9 @@ nh_status coarse_post_correct(nh_mg mg, Level& l, const double* b, double* x) {
 // e1 = A_c^-1 r1 that remains, y_j = N(r1).  The y_j are A_c-orthonormalised
 // (classical Gram-Schmidt, twice), dropping any whose A_c-norm falls below
 // 1e-8 of its norm before the projection.  Without a network, y_j = x1 (the
-// plain solve's own output: the non-learned coarse space of the same size).
+// plain solve's own output: the non-learned coarse space of the same size), or,
+// with learned_accept = 1, the exact error A_c^-1 r1 (the space a perfect
+// network would span; a diagnostic, each vector costs a coarse PCG to 1e-9).
 nh_status build_coarse_space(nh_mg mg) {
   Level& l = mg->L.back();
   cudaStream_t st = mg->ctx->stream;
@@ -1256,7 +1264,15 @@ nh_status build_coarse_space(nh_mg mg) {
     mg->ctx->launches += 2;
     int its = 0;
     ST(coarse_plain(mg, l, r, x1, &its));
-    if (mg->net) {
+    if (!mg->net && mg->o.learned_accept == 1) {
+      // diagnostic: the exact errors the plain solve leaves, A_c^-1 r1 (PCG to 1e-9),
+      // i.e. the coarse space a perfect network would give
+      ST(level_apply(mg, l, NH_F64, x1, ay));
+      CK(kv_axpby<double>(st, l.n, -1.0, ay, 1.0, r));  // r1 = r - A x1
+      mg->ctx->launches++;
+      int its2 = 0;
+      ST(pcg64(mg, l, r, y, 1e-9, 20000, false, &its2));
+    } else if (mg->net) {
       ST(level_apply(mg, l, NH_F64, x1, ay));
       CK(kv_axpby<double>(st, l.n, -1.0, ay, 1.0, r));  // r1 = r - A x1
       CK(kv_mul<double>(st, l.n, l.dinv64, r, y));      // network input: D^-1 r1

@@ -79,7 +79,8 @@ def rhs_vectors(pb, seed, k):
     return out
 
 
-VARIANTS = ("plain_fp64", "mixed_fixed", "mixed_fixed_space", "mixed_fixed_learned", "mixed_geometric")
+VARIANTS = ("plain_fp64", "mixed_fixed", "mixed_fixed_space", "mixed_fixed_learned", "mixed_fixed_exact",
+            "mixed_geometric")
 
 
 def variant_opts(ctx, pb, name, coarse_fixed, vectors=32):
@@ -87,6 +88,8 @@ def variant_opts(ctx, pb, name, coarse_fixed, vectors=32):
               mixed_fixed=dict(mixed=1, coarse_fixed=coarse_fixed, learned_mode=3),
               mixed_fixed_space=dict(mixed=1, coarse_fixed=coarse_fixed, learned_mode=4, learned_vectors=vectors),
               mixed_fixed_learned=dict(mixed=1, coarse_fixed=coarse_fixed, learned_mode=4, learned_vectors=vectors),
+              mixed_fixed_exact=dict(mixed=1, coarse_fixed=coarse_fixed, learned_mode=4, learned_vectors=vectors,
+                                     learned_accept=1),
               mixed_geometric=dict(mixed=1, coarse_solver=1))[name]
     return nh.nh_mg_default_opts(ctx, pb["op"], **kw)
 
@@ -140,14 +143,16 @@ def validation_loss(ctx, net, feats, tgts):
     return float(np.mean(errs)) if errs else float("nan")
 
 
-def linear_eval(ctx, stream, pb, seed, net, coarse_fixed, vectors=(32,), rtol=1e-8, maxit=2000, repeats=1):
+def linear_eval(ctx, stream, pb, seed, net, coarse_fixed, vectors=(32,), rtol=1e-8, maxit=2000, repeats=1,
+                exact=False):
     """Tangent solve J x = b at the current state, per solver variant: setup
     (diagonals, Lanczos, coarse level, coarse space) and solve timed apart, each
     the median over `repeats` runs after one discarded warm-up."""
     import torch
     b = torch.from_numpy(rhs_vectors(pb, 10 ** 6 + seed, 1)[0]).cuda()
     rows = []
-    runs = [(name, k) for name in VARIANTS for k in (vectors if "space" in name or "learned" in name else (0,))]
+    runs = [(name, k) for name in VARIANTS if name != "mixed_fixed_exact" or exact
+            for k in (vectors if "space" in name or "learned" in name or "exact" in name else (0,))]
     for name, k in runs:
         mg = nh.nh_mg_create(ctx, pb["op"], variant_opts(ctx, pb, name, coarse_fixed, k))
         if name == "mixed_fixed_learned":
@@ -165,7 +170,7 @@ def linear_eval(ctx, stream, pb, seed, net, coarse_fixed, vectors=(32,), rtol=1e
             t_setup.append(t1 - t0)
             t_solve.append(time.perf_counter() - t1)
         d = rep.as_dict()
-        d.update(layout=seed, solver=name if k == vectors[0] or k == 0 else f"{name}_{k}",
+        d.update(layout=seed, solver=name if k in (0, vectors[0]) else f"{name}_{k}",
                  t_setup=float(np.median(t_setup[1:])),
                  seconds=float(np.median(t_solve[1:])))
         d["total"] = d["t_setup"] + d["seconds"]
@@ -190,6 +195,8 @@ def main(argv=None):
     ap.add_argument("--delta", type=float, default=0.01)
     ap.add_argument("--repeats", type=int, default=1)
     ap.add_argument("--vectors", default="32")
+    ap.add_argument("--exact-space", action="store_true",
+                    help="also evaluate the coarse space of exact coarse errors (what a perfect network would give)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     stream = torch.cuda.Stream()
@@ -227,7 +234,7 @@ def main(argv=None):
             vloss.append(validation_loss(ctx, net, f, t))
             del f, t
             rows += linear_eval(ctx, stream, pb, s, net, a.coarse_fixed, [int(v) for v in a.vectors.split(",")],
-                                repeats=a.repeats)
+                                repeats=a.repeats, exact=a.exact_space)
             close(pb)
             if a.out:   # partial results after every held-out layout
                 with open(a.out, "w") as f:
