@@ -351,8 +351,8 @@ def test_post_correction_keeps_fcg_exact(nhctx):
 
 
 def test_four_level_network_at_33(nhctx):
-    """The configuration-5 architecture (4 levels, 16/32/48/64 channels, three
-    stride-2 levels 33 -> 17 -> 9 -> 5) in FP32 mode on a 33^3 grid: forward
+    """The architecture of the 65^3 study (4 levels, 16/32/48/64 channels) on a
+    33^3 grid (three stride-2 levels 33 -> 17 -> 9 -> 5) in FP32 mode: forward
     against the FP64 oracle, norm-wise and per entry against the largest entry
     (2e-5)."""
     ctx, _ = nhctx
