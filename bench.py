@@ -759,7 +759,7 @@ def main():
                     help="run the mixed-precision multiscale solve (Q3 on 64^3 by default) instead of the bench")
     ap.add_argument("--learned", action="store_true",
                     help="run the learned-coarse-space study (training on 20 inclusion layouts of Q3 on 64^3, "
-                         "3 held-out layouts; about 30 minutes) instead of the bench; prints its JSON line")
+                         "5 held-out layouts; about 35 minutes) instead of the bench; prints its JSON line")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per apply from an ncu capture of this kernel (reported as is)")
     args = ap.parse_args()
@@ -768,7 +768,7 @@ def main():
         return
     if args.learned:
         from paper_2204_01722_b300 import learned
-        learned.main(["--n", str(args.n or 64), "--p", str(args.p), "--train", "20", "--test", "3", "--rhs", "1",
+        learned.main(["--n", str(args.n or 64), "--p", str(args.p), "--train", "20", "--test", "5", "--rhs", "1",
                       "--pairs", "16", "--epochs", "10", "--coarse-fixed", "30", "--vectors", "32,128"])
         return
     if args.multiscale:

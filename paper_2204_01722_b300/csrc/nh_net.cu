@@ -17,6 +17,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "nh_net.cuh"
@@ -95,6 +96,92 @@ __global__ void __launch_bounds__(128)
     if (yo) yo[(int64_t)c * nout + o] = fromf<TA>(v);  // stored activation: relu mask of the backward pass
     if (yf) yf[(int64_t)c * nout + o] = v + (add ? tof(add[(int64_t)c * nout + o]) : 0.f);
   }
+}
+
+// ---- forward convolution on the tensor cores (BF16 activations and weights) -----
+// Implicit GEMM out[o][co] = sum_k A[o][k] B[k][co] over k = ci * 27 + tap, with
+// A[o][k] = x[ci][neighbour(o, tap)] gathered (zero outside the grid) and
+// B[k][co] = W[co][ci][tap], on mma.sync m16n8k16 (BF16 operands, FP32
+// accumulation).  A warp owns 16 consecutive output voxels and all CO output
+// channels (CO / 8 accumulator tiles); a block of 4 warps owns 64 voxels.  The
+// gathered activations and the weights are read through the L1 cache (every warp
+// of a block reads the same weights).  Same epilogue as k_conv_fwd.
+__device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+template <int CO>
+__global__ void __launch_bounds__(128)
+    k_conv_fwd_mma(const __nv_bfloat16* __restrict__ x, int Cin, int Nin, const __nv_bfloat16* __restrict__ W,
+                   const float* __restrict__ bias, int Nout, int stride, int relu,
+                   const __nv_bfloat16* __restrict__ add, __nv_bfloat16* __restrict__ yo, float* __restrict__ yf) {
+  constexpr int NT = (CO + 7) / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int64_t nout = (int64_t)Nout * Nout * Nout, nin = (int64_t)Nin * Nin * Nin;
+  const int64_t o0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
+  const int K = Cin * 27;
+  // the two output voxels whose A rows this lane supplies (rows g and g + 8)
+  int bi[2], bj[2], bk[2];
+  bool ov[2];
+#pragma unroll
+  for (int r = 0; r < 2; r++) {
+    const int64_t o = o0 + g + 8 * r;
+    ov[r] = o < nout;
+    const int64_t oc = ov[r] ? o : 0;
+    bi[r] = stride * (int)(oc % Nout) - 1;
+    bj[r] = stride * (int)((oc / Nout) % Nout) - 1;
+    bk[r] = stride * (int)(oc / ((int64_t)Nout * Nout)) - 1;
+  }
+  auto fetch = [&](int r, int k) -> __nv_bfloat16 {
+    if (!ov[r] || k >= K) return __float2bfloat16(0.f);
+    const int ci = k / 27, tap = k - ci * 27;
+    const int ii = bi[r] + tap % 3, jj = bj[r] + (tap / 3) % 3, kk = bk[r] + tap / 9;
+    if (ii < 0 || ii >= Nin || jj < 0 || jj >= Nin || kk < 0 || kk >= Nin) return __float2bfloat16(0.f);
+    return x[(int64_t)ci * nin + ii + (int64_t)Nin * (jj + (int64_t)Nin * kk)];
+  };
+  float acc[NT][4];
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc[t][i] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    unsigned a[4];
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        const int k = k0 + 8 * h + 2 * tq;
+        a[2 * h + r] = pack_bf16(fetch(r, k), fetch(r, k + 1));
+      }
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+      const int co = t * 8 + g;
+      unsigned b[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int k = k0 + 8 * h + 2 * tq;  // even, and K is even: k < K implies k + 1 < K
+        b[h] = (co < CO && k < K) ? __ldg(reinterpret_cast<const unsigned*>(W + (int64_t)co * K + k)) : 0u;
+      }
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%0,%1,%2,%3};"
+          : "+f"(acc[t][0]), "+f"(acc[t][1]), "+f"(acc[t][2]), "+f"(acc[t][3])
+          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const int r = i >> 1, co = t * 8 + 2 * tq + (i & 1);
+      if (!ov[r] || co >= CO) continue;
+      const int64_t o = o0 + g + 8 * r;
+      float v = acc[t][i] + bias[co];
+      if (relu) v = fmaxf(v, 0.f);
+      if (yo) yo[(int64_t)co * nout + o] = __float2bfloat16(v);
+      if (yf) yf[(int64_t)co * nout + o] = v + (add ? __bfloat162float(add[(int64_t)co * nout + o]) : 0.f);
+    }
 }
 
 // ---- input gradient of a convolution: one thread per input voxel ---------------
@@ -328,6 +415,7 @@ struct Layer {
 struct nh_net_s {
   nh_ctx ctx = nullptr;
   int N = 0, levels = 0, bf16 = 1;
+  int mma = 1;                  // BF16 forward convolutions on the tensor cores (else the CUDA-core kernel)
   int ch[8] = {0};
   std::vector<int> Ng;
   std::vector<Layer> L;
@@ -352,6 +440,10 @@ namespace {
 size_t tsz(const nh_net_s* n) { return n->bf16 ? 2 : 4; }
 int64_t vox(const nh_net_s* n, int l) { return (int64_t)n->Ng[l] * n->Ng[l] * n->Ng[l]; }
 
+#ifndef NH_NET_MMA
+#define NH_NET_MMA 1
+#endif
+
 template <typename TA>
 cudaError_t conv_fwd(nh_net n, int li, const void* x, const void* add, float* yf, bool store) {
   const Layer& y = n->L[li];
@@ -361,6 +453,24 @@ cudaError_t conv_fwd(nh_net n, int li, const void* x, const void* add, float* yf
   TA* yo = store ? (TA*)n->out[li] : nullptr;
   const unsigned g = (unsigned)((no + 127) / 128);
   cudaStream_t st = n->ctx->stream;
+  if constexpr (std::is_same<TA, __nv_bfloat16>::value) {
+    if (NH_NET_MMA && n->mma && y.cin % 2 == 0 && (int64_t)W % 4 == 0 && (y.woff % 2) == 0) {
+      const unsigned gm = (unsigned)((no + 63) / 64);
+      const __nv_bfloat16* xb = (const __nv_bfloat16*)x;
+      const __nv_bfloat16* ab = (const __nv_bfloat16*)add;
+      switch (y.cout) {
+        case 3: k_conv_fwd_mma<3><<<gm, 128, 0, st>>>(xb, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, ab, yo, yf); break;
+        case 8: k_conv_fwd_mma<8><<<gm, 128, 0, st>>>(xb, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, ab, yo, yf); break;
+        case 16: k_conv_fwd_mma<16><<<gm, 128, 0, st>>>(xb, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, ab, yo, yf); break;
+        case 32: k_conv_fwd_mma<32><<<gm, 128, 0, st>>>(xb, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, ab, yo, yf); break;
+        case 48: k_conv_fwd_mma<48><<<gm, 128, 0, st>>>(xb, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, ab, yo, yf); break;
+        case 64: k_conv_fwd_mma<64><<<gm, 128, 0, st>>>(xb, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, ab, yo, yf); break;
+        default: return cudaErrorInvalidValue;
+      }
+      n->ctx->launches++;
+      return cudaGetLastError();
+    }
+  }
   switch (y.cout) {
     case 3: k_conv_fwd<TA, 3><<<g, 128, 0, st>>>((const TA*)x, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, (const TA*)add, yo, yf); break;
     case 8: k_conv_fwd<TA, 8><<<g, 128, 0, st>>>((const TA*)x, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, (const TA*)add, yo, yf); break;
@@ -605,6 +715,12 @@ nh_status nh_net_forward_internal(nh_net n, const float* in, float* out) {
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------
+extern "C" nh_status nh_net_set_tensor_cores(nh_net n, int on) {
+  if (!n) return NH_ERR_ARG;
+  n->mma = on ? 1 : 0;
+  return NH_OK;
+}
+
 extern "C" nh_status nh_net_destroy(nh_net n) {
   if (!n) return NH_ERR_ARG;
   cudaStreamSynchronize(n->ctx->stream);

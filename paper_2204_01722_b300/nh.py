@@ -74,6 +74,7 @@ SIGNATURES = {
     "nh_solve": (_st, [_vp, _vp, _vp, _vp]),
     "nh_net_create": (_st, [_vp, C.c_int, C.c_int, _vp, C.c_int, C.c_uint64, C.POINTER(_vp)]),
     "nh_net_destroy": (_st, [_vp]),
+    "nh_net_set_tensor_cores": (_st, [_vp, C.c_int]),
     "nh_net_param_count": (_st, [_vp, C.POINTER(_i64)]),
     "nh_net_get_params": (_st, [_vp, _vp]),
     "nh_net_set_params": (_st, [_vp, _vp]),
@@ -454,6 +455,10 @@ def nh_net_create(ctx, N, levels, channels, bf16=True, seed=0):
 
 def nh_net_destroy(net):
     lib.nh_net_destroy(net)
+
+
+def nh_net_set_tensor_cores(ctx, net, on):
+    _check(lib.nh_net_set_tensor_cores(net, 1 if on else 0), ctx)
 
 
 def nh_net_param_count(ctx, net):
