@@ -618,6 +618,69 @@ def run_multiscale(args):
     print(json.dumps({"multiscale": out}), flush=True)
 
 
+def net_flops(N, channels):
+    """Multiply-adds x 2 of one forward pass of the coarse-correction U-Net on an
+    N^3 vertex grid (3x3x3 convolutions; stride-2 ones counted at their output)."""
+    L = len(channels)
+    Ng = [N]
+    for _ in range(1, L):
+        Ng.append((Ng[-1] - 1) // 2 + 1)
+    conv = lambda ci, co, l: 2 * 27 * ci * co * Ng[l] ** 3
+    f = conv(4, channels[0], 0) + conv(channels[0], channels[0], 0)
+    for l in range(1, L):
+        f += conv(channels[l - 1], channels[l], l) + conv(channels[l], channels[l], l)
+    for l in range(L - 2, -1, -1):
+        f += conv(channels[l + 1], channels[l], l) + conv(channels[l], channels[l], l)
+    f += conv(channels[0], 3, 0)
+    return f, f - conv(4, channels[0], 0)  # forward; input gradients (none for the network input)
+
+
+def run_net(args):
+    """Forward and Adam step of the coarse-correction network (BF16, 4 levels,
+    16/32/48/64 channels) on the (n+1)^3 vertex grid, tensor cores against CUDA
+    cores, CUDA events on the launching stream."""
+    import torch
+    from paper_2204_01722_b300 import nh
+    N, ch, B = args.n + 1, (16, 32, 48, 64), 4
+    stream = torch.cuda.Stream()
+    ctx = nh.nh_create(0, stream.cuda_stream)
+    out = {"workload": f"coarse-correction U-Net, {N}^3 vertex grid, channels 16/32/48/64, BF16", "steps": args.steps}
+    with torch.cuda.stream(stream):
+        net = nh.nh_net_create(ctx, N, len(ch), ch, bf16=True, seed=1)
+        g = torch.Generator(device="cuda").manual_seed(1)
+        x = torch.randn((B, 4, N, N, N), device="cuda", generator=g)
+        t = torch.randn((B, 3, N, N, N), device="cuda", generator=g)
+        y = torch.empty((3, N, N, N), device="cuda")
+
+        def timed(fn, k):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(k):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / k
+
+        for tc in (True, False):
+            nh.nh_net_set_tensor_cores(ctx, net, tc)
+            fwd = timed(lambda: nh.nh_net_forward(ctx, net, x[0], y), args.steps)
+            step = timed(lambda: nh.nh_net_train_step(ctx, net, B, x, t, 1e-5), max(1, args.steps // 4))
+            out["tensor_cores" if tc else "cuda_cores"] = {"forward_ms": round(fwd, 4),
+                                                           "train_step_ms": round(step, 3)}
+        nh.nh_net_destroy(net)
+    nh.nh_destroy(ctx)
+    ff, fdx = net_flops(N, ch)
+    out["forward_gflop"] = round(ff / 1e9, 3)
+    out["train_step_gflop"] = round(B * (2 * ff + fdx) / 1e9, 3)
+    for k in ("tensor_cores", "cuda_cores"):
+        out[k]["forward_tflops"] = round(ff / out[k]["forward_ms"] / 1e9, 2)
+        out[k]["train_step_tflops"] = round(B * (2 * ff + fdx) / out[k]["train_step_ms"] / 1e9, 2)
+    out["train_batch"] = B
+    print(json.dumps({"net": out}), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # oracle arm (CPU baseline and --impl reference)
 # ---------------------------------------------------------------------------
@@ -760,6 +823,9 @@ def main():
     ap.add_argument("--learned", action="store_true",
                     help="run the learned-coarse-space study (training on 20 inclusion layouts of Q3 on 64^3, "
                          "5 held-out layouts; about 35 minutes) instead of the bench; prints its JSON line")
+    ap.add_argument("--net", action="store_true",
+                    help="time the coarse-correction network (forward and Adam step on the (n+1)^3 vertex grid, "
+                         "tensor cores against CUDA cores) instead of the bench; prints its JSON line")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per apply from an ncu capture of this kernel (reported as is)")
     args = ap.parse_args()
@@ -770,6 +836,10 @@ def main():
         from paper_2204_01722_b300 import learned
         learned.main(["--n", str(args.n or 64), "--p", str(args.p), "--train", "20", "--test", "5", "--rhs", "1",
                       "--pairs", "16", "--epochs", "10", "--coarse-fixed", "30", "--vectors", "32,128"])
+        return
+    if args.net:
+        args.n = args.n or 64
+        run_net(args)
         return
     if args.multiscale:
         args.n = args.n or 64

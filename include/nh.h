@@ -427,11 +427,13 @@ typedef struct nh_net_s* nh_net;
  * kx + 3 (ky + 3 kz)) then b [Cout].  Fields are channel-major [C][N^3], x fastest. */
 nh_status nh_net_create(nh_ctx ctx, int N, int levels, const int* channels, int bf16, uint64_t seed, nh_net* out);
 nh_status nh_net_destroy(nh_net net);
-/* BF16 networks: forward convolutions as implicit GEMMs on the tensor cores
- * (mma.sync m16n8k16, BF16 operands, FP32 accumulation; on = 1, the default)
- * or on the CUDA cores (on = 0, FP32 FMAs on the BF16 values).  Both round the
- * same FP32 sums to BF16; only the summation order differs.  No effect on FP32
- * networks or on the backward pass. */
+/* BF16 networks: convolutions as implicit GEMMs on the tensor cores (on = 1,
+ * the default) or on the CUDA cores (on = 0, FP32 FMAs on the BF16 values).
+ * Tensor cores: forward mma.sync m16n8k16 (BF16 operands, FP32 accumulation;
+ * the same FP32 sums as the CUDA-core path in another order, rounded to BF16);
+ * input and weight gradients mma.sync m16n8k8 TF32 (the FP32 gradient fields
+ * rounded to TF32, BF16 activations and weights exact; FP32 accumulation).
+ * No effect on FP32 networks. */
 nh_status nh_net_set_tensor_cores(nh_net net, int on);
 nh_status nh_net_param_count(nh_net net, int64_t* count);
 /* FP32 master parameters to / from HOST memory (set resets the Adam state). */

@@ -288,6 +288,216 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---- backward convolutions on the tensor cores (TF32 operands, FP32 accumulation)
+// The gradients stay FP32; mma.sync m16n8k8 rounds them to TF32 (10 explicit
+// mantissa bits) on the way in, while BF16 activations and weights are exact in
+// TF32.  Fragment layouts of m16n8k8 (g = lane / 4, q = lane % 4): A rows g, g + 8,
+// columns q, q + 4; B rows q, q + 4, column g; C rows g, g + 8, columns 2q, 2q + 1.
+__device__ __forceinline__ unsigned to_tf32(float f) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Input gradient as an implicit GEMM: dx[ci][x] = sum_k A[x][k] B[k][ci] over
+// k = co * 27 + tap, A[x][k] = dz[co][o] where x = stride o + tap - 1 (zero when no
+// such output voxel exists), B[k][ci] = W[co][ci][tap] read from the tap-major
+// copy Wt[co][tap][ci].  A warp owns 16 input voxels and all CI channels.
+template <int CI>
+__global__ void __launch_bounds__(128)
+    k_conv_dx_mma(const float* __restrict__ dz, int Cout, int Nout, const __nv_bfloat16* __restrict__ Wt, int Nin,
+                  int stride, float* __restrict__ dx) {
+  constexpr int NT = CI / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int64_t nout = (int64_t)Nout * Nout * Nout, nin = (int64_t)Nin * Nin * Nin;
+  const int64_t m0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
+  int pi[2], pj[2], pk[2];
+  bool rv[2];
+#pragma unroll
+  for (int r = 0; r < 2; r++) {
+    const int64_t xi = m0 + g + 8 * r;
+    rv[r] = xi < nin;
+    const int64_t xc = rv[r] ? xi : 0;
+    pi[r] = (int)(xc % Nin) + 1;
+    pj[r] = (int)((xc / Nin) % Nin) + 1;
+    pk[r] = (int)(xc / ((int64_t)Nin * Nin)) + 1;
+  }
+  float acc[NT][4];
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc[t][i] = 0.f;
+  int co_h[2] = {0, 0}, tap_h[2] = {tq, tq + 4};  // (co, tap) of this lane's columns k0 + q and k0 + q + 4
+  const int K = Cout * 27;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    unsigned a[4];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int co = co_h[h], tap = tap_h[h];
+      const int ti = tap % 3, tj = (tap / 3) % 3, tk = tap / 9;
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        float v = 0.f;
+        int ia = pi[r] - ti, ib = pj[r] - tj, ic = pk[r] - tk;
+        bool ok = rv[r] && co < Cout && ia >= 0 && ib >= 0 && ic >= 0;
+        if (stride == 2) {
+          ok = ok && !((ia | ib | ic) & 1);
+          ia >>= 1;
+          ib >>= 1;
+          ic >>= 1;
+        }
+        if (ok && ia < Nout && ib < Nout && ic < Nout)
+          v = dz[(int64_t)co * nout + ia + (int64_t)Nout * (ib + (int64_t)Nout * ic)];
+        a[2 * h + r] = to_tf32(v);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+      unsigned b[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+        b[h] = co_h[h] < Cout
+                   ? __float_as_uint(__bfloat162float(Wt[((int64_t)co_h[h] * 27 + tap_h[h]) * CI + t * 8 + g]))
+                   : 0u;
+      mma_tf32(acc[t], a, b);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      tap_h[h] += 8;
+      if (tap_h[h] >= 27) {
+        tap_h[h] -= 27;
+        co_h[h]++;
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const int r = i >> 1, c = t * 8 + 2 * tq + (i & 1);
+      if (rv[r]) dx[(int64_t)c * nin + m0 + g + 8 * r] = acc[t][i];
+    }
+}
+
+// Weight gradient as a GEMM over the output voxels: dW[co][ci][tap] = sum_o
+// A[(ci, tap)][o] B[o][co], A[(ci, tap)][o] = x[ci][stride o + tap - 1] (zero
+// outside the grid), B[o][co] = dz[co][o].  A warp owns 16 (ci, tap) rows and all
+// CO columns; the voxels run along x-rows, 8 per step (the row's tail padded with
+// zeros), and a block sums the rows [rows_per_chunk * blockIdx.y, ...) before
+// adding its partial sums atomically.  The bias gradient is k_bias_grad.
+template <int CO>
+__global__ void __launch_bounds__(128)
+    k_conv_dw_mma(const float* __restrict__ dz, int Nout, const __nv_bfloat16* __restrict__ x, int Cin, int Nin,
+                  int stride, int rows_per_chunk, float* __restrict__ dW) {
+  constexpr int NT = (CO + 7) / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int R = Cin * 27;
+  const int64_t nout = (int64_t)Nout * Nout * Nout, nin = (int64_t)Nin * Nin * Nin;
+  const int r0 = (blockIdx.x * 4 + warp) * 16;
+  int rr[2], di[2], dj[2], dk[2];
+  bool rv[2];
+  const __nv_bfloat16* xc[2];
+#pragma unroll
+  for (int r = 0; r < 2; r++) {
+    rr[r] = r0 + g + 8 * r;
+    rv[r] = rr[r] < R;
+    const int ci = rv[r] ? rr[r] / 27 : 0, tap = rv[r] ? rr[r] % 27 : 0;
+    di[r] = tap % 3 - 1;
+    dj[r] = (tap / 3) % 3 - 1;
+    dk[r] = tap / 9 - 1;
+    xc[r] = x + (int64_t)ci * nin;
+  }
+  float acc[NT][4];
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc[t][i] = 0.f;
+  const int nrows = Nout * Nout;
+  const int y0 = blockIdx.y * rows_per_chunk;
+  const int y1 = y0 + rows_per_chunk < nrows ? y0 + rows_per_chunk : nrows;
+  for (int row = y0; row < y1; row++) {
+    const int oj = row % Nout, ok = row / Nout;
+    bool rowok[2];
+    const __nv_bfloat16* base[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      const int jj = stride * oj + dj[r], kk = stride * ok + dk[r];
+      rowok[r] = rv[r] && jj >= 0 && jj < Nin && kk >= 0 && kk < Nin;
+      base[r] = xc[r] + (rowok[r] ? (int64_t)Nin * (jj + (int64_t)Nin * kk) : 0);
+    }
+    const float* dzrow = dz + (int64_t)row * Nout;
+    for (int oi0 = 0; oi0 < Nout; oi0 += 8) {
+      unsigned a[4];
+      bool colok[2];
+      int oi[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        oi[h] = oi0 + tq + 4 * h;
+        colok[h] = oi[h] < Nout;
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+          const int ii = stride * oi[h] + di[r];
+          const bool ok = rowok[r] && colok[h] && ii >= 0 && ii < Nin;
+          a[2 * h + r] = ok ? __float_as_uint(__bfloat162float(base[r][ii])) : 0u;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NT; t++) {
+        const int co = t * 8 + g;
+        unsigned b[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) b[h] = (co < CO && colok[h]) ? to_tf32(dzrow[(int64_t)co * nout + oi[h]]) : 0u;
+        mma_tf32(acc[t], a, b);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const int r = i >> 1, co = t * 8 + 2 * tq + (i & 1);
+      if (rv[r] && co < CO && acc[t][i] != 0.f) atomicAdd(&dW[(int64_t)co * R + rr[r]], acc[t][i]);
+    }
+}
+
+// db[co] += sum_o dz[co][o]: one block per output channel, fixed summation order.
+__global__ void __launch_bounds__(256) k_bias_grad(const float* __restrict__ dz, int64_t nout, float* __restrict__ db) {
+  __shared__ float sh[32];
+  const float* d = dz + (int64_t)blockIdx.x * nout;
+  float v = 0.f;
+  for (int64_t o = threadIdx.x; o < nout; o += blockDim.x) v += d[o];
+  v = block_sum_f(v, sh);
+  if (threadIdx.x == 0) db[blockIdx.x] += v;
+}
+
+// Tap-major copy of every layer's BF16 weights: Wt[co][tap][ci] = W[co][ci][tap]
+// (blockIdx.y = layer).
+struct LayerTable {
+  int n;
+  int64_t off[32];
+  int cin[32], cout[32];
+};
+
+__global__ void k_tap_major(LayerTable tab, const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wt) {
+  const int l = blockIdx.y;
+  const int ci_n = tab.cin[l];
+  const int64_t cnt = (int64_t)tab.cout[l] * ci_n * 27, off = tab.off[l];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    const int tap = (int)(e % 27), ci = (int)((e / 27) % ci_n);
+    const int64_t co = e / (27 * (int64_t)ci_n);
+    wt[off + (co * 27 + tap) * ci_n + ci] = w[off + e];
+  }
+}
+
 // ---- elementwise ---------------------------------------------------------------
 template <typename TA>
 __global__ void k_relu_mask(int64_t n, const TA* __restrict__ y, float* __restrict__ g) {
@@ -422,6 +632,7 @@ struct nh_net_s {
   int64_t np = 0;
   float *theta = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
   void* wc = nullptr;           // compute copy of the parameters (TA)
+  void* wt = nullptr;           // BF16 networks: tap-major copy of the weights (input-gradient GEMM)
   int64_t adam_t = 0;
   std::vector<void*> out;       // per layer: stored activation (TA), [cout][Ng[lout]^3]
   std::vector<void*> ups;       // per decoder block: upsampled input (TA)
@@ -491,6 +702,21 @@ cudaError_t conv_dx(nh_net n, int li, const float* dz, float* dx) {
   const int64_t ni = vox(n, y.lin);
   const unsigned g = (unsigned)((ni + 127) / 128);
   cudaStream_t st = n->ctx->stream;
+  if (std::is_same<TA, __nv_bfloat16>::value && NH_NET_MMA && n->mma) {
+    const __nv_bfloat16* Wt = (const __nv_bfloat16*)n->wt + y.woff;
+    const unsigned gm = (unsigned)((ni + 63) / 64);
+    const int No = n->Ng[y.lout], Ni = n->Ng[y.lin];
+    switch (y.cin) {
+      case 8: k_conv_dx_mma<8><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+      case 16: k_conv_dx_mma<16><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+      case 32: k_conv_dx_mma<32><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+      case 48: k_conv_dx_mma<48><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+      case 64: k_conv_dx_mma<64><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+      default: return cudaErrorInvalidValue;
+    }
+    n->ctx->launches++;
+    return cudaGetLastError();
+  }
   switch (y.cin) {
     case 8: k_conv_dx<TA, 8><<<g, 128, 0, st>>>(dz, y.cout, n->Ng[y.lout], W, n->Ng[y.lin], y.stride, dx); break;
     case 16: k_conv_dx<TA, 16><<<g, 128, 0, st>>>(dz, y.cout, n->Ng[y.lout], W, n->Ng[y.lin], y.stride, dx); break;
@@ -507,6 +733,30 @@ template <typename TA>
 cudaError_t conv_dw(nh_net n, int li, const float* dz, const void* x) {
   const Layer& y = n->L[li];
   const int64_t no = vox(n, y.lout);
+  if (std::is_same<TA, __nv_bfloat16>::value && NH_NET_MMA && n->mma) {
+    cudaStream_t st = n->ctx->stream;
+    const int No = n->Ng[y.lout], Ni = n->Ng[y.lin];
+    const unsigned bx = (unsigned)((y.cin * 27 + 63) / 64);
+    const int rows = No * No;
+    int chunks = (148 * 8 + (int)bx - 1) / (int)bx;  // about 8 blocks per SM
+    if (chunks > rows) chunks = rows;
+    const int per = (rows + chunks - 1) / chunks;
+    const dim3 grid(bx, (unsigned)((rows + per - 1) / per));
+    const __nv_bfloat16* xb = (const __nv_bfloat16*)x;
+    float* dW = n->grad + y.woff;
+    switch (y.cout) {
+      case 3: k_conv_dw_mma<3><<<grid, 128, 0, st>>>(dz, No, xb, y.cin, Ni, y.stride, per, dW); break;
+      case 8: k_conv_dw_mma<8><<<grid, 128, 0, st>>>(dz, No, xb, y.cin, Ni, y.stride, per, dW); break;
+      case 16: k_conv_dw_mma<16><<<grid, 128, 0, st>>>(dz, No, xb, y.cin, Ni, y.stride, per, dW); break;
+      case 32: k_conv_dw_mma<32><<<grid, 128, 0, st>>>(dz, No, xb, y.cin, Ni, y.stride, per, dW); break;
+      case 48: k_conv_dw_mma<48><<<grid, 128, 0, st>>>(dz, No, xb, y.cin, Ni, y.stride, per, dW); break;
+      case 64: k_conv_dw_mma<64><<<grid, 128, 0, st>>>(dz, No, xb, y.cin, Ni, y.stride, per, dW); break;
+      default: return cudaErrorInvalidValue;
+    }
+    k_bias_grad<<<(unsigned)y.cout, 256, 0, st>>>(dz, no, n->grad + y.boff);
+    n->ctx->launches += 2;
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)(y.cout * y.cin), (unsigned)((no + kDWChunk - 1) / kDWChunk));
   k_conv_dw<TA><<<grid, 256, 0, n->ctx->stream>>>(dz, y.cout, n->Ng[y.lout], (const TA*)x, y.cin, n->Ng[y.lin],
                                                   y.stride, n->grad + y.woff, n->grad + y.boff);
@@ -628,9 +878,19 @@ nh_status backward_t(nh_net n, const float* gy) {
 }
 
 nh_status refresh_compute_copy(nh_net n) {
-  if (n->bf16)
+  if (n->bf16) {
     k_from_f32<__nv_bfloat16><<<blocks_for(n->np), 256, 0, n->ctx->stream>>>(n->np, n->theta, (__nv_bfloat16*)n->wc);
-  else
+    LayerTable tab{};
+    tab.n = (int)n->L.size();
+    for (int l = 0; l < tab.n; l++) {
+      tab.off[l] = n->L[l].woff;
+      tab.cin[l] = n->L[l].cin;
+      tab.cout[l] = n->L[l].cout;
+    }
+    k_tap_major<<<dim3(64, (unsigned)tab.n), 256, 0, n->ctx->stream>>>(tab, (const __nv_bfloat16*)n->wc,
+                                                                        (__nv_bfloat16*)n->wt);
+    n->ctx->launches++;
+  } else
     k_from_f32<float><<<blocks_for(n->np), 256, 0, n->ctx->stream>>>(n->np, n->theta, (float*)n->wc);
   n->ctx->launches++;
   NCK(cudaGetLastError());
@@ -728,7 +988,7 @@ extern "C" nh_status nh_net_destroy(nh_net n) {
   for (void* p : n->ups) cudaFree(p);
   for (void* p : n->sums) cudaFree(p);
   for (float* p : n->sg) cudaFree(p);
-  for (void* p : {(void*)n->theta, (void*)n->grad, (void*)n->m1, (void*)n->m2, n->wc, n->xin, (void*)n->yout,
+  for (void* p : {(void*)n->theta, (void*)n->grad, (void*)n->m1, (void*)n->m2, n->wc, n->wt, n->xin, (void*)n->yout,
                   (void*)n->g0, (void*)n->g1, (void*)n->ls, (void*)n->gy})
     cudaFree(p);
   cudaFreeHost(n->ls_host);
@@ -783,7 +1043,8 @@ extern "C" nh_status nh_net_create(nh_ctx ctx, int N, int levels, const int* cha
   };
   const size_t ts = tsz(n);
   if (cudaMalloc(&n->theta, 4 * n->np) || cudaMalloc(&n->grad, 4 * n->np) || cudaMalloc(&n->m1, 4 * n->np) ||
-      cudaMalloc(&n->m2, 4 * n->np) || cudaMalloc(&n->wc, ts * n->np))
+      cudaMalloc(&n->m2, 4 * n->np) || cudaMalloc(&n->wc, ts * n->np) ||
+      (n->bf16 && cudaMalloc(&n->wt, ts * n->np)))
     return fail();
   int64_t maxc = 4 * vox(n, 0);
   n->out.assign(n->L.size(), nullptr);

@@ -72,39 +72,48 @@ def test_forward_and_gradient(nhctx, sample, bf16):
 
 
 @pytest.mark.parametrize("N,ch", [(9, (8, 16, 32)), (13, (16, 48, 64)), (7, (32, 8))])
-def test_tensor_core_forward(nhctx, N, ch):
-    """BF16 forward on the tensor cores against the CUDA-core kernel and the oracle.
+def test_tensor_core_forward_and_gradient(nhctx, N, ch):
+    """BF16 network on the tensor cores against the CUDA-core kernels and the oracle.
 
-    Both paths round the same FP32 sums (taken in another order) to BF16, so a
-    stored activation differs only where its FP32 value lies within rounding
-    noise of a BF16 rounding boundary: outputs agree to ~1e-3 relative.  Grids of
-    9^3, 13^3 and 7^3 voxels leave ragged 64-voxel tails; the channel sets cover
-    every output width of the network (3, 8, 16, 32, 48, 64).  Against the FP64
-    oracle on the BF16-rounded inputs and weights the bound is that of BF16
-    activations (3e-2)."""
+    Forward: both paths round the same FP32 sums (taken in another order) to
+    BF16, so a stored activation differs only where its FP32 value lies within
+    rounding noise of a BF16 rounding boundary: outputs agree to ~1e-3 relative.
+    Gradient: the tensor-core backward rounds the FP32 gradient fields to TF32
+    (relative 2^-11 per operand), so the parameter gradients agree to ~5e-3.
+    Grids of 9^3, 13^3 and 7^3 voxels leave ragged 64-voxel tails; the channel
+    sets cover every layer width of the network (3, 8, 16, 32, 48, 64) and both
+    strides.  Against the FP64 oracle on the BF16-rounded inputs and weights the
+    bounds are those of BF16 activations (3e-2 forward, gradient cosine > 0.99)."""
     ctx, _ = nhctx
     from paper_2204_01722_b300 import nh
     Lv = len(ch)
     rng = np.random.default_rng(N)
     x = rng.normal(size=(4, N, N, N))
+    t = rng.normal(size=(3, N, N, N))
     theta = learned.init_params(Lv, ch, seed=2) + 0.01 * rng.normal(size=learned.n_params(Lv, ch))
     net = nh.nh_net_create(ctx, N, Lv, ch, bf16=True, seed=3)
     nh.nh_net_set_params(ctx, net, theta.astype(np.float32))
     xd = torch.from_numpy(x.astype(np.float32)).cuda()
-    y_tc = torch.empty((3, N, N, N), dtype=torch.float32, device="cuda")
-    y_cc = torch.empty_like(y_tc)
-    nh.nh_net_set_tensor_cores(ctx, net, True)
-    nh.nh_net_forward(ctx, net, xd, y_tc)
-    nh.nh_net_set_tensor_cores(ctx, net, False)
-    nh.nh_net_forward(ctx, net, xd, y_cc)
+    td = torch.from_numpy(t.astype(np.float32)).cuda()
+    ys, gs = {}, {}
+    for tc in (True, False):
+        nh.nh_net_set_tensor_cores(ctx, net, tc)
+        ys[tc] = torch.empty((3, N, N, N), dtype=torch.float32, device="cuda")
+        nh.nh_net_forward(ctx, net, xd, ys[tc])
+        gs[tc] = torch.empty(theta.size, dtype=torch.float32, device="cuda")
+        nh.nh_net_gradient(ctx, net, xd, td, gs[tc])
     nh.nh_net_set_tensor_cores(ctx, net, True)
     torch.cuda.current_stream().synchronize()
-    a, b = y_tc.double().cpu().numpy(), y_cc.double().cpu().numpy()
-    assert np.all(np.isfinite(a))
+    a, b = ys[True].double().cpu().numpy(), ys[False].double().cpu().numpy()
+    ga, gb = gs[True].double().cpu().numpy(), gs[False].double().cpu().numpy()
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(ga))
     assert rel(a, b) < 1e-3
+    assert rel(ga, gb) < 5e-3
     bf = lambda v: torch.from_numpy(np.asarray(v, dtype=np.float32)).bfloat16().double().numpy()
-    y_ref = learned.forward(bf(theta), bf(x), Lv, ch)
-    assert rel(a, y_ref) < 3e-2
+    th, xb = bf(theta), bf(x)
+    assert rel(a, learned.forward(th, xb, Lv, ch)) < 3e-2
+    g_ref = learned.loss_grad(th, xb, t.astype(np.float32).astype(np.float64), Lv, ch)
+    assert float(ga @ g_ref / (np.linalg.norm(ga) * np.linalg.norm(g_ref))) > 0.99
     nh.nh_net_destroy(net)
 
 
