@@ -184,6 +184,87 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// Same GEMM with K in tap-major order, k = tap * Cin + ci, for Cin a multiple of
+// 16: a k-step then stays within one tap, so each row's neighbour offset and
+// bounds test are taken once per tap, and B pairs come from the tap-major copy
+// Wt[co][tap][ci].
+template <int CO>
+__global__ void __launch_bounds__(128)
+    k_conv_fwd_mma_t(const __nv_bfloat16* __restrict__ x, int Cin, int Nin, const __nv_bfloat16* __restrict__ Wt,
+                     const float* __restrict__ bias, int Nout, int stride, int relu,
+                     const __nv_bfloat16* __restrict__ add, __nv_bfloat16* __restrict__ yo, float* __restrict__ yf) {
+  constexpr int NT = (CO + 7) / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int64_t nout = (int64_t)Nout * Nout * Nout, nin = (int64_t)Nin * Nin * Nin;
+  const int64_t o0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
+  int bi[2], bj[2], bk[2];
+  bool ov[2];
+#pragma unroll
+  for (int r = 0; r < 2; r++) {
+    const int64_t o = o0 + g + 8 * r;
+    ov[r] = o < nout;
+    const int64_t oc = ov[r] ? o : 0;
+    bi[r] = stride * (int)(oc % Nout) - 1;
+    bj[r] = stride * (int)((oc / Nout) % Nout) - 1;
+    bk[r] = stride * (int)(oc / ((int64_t)Nout * Nout)) - 1;
+  }
+  float acc[NT][4];
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc[t][i] = 0.f;
+  const unsigned short* xs = reinterpret_cast<const unsigned short*>(x);
+  for (int tap = 0; tap < 27; tap++) {
+    const int ti = tap % 3, tj = (tap / 3) % 3, tk = tap / 9;
+    bool ok[2];
+    int64_t off[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      const int ii = bi[r] + ti, jj = bj[r] + tj, kk = bk[r] + tk;
+      ok[r] = ov[r] && ii >= 0 && ii < Nin && jj >= 0 && jj < Nin && kk >= 0 && kk < Nin;
+      off[r] = ok[r] ? ii + (int64_t)Nin * (jj + (int64_t)Nin * kk) : 0;
+    }
+    for (int ci0 = 0; ci0 < Cin; ci0 += 16) {
+      unsigned a[4];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int64_t c = (int64_t)(ci0 + 8 * h + 2 * tq) * nin;
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+          a[2 * h + r] = ok[r] ? ((unsigned)xs[c + off[r]] | ((unsigned)xs[c + nin + off[r]] << 16)) : 0u;
+      }
+#pragma unroll
+      for (int t = 0; t < NT; t++) {
+        const int co = t * 8 + g;
+        unsigned b[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+          b[h] = co < CO ? __ldg(reinterpret_cast<const unsigned*>(Wt + ((int64_t)co * 27 + tap) * Cin + ci0 + 8 * h +
+                                                                    2 * tq))
+                         : 0u;
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(acc[t][0]), "+f"(acc[t][1]), "+f"(acc[t][2]), "+f"(acc[t][3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const int r = i >> 1, co = t * 8 + 2 * tq + (i & 1);
+      if (!ov[r] || co >= CO) continue;
+      const int64_t o = o0 + g + 8 * r;
+      float v = acc[t][i] + bias[co];
+      if (relu) v = fmaxf(v, 0.f);
+      if (yo) yo[(int64_t)co * nout + o] = __float2bfloat16(v);
+      if (yf) yf[(int64_t)co * nout + o] = v + (add ? __bfloat162float(add[(int64_t)co * nout + o]) : 0.f);
+    }
+}
+
 // ---- input gradient of a convolution: one thread per input voxel ---------------
 // dx[ci][x] = sum_co sum_tap W[co][ci][tap] dz[co][o],  x = stride o + tap - 1
 template <typename TA, int CI>
@@ -375,6 +456,77 @@ __global__ void __launch_bounds__(128)
       if (tap_h[h] >= 27) {
         tap_h[h] -= 27;
         co_h[h]++;
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const int r = i >> 1, c = t * 8 + 2 * tq + (i & 1);
+      if (rv[r]) dx[(int64_t)c * nin + m0 + g + 8 * r] = acc[t][i];
+    }
+}
+
+// Same GEMM with K in tap-outer order, k = tap * Cout + co, for Cout a multiple
+// of 8: each row's source offset and tests are taken once per tap.
+template <int CI>
+__global__ void __launch_bounds__(128)
+    k_conv_dx_mma_t(const float* __restrict__ dz, int Cout, int Nout, const __nv_bfloat16* __restrict__ Wt, int Nin,
+                    int stride, float* __restrict__ dx) {
+  constexpr int NT = CI / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int64_t nout = (int64_t)Nout * Nout * Nout, nin = (int64_t)Nin * Nin * Nin;
+  const int64_t m0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
+  int pi[2], pj[2], pk[2];
+  bool rv[2];
+#pragma unroll
+  for (int r = 0; r < 2; r++) {
+    const int64_t xi = m0 + g + 8 * r;
+    rv[r] = xi < nin;
+    const int64_t xc = rv[r] ? xi : 0;
+    pi[r] = (int)(xc % Nin) + 1;
+    pj[r] = (int)((xc / Nin) % Nin) + 1;
+    pk[r] = (int)(xc / ((int64_t)Nin * Nin)) + 1;
+  }
+  float acc[NT][4];
+#pragma unroll
+  for (int t = 0; t < NT; t++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc[t][i] = 0.f;
+  for (int tap = 0; tap < 27; tap++) {
+    const int ti = tap % 3, tj = (tap / 3) % 3, tk = tap / 9;
+    bool ok[2];
+    int64_t off[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      int ia = pi[r] - ti, ib = pj[r] - tj, ic = pk[r] - tk;
+      bool v = rv[r] && ia >= 0 && ib >= 0 && ic >= 0;
+      if (stride == 2) {
+        v = v && !((ia | ib | ic) & 1);
+        ia >>= 1;
+        ib >>= 1;
+        ic >>= 1;
+      }
+      ok[r] = v && ia < Nout && ib < Nout && ic < Nout;
+      off[r] = ok[r] ? ia + (int64_t)Nout * (ib + (int64_t)Nout * ic) : 0;
+    }
+    if (!__any_sync(0xffffffffu, ok[0] || ok[1])) continue;  // stride 2: most taps have no source for the warp
+    for (int co0 = 0; co0 < Cout; co0 += 8) {
+      unsigned a[4];
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+          a[2 * h + r] = ok[r] ? to_tf32(dz[(int64_t)(co0 + tq + 4 * h) * nout + off[r]]) : 0u;
+#pragma unroll
+      for (int t = 0; t < NT; t++) {
+        unsigned b[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+          b[h] = __float_as_uint(__bfloat162float(Wt[((int64_t)(co0 + tq + 4 * h) * 27 + tap) * CI + t * 8 + g]));
+        mma_tf32(acc[t], a, b);
       }
     }
   }
@@ -669,6 +821,21 @@ cudaError_t conv_fwd(nh_net n, int li, const void* x, const void* add, float* yf
       const unsigned gm = (unsigned)((no + 63) / 64);
       const __nv_bfloat16* xb = (const __nv_bfloat16*)x;
       const __nv_bfloat16* ab = (const __nv_bfloat16*)add;
+      const __nv_bfloat16* Wt = (const __nv_bfloat16*)n->wt + y.woff;
+      const int Ni = n->Ng[y.lin], No = n->Ng[y.lout];
+      if (y.cin % 16 == 0) {
+        switch (y.cout) {
+          case 3: k_conv_fwd_mma_t<3><<<gm, 128, 0, st>>>(xb, y.cin, Ni, Wt, b, No, y.stride, y.relu, ab, yo, yf); break;
+          case 8: k_conv_fwd_mma_t<8><<<gm, 128, 0, st>>>(xb, y.cin, Ni, Wt, b, No, y.stride, y.relu, ab, yo, yf); break;
+          case 16: k_conv_fwd_mma_t<16><<<gm, 128, 0, st>>>(xb, y.cin, Ni, Wt, b, No, y.stride, y.relu, ab, yo, yf); break;
+          case 32: k_conv_fwd_mma_t<32><<<gm, 128, 0, st>>>(xb, y.cin, Ni, Wt, b, No, y.stride, y.relu, ab, yo, yf); break;
+          case 48: k_conv_fwd_mma_t<48><<<gm, 128, 0, st>>>(xb, y.cin, Ni, Wt, b, No, y.stride, y.relu, ab, yo, yf); break;
+          case 64: k_conv_fwd_mma_t<64><<<gm, 128, 0, st>>>(xb, y.cin, Ni, Wt, b, No, y.stride, y.relu, ab, yo, yf); break;
+          default: return cudaErrorInvalidValue;
+        }
+        n->ctx->launches++;
+        return cudaGetLastError();
+      }
       switch (y.cout) {
         case 3: k_conv_fwd_mma<3><<<gm, 128, 0, st>>>(xb, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, ab, yo, yf); break;
         case 8: k_conv_fwd_mma<8><<<gm, 128, 0, st>>>(xb, y.cin, n->Ng[y.lin], W, b, n->Ng[y.lout], y.stride, y.relu, ab, yo, yf); break;
@@ -706,6 +873,18 @@ cudaError_t conv_dx(nh_net n, int li, const float* dz, float* dx) {
     const __nv_bfloat16* Wt = (const __nv_bfloat16*)n->wt + y.woff;
     const unsigned gm = (unsigned)((ni + 63) / 64);
     const int No = n->Ng[y.lout], Ni = n->Ng[y.lin];
+    if (y.cout % 8 == 0) {
+      switch (y.cin) {
+        case 8: k_conv_dx_mma_t<8><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+        case 16: k_conv_dx_mma_t<16><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+        case 32: k_conv_dx_mma_t<32><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+        case 48: k_conv_dx_mma_t<48><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+        case 64: k_conv_dx_mma_t<64><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
+        default: return cudaErrorInvalidValue;
+      }
+      n->ctx->launches++;
+      return cudaGetLastError();
+    }
     switch (y.cin) {
       case 8: k_conv_dx_mma<8><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
       case 16: k_conv_dx_mma<16><<<gm, 128, 0, st>>>(dz, y.cout, No, Wt, Ni, y.stride, dx); break;
