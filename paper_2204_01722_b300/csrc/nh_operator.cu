@@ -621,6 +621,35 @@ __device__ __forceinline__ void red_run(float* y, const float (&v)[N]) {
   }
 }
 
+// Vector loads of du[3 n0 .. 3 (n0 + N / 3)) into v, the mirror of red_run (A = the
+// run's start modulo 4 floats, the base 16-byte aligned); read-only path.
+template <int A, int K, int N>
+__device__ __forceinline__ void ld_run(const float* x, float (&v)[N]) {
+  if constexpr (K < N) {
+    constexpr int al = (A + K) & 3;
+    if constexpr (al == 0 && K + 4 <= N) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(x + K));
+      v[K] = q.x;
+      v[K + 1] = q.y;
+      v[K + 2] = q.z;
+      v[K + 3] = q.w;
+      ld_run<A, K + 4, N>(x, v);
+    } else if constexpr ((al & 1) == 0 && K + 2 <= N) {
+      const float2 q = __ldg(reinterpret_cast<const float2*>(x + K));
+      v[K] = q.x;
+      v[K + 1] = q.y;
+      ld_run<A, K + 2, N>(x, v);
+    } else {
+      v[K] = __ldg(x + K);
+      ld_run<A, K + 1, N>(x, v);
+    }
+  }
+}
+
+#ifndef NH_F32_VGATHER
+#define NH_F32_VGATHER 1
+#endif
+
 #ifndef NH_F32_DIRECT_MINB
 #define NH_F32_DIRECT_MINB 1
 #endif
@@ -712,12 +741,33 @@ __global__ void NH_F32L_BOUNDS(Q)
 #pragma unroll
       for (int i = 0; i < P; i++) nid[i] = live ? __ldg(&emapb[e * P3 + (v * P + u) * P + i]) : 0u;
     }
+    // the line's P nodes consecutive and unconstrained (or lifted): its 3P values
+    // are one contiguous run of du, read with vector loads
+    bool vrun = NH_F32_VGATHER && live && (vec_ok & 2);
+    const unsigned n0 = nid[0] & kNodeMask;
 #pragma unroll
-    for (int i = 0; i < P; i++) {
-      const int64_t n = nid[i] & kNodeMask;
-      const unsigned m = (live && !lift) ? nid[i] >> kNodeBits : 0u;
+    for (int i = 0; i < P; i++) vrun = vrun && (lift ? (nid[i] & kNodeMask) : nid[i]) == n0 + (unsigned)i;
+    if (vrun) {
+      float vv[3 * P];
+      const float* xr = du + 3 * (int64_t)n0;
+      switch ((3u * n0) & 3u) {
+        case 0: ld_run<0, 0, 3 * P>(xr, vv); break;
+        case 1: ld_run<1, 0, 3 * P>(xr, vv); break;
+        case 2: ld_run<2, 0, 3 * P>(xr, vv); break;
+        default: ld_run<3, 0, 3 * P>(xr, vv); break;
+      }
 #pragma unroll
-      for (int c = 0; c < 3; c++) w[c][i] = (live && !((m >> c) & 1u)) ? __ldg(&du[3 * n + c]) : 0.f;
+      for (int i = 0; i < P; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) w[c][i] = vv[3 * i + c];
+    } else {
+#pragma unroll
+      for (int i = 0; i < P; i++) {
+        const int64_t n = nid[i] & kNodeMask;
+        const unsigned m = (live && !lift) ? nid[i] >> kNodeBits : 0u;
+#pragma unroll
+        for (int c = 0; c < 3; c++) w[c][i] = (live && !((m >> c) & 1u)) ? __ldg(&du[3 * n + c]) : 0.f;
+      }
     }
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -965,7 +1015,7 @@ __global__ void NH_F32L_BOUNDS(Q)
     // the line's P nodes consecutive and unconstrained (box meshes away from
     // Dirichlet faces): their 3P values are one contiguous run of y
     n0 = nid[0] & kNodeMask;
-    run = live && vec_ok != 0;
+    run = live && (vec_ok & 1) != 0;
 #pragma unroll
     for (int i = 0; i < P; i++) run = run && nid[i] == n0 + (unsigned)i;
     if (rows_ok) srun[(el * P + v) * P + u] = run ? n0 : 0xffffffffu;
@@ -1440,7 +1490,8 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
     cudaError_t e = prep<k_jacobian_apply_f32l<P, Q, LAYOUT, true>>(smem);
     if (e != cudaSuccess) return e;
     k_jacobian_apply_f32l<P, Q, LAYOUT, true><<<(unsigned)grid, threads, smem, s>>>(
-        A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift, 1, 1, A.err, A.colour, nbx,
+        A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift,
+        1 | (((uintptr_t)A.in & 15) == 0 ? 2 : 0), 1, A.err, A.colour, nbx,
         A.ny, A.nz);
     return cudaGetLastError();
   }
@@ -1448,7 +1499,8 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   k_jacobian_apply_f32l<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
       A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift,
-      ((uintptr_t)A.out & 15) == 0 ? 1 : 0, ((uintptr_t)A.out & 15) == 0 && A.nx > 0 && (NH_F32_ROWS_ANY || Q <= 3 || A.nx % EPB == 0) ? 1 : 0, A.err,
+      (((uintptr_t)A.out & 15) == 0 ? 1 : 0) | (((uintptr_t)A.in & 15) == 0 ? 2 : 0),
+      ((uintptr_t)A.out & 15) == 0 && A.nx > 0 && (NH_F32_ROWS_ANY || Q <= 3 || A.nx % EPB == 0) ? 1 : 0, A.err,
       -1, nbx, A.ny, A.nz);
   return cudaGetLastError();
 }
