@@ -373,6 +373,36 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<T, Q>())
 
 // element stride in ff words, padded like elem_stride so that consecutive
 // elements of a warp start on different banks
+#ifndef NH_FF_DOT2
+#define NH_FF_DOT2 1
+#endif
+// sum_{m < N} a_m b_m for the terms (a_m, b_m) = term(m): a compensated dot
+// product (ffd_*), or a chain of float-float multiply-adds with NH_FF_DOT2=0
+struct ffpair {
+  ff a, b;
+};
+template <int N, typename F>
+__device__ __forceinline__ ff ff_dot(F term) {
+#if NH_FF_DOT2
+  const ffpair t0 = term(0);
+  ffdot d = ffd_first(t0.a, t0.b);
+#pragma unroll
+  for (int m = 1; m < N; m++) {
+    const ffpair t = term(m);
+    ffd_add(d, t.a, t.b);
+  }
+  return ffd_done(d);
+#else
+  ff s = ff(0);
+#pragma unroll
+  for (int m = 0; m < N; m++) {
+    const ffpair t = term(m);
+    s = ff_madd(s, t.a, t.b);
+  }
+  return s;
+#endif
+}
+
 template <int Q>
 __host__ __device__ constexpr int ffr_stride() {
   constexpr int base = 12 * Q * Q * Q, W = 16, want = (Q * Q) % W;
@@ -419,12 +449,8 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<ff, Q>())
 #pragma unroll 1
     for (int qk = 0; qk < Q; qk++) {
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        ff s = ff(0);
-#pragma unroll
-        for (int k = 0; k < P; k++) s = madd(s, tab.B[qk][k], r[c][k]);
-        bA[sidx<Q>(c, qk, b, a)] = s;
-      }
+      for (int c = 0; c < 3; c++)
+        bA[sidx<Q>(c, qk, b, a)] = ff_dot<P>([&](int k) { return ffpair{tab.B[qk][k], r[c][k]}; });
     }
   } else {
 #pragma unroll
@@ -435,24 +461,16 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<ff, Q>())
 #pragma unroll 1
     for (int qk = 0; qk < Q; qk++) {
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        ff s = ff(0);
-#pragma unroll
-        for (int j = 0; j < P; j++) s = madd(s, tab.B[b][j], bA[sidx<Q>(c, qk, j, a)]);
-        bB[sidx<Q>(c, qk, b, a)] = s;
-      }
+      for (int c = 0; c < 3; c++)
+        bB[sidx<Q>(c, qk, b, a)] = ff_dot<P>([&](int j) { return ffpair{tab.B[b][j], bA[sidx<Q>(c, qk, j, a)]}; });
     }
   }
   __syncthreads();
 #pragma unroll 1
   for (int qk = 0; qk < Q; qk++) {
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      ff s = ff(0);
-#pragma unroll
-      for (int i = 0; i < P; i++) s = madd(s, tab.B[a][i], bB[sidx<Q>(c, qk, b, i)]);
-      bC[sidx<Q>(c, qk, b, a)] = s;
-    }
+    for (int c = 0; c < 3; c++)
+      bC[sidx<Q>(c, qk, b, a)] = ff_dot<P>([&](int i) { return ffpair{tab.B[a][i], bB[sidx<Q>(c, qk, b, i)]}; });
   }
   __syncthreads();
   // gradients, pointwise, fluxes: x-, y-flux to bA, bB; z-flux to bD
@@ -462,16 +480,9 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<ff, Q>())
     ff g[3][3], f[3][3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      ff gx = ff(0), gy = ff(0), gz = ff(0);
-#pragma unroll
-      for (int m = 0; m < Q; m++) {
-        gx = madd(gx, tab.D[a][m], bC[sidx<Q>(c, qk, b, m)]);
-        gy = madd(gy, tab.D[b][m], bC[sidx<Q>(c, qk, m, a)]);
-        gz = madd(gz, tab.D[qk][m], bC[sidx<Q>(c, m, b, a)]);
-      }
-      g[c][0] = gx;
-      g[c][1] = gy;
-      g[c][2] = gz;
+      g[c][0] = ff_dot<Q>([&](int m) { return ffpair{tab.D[a][m], bC[sidx<Q>(c, qk, b, m)]}; });
+      g[c][1] = ff_dot<Q>([&](int m) { return ffpair{tab.D[b][m], bC[sidx<Q>(c, qk, m, a)]}; });
+      g[c][2] = ff_dot<Q>([&](int m) { return ffpair{tab.D[qk][m], bC[sidx<Q>(c, m, b, a)]}; });
     }
     if (live) {
       pointwise_ff<LAYOUT>(qe + qk * Q2, qstride, g, f);
@@ -491,48 +502,59 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<ff, Q>())
 #pragma unroll 1
   for (int qk = 0; qk < Q; qk++) {
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      ff s = ff(0);
-#pragma unroll
-      for (int m = 0; m < Q; m++) {
-        s = madd(s, tab.D[m][a], bA[sidx<Q>(c, qk, b, m)]);
-        s = madd(s, tab.D[m][b], bB[sidx<Q>(c, qk, m, a)]);
-        s = madd(s, tab.D[m][qk], bD[sidx<Q>(c, m, b, a)]);
-      }
-      bC[sidx<Q>(c, qk, b, a)] = s;
-    }
+    for (int c = 0; c < 3; c++)
+      bC[sidx<Q>(c, qk, b, a)] = ff_dot<3 * Q>([&](int i) {
+        const int m = i / 3, d = i % 3;
+        return d == 0   ? ffpair{tab.D[m][a], bA[sidx<Q>(c, qk, b, m)]}
+               : d == 1 ? ffpair{tab.D[m][b], bB[sidx<Q>(c, qk, m, a)]}
+                        : ffpair{tab.D[m][qk], bD[sidx<Q>(c, m, b, a)]};
+      });
   }
   __syncthreads();
   if (a < P) {  // B_I^T along x
 #pragma unroll 1
     for (int qk = 0; qk < Q; qk++) {
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        ff s = ff(0);
-#pragma unroll
-        for (int qi = 0; qi < Q; qi++) s = madd(s, tab.B[qi][a], bC[sidx<Q>(c, qk, b, qi)]);
-        bA[sidx<Q>(c, qk, b, a)] = s;
-      }
+      for (int c = 0; c < 3; c++)
+        bA[sidx<Q>(c, qk, b, a)] = ff_dot<Q>([&](int qi) { return ffpair{tab.B[qi][a], bC[sidx<Q>(c, qk, b, qi)]}; });
     }
   }
   __syncthreads();
   if (a < P && b < P) {  // B_I^T along y, then along z into the node column's registers
     ff out[3][P];
+#if NH_FF_DOT2
+    ffdot od[3][P];  // compensated sums over the rolled plane loop, renormalised after it
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int k = 0; k < P; k++) od[c][k] = ffdot{0.f, 0.f};
+#else
 #pragma unroll
     for (int c = 0; c < 3; c++)
 #pragma unroll
       for (int k = 0; k < P; k++) out[c][k] = ff(0);
+#endif
 #pragma unroll 1
     for (int qk = 0; qk < Q; qk++) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        ff w = ff(0);
+        const ff w = ff_dot<Q>([&](int qj) { return ffpair{tab.B[qj][b], bA[sidx<Q>(c, qk, qj, a)]}; });
 #pragma unroll
-        for (int qj = 0; qj < Q; qj++) w = madd(w, tab.B[qj][b], bA[sidx<Q>(c, qk, qj, a)]);
-#pragma unroll
-        for (int k = 0; k < P; k++) out[c][k] = madd(out[c][k], tab.B[qk][k], w);
+        for (int k = 0; k < P; k++) {
+#if NH_FF_DOT2
+          ffd_add(od[c][k], tab.B[qk][k], w);
+#else
+          out[c][k] = madd(out[c][k], tab.B[qk][k], w);
+#endif
+        }
       }
     }
+#if NH_FF_DOT2
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int k = 0; k < P; k++) out[c][k] = ffd_done(od[c][k]);
+#endif
     if (live) {
 #pragma unroll
       for (int k = 0; k < P; k++) {
@@ -742,8 +764,10 @@ __global__ void NH_F32L_BOUNDS(Q)
       for (int i = 0; i < P; i++) nid[i] = live ? __ldg(&emapb[e * P3 + (v * P + u) * P + i]) : 0u;
     }
     // the line's P nodes consecutive and unconstrained (or lifted): its 3P values
-    // are one contiguous run of du, read with vector loads
-    bool vrun = NH_F32_VGATHER && live && (vec_ok & 2);
+    // are one contiguous run of du, read with vector loads.  Taken for P >= 5 only:
+    // measured at full size, +2% at q = 5, -1 to -2% at q = 3 and 4 (the extra
+    // registers and branches cost more than the fewer load requests save)
+    bool vrun = NH_F32_VGATHER && P >= 5 && live && (vec_ok & 2);
     const unsigned n0 = nid[0] & kNodeMask;
 #pragma unroll
     for (int i = 0; i < P; i++) vrun = vrun && (lift ? (nid[i] & kNodeMask) : nid[i]) == n0 + (unsigned)i;
