@@ -2,8 +2,56 @@
 // matrix-free kernels and the Q1 stencil assembly.  Internal.
 #pragma once
 #include "nh_internal.cuh"
+#include "nh_ff.cuh"
 
 namespace nhpw {
+
+// Short dot products a0 b0 + a1 b1 + ...: for FP64 and FP32 the plain left-to-right
+// expression (contracted to FMAs as written), in float-float a compensated dot
+// product (ffd_*: one TwoSum per term, a single renormalisation).
+template <typename T>
+__device__ __forceinline__ T dot3(T a0, T b0, T a1, T b1, T a2, T b2) {
+  return a0 * b0 + a1 * b1 + a2 * b2;
+}
+template <typename T>
+__device__ __forceinline__ T dot4(T a0, T b0, T a1, T b1, T a2, T b2, T a3, T b3) {
+  return a0 * b0 + a1 * b1 + a2 * b2 + a3 * b3;
+}
+template <typename T>
+__device__ __forceinline__ T dot6(T a0, T b0, T a1, T b1, T a2, T b2, T a3, T b3, T a4, T b4, T a5, T b5) {
+  return a0 * b0 + a1 * b1 + a2 * b2 + a3 * b3 + a4 * b4 + a5 * b5;
+}
+#ifndef NH_FF_DOT2_PW
+#define NH_FF_DOT2_PW 1
+#endif
+#if NH_FF_DOT2_PW
+template <>
+__device__ __forceinline__ ff dot3<ff>(ff a0, ff b0, ff a1, ff b1, ff a2, ff b2) {
+  ffdot d = ffd_first(a0, b0);
+  ffd_add(d, a1, b1);
+  ffd_add(d, a2, b2);
+  return ffd_done(d);
+}
+template <>
+__device__ __forceinline__ ff dot4<ff>(ff a0, ff b0, ff a1, ff b1, ff a2, ff b2, ff a3, ff b3) {
+  ffdot d = ffd_first(a0, b0);
+  ffd_add(d, a1, b1);
+  ffd_add(d, a2, b2);
+  ffd_add(d, a3, b3);
+  return ffd_done(d);
+}
+template <>
+__device__ __forceinline__ ff dot6<ff>(ff a0, ff b0, ff a1, ff b1, ff a2, ff b2, ff a3, ff b3, ff a4, ff b4, ff a5,
+                                       ff b5) {
+  ffdot d = ffd_first(a0, b0);
+  ffd_add(d, a1, b1);
+  ffd_add(d, a2, b2);
+  ffd_add(d, a3, b3);
+  ffd_add(d, a4, b4);
+  ffd_add(d, a5, b5);
+  return ffd_done(d);
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // Pointwise linearised stress (the D of A = E^T B^T D B E).
@@ -30,21 +78,21 @@ __device__ __forceinline__ void pw_current_ld(LD ld, const T (&g)[3][3], T (&f)[
 #pragma unroll
   for (int c = 0; c < 3; c++)
 #pragma unroll
-    for (int k = 0; k < 3; k++) G[c][k] = g[c][0] * X[0][k] + g[c][1] * X[1][k] + g[c][2] * X[2][k];
+    for (int k = 0; k < 3; k++) G[c][k] = dot3(g[c][0], X[0][k], g[c][1], X[1][k], g[c][2], X[2][k]);
   const T trG = wl * (G[0][0] + G[1][1] + G[2][2]);
   T S[3][3];
 #pragma unroll
   for (int c = 0; c < 3; c++)
 #pragma unroll
     for (int k = 0; k < 3; k++)
-      S[c][k] = G[c][0] * tau[0][k] + G[c][1] * tau[1][k] + G[c][2] * tau[2][k] + wm * (G[c][k] + G[k][c]);
+      S[c][k] = dot4(G[c][0], tau[0][k], G[c][1], tau[1][k], G[c][2], tau[2][k], wm, G[c][k] + G[k][c]);
   S[0][0] += trG;
   S[1][1] += trG;
   S[2][2] += trG;
 #pragma unroll
   for (int c = 0; c < 3; c++)
 #pragma unroll
-    for (int d = 0; d < 3; d++) f[c][d] = S[c][0] * X[d][0] + S[c][1] * X[d][1] + S[c][2] * X[d][2];
+    for (int d = 0; d < 3; d++) f[c][d] = dot3(S[c][0], X[d][0], S[c][1], X[d][1], S[c][2], X[d][2]);
 }
 
 // Initial configuration (Sec. V-E, "initial tuned" storage): dF = g grad_X xi,
@@ -67,12 +115,12 @@ __device__ __forceinline__ void pw_initial_ld(LD ld, const T (&g)[3][3], T (&f)[
 #pragma unroll
   for (int c = 0; c < 3; c++)
 #pragma unroll
-    for (int k = 0; k < 3; k++) dF[c][k] = g[c][0] * R[0][k] + g[c][1] * R[1][k] + g[c][2] * R[2][k];
+    for (int k = 0; k < 3; k++) dF[c][k] = dot3(g[c][0], R[0][k], g[c][1], R[1][k], g[c][2], R[2][k]);
   T dE[3][3];
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
-    for (int l = 0; l < 3; l++) dE[k][l] = F[0][k] * dF[0][l] + F[1][k] * dF[1][l] + F[2][k] * dF[2][l];
+    for (int l = 0; l < 3; l++) dE[k][l] = dot3(F[0][k], dF[0][l], F[1][k], dF[1][l], F[2][k], dF[2][l]);
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
@@ -90,14 +138,14 @@ __device__ __forceinline__ void pw_initial_ld(LD ld, const T (&g)[3][3], T (&f)[
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
-    for (int l = 0; l < 3; l++) CdE[k][l] = Ci[k][0] * dE[0][l] + Ci[k][1] * dE[1][l] + Ci[k][2] * dE[2][l];
+    for (int l = 0; l < 3; l++) CdE[k][l] = dot3(Ci[k][0], dE[0][l], Ci[k][1], dE[1][l], Ci[k][2], dE[2][l]);
   const T two_m = T(2) * (wmu - wll);
   T WdS[3][3], WS[3][3];
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
     for (int l = 0; l < 3; l++) {
-      T cdec = CdE[k][0] * Ci[0][l] + CdE[k][1] * Ci[1][l] + CdE[k][2] * Ci[2][l];
+      T cdec = dot3(CdE[k][0], Ci[0][l], CdE[k][1], Ci[1][l], CdE[k][2], Ci[2][l]);
       WdS[k][l] = wl * trc * Ci[k][l] + two_m * cdec;
       WS[k][l] = (wll - wmu) * Ci[k][l] + (k == l ? wmu : T(0));
     }
@@ -106,12 +154,12 @@ __device__ __forceinline__ void pw_initial_ld(LD ld, const T (&g)[3][3], T (&f)[
   for (int c = 0; c < 3; c++)
 #pragma unroll
     for (int K = 0; K < 3; K++)
-      dP[c][K] = dF[c][0] * WS[0][K] + dF[c][1] * WS[1][K] + dF[c][2] * WS[2][K] + F[c][0] * WdS[0][K] +
-                 F[c][1] * WdS[1][K] + F[c][2] * WdS[2][K];
+      dP[c][K] = dot6(dF[c][0], WS[0][K], dF[c][1], WS[1][K], dF[c][2], WS[2][K], F[c][0], WdS[0][K], F[c][1],
+                      WdS[1][K], F[c][2], WdS[2][K]);
 #pragma unroll
   for (int c = 0; c < 3; c++)
 #pragma unroll
-    for (int d = 0; d < 3; d++) f[c][d] = dP[c][0] * R[d][0] + dP[c][1] * R[d][1] + dP[c][2] * R[d][2];
+    for (int d = 0; d < 3; d++) f[c][d] = dot3(dP[c][0], R[d][0], dP[c][1], R[d][1], dP[c][2], R[d][2]);
 }
 
 // AD-style tape (Sec. V-E, "initial AD" storage): the same dP = dF S + F dS with
@@ -135,14 +183,14 @@ __device__ __forceinline__ void pw_tape_ld(LD ld, const T (&g)[3][3], T (&f)[3][
 #pragma unroll
   for (int c = 0; c < 3; c++)
 #pragma unroll
-    for (int k = 0; k < 3; k++) dF[c][k] = g[c][0] * R[0][k] + g[c][1] * R[1][k] + g[c][2] * R[2][k];
+    for (int k = 0; k < 3; k++) dF[c][k] = dot3(g[c][0], R[0][k], g[c][1], R[1][k], g[c][2], R[2][k]);
   T dE[3][3];
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
     for (int l = k; l < 3; l++) {
-      const T a = F[0][k] * dF[0][l] + F[1][k] * dF[1][l] + F[2][k] * dF[2][l];
-      const T b = F[0][l] * dF[0][k] + F[1][l] * dF[1][k] + F[2][l] * dF[2][k];
+      const T a = dot3(F[0][k], dF[0][l], F[1][k], dF[1][l], F[2][k], dF[2][l]);
+      const T b = dot3(F[0][l], dF[0][k], F[1][l], dF[1][k], F[2][l], dF[2][k]);
       dE[k][l] = T(0.5) * (a + b);
       dE[l][k] = dE[k][l];
     }
@@ -155,24 +203,24 @@ __device__ __forceinline__ void pw_tape_ld(LD ld, const T (&g)[3][3], T (&f)[3][
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
-    for (int l = 0; l < 3; l++) CdE[k][l] = Ci[k][0] * dE[0][l] + Ci[k][1] * dE[1][l] + Ci[k][2] * dE[2][l];
+    for (int l = 0; l < 3; l++) CdE[k][l] = dot3(Ci[k][0], dE[0][l], Ci[k][1], dE[1][l], Ci[k][2], dE[2][l]);
   T WdS[3][3];
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
     for (int l = 0; l < 3; l++)
-      WdS[k][l] = wl * trc * Ci[k][l] + two_m * (CdE[k][0] * Ci[0][l] + CdE[k][1] * Ci[1][l] + CdE[k][2] * Ci[2][l]);
+      WdS[k][l] = wl * trc * Ci[k][l] + two_m * dot3(CdE[k][0], Ci[0][l], CdE[k][1], Ci[1][l], CdE[k][2], Ci[2][l]);
   T dP[3][3];
 #pragma unroll
   for (int c = 0; c < 3; c++)
 #pragma unroll
     for (int K = 0; K < 3; K++)
-      dP[c][K] = dF[c][0] * WS[0][K] + dF[c][1] * WS[1][K] + dF[c][2] * WS[2][K] + F[c][0] * WdS[0][K] +
-                 F[c][1] * WdS[1][K] + F[c][2] * WdS[2][K];
+      dP[c][K] = dot6(dF[c][0], WS[0][K], dF[c][1], WS[1][K], dF[c][2], WS[2][K], F[c][0], WdS[0][K], F[c][1],
+                      WdS[1][K], F[c][2], WdS[2][K]);
 #pragma unroll
   for (int c = 0; c < 3; c++)
 #pragma unroll
-    for (int d = 0; d < 3; d++) f[c][d] = dP[c][0] * R[d][0] + dP[c][1] * R[d][1] + dP[c][2] * R[d][2];
+    for (int d = 0; d < 3; d++) f[c][d] = dot3(dP[c][0], R[d][0], dP[c][1], R[d][1], dP[c][2], R[d][2]);
 }
 
 template <int LAYOUT, typename T, typename LD>
