@@ -100,8 +100,13 @@ def n_params(levels, ch):
     return sum(co * ci * 27 + co for co, ci, _ in layer_shapes(levels, ch))
 
 
-def forward(theta, x, levels, ch, keep=False):
+def forward(theta, x, levels, ch, keep=False, store=None):
+    """The network's output for input x.  ``store``, if given, is applied to every
+    field an implementation keeps between layers -- the input, each ReLU output,
+    each upsampled field and each skip sum -- to model the precision it stores
+    them in (the output layer's field is not stored)."""
     P = unpack(np.asarray(theta, dtype=np.float64), levels, ch)
+    keep_field = store if store is not None else (lambda v: v)
     tape = []
     k = 0
 
@@ -110,10 +115,10 @@ def forward(theta, x, levels, ch, keep=False):
         W, b, s = P[k]
         k += 1
         z = conv3d(h, W, b, s)
-        y = np.maximum(z, 0.0) if relu else z
+        y = keep_field(np.maximum(z, 0.0)) if relu else z
         tape.append((h, W, s, relu, y))
         return y
-    h = conv(x, True)
+    h = conv(keep_field(x), True)
     h = conv(h, True)
     skips = [h]
     for _ in range(1, levels):
@@ -121,9 +126,9 @@ def forward(theta, x, levels, ch, keep=False):
         h = conv(h, True)
         skips.append(h)
     for l in range(levels - 2, -1, -1):
-        u = upsample(h)
+        u = keep_field(upsample(h))
         tape.append(("up",))
-        h = conv(u, True) + skips[l]
+        h = keep_field(conv(u, True) + skips[l])
         h = conv(h, True)
     y = conv(h, False)
     return (y, tape) if keep else y

@@ -151,6 +151,39 @@ def test_tensor_core_network_exact(nhctx, N, ch, wseed, xseed):
     parity.check_inf(gs[True], g_ref, 2e-2, "tensor-core gradient")
 
 
+def test_tensor_core_network_exact_at_33(nhctx):
+    """The 4-level 16/32/48/64 network at 33^3 (launch shapes of the production
+    grids), integer data.  Not every field is exact in BF16 here, but every field
+    is an integer and every convolution's sum of absolute terms stays far below
+    2^24, so each FP32 sum is exact in any order and both paths round the same
+    values to BF16 at the same points: their outputs must equal the oracle's with
+    BF16 rounding applied to every stored field, bit for bit.  The gradients of
+    the two paths differ only by the tensor-core backward's TF32 operands (2e-2)."""
+    ctx, _ = nhctx
+    from paper_2204_01722_b300 import nh
+    N, ch = 33, (16, 32, 48, 64)
+    theta = _integer_network(4, ch, 0)
+    x = np.random.default_rng(100).integers(0, 4, size=(4, N, N, N)).astype(np.float64)
+    bf = lambda v: torch.from_numpy(np.asarray(v, dtype=np.float32)).bfloat16().double().numpy()
+    y_ref, tape = learned.forward(theta, x, 4, ch, keep=True, store=bf)
+    for h, W, *_ in (t for t in tape if not isinstance(t[0], str)):
+        assert np.array_equal(h, np.round(h)), "precondition: integer fields"
+        assert np.abs(W).reshape(W.shape[0], -1).sum(axis=1).max() * np.abs(h).max() < 2.0 ** 24, "precondition"
+    rng = np.random.default_rng(7)
+    t = np.zeros(3 * N ** 3)
+    k = 1 << int(np.log2(t.size))
+    t[rng.choice(t.size, size=k, replace=False)] = rng.choice([-1.0, 1.0], size=k)
+    net = nh.nh_net_create(ctx, N, 4, ch, bf16=True, seed=3)
+    nh.nh_net_set_params(ctx, net, theta.astype(np.float32))
+    ys, gs = _both_paths(ctx, nh, net, N, torch.from_numpy(x.astype(np.float32)).cuda(),
+                         torch.from_numpy(t.reshape(3, N, N, N).astype(np.float32)).cuda())
+    nh.nh_net_destroy(net)
+    assert np.array_equal(ys[False], y_ref), "CUDA-core forward"
+    assert np.array_equal(ys[True], y_ref), "tensor-core forward"
+    assert np.count_nonzero(y_ref) > 0.2 * y_ref.size
+    assert rel(gs[True], gs[False]) < 2e-2
+
+
 @pytest.mark.parametrize("N,ch", [(9, (8, 16, 32)), (13, (16, 48, 64)), (7, (32, 8))])
 def test_tensor_core_network_random(nhctx, N, ch):
     """Random inputs and He-normal weights: both BF16 paths against the FP64
