@@ -43,12 +43,15 @@ __host__ __device__ constexpr int epb_for(int Q) { return nh_epb(Q); }
 #ifndef NH_FF_MIN_BLOCKS_SMALLQ
 #define NH_FF_MIN_BLOCKS_SMALLQ 4
 #endif
+#ifndef NH_FF_MIN_BLOCKS_Q3
+#define NH_FF_MIN_BLOCKS_Q3 5
+#endif
 // Rolled float-float kernel (Q2 / Q3 / Q4 GDoF/s on B300 with 3, 4, 5 blocks of
 // registers per SM): q = 3 6.08 / 6.08 / 6.40, q = 4 6.99 / 7.58 / 7.26, q = 5
 // 7.07 / 7.06 / 7.09 (2, 3, 4 blocks).
 template <typename T, int Q>
 __host__ __device__ constexpr int apply_min_blocks() {
-  return std::is_same<T, ff>::value ? (Q <= 3 ? 5 : Q == 4 ? NH_FF_MIN_BLOCKS_SMALLQ : 3) : 1;
+  return std::is_same<T, ff>::value ? (Q <= 3 ? NH_FF_MIN_BLOCKS_Q3 : Q == 4 ? NH_FF_MIN_BLOCKS_SMALLQ : 3) : 1;
 }
 
 // Shared-memory stride of one element's [9][Q^3] work area, padded so that the
