@@ -25,16 +25,23 @@ __host__ __device__ constexpr int nh_epb(int Q) { return (128 / (Q * Q)) > 0 ? 1
 // in slot (k + nh_f32_rot(S, p)) mod S/4 -- a per-point rotation that puts the 8
 // lanes of one 16-byte shared load on distinct banks -- and its last S mod 4
 // scalars at [NP][S mod 4] after all points' chunks.
-// NH_F32_DIRECT = 1 (experimental): the FP32 apply loads its quadrature data from
+// Direct form (nh_f32_direct(q)): the FP32 apply loads its quadrature data from
 // global memory straight into registers; a plane is then scalar-major,
 // [S][NPP] with NPP = NP rounded up to 32 points, so that each warp load of one
-// scalar reads 128 contiguous bytes.
+// scalar reads 128 contiguous bytes.  Taken for the q whose bit is set in
+// NH_F32_DIRECT_QMASK, or for every q with NH_F32_DIRECT = 1.  Measured at full
+// size against the plane ring: q = 3 +4.5%, q = 5 equal (with the vector gather
+// of node lines in both), q = 4 -3%; so q = 3 only.
 #ifndef NH_F32_DIRECT
 #define NH_F32_DIRECT 0
 #endif
+#ifndef NH_F32_DIRECT_QMASK
+#define NH_F32_DIRECT_QMASK (1 << 3)
+#endif
+__host__ __device__ constexpr bool nh_f32_direct(int Q) { return NH_F32_DIRECT || ((NH_F32_DIRECT_QMASK >> Q) & 1); }
 __host__ __device__ constexpr int nh_f32_npp(int Q) { return (nh_epb(Q) * Q * Q + 31) / 32 * 32; }
 __host__ __device__ constexpr long long nh_f32_plane_floats(int Q, int S) {
-  return NH_F32_DIRECT ? (long long)S * nh_f32_npp(Q) : ((long long)S * nh_epb(Q) * Q * Q + 3) / 4 * 4;
+  return nh_f32_direct(Q) ? (long long)S * nh_f32_npp(Q) : ((long long)S * nh_epb(Q) * Q * Q + 3) / 4 * 4;
 }
 __host__ __device__ constexpr long long nh_f32_batch_floats(int Q, int S) { return (long long)Q * nh_f32_plane_floats(Q, S); }
 __host__ __device__ constexpr int nh_f32_rot(int S, int p) { return S / 4 == 4 ? ((p & 7) >> 1) : ((p & 7) >> 2); }

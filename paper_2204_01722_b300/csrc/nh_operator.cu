@@ -676,26 +676,27 @@ __device__ __forceinline__ void ld_run(const float* x, float (&v)[N]) {
 #endif
 
 #ifndef NH_F32_DIRECT_MINB
-#define NH_F32_DIRECT_MINB 1
+#define NH_F32_DIRECT_MINB 7
 #endif
 #ifndef NH_F32_DIRECT_PF
 #define NH_F32_DIRECT_PF 1
 #endif
-#if NH_F32_DIRECT
-#define NH_F32L_BOUNDS(Q) __launch_bounds__(Q* Q* epb_for(Q), NH_F32_DIRECT_MINB)
-#else
-#define NH_F32L_BOUNDS(Q) __launch_bounds__(Q* Q* epb_for(Q))
-#endif
-template <int P, int Q, int LAYOUT, bool COL = false>
-__global__ void NH_F32L_BOUNDS(Q)
+// DIRECT (= nh_f32_direct(Q)): the quadrature data is loaded straight into
+// registers, plane by plane with the next plane requested ahead, instead of
+// through the shared-memory plane ring; registers are then capped for
+// NH_F32_DIRECT_MINB resident blocks (a minimum of 0 blocks leaves the ring form's
+// register count to the compiler, as without the argument).
+template <int P, int Q, int LAYOUT, bool COL = false, bool DIRECT = nh_f32_direct(Q)>
+__global__ void __launch_bounds__(Q* Q* epb_for(Q), DIRECT ? NH_F32_DIRECT_MINB : 0)
     k_jacobian_apply_f32l(int64_t ne, const unsigned* __restrict__ emapb, const float* __restrict__ qdb,
                           const KTab<P, Q, float> tab, const float* __restrict__ du, float* __restrict__ y, int lift,
                           int vec_ok, int rows_ok, int* __restrict__ err, int colour, int nbx, int ny, int nz) {
+  static_assert(DIRECT == nh_f32_direct(Q), "the quadrature-data layout follows nh_f32_direct");
   using L = LineLayout<Q>;
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   constexpr int S = nh_layout_scalars(LAYOUT);
   constexpr long long BS = nh_f32_batch_floats(Q, S), PL = nh_f32_plane_floats(Q, S);
-  constexpr long long RING = NH_F32_DIRECT ? 0 : 2 * PL;  // floats of the plane ring in shared memory
+  constexpr long long RING = DIRECT ? 0 : 2 * PL;  // floats of the plane ring in shared memory
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ unsigned srun[EPB * P * P];        // start node of each node line's run (or ~0)
@@ -730,27 +731,27 @@ __global__ void NH_F32L_BOUNDS(Q)
       bulk_g2s(dst + off, src + off, chunk, b);
     }
   };
-#if NH_F32_DIRECT
-  // plane 0 of this thread's point, loaded at the start so that it arrives
-  // during the interpolation stages
+  // DIRECT: plane 0 of this thread's point, loaded at the start so that it
+  // arrives during the interpolation stages
   const float* qg = qdb + batch * BS + t;
-  float qv[S];
-  if constexpr (NH_F32_DIRECT_PF) {
+  float qv[DIRECT ? S : 1];
+  if constexpr (DIRECT) {
+    if constexpr (NH_F32_DIRECT_PF) {
 #pragma unroll
-    for (int k = 0; k < S; k++) qv[k] = ldg_stream(qg + k * nh_f32_npp(Q));
+      for (int k = 0; k < S; k++) qv[k] = ldg_stream(qg + k * nh_f32_npp(Q));
+    }
+    (void)issue_plane;
+  } else {
+    if (t == 0) {
+      mbar_init(&bar[0]);
+      mbar_init(&bar[1]);
+    }
+    __syncthreads();
+    if (t == 0) {
+      issue_plane(0);
+      issue_plane(1);
+    }
   }
-  (void)issue_plane;
-#else
-  if (t == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
-  }
-  __syncthreads();
-  if (t == 0) {
-    issue_plane(0);
-    issue_plane(1);
-  }
-#endif
   // x-lines over nodes (j = u, k = v): gather and B_I along x
   const bool node_line = u < P && v < P;
   unsigned nid[P];
@@ -886,21 +887,21 @@ __global__ void NH_F32L_BOUNDS(Q)
     float fz[3][Q];
 #pragma unroll
     for (int qz = 0; qz < Q; qz++) {
-#if NH_F32_DIRECT
-      float qn[S];  // the next plane's scalars, requested before this plane's work
-      if constexpr (NH_F32_DIRECT_PF) {
-        if (qz + 1 < Q) {
+      float qn[DIRECT ? S : 1];               // DIRECT: the next plane's scalars, requested before this plane's work
+      const float* qp = qs + (qz & 1) * PL;  // ring: this plane's slot
+      if constexpr (DIRECT) {
+        if constexpr (NH_F32_DIRECT_PF) {
+          if (qz + 1 < Q) {
 #pragma unroll
-          for (int k = 0; k < S; k++) qn[k] = ldg_stream(qg + (qz + 1) * PL + k * nh_f32_npp(Q));
+            for (int k = 0; k < S; k++) qn[k] = ldg_stream(qg + (qz + 1) * PL + k * nh_f32_npp(Q));
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < S; k++) qv[k] = ldg_stream(qg + qz * PL + k * nh_f32_npp(Q));
         }
       } else {
-#pragma unroll
-        for (int k = 0; k < S; k++) qv[k] = ldg_stream(qg + qz * PL + k * nh_f32_npp(Q));
+        mbar_wait_bounded(&bar[qz & 1], (qz >> 1) & 1, err);
       }
-#else
-      mbar_wait_bounded(&bar[qz & 1], (qz >> 1) & 1, err);
-      const float* qp = qs + (qz & 1) * PL;  // this plane's slot
-#endif
       float g[3][3], f[3][3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -909,24 +910,24 @@ __global__ void NH_F32L_BOUNDS(Q)
         g[c][2] = gz[c][qz];
       }
       if (live) {
-#if NH_F32_DIRECT
-        nhpw::pointwise_ld<LAYOUT, float>([&](int i) { return qv[i]; }, g, f);
-#else
-        // this point's scalars: S/4 rotated 16-byte chunks, then the remainder
-        constexpr int NC = S / 4, R = S - 4 * NC, NP = EPB * Q2;
-        float qv[S];
+        if constexpr (DIRECT) {
+          nhpw::pointwise_ld<LAYOUT, float>([&](int i) { return qv[i]; }, g, f);
+        } else {
+          // this point's scalars: S/4 rotated 16-byte chunks, then the remainder
+          constexpr int NC = S / 4, R = S - 4 * NC, NP = EPB * Q2;
+          float qr[S];
 #pragma unroll
-        for (int k = 0; k < NC; k++) {
-          const float4 c4 = *reinterpret_cast<const float4*>(qp + t * 4 * NC + ((k + nh_f32_rot(S, t)) % NC) * 4);
-          qv[4 * k] = c4.x;
-          qv[4 * k + 1] = c4.y;
-          qv[4 * k + 2] = c4.z;
-          qv[4 * k + 3] = c4.w;
+          for (int k = 0; k < NC; k++) {
+            const float4 c4 = *reinterpret_cast<const float4*>(qp + t * 4 * NC + ((k + nh_f32_rot(S, t)) % NC) * 4);
+            qr[4 * k] = c4.x;
+            qr[4 * k + 1] = c4.y;
+            qr[4 * k + 2] = c4.z;
+            qr[4 * k + 3] = c4.w;
+          }
+#pragma unroll
+          for (int j = 0; j < R; j++) qr[4 * NC + j] = qp[NP * 4 * NC + t * R + j];
+          nhpw::pointwise_ld<LAYOUT, float>([&](int i) { return qr[i]; }, g, f);
         }
-#pragma unroll
-        for (int j = 0; j < R; j++) qv[4 * NC + j] = qp[NP * 4 * NC + t * R + j];
-        nhpw::pointwise_ld<LAYOUT, float>([&](int i) { return qv[i]; }, g, f);
-#endif
       } else {
 #pragma unroll
         for (int i = 0; i < 9; i++) f[i / 3][i % 3] = 0.f;
@@ -937,17 +938,17 @@ __global__ void NH_F32L_BOUNDS(Q)
         Bf[L::ix(c, qz, v, u)] = f[c][1];
         fz[c][qz] = f[c][2];
       }
-#if NH_F32_DIRECT
-      if (NH_F32_DIRECT_PF && qz + 1 < Q) {
+      if constexpr (DIRECT) {
+        if (NH_F32_DIRECT_PF && qz + 1 < Q) {
 #pragma unroll
-        for (int k = 0; k < S; k++) qv[k] = qn[k];
+          for (int k = 0; k < S; k++) qv[k] = qn[k];
+        }
+      } else {
+        if (qz + 2 < Q) {
+          __syncthreads();
+          if (t == 0) issue_plane(qz + 2);
+        }
       }
-#else
-      if (qz + 2 < Q) {
-        __syncthreads();
-        if (t == 0) issue_plane(qz + 2);
-      }
-#endif
     }
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -1505,7 +1506,7 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
   const int threads = Q * Q * EPB;
   const int64_t blocks = (A.ne + EPB - 1) / EPB;
   if (blocks == 0) return cudaSuccess;
-  const size_t smem = ((NH_F32_DIRECT ? 0 : (size_t)2 * nh_f32_plane_floats(Q, S)) +
+  const size_t smem = ((nh_f32_direct(Q) ? 0 : (size_t)2 * nh_f32_plane_floats(Q, S)) +
                        (size_t)LineLayout<Q>::block_floats(EPB)) * sizeof(float);
   const KTab<P, Q, float> tab = make_ktab<P, Q, float>(*A.tab);
   const int nbx = A.nx > 0 ? A.nx / EPB : 0;
@@ -1514,17 +1515,19 @@ cudaError_t apply_f32l_launch(const OpArgs& A, cudaStream_t s) {
     const int px = A.colour & 1, py = (A.colour >> 1) & 1, pz = A.colour >> 2;
     const int64_t grid = (int64_t)((nbx - px + 1) / 2) * ((A.ny - py + 1) / 2) * ((A.nz - pz + 1) / 2);
     if (grid == 0) return cudaSuccess;
-    cudaError_t e = prep<k_jacobian_apply_f32l<P, Q, LAYOUT, true>>(smem);
+    constexpr auto kern = k_jacobian_apply_f32l<P, Q, LAYOUT, true>;
+    cudaError_t e = prep<kern>(smem);
     if (e != cudaSuccess) return e;
-    k_jacobian_apply_f32l<P, Q, LAYOUT, true><<<(unsigned)grid, threads, smem, s>>>(
+    kern<<<(unsigned)grid, threads, smem, s>>>(
         A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift,
         1 | (((uintptr_t)A.in & 15) == 0 ? 2 : 0), 1, A.err, A.colour, nbx,
         A.ny, A.nz);
     return cudaGetLastError();
   }
-  cudaError_t e = prep<k_jacobian_apply_f32l<P, Q, LAYOUT>>(smem);
+  constexpr auto kern = k_jacobian_apply_f32l<P, Q, LAYOUT, false>;
+  cudaError_t e = prep<kern>(smem);
   if (e != cudaSuccess) return e;
-  k_jacobian_apply_f32l<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(
+  kern<<<(unsigned)blocks, threads, smem, s>>>(
       A.ne, A.emapb, (const float*)A.qd, tab, (const float*)A.in, (float*)A.out, A.lift,
       (((uintptr_t)A.out & 15) == 0 ? 1 : 0) | (((uintptr_t)A.in & 15) == 0 ? 2 : 0),
       ((uintptr_t)A.out & 15) == 0 && A.nx > 0 && (NH_F32_ROWS_ANY || Q <= 3 || A.nx % EPB == 0) ? 1 : 0, A.err,

@@ -61,7 +61,7 @@ __global__ void k_f32_blocked(int Q, int EPB, int S, long long PL, int64_t ne, c
     const int s = (int)(i / (ne * Q3));
     const int64_t r = i - s * ne * Q3, e = r / Q3;
     const int q = (int)(r - e * Q3), qz = q / Q2, p = (int)(e % EPB) * Q2 + (q - qz * Q2);
-    const int64_t pos = NH_F32_DIRECT ? (int64_t)s * nh_f32_npp(Q) + p
+    const int64_t pos = nh_f32_direct(Q) ? (int64_t)s * nh_f32_npp(Q) + p
                         : s < 4 * NC ? (int64_t)p * 4 * NC + (((s >> 2) + nh_f32_rot(S, p)) % NC) * 4 + (s & 3)
                                      : (int64_t)NP * 4 * NC + (int64_t)p * R + (s - 4 * NC);
     qdf[((e / EPB) * Q + qz) * PL + pos] = (float)qd[i];
