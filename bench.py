@@ -71,7 +71,7 @@ def n_dof_of(p, n):
 # capture summarised in profiles/ (small case, scaled to the full launch by
 # elements); reset to None whenever the kernel changes.
 NCU_TRAFFIC = {("f64", 3, 48): 1.203e9,
-               ("f32", 3, 48): 6.06e8, ("f32", 4, 37): 5.66e8,
+               ("f32", 2, 74): 9.00e8, ("f32", 3, 48): 6.06e8, ("f32", 4, 37): 5.66e8,
                ("f64x", 3, 48): 1.212e9}
 
 
