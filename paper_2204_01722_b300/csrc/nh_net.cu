@@ -1060,7 +1060,8 @@ nh_status refresh_compute_copy(nh_net n) {
   if (n->bf16) {
     k_from_f32<__nv_bfloat16><<<blocks_for(n->np), 256, 0, n->ctx->stream>>>(n->np, n->theta, (__nv_bfloat16*)n->wc);
     LayerTable tab{};
-    tab.n = (int)n->L.size();
+    tab.n = (int)n->L.size();  // 4 L - 1 <= 23 layers for L <= 6 levels (checked at creation)
+    if (tab.n > 32) return nh_fail(n->ctx, NH_ERR_UNSUPPORTED, "network: more than 32 layers");
     for (int l = 0; l < tab.n; l++) {
       tab.off[l] = n->L[l].woff;
       tab.cin[l] = n->L[l].cin;
