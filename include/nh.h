@@ -179,7 +179,11 @@ nh_status nh_op_info(nh_op op, nh_prec prec, int* scalars_per_qp, int64_t* qdata
  * W (Eq. Kirchhoff-stress, Sec. III-B), always in FP64; an FP32 copy is made
  * on first FP32 use.  Writes min det F over all points to *min_J (HOST;
  * this call synchronises).  Returns NH_ERR_INVERTED if min det F <= 0 or is
- * not finite (the stored data are then invalid).
+ * not finite (the stored data are then invalid).  The first call (or the first
+ * nh_residual) also keeps the mesh's geometry factors grad_X xi and
+ * det(dX/dxi) per point on the operator (80 bytes per point, FP64); later calls
+ * read them instead of recomputing them from the coordinates, with the same
+ * values.  Without memory for them every call recomputes.
  * Errors: NH_ERR_ARG, NH_ERR_STATE (coarse op). */
 nh_status nh_qdata_setup(nh_op op, const double* u, double* min_J);
 
@@ -201,7 +205,8 @@ nh_status nh_qdata_setup_rediscretized(nh_op op, nh_op fine, const double* u_fin
 /* Residual r = F(u) (Eq. residual-discrete-ref with f_1 = tau, f_0 = 0):
  * sum_e E^T B_xi^T W tau (grad_x xi)^T; constrained rows r = u - g_bc.
  * g_bc may be NULL (zero).  FP64 device vectors; does not touch the stored
- * quadrature data.  Errors: NH_ERR_ARG, NH_ERR_STATE (coarse op). */
+ * quadrature data (it reads or keeps the geometry factors as nh_qdata_setup).
+ * Errors: NH_ERR_ARG, NH_ERR_STATE (coarse op). */
 nh_status nh_residual(nh_op op, const double* u, const double* g_bc, double* r);
 
 /* Jacobian action y = J du (Eq. Jacobian-discrete-ref with Eqs. dtau and

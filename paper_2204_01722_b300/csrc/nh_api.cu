@@ -532,6 +532,7 @@ extern "C" nh_status nh_op_destroy(nh_op op) {
     cudaFree(op->qd);
     cudaFree(op->qd_f);
     cudaFree(op->qd_ff);
+    cudaFree(op->geom);
   }
   cudaFree(op->u_state);
   cudaFree(op->hbuf_in);
@@ -571,6 +572,23 @@ static OpArgs base_args(nh_op op) {
   return a;
 }
 
+#ifndef NH_GEOM_CACHE
+#define NH_GEOM_CACHE 1
+#endif
+// The setup kernel's geometry factors (grad_X xi, det(dX/dxi): 10 doubles per
+// point) are kept on the fine operator after its first setup or residual launch;
+// later launches read them instead of recomputing them from the coordinates.
+// Without memory for them every launch recomputes.
+static void attach_geom(nh_op op, OpArgs& a) {
+  if (!NH_GEOM_CACHE) return;
+  if (!op->geom && cudaMalloc(&op->geom, sizeof(double) * 10 * a.qstride) != cudaSuccess) {
+    cudaGetLastError();
+    op->geom = nullptr;
+  }
+  a.geom = op->geom;
+  a.geom_mode = op->geom_valid ? 2 : 1;
+}
+
 extern "C" nh_status nh_qdata_setup(nh_op op, const double* u, double* min_J) {
   if (!op || !u) return NH_ERR_ARG;
   nh_ctx ctx = op->space->ctx;
@@ -583,9 +601,11 @@ extern "C" nh_status nh_qdata_setup(nh_op op, const double* u, double* min_J) {
   a.store = 1;
   a.resid = 0;
   a.minj = ctx->minj;
+  attach_geom(op, a);
   NH_CUDA(ctx, cudaMemsetAsync(ctx->minj, 0xff, sizeof(unsigned long long), ctx->stream));
   NH_CUDA(ctx, nh_launch_setup(op->space->P, op->space->Q, a, ctx->stream));
   ctx->launches++;
+  if (a.geom) op->geom_valid = true;
   unsigned long long bits = 0;
   NH_CUDA(ctx, cudaMemcpyAsync(ctx->red_host, ctx->minj, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
   NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -627,9 +647,11 @@ extern "C" nh_status nh_residual(nh_op op, const double* u, const double* g_bc, 
   a.gbc = g_bc;
   a.store = 0;
   a.resid = 1;
+  attach_geom(op, a);
   NH_CUDA(ctx, cudaMemsetAsync(r, 0, sizeof(double) * op->space->n_dof, ctx->stream));
   NH_CUDA(ctx, nh_launch_setup(op->space->P, op->space->Q, a, ctx->stream));
   ctx->launches++;
+  if (a.geom) op->geom_valid = true;
   return NH_OK;
 }
 

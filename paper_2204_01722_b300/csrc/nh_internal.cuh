@@ -145,6 +145,8 @@ struct nh_op_s {
   float* qd_f = nullptr;          // FP32 copy, blocked per element batch (nh_f32_batch_floats)
   float* qd_ff = nullptr;         // float-float pairs (h, l), same indexing as qd (NH_F64X)
   double* u_state = nullptr;      // copy of the u of the last nh_qdata_setup (rediscretised levels)
+  double* geom = nullptr;         // [10][ne*Q^3] grad_X xi and det(dX/dxi) per point (fine op only)
+  bool geom_valid = false;
   int scatter = 0;                // E^T of the applies: 0 = atomic scatter-add, 1 = eight-colour passes
   bool qd_ff_valid = false;
   bool have_qd = false;
@@ -190,6 +192,8 @@ struct OpArgs {
   int colour;          // apply: -1 = atomic scatter; 0..7 = the parity class of the eight-colour scatter
   int* err;            // device error flag for bounded waits
   const Tab1D* tab;
+  double* geom;        // setup: geometry factors kept per point (nullable)
+  int geom_mode;       // setup: 1 = compute and keep them in geom, 2 = read them
 };
 
 // Return cudaErrorInvalidValue if (P, Q) is outside the compiled set.

@@ -1212,13 +1212,13 @@ struct SetupTab {
   double w[Q];
 };
 
-template <int P, int Q, int LAYOUT>
+template <int P, int Q, int LAYOUT, int GEOM>
 __global__ void __launch_bounds__(Q* Q* epb_for(Q))
     k_setup(int64_t ne, const int* __restrict__ emap, const uint8_t* __restrict__ bc,
             const double* __restrict__ coords, const double* __restrict__ u, const double* __restrict__ lamv,
             const double* __restrict__ muv, const SetupTab<P, Q> st, double* __restrict__ qd, int64_t qstride,
             int store, int resid, const double* __restrict__ gbc, double* __restrict__ r,
-            unsigned long long* __restrict__ minj) {
+            unsigned long long* __restrict__ minj, double* __restrict__ geom) {
   constexpr int EPB = epb_for(Q), Q2 = Q * Q, Q3 = Q * Q * Q;
   extern __shared__ __align__(16) unsigned char smraw[];
   double* sm = reinterpret_cast<double*>(smraw);
@@ -1233,10 +1233,15 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
   double* bU = bX + 3 * Q3;
   const KTab<P, Q, double>& tab = st.k;
 
+  // geometry factors grad_X xi and det(dX/dxi) per point, [10][ne Q^3] in geom:
+  // GEOM 0 computes them from the node coordinates, 1 computes and keeps them,
+  // 2 reads the kept ones (the mesh does not move)
   double UX[3][Q], UU[3][Q];
   int nid[P];
-  gather_interp<P, Q, double>(live, false, e, a, b, emap, bc, coords, tab, bA, bB, bX, UX, nid);
-  __syncthreads();
+  if constexpr (GEOM != 2) {
+    gather_interp<P, Q, double>(live, false, e, a, b, emap, bc, coords, tab, bA, bB, bX, UX, nid);
+    __syncthreads();
+  }
   gather_interp<P, Q, double>(live, false, e, a, b, emap, bc, u, tab, bA, bB, bU, UU, nid);
   __syncthreads();
 
@@ -1244,13 +1249,29 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q))
   double Fz[3][Q];
   double jmin = 1e300;
   for (int qk = 0; qk < Q; qk++) {
-    double gX[3][3], gU[3][3];
-    colloc_grad<P, Q, double>(a, b, qk, tab, bX, UX, gX);
+    double gU[3][3], R[3][3], detx = 1.0;
     colloc_grad<P, Q, double>(a, b, qk, tab, bU, UU, gU);
+    const int64_t pt = e * Q3 + qk * Q2 + b * Q + a;
+    if constexpr (GEOM == 2) {
+      if (live) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) R[i / 3][i % 3] = geom[i * qstride + pt];
+        detx = geom[9 * qstride + pt];
+      }
+    } else {
+      double gX[3][3];
+      colloc_grad<P, Q, double>(a, b, qk, tab, bX, UX, gX);
+      detx = nh_inv3(gX, R);
+      if (GEOM == 1 && live) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) geom[i * qstride + pt] = R[i / 3][i % 3];
+        geom[9 * qstride + pt] = detx;
+      }
+    }
     double f[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     if (live)
-      nh_setup_point<LAYOUT>(gX, gU, st.w[a] * st.w[b] * st.w[qk], lam, mu, qd + e * Q3 + qk * Q2 + b * Q + a, qstride,
-                             store, resid, f, jmin);
+      nh_setup_point_geom<LAYOUT>(R, detx, gU, st.w[a] * st.w[b] * st.w[qk], lam, mu, qd + pt, qstride, store, resid, f,
+                                  jmin);
     if (resid) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
@@ -1554,6 +1575,17 @@ cudaError_t apply_pq(nh_prec prec, const OpArgs& A, cudaStream_t s) {
                                          : apply_f32l_launch<P, Q, NH_LAYOUT_TAPE>(A, s);
 }
 
+template <int P, int Q, int LAYOUT, int GEOM>
+cudaError_t setup_go(const OpArgs& A, const SetupTab<P, Q>& st, int64_t blocks, int threads, size_t smem,
+                     cudaStream_t s) {
+  cudaError_t e = prep<k_setup<P, Q, LAYOUT, GEOM>>(smem);
+  if (e != cudaSuccess) return e;
+  k_setup<P, Q, LAYOUT, GEOM><<<(unsigned)blocks, threads, smem, s>>>(
+      A.ne, A.emap, A.bc, A.coords, (const double*)A.in, A.lam, A.mu, st, A.qd_out, A.qstride, A.store, A.resid, A.gbc,
+      (double*)A.out, A.minj, A.geom);
+  return cudaGetLastError();
+}
+
 template <int P, int Q, int LAYOUT>
 cudaError_t setup_launch(const OpArgs& A, cudaStream_t s) {
   constexpr int EPB = epb_for(Q), Q3 = Q * Q * Q;
@@ -1564,12 +1596,10 @@ cudaError_t setup_launch(const OpArgs& A, cudaStream_t s) {
   SetupTab<P, Q> st;
   st.k = make_ktab<P, Q, double>(*A.tab);
   for (int i = 0; i < Q; i++) st.w[i] = A.tab->w[i];
-  cudaError_t e = prep<k_setup<P, Q, LAYOUT>>(smem);
-  if (e != cudaSuccess) return e;
-  k_setup<P, Q, LAYOUT><<<(unsigned)blocks, threads, smem, s>>>(A.ne, A.emap, A.bc, A.coords, (const double*)A.in,
-                                                                A.lam, A.mu, st, A.qd_out, A.qstride, A.store,
-                                                                A.resid, A.gbc, (double*)A.out, A.minj);
-  return cudaGetLastError();
+  const int mode = A.geom ? A.geom_mode : 0;
+  return mode == 2   ? setup_go<P, Q, LAYOUT, 2>(A, st, blocks, threads, smem, s)
+         : mode == 1 ? setup_go<P, Q, LAYOUT, 1>(A, st, blocks, threads, smem, s)
+                     : setup_go<P, Q, LAYOUT, 0>(A, st, blocks, threads, smem, s);
 }
 
 template <int P, int Q>

@@ -32,12 +32,13 @@ __device__ __forceinline__ double nh_inv3(const double (&A)[3][3], double (&Ai)[
   return det;
 }
 
+// The same from the geometry factors R = grad_X xi and detx = det(dX/dxi), which
+// depend on the mesh only (computed once and kept by the setup kernel).
 template <int LAYOUT>
-__device__ __forceinline__ void nh_setup_point(const double (&gX)[3][3], const double (&gU)[3][3], double wq,
-                                               double lam, double mu, double* __restrict__ qp, int64_t qstride,
-                                               int store, int resid, double (&f)[3][3], double& jmin) {
-  double R[3][3];  // grad_X xi
-  const double detx = nh_inv3(gX, R);
+__device__ __forceinline__ void nh_setup_point_geom(const double (&R)[3][3], double detx, const double (&gU)[3][3],
+                                                    double wq, double lam, double mu, double* __restrict__ qp,
+                                                    int64_t qstride, int store, int resid, double (&f)[3][3],
+                                                    double& jmin) {
   const double W = wq * detx;
   double H[3][3];
 #pragma unroll
@@ -133,4 +134,13 @@ __device__ __forceinline__ void nh_setup_point(const double (&gX)[3][3], const d
       for (int d = 0; d < 3; d++)
         f[c][d] = W * (tau[c][0] * X[d][0] + tau[c][1] * X[d][1] + tau[c][2] * X[d][2]);
   }
+}
+
+template <int LAYOUT>
+__device__ __forceinline__ void nh_setup_point(const double (&gX)[3][3], const double (&gU)[3][3], double wq,
+                                               double lam, double mu, double* __restrict__ qp, int64_t qstride,
+                                               int store, int resid, double (&f)[3][3], double& jmin) {
+  double R[3][3];  // grad_X xi
+  const double detx = nh_inv3(gX, R);
+  nh_setup_point_geom<LAYOUT>(R, detx, gU, wq, lam, mu, qp, qstride, store, resid, f, jmin);
 }
