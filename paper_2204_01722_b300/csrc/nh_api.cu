@@ -106,6 +106,7 @@ extern "C" nh_status nh_destroy(nh_ctx c) {
   for (cudaEvent_t ev : c->ev_chunk) cudaEventDestroy(ev);
   if (c->s_in) cudaStreamDestroy(c->s_in);
   if (c->s_out) cudaStreamDestroy(c->s_out);
+  if (c->s_k2) cudaStreamDestroy(c->s_k2);
   cudaFree(c->red);
   cudaFree(c->minj);
   cudaFree(c->dev_err);
@@ -845,6 +846,7 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
   if (!ctx->s_in) {
     NH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
     NH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
+    NH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_k2, cudaStreamNonBlocking));
   }
   if (sp->hex) {
     // unstructured mesh in first-touch numbering: elements [e0, e1) read du on the
@@ -915,11 +917,17 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
   char* hout = static_cast<char*>(y_h);
   char* din = static_cast<char*>(op->hbuf_in);
   char* dout = static_cast<char*>(op->hbuf_out);
-  // y = 0 on the compute stream, ordered before every chunk's kernel
+  // y = 0 on the compute stream, ordered before every chunk's kernel.  Chunks'
+  // kernels alternate between the compute stream and a second one, so that a
+  // chunk's kernel starts while the previous one drains its last blocks (they
+  // meet only in atomic adds on their shared node layer); a download waits for
+  // the latest kernel on both.
   NH_CUDA(ctx, cudaMemsetAsync(dout, 0, bytes, ctx->stream));
   NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[0], ctx->stream));
   NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_chunk[0], 0));  // hbuf reuse after earlier work
+  NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_k2, ctx->ev_chunk[0], 0));
   int64_t up = 0, down = 0;                                          // DoF uploaded / downloaded so far
+  int lastk[2] = {-1, -1};                                           // event of the last kernel per stream
   for (int c = 0; c < nch; c++) {
     const int64_t z0 = std::min<int64_t>(sp->nz, nsteps * c / nch * step);
     const int64_t z1 = c + 1 == nch ? sp->nz : std::min<int64_t>(sp->nz, nsteps * (c + 1) / nch * step);
@@ -929,20 +937,25 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
       NH_CUDA(ctx, cudaMemcpyAsync(din + w * up, hin + w * up, w * (need - up), cudaMemcpyHostToDevice, ctx->s_in));
       up = need;
     }
+    const int ks = c & 1;
+    cudaStream_t kst = ks ? ctx->s_k2 : ctx->stream;
     NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c], ctx->s_in));
-    NH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_chunk[2 * c], 0));
-    nh_status st = launch_apply_range(op, prec, din, dout, z0 * nxy, z1 * nxy, ctx->stream);
+    NH_CUDA(ctx, cudaStreamWaitEvent(kst, ctx->ev_chunk[2 * c], 0));
+    nh_status st = launch_apply_range(op, prec, din, dout, z0 * nxy, z1 * nxy, kst);
     if (st != NH_OK) return st;
-    NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c + 1], ctx->stream));
+    NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c + 1], kst));
+    lastk[ks] = 2 * c + 1;
     const int64_t fin = c + 1 == nch ? sp->n_dof : std::min<int64_t>(sp->n_dof, z1 * sp->p * lay);
     if (fin > down) {
-      NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_chunk[2 * c + 1], 0));
+      for (int k = 0; k < 2; k++)
+        if (lastk[k] >= 0) NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_chunk[lastk[k]], 0));
       NH_CUDA(ctx, cudaMemcpyAsync(hout + w * down, dout + w * down, w * (fin - down), cudaMemcpyDeviceToHost,
                                    ctx->s_out));
       down = fin;
     }
   }
   NH_CUDA(ctx, cudaStreamSynchronize(ctx->s_out));
+  NH_CUDA(ctx, cudaStreamSynchronize(ctx->s_k2));
   NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return NH_OK;
 }

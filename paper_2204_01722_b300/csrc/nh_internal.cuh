@@ -106,7 +106,7 @@ struct nh_ctx_s {
   std::vector<cudaEvent_t> ev_pool;   // 2 per recorded launch
   size_t ev_used = 0;
   // host-buffer apply pipeline: upload and download streams, per-chunk events
-  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaStream_t s_in = nullptr, s_out = nullptr, s_k2 = nullptr;  // host apply: upload, download, second kernel stream
   std::vector<cudaEvent_t> ev_chunk;  // 2 per chunk (uploaded, computed)
 };
 
