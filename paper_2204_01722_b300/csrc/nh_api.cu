@@ -866,7 +866,9 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
     NH_CUDA(ctx, cudaMemsetAsync(dout, 0, bytes, ctx->stream));
     NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[0], ctx->stream));
     NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_chunk[0], 0));
+    NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_k2, ctx->ev_chunk[0], 0));
     int64_t up = 0, down = 0;  // DoF uploaded / downloaded so far
+    int lastk[2] = {-1, -1};   // event of the last kernel per compute stream (as on the box)
     for (int c = 0; c < nch; c++) {
       const int64_t e0 = ne * c / nch / al * al;
       const int64_t e1 = c + 1 == nch ? ne : ne * (c + 1) / nch / al * al;
@@ -876,20 +878,25 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
         NH_CUDA(ctx, cudaMemcpyAsync(din + w * up, hin + w * up, w * (need - up), cudaMemcpyHostToDevice, ctx->s_in));
         up = need;
       }
+      const int ks = c & 1;
+      cudaStream_t kst = ks ? ctx->s_k2 : ctx->stream;
       NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c], ctx->s_in));
-      NH_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_chunk[2 * c], 0));
-      nh_status st = launch_apply_range(op, prec, din, dout, e0, e1, ctx->stream);
+      NH_CUDA(ctx, cudaStreamWaitEvent(kst, ctx->ev_chunk[2 * c], 0));
+      nh_status st = launch_apply_range(op, prec, din, dout, e0, e1, kst);
       if (st != NH_OK) return st;
-      NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c + 1], ctx->stream));
+      NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c + 1], kst));
+      lastk[ks] = 2 * c + 1;
       const int64_t fin = c + 1 == nch ? sp->n_dof : 3 * sp->hex_fin[e1];
       if (fin > down) {
-        NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_chunk[2 * c + 1], 0));
+        for (int k = 0; k < 2; k++)
+          if (lastk[k] >= 0) NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_out, ctx->ev_chunk[lastk[k]], 0));
         NH_CUDA(ctx, cudaMemcpyAsync(hout + w * down, dout + w * down, w * (fin - down), cudaMemcpyDeviceToHost,
                                      ctx->s_out));
         down = fin;
       }
     }
     NH_CUDA(ctx, cudaStreamSynchronize(ctx->s_out));
+    NH_CUDA(ctx, cudaStreamSynchronize(ctx->s_k2));
     NH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return NH_OK;
   }
