@@ -878,7 +878,7 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
         NH_CUDA(ctx, cudaMemcpyAsync(din + w * up, hin + w * up, w * (need - up), cudaMemcpyHostToDevice, ctx->s_in));
         up = need;
       }
-      const int ks = c & 1;
+      const int ks = prec == NH_F32 ? 0 : c & 1;  // FP32 chunks are transfer-bound: one kernel stream
       cudaStream_t kst = ks ? ctx->s_k2 : ctx->stream;
       NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c], ctx->s_in));
       NH_CUDA(ctx, cudaStreamWaitEvent(kst, ctx->ev_chunk[2 * c], 0));
@@ -924,11 +924,12 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
   char* hout = static_cast<char*>(y_h);
   char* din = static_cast<char*>(op->hbuf_in);
   char* dout = static_cast<char*>(op->hbuf_out);
-  // y = 0 on the compute stream, ordered before every chunk's kernel.  Chunks'
-  // kernels alternate between the compute stream and a second one, so that a
-  // chunk's kernel starts while the previous one drains its last blocks (they
-  // meet only in atomic adds on their shared node layer); a download waits for
-  // the latest kernel on both.
+  // y = 0 on the compute stream, ordered before every chunk's kernel.  FP64 and
+  // float-float chunks' kernels alternate between the compute stream and a second
+  // one, so that a chunk's kernel starts while the previous one drains its last
+  // blocks (they meet only in atomic adds on their shared node layer); a download
+  // waits for the latest kernel on both.  (FP32 keeps one stream: its transfers
+  // dominate, and on Z-ordered unstructured meshes the alternation measured slower.)
   NH_CUDA(ctx, cudaMemsetAsync(dout, 0, bytes, ctx->stream));
   NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[0], ctx->stream));
   NH_CUDA(ctx, cudaStreamWaitEvent(ctx->s_in, ctx->ev_chunk[0], 0));  // hbuf reuse after earlier work
@@ -944,7 +945,7 @@ extern "C" nh_status nh_jacobian_apply_host(nh_op op, nh_prec prec, const void* 
       NH_CUDA(ctx, cudaMemcpyAsync(din + w * up, hin + w * up, w * (need - up), cudaMemcpyHostToDevice, ctx->s_in));
       up = need;
     }
-    const int ks = c & 1;
+    const int ks = prec == NH_F32 ? 0 : c & 1;  // FP32 chunks are transfer-bound: one kernel stream
     cudaStream_t kst = ks ? ctx->s_k2 : ctx->stream;
     NH_CUDA(ctx, cudaEventRecord(ctx->ev_chunk[2 * c], ctx->s_in));
     NH_CUDA(ctx, cudaStreamWaitEvent(kst, ctx->ev_chunk[2 * c], 0));
