@@ -59,3 +59,27 @@ def test_gradient_matches_central_differences(levels, ch, N):
         e[i] = h
         fd = (learned.loss(theta + e, x, t, levels, ch) - learned.loss(theta - e, x, t, levels, ch)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_storage_hook():
+    """forward(store=...) applies the hook to every stored field: the identity
+    reproduces the plain forward exactly; rounding every stored field to a 1/8 grid
+    changes a random network's output, while on integer data through integer
+    weights (every field already on that grid) it changes nothing."""
+    levels, ch, N = 2, (4, 8), 5
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(4, N, N, N))
+    theta = learned.init_params(levels, ch, seed=4)
+    y = learned.forward(theta, x, levels, ch)
+    assert np.array_equal(learned.forward(theta, x, levels, ch, store=lambda v: v), y)
+    grid = lambda v: np.round(np.asarray(v) * 8.0) / 8.0
+    assert not np.array_equal(learned.forward(theta, x, levels, ch, store=grid), y)
+    ti = np.zeros_like(theta)
+    nz = rng.choice(theta.size, size=theta.size // 10, replace=False)
+    ti[nz] = rng.choice([-1.0, 1.0], size=nz.size)
+    xi = rng.integers(0, 4, size=(4, N, N, N)).astype(np.float64)
+    yi = learned.forward(ti, xi, levels, ch)
+    # upsampling halves odd nodes: integer fields stay on the 1/8 grid one level down
+    assert np.array_equal(learned.forward(ti, xi, levels, ch, store=grid), yi)
+    _, tape = learned.forward(ti, xi, levels, ch, keep=True, store=grid)
+    assert all(np.array_equal(t[0], grid(t[0])) for t in tape if not isinstance(t[0], str))
