@@ -49,9 +49,20 @@ __host__ __device__ constexpr int epb_for(int Q) { return nh_epb(Q); }
 // Rolled float-float kernel (Q2 / Q3 / Q4 GDoF/s on B300 with 3, 4, 5 blocks of
 // registers per SM): q = 3 6.08 / 6.08 / 6.40, q = 4 6.99 / 7.58 / 7.26, q = 5
 // 7.07 / 7.06 / 7.09 (2, 3, 4 blocks).
+// z-fluxes of the rolled float-float kernel in thread-local memory instead of a
+// fourth shared buffer (each thread reads back only its own column): for q with
+// the bit set in NH_FF_ZLOCAL_QMASK, where the shared buffer bounds the resident
+// blocks (q = 5: 3 -> 4 blocks per SM)
+#ifndef NH_FF_ZLOCAL_QMASK
+#define NH_FF_ZLOCAL_QMASK (1 << 5)
+#endif
+__host__ __device__ constexpr bool ffr_zlocal(int Q) { return (NH_FF_ZLOCAL_QMASK >> Q) & 1; }
+
 template <typename T, int Q>
 __host__ __device__ constexpr int apply_min_blocks() {
-  return std::is_same<T, ff>::value ? (Q <= 3 ? NH_FF_MIN_BLOCKS_Q3 : Q == 4 ? NH_FF_MIN_BLOCKS_SMALLQ : 3) : 1;
+  return std::is_same<T, ff>::value
+             ? (Q <= 3 ? NH_FF_MIN_BLOCKS_Q3 : Q == 4 ? NH_FF_MIN_BLOCKS_SMALLQ : ffr_zlocal(Q) ? 4 : 3)
+             : 1;
 }
 
 // Shared-memory stride of one element's [9][Q^3] work area, padded so that the
@@ -408,7 +419,7 @@ __device__ __forceinline__ ff ff_dot(F term) {
 
 template <int Q>
 __host__ __device__ constexpr int ffr_stride() {
-  constexpr int base = 12 * Q * Q * Q, W = 16, want = (Q * Q) % W;
+  constexpr int base = (ffr_zlocal(Q) ? 9 : 12) * Q * Q * Q, W = 16, want = (Q * Q) % W;
   return Q * Q >= W ? base : base + ((want - base % W) % W + W) % W;
 }
 
@@ -436,7 +447,8 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<ff, Q>())
   ff* bA = sm + el * ffr_stride<Q>();  // [3][Q^3] each
   ff* bB = bA + 3 * Q3;
   ff* bC = bB + 3 * Q3;                 // point values
-  ff* bD = bC + 3 * Q3;                 // z-fluxes
+  ff* bD = bC + 3 * Q3;                 // z-fluxes (shared form)
+  ff zl[3][Q];                          // z-fluxes (thread-local form)
   // E and B_I along x: thread (a, b) < P owns node column (i = a, j = b) over k
   int nid[P];
   if (a < P && b < P) {
@@ -497,7 +509,10 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<ff, Q>())
     for (int c = 0; c < 3; c++) {
       bA[sidx<Q>(c, qk, b, a)] = f[c][0];
       bB[sidx<Q>(c, qk, b, a)] = f[c][1];
-      bD[sidx<Q>(c, qk, b, a)] = f[c][2];
+      if constexpr (ffr_zlocal(Q))
+        zl[c][qk] = f[c][2];
+      else
+        bD[sidx<Q>(c, qk, b, a)] = f[c][2];
     }
   }
   __syncthreads();
@@ -510,7 +525,7 @@ __global__ void __launch_bounds__(Q* Q* epb_for(Q), apply_min_blocks<ff, Q>())
         const int m = i / 3, d = i % 3;
         return d == 0   ? ffpair{tab.D[m][a], bA[sidx<Q>(c, qk, b, m)]}
                : d == 1 ? ffpair{tab.D[m][b], bB[sidx<Q>(c, qk, m, a)]}
-                        : ffpair{tab.D[m][qk], bD[sidx<Q>(c, m, b, a)]};
+                        : ffpair{tab.D[m][qk], ffr_zlocal(Q) ? zl[c][m] : bD[sidx<Q>(c, m, b, a)]};
       });
   }
   __syncthreads();
