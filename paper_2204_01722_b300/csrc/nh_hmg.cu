@@ -67,28 +67,62 @@ __global__ void __launch_bounds__(kT) k_rap(int Nfx, int Nfy, int Nfz, int Ncx, 
   double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (Jx >= 0 && Jx < Ncx && Jy >= 0 && Jy < Ncy && Jz >= 0 && Jz < Ncz) {
     const unsigned mI = bcc[I], mJ = bcc[Jx + (int64_t)Ncx * (Jy + (int64_t)Ncy * Jz)];
-    for (int dz = -1; dz <= 1; dz++)
-      for (int dy = -1; dy <= 1; dy++)
-        for (int dx = -1; dx <= 1; dx++) {
-          const int ix = 2 * Ix + dx, iy = 2 * Iy + dy, iz = 2 * Iz + dz;
+    // per direction and fine offset a = i - 2 I: the stencil offsets s = j - i
+    // with j inside the lattice and in the support of J (|j - 2 J| <= 1), in
+    // increasing order -- the terms the full 27 x 27 walk would keep, in its order
+    const int Ic[3] = {Ix, Iy, Iz}, Jc[3] = {Jx, Jy, Jz}, Nf[3] = {Nfx, Nfy, Nfz};
+    unsigned vm[3];  // direction d: bit 3 (a + 1) + sd + 1 set when offset sd is kept for i = 2 I + a
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      unsigned m = 0;
+#pragma unroll
+      for (int a = -1; a <= 1; a++) {
+        const int i = 2 * Ic[d] + a;
+#pragma unroll
+        for (int sd = -1; sd <= 1; sd++) {
+          const int j = i + sd;
+          if (i >= 0 && i < Nf[d] && j >= 0 && j < Nf[d] && j - 2 * Jc[d] >= -1 && j - 2 * Jc[d] <= 1)
+            m |= 1u << (3 * (a + 1) + sd + 1);
+        }
+      }
+      vm[d] = m;
+    }
+    const unsigned vmx = vm[0], vmy = vm[1], vmz = vm[2];
+#pragma unroll 1
+    for (int az = -1; az <= 1; az++)
+#pragma unroll 1
+      for (int ay = -1; ay <= 1; ay++)
+#pragma unroll 1
+        for (int ax = -1; ax <= 1; ax++) {
+          const int ix = 2 * Ix + ax, iy = 2 * Iy + ay, iz = 2 * Iz + az;
           if (ix < 0 || ix >= Nfx || iy < 0 || iy >= Nfy || iz < 0 || iz >= Nfz) continue;
           const double wi = w1(ix, Ix) * w1(iy, Iy) * w1(iz, Iz);
           const int64_t ii = ix + (int64_t)Nfx * (iy + (int64_t)Nfy * iz);
           const unsigned mi = bcf[ii] | mI;
-          for (int sf = 0; sf < 27; sf++) {
-            const int jx = ix + sf % 3 - 1, jy = iy + (sf / 3) % 3 - 1, jz = iz + sf / 9 - 1;
-            if (jx < 0 || jx >= Nfx || jy < 0 || jy >= Nfy || jz < 0 || jz >= Nfz) continue;
-            const double wj = w1(jx, Jx) * w1(jy, Jy) * w1(jz, Jz);
-            if (wj == 0.0) continue;
-            const unsigned mj = bcf[jx + (int64_t)Nfx * (jy + (int64_t)Nfy * jz)] | mJ;
-            const double* a = Af + (int64_t)sf * 9 * nnf + ii;
-            const double w = wi * wj;
+          const unsigned bx = vmx >> (3 * (ax + 1)), by = vmy >> (3 * (ay + 1)), bz = vmz >> (3 * (az + 1));
+#pragma unroll 1
+          for (int sz = -1; sz <= 1; sz++) {
+            if (!((bz >> (sz + 1)) & 1u)) continue;
+#pragma unroll 1
+            for (int sy = -1; sy <= 1; sy++) {
+              if (!((by >> (sy + 1)) & 1u)) continue;
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-              if ((mi >> c) & 1u) continue;
+              for (int sx = -1; sx <= 1; sx++) {
+                if (!((bx >> (sx + 1)) & 1u)) continue;
+                const int sf = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
+                const int jx = ix + sx, jy = iy + sy, jz = iz + sz;
+                const double wj = w1(jx, Jx) * w1(jy, Jy) * w1(jz, Jz);
+                const unsigned mj = bcf[jx + (int64_t)Nfx * (jy + (int64_t)Nfy * jz)] | mJ;
+                const double* a = Af + (int64_t)sf * 9 * nnf + ii;
+                const double w = wi * wj;
 #pragma unroll
-              for (int cp = 0; cp < 3; cp++)
-                if (!((mj >> cp) & 1u)) acc[3 * c + cp] += w * a[(int64_t)(3 * c + cp) * nnf];
+                for (int c = 0; c < 3; c++) {
+                  if ((mi >> c) & 1u) continue;
+#pragma unroll
+                  for (int cp = 0; cp < 3; cp++)
+                    if (!((mj >> cp) & 1u)) acc[3 * c + cp] += w * a[(int64_t)(3 * c + cp) * nnf];
+                }
+              }
             }
           }
         }
