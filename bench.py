@@ -70,9 +70,9 @@ def n_dof_of(p, n):
 # dram__bytes_read.sum + dram__bytes_write.sum per apply launch from the ncu
 # capture summarised in profiles/ (small case, scaled to the full launch by
 # elements); reset to None whenever the kernel changes.
-NCU_TRAFFIC = {("f64", 3, 48): 1.203e9,
+NCU_TRAFFIC = {("f64", 2, 74): 1.770e9, ("f64", 3, 48): 1.203e9, ("f64", 4, 37): 1.115e9,
                ("f32", 2, 74): 9.00e8, ("f32", 3, 48): 6.06e8, ("f32", 4, 37): 5.66e8,
-               ("f64x", 3, 48): 1.212e9}
+               ("f64x", 2, 74): 1.795e9, ("f64x", 3, 48): 1.212e9, ("f64x", 4, 37): 1.179e9}
 
 
 def apply_bytes(p, n, wbytes, S=17, bc_byte=True):
